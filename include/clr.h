@@ -1,0 +1,218 @@
+/*
+ * clr.h -- C ABI of a GB300 (sm_103a) library for products of Clustered Low-Rank (CLR,
+ * block-rank-sparse) matrices and the Newton–Schulz iteration for S^-1/2.
+ *
+ * Method: Calvin, Lewis & Valeev, "Scalable Task-Based Algorithm for Multiplication of
+ * Block-Rank-Sparse Matrices", IA^3 2015.  Section 4.1 defines the CLR representation and its
+ * block arithmetic; Section 4.2 the Newton–Schulz iteration.
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an int status: CLR_OK (0) or a negative CLR_E* code.  No C++
+ *    exception crosses this boundary.  clr_strerror() names a code; clr_last_error() gives
+ *    the context's last detailed message.
+ *  - A CLR matrix (clr_mat_t) is an opaque, library-owned handle living on the context's
+ *    device.  Handles returned through an out-pointer are new and owned by the caller, who
+ *    releases them with clr_mat_free().  Input matrices are never modified.
+ *  - Block layout (used by clr_mat_from_blocks / clr_mat_get_blocks): a matrix with row
+ *    clusters of sizes m_0..m_{nr-1} and column clusters n_0..n_{nc-1} owns a pool of
+ *    n_rows * n_cols doubles.  Block (I,J) owns the fixed slot starting at
+ *    row_off[I] * n_cols + m_I * col_off[J] (row_off / col_off: exclusive prefix sums of
+ *    the cluster sizes).  A dense block stores its m x n values column-major (element (i,j)
+ *    at i + j*m).  A low-rank block of rank r stores X (m x r, column-major) followed by W
+ *    (n x r, column-major); the block equals X W^T.  Low-rank blocks have
+ *    1 <= r <= floor(min(m,n)/2) (blocks of larger rank are stored dense, Section 4.1), so
+ *    (m + n) r <= m n and every block fits its slot.  Block (I,J) has index I*nc + J.
+ *  - Cluster sizes must be in [1, CLR_MAX_CLUSTER].
+ *  - Device work is issued on the caller's stream (a cudaStream_t passed as void*; NULL is
+ *    the legacy default stream).  Calls that must read device results on the host
+ *    (sizes, statistics, convergence tests) synchronise that stream; each such call says so.
+ *  - There is no CPU fallback: without a usable sm_103a device, clr_create fails with
+ *    CLR_ECUDA.
+ */
+#ifndef CLR_H_
+#define CLR_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ------------------------------------------------------------------------ */
+#define CLR_OK        0
+#define CLR_EINVAL   -1   /* bad argument: tiling mismatch, size out of range, NaN input ... */
+#define CLR_ENOMEM   -2   /* device allocation failed */
+#define CLR_ENOCONV  -3   /* Newton–Schulz did not reach ns_tol within ns_max_iter */
+#define CLR_ETIMEOUT -4   /* a bounded device-side wait gave up (error flag set by a kernel) */
+#define CLR_ECUDA    -5   /* CUDA runtime/driver error (see clr_last_error) */
+#define CLR_ENOTSUP  -6   /* operation not supported for these arguments */
+
+/* ---- block kinds (Section 4.1: each block is zero, dense, or low-rank X W^T) ------------- */
+#define CLR_KIND_ZERO  0
+#define CLR_KIND_DENSE 1
+#define CLR_KIND_LR    2
+
+/* ---- arithmetic of dense x dense tile products ------------------------------------------ */
+#define CLR_PREC_FP64   0  /* FP64 on CUDA cores */
+#define CLR_PREC_BF16X3 1  /* 2-term bf16 split, 3 tensor-core products, FP32 accumulation */
+#define CLR_PREC_BF16X6 2  /* 3-term bf16 split, 6 tensor-core products, FP32 accumulation */
+#define CLR_PREC_AUTO   3  /* cheapest of the above whose a-priori error bound meets eps_lr */
+
+#define CLR_MAX_CLUSTER 256
+
+typedef struct clr_ctx_s* clr_ctx_t;
+typedef struct clr_mat_s* clr_mat_t;
+typedef struct clr_tape_s* clr_tape_t;
+
+/* Options of a context.  Fill with clr_opts_default() and override fields. */
+typedef struct clr_opts {
+  double eps_lr;         /* truncation threshold: Frobenius error per block (Section 4.1) */
+  double eps_sp;         /* screening threshold: C_IJ computed only if its norm estimate
+                            exceeds eps_sp * area(C_IJ) (Section 4.1); 0 disables */
+  int precision;         /* CLR_PREC_* for dense x dense tile products */
+  int recompress_dense;  /* 1: dense-accumulated C tiles are re-tested for low rank */
+  int ns_max_iter;       /* Newton–Schulz: maximum number of Z updates */
+  double ns_tol;         /* NS stops when ||X_n - I||_F / sqrt(N) <= ns_tol; 0 runs
+                            exactly ns_max_iter updates */
+  double ns_alpha;       /* NS scale alpha; 0 = 1 / (1.01 * power-iteration estimate) */
+  int ns_power_steps;    /* power iterations for the alpha estimate (default 30) */
+  int ns_fp64_tail;      /* precision ladder: switch tile products to FP64 once
+                            ||X_n - I||_F / sqrt(N) <= ns_ladder_switch */
+  double ns_ladder_switch;
+  int jacobi_max_sweeps; /* one-sided Jacobi sweep limit (default 40) */
+  int reserved[8];
+} clr_opts;
+
+/* Summary of a CLR matrix (clr_mat_info). */
+typedef struct clr_info {
+  int64_t n_rows, n_cols;
+  int32_t n_row_clusters, n_col_clusters;
+  int64_t n_blocks[3];      /* by kind: zero, dense, low rank */
+  int32_t max_rank;         /* over low-rank blocks */
+  int64_t sum_rank;         /* over low-rank blocks */
+  int64_t stored_doubles;   /* doubles actually used by dense values and factors */
+  double frob_norm;         /* sqrt(sum of squared block norms) */
+  int32_t rank_hist[CLR_MAX_CLUSTER / 2 + 2]; /* low-rank blocks by rank; [0] counts zero
+                                                 blocks, the last bin counts dense blocks */
+} clr_info;
+
+/* Work statistics of one product (clr_multiply_into with a non-NULL stats pointer). */
+typedef struct clr_product_stats {
+  int64_t n_triples[4];     /* tile products by kind: DD, DL, LD, LL */
+  int64_t flops;            /* algorithmic flops of the tile products */
+  int64_t n_tiles[3];       /* C tiles accumulated as: none, dense, low rank */
+  int64_t max_rank_sum;     /* largest concatenated rank of a low-rank C tile */
+  int32_t precision;        /* precision used for dense x dense products */
+  int32_t pad;
+} clr_product_stats;
+
+/* Newton–Schulz statistics (clr_sqrt_inv). */
+#define CLR_NS_MAX_HISTORY 256
+typedef struct clr_ns_stats {
+  int32_t iters;            /* Z updates applied */
+  int32_t converged;
+  double alpha;
+  double residual;          /* ||alpha Z S Z - I||_F / sqrt(N) of the returned Z */
+  double proxy[CLR_NS_MAX_HISTORY]; /* ||X_n - I||_F / sqrt(N), n = 0..iters */
+  int32_t precision_used[CLR_NS_MAX_HISTORY];
+  double ms_total;          /* device time of the iteration loop (CUDA events) */
+} clr_ns_stats;
+
+/* ---- errors and options ------------------------------------------------------------------ */
+const char* clr_strerror(int status);
+const char* clr_last_error(clr_ctx_t ctx);
+void clr_opts_default(clr_opts* opts);
+
+/* ---- context ------------------------------------------------------------------------------
+ * clr_create: binds a context to CUDA device `device` (made current on the calling thread),
+ * checks that it is an sm_103 part, and loads the TMA encoder from the driver.  Fails with
+ * CLR_ECUDA when no such device exists.  clr_destroy frees the context's workspaces; it does
+ * not free matrices. */
+int clr_create(clr_ctx_t* ctx, int device, const clr_opts* opts);
+int clr_destroy(clr_ctx_t ctx);
+int clr_set_opts(clr_ctx_t ctx, const clr_opts* opts);
+int clr_get_opts(clr_ctx_t ctx, clr_opts* opts);
+
+/* ---- matrices -----------------------------------------------------------------------------
+ * clr_mat_create: an all-zero matrix with the given clusters (capacity for any content).
+ * clr_mat_from_dense: CLR form of a dense row-major n_rows x n_cols FP64 matrix `a` (leading
+ *   dimension lda >= n_cols; `a_on_host` 1 for host memory, 0 for device memory).  Each block
+ *   is dropped when ||block||_F < drop_norm, else truncated by its SVD at Frobenius error
+ *   eps_lr (Section 4.1 builds X, W by rank-revealing QR; the SVD gives the minimal rank of
+ *   the same criterion), else stored dense when the rank exceeds floor(min(m,n)/2).  With
+ *   eps_lr == 0 every block that is not dropped is stored dense.
+ * clr_mat_from_blocks: copies kinds[nr*nc], ranks[nr*nc] and a host pool of n_rows*n_cols
+ *   doubles in the block layout above; no compression is applied.
+ * clr_mat_to_dense: reconstructs the matrix into row-major `out` (leading dimension ldo).
+ * clr_mat_get_blocks: copies kinds, ranks, block Frobenius norms and the pool to the host
+ *   (any pointer may be NULL).  Synchronises `stream`.
+ * clr_mat_info: summary statistics; synchronises `stream`. */
+int clr_mat_create(clr_ctx_t ctx, int n_rt, const int32_t* row_sizes, int n_ct,
+                   const int32_t* col_sizes, clr_mat_t* out);
+int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, int a_on_host, int n_rt,
+                       const int32_t* row_sizes, int n_ct, const int32_t* col_sizes,
+                       double eps_lr, double drop_norm, void* stream, clr_mat_t* out);
+int clr_mat_from_blocks(clr_ctx_t ctx, int n_rt, const int32_t* row_sizes, int n_ct,
+                        const int32_t* col_sizes, const int32_t* kinds, const int32_t* ranks,
+                        const double* pool_host, void* stream, clr_mat_t* out);
+int clr_mat_to_dense(clr_ctx_t ctx, clr_mat_t m, double* out, int64_t ldo, int out_on_host,
+                     void* stream);
+int clr_mat_get_blocks(clr_ctx_t ctx, clr_mat_t m, int32_t* kinds, int32_t* ranks,
+                       double* norms, double* pool_host, void* stream);
+int clr_mat_info(clr_ctx_t ctx, clr_mat_t m, clr_info* info, void* stream);
+int clr_mat_shape(clr_mat_t m, int64_t* n_rows, int64_t* n_cols, int* n_rt, int* n_ct);
+int clr_mat_copy(clr_ctx_t ctx, clr_mat_t src, clr_mat_t dst, void* stream);
+int clr_mat_transpose(clr_ctx_t ctx, clr_mat_t src, clr_mat_t* out, void* stream);
+int clr_mat_free(clr_ctx_t ctx, clr_mat_t m);
+
+/* ---- the CLR product (Section 4.1) --------------------------------------------------------
+ * C = alpha * (A B): every C tile receives the tile products A_IK B_KJ with both blocks
+ * nonzero (dense x dense, dense x low-rank, low-rank x dense, low-rank x low-rank with
+ * Z = W_A^T X_B contracted on the side of smaller output rank), screened with eps_sp; tiles
+ * with a dense x dense product are accumulated dense, the others by concatenating factors
+ * and recompressing (QR of both factors, SVD of the small core, truncation at eps_lr).  The
+ * truncation happens before the scaling by alpha.  A's column clusters must equal B's row
+ * clusters (else CLR_EINVAL).
+ * clr_multiply: allocates C.  clr_multiply_into: C must have A's row clusters and B's column
+ *   clusters and must not be A or B; no host synchronisation unless `stats` is non-NULL.
+ * clr_multiply_batched: n independent products issued together on one stream. */
+int clr_multiply(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t* c, void* stream);
+int clr_multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double alpha,
+                      clr_product_stats* stats, void* stream);
+int clr_multiply_batched(clr_ctx_t ctx, int n, const clr_mat_t* a, const clr_mat_t* b,
+                         clr_mat_t* c, void* stream);
+
+/* ---- CLR linear combination (low-rank addition, Section 4.1, Eq. lr_addition) ------------
+ * out = a X + b Y + diag I.  A block present in one operand only is scaled exactly; a block
+ * with a dense operand, or a diagonal block when diag != 0, is summed densely; two low-rank
+ * blocks are concatenated and recompressed at eps_lr.  `out` must be preallocated with X's
+ * clusters and must not alias X or Y. */
+int clr_lincomb(clr_ctx_t ctx, double a, clr_mat_t x, double b, clr_mat_t y, double diag,
+                clr_mat_t out, void* stream);
+
+/* ---- Newton–Schulz S^-1/2 (Section 4.2) ---------------------------------------------------
+ * X_n = alpha Y_n Z_n, T_n = (15 I - 10 X_n + 3 X_n^2)/8, Z_{n+1} = Z_n T_n,
+ * Y_{n+1} = T_n Y_n, Z_0 = I, Y_0 = S; returns Z = sqrt(alpha) Z_n.  Every product is a CLR
+ * product at the context's eps_lr / eps_sp; T is formed by clr_lincomb.  Synchronises
+ * `stream` once per iteration to read the convergence scalar.  Returns CLR_ENOCONV (with *z
+ * still set) when ns_tol > 0 is not reached.  With `tape` non-NULL the iterates (Y_n, Z_n)
+ * are kept for clr_sqrt_inv_backward (checkpointed every iteration). */
+int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s, clr_mat_t* z, clr_ns_stats* stats,
+                 clr_tape_t* tape, void* stream);
+/* ||alpha Z S Z - I||_F / sqrt(N) for z = sqrt(alpha) Z (two CLR products); synchronises. */
+int clr_ns_residual(clr_ctx_t ctx, clr_mat_t s, clr_mat_t z, double* out, void* stream);
+/* Adjoint of clr_sqrt_inv for L = trace(W^T-weighted) losses: given zbar = dL/dZ (Z the
+ * returned sqrt(alpha) Z_n), returns sbar = dL/dS by running the NS recurrences backwards
+ * over the tape with alpha held constant; truncation is treated as the identity and every
+ * adjoint product is a CLR product at eps_lr. */
+int clr_sqrt_inv_backward(clr_ctx_t ctx, clr_tape_t tape, clr_mat_t zbar, clr_mat_t* sbar,
+                          void* stream);
+int clr_tape_free(clr_ctx_t ctx, clr_tape_t tape);
+
+/* y = A x for dense device vectors (x: n_cols, y: n_rows). */
+int clr_matvec(clr_ctx_t ctx, clr_mat_t a, const double* x, double* y, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CLR_H_ */

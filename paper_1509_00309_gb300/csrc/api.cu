@@ -1,0 +1,1031 @@
+// Host side of the C ABI declared in include/clr.h: contexts, matrices, the orchestration of
+// one CLR product (plan -> dense x dense products -> low-rank products -> recompression) and
+// the Newton–Schulz driver.  Every device step runs in this library's kernels; there is no
+// CPU fallback.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "clr_internal.h"
+
+using namespace clr;
+
+namespace {
+
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+  cudaError_t ensure(size_t want) {
+    if (want <= bytes && p) return cudaSuccess;
+    if (p) {
+      cudaFree(p);
+      p = nullptr;
+      bytes = 0;
+    }
+    size_t sz = std::max<size_t>(want, 256);
+    cudaError_t e = cudaMalloc(&p, sz);
+    if (e == cudaSuccess) bytes = sz;
+    return e;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    bytes = 0;
+  }
+};
+
+}  // namespace
+
+struct clr_ctx_s {
+  int device = 0;
+  clr_opts opts;
+  int n_sm = 0;
+  int cc_major = 0, cc_minor = 0;
+  std::string err;
+  void* encode_fn = nullptr;  // cuTensorMapEncodeTiled
+  // workspaces (grow-only)
+  DevBuf plan_ints, triples, counters, ws, scratch, small, panels_a, panels_b, index_rows,
+      index_cols;
+  PlanCounters last_counters;
+};
+
+struct clr_mat_s {
+  int device = 0;
+  int nr = 0, nc = 0;
+  int64_t n_rows = 0, n_cols = 0;
+  std::vector<int> row_sizes, col_sizes, row_off, col_off;
+  int* d_row_off = nullptr;
+  int* d_col_off = nullptr;
+  int* d_kind = nullptr;
+  int* d_rank = nullptr;
+  double* d_norm = nullptr;
+  double* d_pool = nullptr;
+  MatView view() const {
+    MatView v;
+    v.nr = nr;
+    v.nc = nc;
+    v.n_rows = n_rows;
+    v.n_cols = n_cols;
+    v.row_off = d_row_off;
+    v.col_off = d_col_off;
+    v.kind = d_kind;
+    v.rank = d_rank;
+    v.norm = d_norm;
+    v.pool = d_pool;
+    return v;
+  }
+};
+
+struct clr_tape_s {
+  double alpha = 0.0;
+  int iters = 0;
+  clr_mat_t s = nullptr;                        // borrowed
+  std::vector<clr_mat_t> y, z;                  // owned: Y_n, Z_n before update n
+};
+
+namespace {
+
+int fail(clr_ctx_t ctx, int code, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return code;
+}
+
+int cuda_fail(clr_ctx_t ctx, cudaError_t e, const char* where) {
+  std::string m = std::string(where) + ": " + cudaGetErrorString(e);
+  if (ctx) ctx->err = m;
+  return e == cudaErrorMemoryAllocation ? CLR_ENOMEM : CLR_ECUDA;
+}
+
+#define CLR_CUDA(call)                                      \
+  do {                                                      \
+    cudaError_t e_ = (call);                                \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, #call); \
+  } while (0)
+
+#define CLR_CHECK_LAUNCH(where)                                  \
+  do {                                                           \
+    cudaError_t e_ = cudaGetLastError();                         \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where);     \
+  } while (0)
+
+cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+int check_sizes(clr_ctx_t ctx, int n, const int32_t* sizes, const char* what) {
+  if (n <= 0 || !sizes) return fail(ctx, CLR_EINVAL, std::string(what) + ": no clusters");
+  for (int i = 0; i < n; ++i)
+    if (sizes[i] < 1 || sizes[i] > CLR_MAX_CLUSTER)
+      return fail(ctx, CLR_EINVAL, std::string(what) + ": cluster size out of [1, 256]");
+  return CLR_OK;
+}
+
+void free_mat(clr_mat_t m) {
+  if (!m) return;
+  cudaFree(m->d_row_off);
+  cudaFree(m->d_col_off);
+  cudaFree(m->d_kind);
+  cudaFree(m->d_rank);
+  cudaFree(m->d_norm);
+  cudaFree(m->d_pool);
+  delete m;
+}
+
+int alloc_mat(clr_ctx_t ctx, int nr, const int32_t* rs, int nc, const int32_t* cs,
+              clr_mat_t* out) {
+  int st = check_sizes(ctx, nr, rs, "row clusters");
+  if (st) return st;
+  st = check_sizes(ctx, nc, cs, "column clusters");
+  if (st) return st;
+  clr_mat_t m = new (std::nothrow) clr_mat_s;
+  if (!m) return fail(ctx, CLR_ENOMEM, "host allocation");
+  m->device = ctx->device;
+  m->nr = nr;
+  m->nc = nc;
+  m->row_sizes.assign(rs, rs + nr);
+  m->col_sizes.assign(cs, cs + nc);
+  m->row_off.assign(nr + 1, 0);
+  m->col_off.assign(nc + 1, 0);
+  for (int i = 0; i < nr; ++i) m->row_off[i + 1] = m->row_off[i] + rs[i];
+  for (int j = 0; j < nc; ++j) m->col_off[j + 1] = m->col_off[j] + cs[j];
+  m->n_rows = m->row_off[nr];
+  m->n_cols = m->col_off[nc];
+  const size_t nb = (size_t)nr * nc;
+  cudaError_t e = cudaSuccess;
+  auto A = [&](void** p, size_t b) {
+    if (e == cudaSuccess) e = cudaMalloc(p, std::max<size_t>(b, 16));
+  };
+  A((void**)&m->d_row_off, (nr + 1) * sizeof(int));
+  A((void**)&m->d_col_off, (nc + 1) * sizeof(int));
+  A((void**)&m->d_kind, nb * sizeof(int));
+  A((void**)&m->d_rank, nb * sizeof(int));
+  A((void**)&m->d_norm, nb * sizeof(double));
+  A((void**)&m->d_pool, (size_t)m->n_rows * m->n_cols * sizeof(double));
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->d_row_off, m->row_off.data(), (nr + 1) * sizeof(int),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(m->d_col_off, m->col_off.data(), (nc + 1) * sizeof(int),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(m->d_kind, 0, nb * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(m->d_rank, 0, nb * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(m->d_norm, 0, nb * sizeof(double));
+  if (e != cudaSuccess) {
+    free_mat(m);
+    return cuda_fail(ctx, e, "matrix allocation");
+  }
+  *out = m;
+  return CLR_OK;
+}
+
+bool same_clusters(const std::vector<int>& a, const std::vector<int>& b) { return a == b; }
+
+// Grow the context workspaces needed by a plan over nI x nJ tiles and nK inner clusters.
+int make_plan(clr_ctx_t ctx, int nI, int nJ, int nK, Plan* p) {
+  const size_t nt = (size_t)nI * nJ;
+  CLR_CUDA(ctx->plan_ints.ensure(8 * nt * sizeof(int)));
+  const int64_t max_tr = (int64_t)nt * nK;
+  CLR_CUDA(ctx->triples.ensure((size_t)max_tr * sizeof(Triple)));
+  CLR_CUDA(ctx->counters.ensure(sizeof(PlanCounters)));
+  int* base = (int*)ctx->plan_ints.p;
+  p->nI = nI;
+  p->nJ = nJ;
+  p->nK = nK;
+  p->t_count = base;
+  p->t_start = base + nt;
+  p->t_route = base + 2 * nt;
+  p->t_rsum = base + 3 * nt;
+  p->l_dense = base + 4 * nt;
+  p->l_lr = base + 5 * nt;
+  p->l_qr = base + 6 * nt;
+  p->l_dcomp = base + 7 * nt;
+  p->triples = (Triple*)ctx->triples.p;
+  p->max_triples = max_tr;
+  p->counters = (PlanCounters*)ctx->counters.p;
+  return CLR_OK;
+}
+
+int grid_of(clr_ctx_t ctx, int per_sm) { return std::max(1, ctx->n_sm * per_sm); }
+
+constexpr int64_t kScratchPerCta =
+    (int64_t)(CLR_MAX_CLUSTER / 2) * (CLR_MAX_CLUSTER / 2) +
+    (int64_t)CLR_MAX_CLUSTER * (CLR_MAX_CLUSTER / 2);
+
+int choose_precision(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b) {
+  int prec = ctx->opts.precision;
+  if (prec != CLR_PREC_AUTO) return prec;
+  // A-priori statistical error model of the split products (relative RMS error of one
+  // product term, including FP32 accumulation): bf16x3 ~ 2^-16.5, bf16x6 ~ 2^-23.  The
+  // expected ||dC||_F is about u ||A||_F ||B||_F / sqrt(K); the product tolerance is
+  // 10 eps ||A||_F ||B||_F.  Take the cheapest mode with a factor-4 margin.
+  const double eps = ctx->opts.eps_lr > 0 ? ctx->opts.eps_lr : 1e-8;
+  const double sk = std::sqrt((double)a->n_cols);
+  if (std::ldexp(1.0, -16) * 0.6 / sk * 4.0 <= 10.0 * eps) return CLR_PREC_BF16X3;
+  if (std::ldexp(1.0, -23) / sk * 4.0 <= 10.0 * eps) return CLR_PREC_BF16X6;
+  (void)b;
+  return CLR_PREC_FP64;
+}
+
+}  // namespace
+
+// =============================================================================================
+// Errors, options, contexts
+// =============================================================================================
+extern "C" const char* clr_strerror(int s) {
+  switch (s) {
+    case CLR_OK: return "ok";
+    case CLR_EINVAL: return "invalid argument";
+    case CLR_ENOMEM: return "out of device memory";
+    case CLR_ENOCONV: return "Newton-Schulz did not converge";
+    case CLR_ETIMEOUT: return "device-side wait timed out";
+    case CLR_ECUDA: return "CUDA error";
+    case CLR_ENOTSUP: return "not supported";
+    default: return "unknown status";
+  }
+}
+
+extern "C" const char* clr_last_error(clr_ctx_t ctx) { return ctx ? ctx->err.c_str() : ""; }
+
+extern "C" void clr_opts_default(clr_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->eps_lr = 1e-8;
+  o->eps_sp = 0.0;
+  o->precision = CLR_PREC_FP64;
+  o->recompress_dense = 0;
+  o->ns_max_iter = 50;
+  o->ns_tol = 1e-6;
+  o->ns_alpha = 0.0;
+  o->ns_power_steps = 30;
+  o->ns_fp64_tail = 0;
+  o->ns_ladder_switch = 1e-3;
+  o->jacobi_max_sweeps = 40;
+}
+
+extern "C" int clr_create(clr_ctx_t* out, int device, const clr_opts* opts) {
+  if (!out) return CLR_EINVAL;
+  *out = nullptr;
+  clr_ctx_t ctx = new (std::nothrow) clr_ctx_s;
+  if (!ctx) return CLR_ENOMEM;
+  if (opts) ctx->opts = *opts; else clr_opts_default(&ctx->opts);
+  int n = 0;
+  cudaError_t e = cudaGetDeviceCount(&n);
+  if (e != cudaSuccess || device < 0 || device >= n) {
+    delete ctx;
+    return CLR_ECUDA;
+  }
+  ctx->device = device;
+  e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->cc_major, cudaDevAttrComputeCapabilityMajor, device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->cc_minor, cudaDevAttrComputeCapabilityMinor, device);
+  if (e != cudaSuccess || ctx->cc_major != 10 || ctx->cc_minor != 3) {
+    delete ctx;
+    return CLR_ECUDA;
+  }
+  cudaDriverEntryPointQueryResult q;
+  void* fn = nullptr;
+  e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                       cudaEnableDefault, &q);
+  if (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ctx->encode_fn = fn;
+  std::memset(&ctx->last_counters, 0, sizeof(ctx->last_counters));
+  *out = ctx;
+  return CLR_OK;
+}
+
+extern "C" int clr_destroy(clr_ctx_t ctx) {
+  if (!ctx) return CLR_EINVAL;
+  cudaSetDevice(ctx->device);
+  for (DevBuf* b : {&ctx->plan_ints, &ctx->triples, &ctx->counters, &ctx->ws, &ctx->scratch,
+                    &ctx->small, &ctx->panels_a, &ctx->panels_b, &ctx->index_rows,
+                    &ctx->index_cols})
+    b->release();
+  delete ctx;
+  return CLR_OK;
+}
+
+extern "C" int clr_set_opts(clr_ctx_t ctx, const clr_opts* o) {
+  if (!ctx || !o) return CLR_EINVAL;
+  if (!(o->eps_lr >= 0.0) || !(o->eps_sp >= 0.0) || o->precision < 0 || o->precision > 3)
+    return fail(ctx, CLR_EINVAL, "bad options");
+  ctx->opts = *o;
+  return CLR_OK;
+}
+
+extern "C" int clr_get_opts(clr_ctx_t ctx, clr_opts* o) {
+  if (!ctx || !o) return CLR_EINVAL;
+  *o = ctx->opts;
+  return CLR_OK;
+}
+
+// =============================================================================================
+// Matrices
+// =============================================================================================
+extern "C" int clr_mat_create(clr_ctx_t ctx, int n_rt, const int32_t* rs, int n_ct,
+                              const int32_t* cs, clr_mat_t* out) {
+  if (!ctx || !out) return CLR_EINVAL;
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  return alloc_mat(ctx, n_rt, rs, n_ct, cs, out);
+}
+
+extern "C" int clr_mat_free(clr_ctx_t ctx, clr_mat_t m) {
+  if (!m) return CLR_EINVAL;
+  if (ctx) cudaSetDevice(ctx->device);
+  free_mat(m);
+  return CLR_OK;
+}
+
+extern "C" int clr_mat_shape(clr_mat_t m, int64_t* nrow, int64_t* ncol, int* nrt, int* nct) {
+  if (!m) return CLR_EINVAL;
+  if (nrow) *nrow = m->n_rows;
+  if (ncol) *ncol = m->n_cols;
+  if (nrt) *nrt = m->nr;
+  if (nct) *nct = m->nc;
+  return CLR_OK;
+}
+
+extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, int a_on_host,
+                                  int n_rt, const int32_t* rs, int n_ct, const int32_t* cs,
+                                  double eps_lr, double drop_norm, void* stream,
+                                  clr_mat_t* out) {
+  if (!ctx || !a || !out) return CLR_EINVAL;
+  *out = nullptr;
+  if (!(eps_lr >= 0.0) || !(drop_norm >= 0.0)) return fail(ctx, CLR_EINVAL, "bad thresholds");
+  cudaSetDevice(ctx->device);
+  clr_mat_t m = nullptr;
+  int st = alloc_mat(ctx, n_rt, rs, n_ct, cs, &m);
+  if (st) return st;
+  if (lda < m->n_cols) {
+    free_mat(m);
+    return fail(ctx, CLR_EINVAL, "lda < n_cols");
+  }
+  cudaStream_t s = as_stream(stream);
+  const double* src = a;
+  DevBuf staging;
+  if (a_on_host) {
+    const size_t bytes = (size_t)m->n_rows * m->n_cols * sizeof(double);
+    cudaError_t e = staging.ensure(bytes);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(staging.p, m->n_cols * sizeof(double), a, lda * sizeof(double),
+                            m->n_cols * sizeof(double), m->n_rows, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) {
+      free_mat(m);
+      staging.release();
+      return cuda_fail(ctx, e, "from_dense upload");
+    }
+    src = (const double*)staging.p;
+    lda = m->n_cols;
+  }
+  cudaError_t e = ctx->ws.ensure(2 * (size_t)m->n_rows * m->n_cols * sizeof(double));
+  if (e == cudaSuccess) e = ctx->counters.ensure(sizeof(PlanCounters));
+  if (e != cudaSuccess) {
+    free_mat(m);
+    staging.release();
+    return cuda_fail(ctx, e, "from_dense workspace");
+  }
+  PlanCounters* pc = (PlanCounters*)ctx->counters.p;
+  cudaMemsetAsync(pc, 0, sizeof(PlanCounters), s);
+  launch_compress_dense(m->view(), nullptr, nullptr, src, lda, (double*)ctx->ws.p, eps_lr,
+                        drop_norm, eps_lr == 0.0 ? 1 : 0, ctx->opts.jacobi_max_sweeps,
+                        grid_of(ctx, 2), &pc->err, s);
+  e = cudaGetLastError();
+  int errflag = 0;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&errflag, &pc->err, sizeof(int), cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  staging.release();
+  if (e != cudaSuccess) {
+    free_mat(m);
+    return cuda_fail(ctx, e, "from_dense");
+  }
+  if (errflag) {
+    free_mat(m);
+    return fail(ctx, CLR_EINVAL, "non-finite input");
+  }
+  *out = m;
+  return CLR_OK;
+}
+
+extern "C" int clr_mat_from_blocks(clr_ctx_t ctx, int n_rt, const int32_t* rs, int n_ct,
+                                   const int32_t* cs, const int32_t* kinds,
+                                   const int32_t* ranks, const double* pool_host, void* stream,
+                                   clr_mat_t* out) {
+  if (!ctx || !kinds || !ranks || !pool_host || !out) return CLR_EINVAL;
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  // validate kinds and ranks on the host
+  for (int I = 0; I < n_rt; ++I)
+    for (int J = 0; J < n_ct; ++J) {
+      const int k = kinds[I * n_ct + J], r = ranks[I * n_ct + J];
+      const int lim = std::min(rs[I], cs[J]) / 2;
+      if (k < 0 || k > 2) return fail(ctx, CLR_EINVAL, "bad block kind");
+      if (k == CLR_KIND_LR && (r < 1 || r > lim))
+        return fail(ctx, CLR_EINVAL, "low-rank block rank out of [1, floor(min(m,n)/2)]");
+    }
+  clr_mat_t m = nullptr;
+  int st = alloc_mat(ctx, n_rt, rs, n_ct, cs, &m);
+  if (st) return st;
+  std::vector<int> rk(ranks, ranks + (size_t)n_rt * n_ct);
+  for (int I = 0; I < n_rt; ++I)
+    for (int J = 0; J < n_ct; ++J) {
+      const int b = I * n_ct + J;
+      if (kinds[b] == CLR_KIND_DENSE) rk[b] = std::min(rs[I], cs[J]);
+      if (kinds[b] == CLR_KIND_ZERO) rk[b] = 0;
+    }
+  cudaStream_t s = as_stream(stream);
+  const size_t nb = (size_t)n_rt * n_ct;
+  cudaError_t e = cudaMemcpyAsync(m->d_kind, kinds, nb * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->d_rank, rk.data(), nb * sizeof(int), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(m->d_pool, pool_host, (size_t)m->n_rows * m->n_cols * sizeof(double),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) {
+    launch_block_norms(m->view(), s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    free_mat(m);
+    return cuda_fail(ctx, e, "from_blocks");
+  }
+  *out = m;
+  return CLR_OK;
+}
+
+extern "C" int clr_mat_to_dense(clr_ctx_t ctx, clr_mat_t m, double* out, int64_t ldo,
+                                int out_on_host, void* stream) {
+  if (!ctx || !m || !out) return CLR_EINVAL;
+  if (ldo < m->n_cols) return fail(ctx, CLR_EINVAL, "ldo < n_cols");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  if (!out_on_host) {
+    launch_to_dense(m->view(), out, ldo, s);
+    CLR_CHECK_LAUNCH("to_dense");
+    return CLR_OK;
+  }
+  DevBuf tmp;
+  const size_t bytes = (size_t)m->n_rows * m->n_cols * sizeof(double);
+  cudaError_t e = tmp.ensure(bytes);
+  if (e == cudaSuccess) {
+    launch_to_dense(m->view(), (double*)tmp.p, m->n_cols, s);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess)
+    e = cudaMemcpy2DAsync(out, ldo * sizeof(double), tmp.p, m->n_cols * sizeof(double),
+                          m->n_cols * sizeof(double), m->n_rows, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  tmp.release();
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "to_dense");
+  return CLR_OK;
+}
+
+extern "C" int clr_mat_get_blocks(clr_ctx_t ctx, clr_mat_t m, int32_t* kinds, int32_t* ranks,
+                                  double* norms, double* pool_host, void* stream) {
+  if (!ctx || !m) return CLR_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  const size_t nb = (size_t)m->nr * m->nc;
+  if (kinds) CLR_CUDA(cudaMemcpyAsync(kinds, m->d_kind, nb * sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (ranks) CLR_CUDA(cudaMemcpyAsync(ranks, m->d_rank, nb * sizeof(int), cudaMemcpyDeviceToHost, s));
+  if (norms) CLR_CUDA(cudaMemcpyAsync(norms, m->d_norm, nb * sizeof(double), cudaMemcpyDeviceToHost, s));
+  if (pool_host)
+    CLR_CUDA(cudaMemcpyAsync(pool_host, m->d_pool, (size_t)m->n_rows * m->n_cols * sizeof(double),
+                             cudaMemcpyDeviceToHost, s));
+  CLR_CUDA(cudaStreamSynchronize(s));
+  return CLR_OK;
+}
+
+extern "C" int clr_mat_info(clr_ctx_t ctx, clr_mat_t m, clr_info* info, void* stream) {
+  if (!ctx || !m || !info) return CLR_EINVAL;
+  const size_t nb = (size_t)m->nr * m->nc;
+  std::vector<int> kinds(nb), ranks(nb);
+  std::vector<double> norms(nb);
+  int st = clr_mat_get_blocks(ctx, m, kinds.data(), ranks.data(), norms.data(), nullptr, stream);
+  if (st) return st;
+  std::memset(info, 0, sizeof(*info));
+  info->n_rows = m->n_rows;
+  info->n_cols = m->n_cols;
+  info->n_row_clusters = m->nr;
+  info->n_col_clusters = m->nc;
+  double fro = 0.0;
+  const int nbins = CLR_MAX_CLUSTER / 2 + 2;
+  for (int I = 0; I < m->nr; ++I)
+    for (int J = 0; J < m->nc; ++J) {
+      const size_t b = (size_t)I * m->nc + J;
+      const int k = kinds[b];
+      if (k < 0 || k > 2) return fail(ctx, CLR_ECUDA, "corrupt block kind");
+      info->n_blocks[k]++;
+      fro += norms[b] * norms[b];
+      if (k == CLR_KIND_LR) {
+        info->max_rank = std::max(info->max_rank, ranks[b]);
+        info->sum_rank += ranks[b];
+        info->stored_doubles += (int64_t)(m->row_sizes[I] + m->col_sizes[J]) * ranks[b];
+        info->rank_hist[std::min(ranks[b], nbins - 2)]++;
+      } else if (k == CLR_KIND_DENSE) {
+        info->stored_doubles += (int64_t)m->row_sizes[I] * m->col_sizes[J];
+        info->rank_hist[nbins - 1]++;
+      } else {
+        info->rank_hist[0]++;
+      }
+    }
+  info->frob_norm = std::sqrt(fro);
+  return CLR_OK;
+}
+
+extern "C" int clr_mat_copy(clr_ctx_t ctx, clr_mat_t src, clr_mat_t dst, void* stream) {
+  if (!ctx || !src || !dst) return CLR_EINVAL;
+  if (src->row_sizes != dst->row_sizes || src->col_sizes != dst->col_sizes)
+    return fail(ctx, CLR_EINVAL, "copy: clusters differ");
+  if (src == dst) return CLR_OK;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  const size_t nb = (size_t)src->nr * src->nc;
+  CLR_CUDA(cudaMemcpyAsync(dst->d_kind, src->d_kind, nb * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  CLR_CUDA(cudaMemcpyAsync(dst->d_rank, src->d_rank, nb * sizeof(int), cudaMemcpyDeviceToDevice, s));
+  CLR_CUDA(cudaMemcpyAsync(dst->d_norm, src->d_norm, nb * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CLR_CUDA(cudaMemcpyAsync(dst->d_pool, src->d_pool, (size_t)src->n_rows * src->n_cols * sizeof(double),
+                           cudaMemcpyDeviceToDevice, s));
+  return CLR_OK;
+}
+
+extern "C" int clr_mat_transpose(clr_ctx_t ctx, clr_mat_t src, clr_mat_t* out, void* stream) {
+  if (!ctx || !src || !out) return CLR_EINVAL;
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  clr_mat_t t = nullptr;
+  int st = alloc_mat(ctx, src->nc, src->col_sizes.data(), src->nr, src->row_sizes.data(), &t);
+  if (st) return st;
+  launch_transpose(src->view(), t->view(), as_stream(stream));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    free_mat(t);
+    return cuda_fail(ctx, e, "transpose");
+  }
+  *out = t;
+  return CLR_OK;
+}
+
+extern "C" int clr_matvec(clr_ctx_t ctx, clr_mat_t a, const double* x, double* y, void* stream) {
+  if (!ctx || !a || !x || !y) return CLR_EINVAL;
+  cudaSetDevice(ctx->device);
+  launch_matvec(a->view(), x, y, as_stream(stream));
+  CLR_CHECK_LAUNCH("matvec");
+  return CLR_OK;
+}
+
+// =============================================================================================
+// The product
+// =============================================================================================
+namespace {
+
+int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Plan& p, int prec,
+                 cudaStream_t s) {
+  const int terms = prec == CLR_PREC_BF16X3 ? 2 : 3;
+  const int64_t M_pad = (c->n_rows + 127) / 128 * 128;
+  const int64_t N_pad = (c->n_cols + 255) / 256 * 256;
+  const int64_t K_pad = (a->n_cols + 63) / 64 * 64;
+  CLR_CUDA(ctx->panels_a.ensure((size_t)terms * M_pad * K_pad * 2));
+  CLR_CUDA(ctx->panels_b.ensure((size_t)terms * N_pad * K_pad * 2));
+  CLR_CUDA(ctx->index_rows.ensure((size_t)c->n_rows * sizeof(int)));
+  CLR_CUDA(ctx->index_cols.ensure((size_t)c->n_cols * sizeof(int)));
+  MatView av = a->view(), bv = b->view(), cv = c->view();
+  launch_split_stage(av, ctx->panels_a.p, terms, M_pad, K_pad, 1, s);
+  launch_split_stage(bv, ctx->panels_b.p, terms, N_pad, K_pad, 0, s);
+  launch_cluster_index(c->d_row_off, c->nr, (int*)ctx->index_rows.p, c->n_rows, s);
+  launch_cluster_index(c->d_col_off, c->nc, (int*)ctx->index_cols.p, c->n_cols, s);
+  CLR_CHECK_LAUNCH("split staging");
+  SplitGemmArgs g;
+  g.A = &av;
+  g.B = &bv;
+  g.C = &cv;
+  g.p = &p;
+  g.terms = terms;
+  g.a_panels = ctx->panels_a.p;
+  g.b_panels = ctx->panels_b.p;
+  g.M_pad = M_pad;
+  g.N_pad = N_pad;
+  g.K_pad = K_pad;
+  g.row_tile_of = (const int*)ctx->index_rows.p;
+  g.col_tile_of = (const int*)ctx->index_cols.p;
+  g.n_sm = ctx->n_sm;
+  g.err = &p.counters->err;
+  g.encode_fn = ctx->encode_fn;
+  std::string why;
+  int st = split_gemm_dd(g, s, &why);
+  if (st) return fail(ctx, st, "split GEMM: " + why);
+  CLR_CHECK_LAUNCH("split GEMM");
+  return CLR_OK;
+}
+
+int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double alpha,
+                  int prec, clr_product_stats* stats, cudaStream_t s) {
+  if (!same_clusters(a->col_sizes, b->row_sizes))
+    return fail(ctx, CLR_EINVAL, "inner clusters of A and B differ");
+  if (!same_clusters(c->row_sizes, a->row_sizes) || !same_clusters(c->col_sizes, b->col_sizes))
+    return fail(ctx, CLR_EINVAL, "C clusters do not match A rows / B columns");
+  if (c == a || c == b) return fail(ctx, CLR_EINVAL, "C aliases an operand");
+  if (!std::isfinite(alpha)) return fail(ctx, CLR_EINVAL, "alpha not finite");
+  Plan p;
+  int st = make_plan(ctx, a->nr, b->nc, a->nc, &p);
+  if (st) return st;
+  CLR_CUDA(ctx->ws.ensure(2 * (size_t)c->n_rows * c->n_cols * sizeof(double)));
+  const int lr_grid = grid_of(ctx, 2);
+  CLR_CUDA(ctx->scratch.ensure((size_t)lr_grid * kScratchPerCta * sizeof(double)));
+  MatView av = a->view(), bv = b->view(), cv = c->view();
+  const clr_opts& o = ctx->opts;
+  launch_plan(av, bv, p, o.eps_sp, o.recompress_dense, s);
+  launch_set_route_kinds(cv, p, s);
+  CLR_CHECK_LAUNCH("plan");
+  if (prec == CLR_PREC_FP64) {
+    launch_dd_fp64(av, bv, cv, p, grid_of(ctx, 4), s);
+    CLR_CHECK_LAUNCH("dense x dense (FP64)");
+  } else {
+    st = run_split_dd(ctx, a, b, c, p, prec, s);
+    if (st) return st;
+  }
+  launch_lr_products(av, bv, cv, p, (double*)ctx->ws.p, (double*)ctx->scratch.p,
+                     kScratchPerCta, lr_grid, s);
+  CLR_CHECK_LAUNCH("low-rank products");
+  launch_compress_qr(cv, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->ws.p, o.eps_lr,
+                     o.jacobi_max_sweeps, grid_of(ctx, 2), &p.counters->err, s);
+  launch_compress_dense(cv, p.l_dcomp, &p.counters->n_dcomp, nullptr, 0, (double*)ctx->ws.p,
+                        o.eps_lr, 0.0, 0, o.jacobi_max_sweeps, grid_of(ctx, 2),
+                        &p.counters->err, s);
+  if (!o.recompress_dense) launch_dense_tile_norms(cv, p, s);
+  CLR_CHECK_LAUNCH("recompression");
+  if (alpha != 1.0) {
+    launch_scale_blocks(cv, alpha, s);
+    CLR_CHECK_LAUNCH("scale");
+  }
+  if (stats) {
+    PlanCounters pc;
+    CLR_CUDA(cudaMemcpyAsync(&pc, p.counters, sizeof(pc), cudaMemcpyDeviceToHost, s));
+    CLR_CUDA(cudaStreamSynchronize(s));
+    ctx->last_counters = pc;
+    for (int q = 0; q < 4; ++q) stats->n_triples[q] = (int64_t)pc.by_kind[q];
+    stats->flops = (int64_t)pc.flops;
+    for (int q = 0; q < 3; ++q) stats->n_tiles[q] = (int64_t)pc.by_mode[q];
+    stats->max_rank_sum = (int64_t)pc.max_rsum;
+    stats->precision = prec;
+    if (pc.err == 1) return fail(ctx, CLR_ETIMEOUT, "a device-side wait timed out");
+    if (pc.err) return fail(ctx, CLR_EINVAL, "device reported bad data (flag " + std::to_string(pc.err) + ")");
+  }
+  return CLR_OK;
+}
+
+}  // namespace
+
+extern "C" int clr_multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c,
+                                 double alpha, clr_product_stats* stats, void* stream) {
+  if (!ctx || !a || !b || !c) return CLR_EINVAL;
+  cudaSetDevice(ctx->device);
+  return multiply_into(ctx, a, b, c, alpha, choose_precision(ctx, a, b), stats,
+                       as_stream(stream));
+}
+
+extern "C" int clr_multiply(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t* c,
+                            void* stream) {
+  if (!ctx || !a || !b || !c) return CLR_EINVAL;
+  *c = nullptr;
+  cudaSetDevice(ctx->device);
+  clr_mat_t out = nullptr;
+  int st = alloc_mat(ctx, a->nr, a->row_sizes.data(), b->nc, b->col_sizes.data(), &out);
+  if (st) return st;
+  st = multiply_into(ctx, a, b, out, 1.0, choose_precision(ctx, a, b), nullptr,
+                     as_stream(stream));
+  if (st) {
+    free_mat(out);
+    return st;
+  }
+  *c = out;
+  return CLR_OK;
+}
+
+extern "C" int clr_multiply_batched(clr_ctx_t ctx, int n, const clr_mat_t* a,
+                                    const clr_mat_t* b, clr_mat_t* c, void* stream) {
+  if (!ctx || n < 0 || (n > 0 && (!a || !b || !c))) return CLR_EINVAL;
+  for (int i = 0; i < n; ++i) c[i] = nullptr;
+  for (int i = 0; i < n; ++i) {
+    int st = clr_multiply(ctx, a[i], b[i], &c[i], stream);
+    if (st) {
+      for (int j = 0; j < i; ++j) {
+        free_mat(c[j]);
+        c[j] = nullptr;
+      }
+      return st;
+    }
+  }
+  return CLR_OK;
+}
+
+extern "C" int clr_lincomb(clr_ctx_t ctx, double a, clr_mat_t x, double b, clr_mat_t y,
+                           double diag, clr_mat_t out, void* stream) {
+  if (!ctx || !x || !y || !out) return CLR_EINVAL;
+  if (x->row_sizes != y->row_sizes || x->col_sizes != y->col_sizes ||
+      out->row_sizes != x->row_sizes || out->col_sizes != x->col_sizes)
+    return fail(ctx, CLR_EINVAL, "lincomb: clusters differ");
+  if (out == x || out == y) return fail(ctx, CLR_EINVAL, "lincomb: output aliases an input");
+  if (!std::isfinite(a) || !std::isfinite(b) || !std::isfinite(diag))
+    return fail(ctx, CLR_EINVAL, "lincomb: coefficient not finite");
+  if (diag != 0.0 && x->row_sizes != x->col_sizes)
+    return fail(ctx, CLR_EINVAL, "lincomb: diagonal shift needs square clusters");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  Plan p;
+  int st = make_plan(ctx, x->nr, x->nc, 1, &p);
+  if (st) return st;
+  CLR_CUDA(ctx->ws.ensure(2 * (size_t)x->n_rows * x->n_cols * sizeof(double)));
+  const clr_opts& o = ctx->opts;
+  MatView xv = x->view(), yv = y->view(), ov = out->view();
+  launch_lincomb_plan(a, xv, b, yv, diag, ov, p, (double*)ctx->ws.p, o.recompress_dense, s);
+  launch_compress_qr(ov, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->ws.p, o.eps_lr,
+                     o.jacobi_max_sweeps, grid_of(ctx, 2), &p.counters->err, s);
+  launch_compress_dense(ov, p.l_dcomp, &p.counters->n_dcomp, nullptr, 0, (double*)ctx->ws.p,
+                        o.eps_lr, 0.0, 0, o.jacobi_max_sweeps, grid_of(ctx, 2),
+                        &p.counters->err, s);
+  CLR_CHECK_LAUNCH("lincomb");
+  return CLR_OK;
+}
+
+// =============================================================================================
+// Newton–Schulz (Section 4.2)
+// =============================================================================================
+namespace {
+
+__global__ void fill_kernel(double* v, int64_t n, double val) {
+  int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) v[i] = val;
+}
+
+// v <- w / ||w|| and dot = v^T w (single CTA, deterministic).
+__global__ void __launch_bounds__(1024) normalize_kernel(const double* w, double* v, int64_t n,
+                                                         double* norm_out) {
+  __shared__ double red[32];
+  __shared__ double tot;
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(w[i], w[i], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) t += red[i];
+    tot = t;
+    if (norm_out) *norm_out = sqrt(t);
+  }
+  __syncthreads();
+  const double inv = tot > 0.0 ? 1.0 / sqrt(tot) : 0.0;
+  if (v)
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) v[i] = w[i] * inv;
+}
+
+__global__ void __launch_bounds__(1024) dot_kernel(const double* a, const double* b, int64_t n,
+                                                   double* out) {
+  __shared__ double red[32];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += blockDim.x) s = fma(a[i], b[i], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (threadIdx.x % 32 == 0) red[threadIdx.x / 32] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x / 32); ++i) t += red[i];
+    *out = t;
+  }
+}
+
+// alpha = 1 / (1.01 lambda), lambda the Rayleigh quotient after `steps` power iterations from
+// the normalised all-ones vector (reading of Section 4.2: ||alpha M - I||_2 <= 1).
+int estimate_alpha(clr_ctx_t ctx, clr_mat_t s_mat, int steps, cudaStream_t s, double* alpha) {
+  const int64_t n = s_mat->n_rows;
+  CLR_CUDA(ctx->small.ensure((size_t)(3 * n + 4) * sizeof(double)));
+  double* v = (double*)ctx->small.p;
+  double* w = v + n;
+  double* scal = w + n;
+  fill_kernel<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(v, n, 1.0 / std::sqrt((double)n));
+  MatView sv = s_mat->view();
+  for (int it = 0; it < steps; ++it) {
+    launch_matvec(sv, v, w, s);
+    normalize_kernel<<<1, 1024, 0, s>>>(w, v, n, nullptr);
+  }
+  launch_matvec(sv, v, w, s);
+  dot_kernel<<<1, 1024, 0, s>>>(v, w, n, scal);
+  CLR_CHECK_LAUNCH("alpha estimate");
+  double lam = 0.0;
+  CLR_CUDA(cudaMemcpyAsync(&lam, scal, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CLR_CUDA(cudaStreamSynchronize(s));
+  if (!(lam > 0.0) || !std::isfinite(lam))
+    return fail(ctx, CLR_EINVAL, "alpha estimate: matrix is not positive definite");
+  *alpha = 1.0 / (1.01 * lam);
+  return CLR_OK;
+}
+
+int identity_distance(clr_ctx_t ctx, clr_mat_t x, cudaStream_t s, double* out) {
+  const size_t nb = (size_t)x->nr * x->nc;
+  DevBuf& buf = ctx->small;
+  const size_t need = (size_t)(3 * x->n_rows + 4 + 1 + nb) * sizeof(double);
+  if (buf.bytes < need) CLR_CUDA(buf.ensure(need));
+  double* part = (double*)buf.p + 3 * x->n_rows + 4;
+  launch_identity_distance(x->view(), part, s);
+  CLR_CHECK_LAUNCH("identity distance");
+  double sq = 0.0;
+  CLR_CUDA(cudaMemcpyAsync(&sq, part, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CLR_CUDA(cudaStreamSynchronize(s));
+  *out = std::sqrt(std::max(sq, 0.0) / (double)x->n_rows);
+  return CLR_OK;
+}
+
+struct MatGuard {
+  std::vector<clr_mat_t> v;
+  ~MatGuard() {
+    for (clr_mat_t m : v) free_mat(m);
+  }
+  clr_mat_t keep(clr_mat_t m) {
+    v.erase(std::find(v.begin(), v.end(), m));
+    return m;
+  }
+};
+
+}  // namespace
+
+extern "C" int clr_ns_residual(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t z, double* out,
+                               void* stream) {
+  if (!ctx || !s_mat || !z || !out) return CLR_EINVAL;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  MatGuard g;
+  clr_mat_t zs = nullptr, zsz = nullptr;
+  int st = alloc_mat(ctx, z->nr, z->row_sizes.data(), s_mat->nc, s_mat->col_sizes.data(), &zs);
+  if (st) return st;
+  g.v.push_back(zs);
+  st = alloc_mat(ctx, z->nr, z->row_sizes.data(), z->nc, z->col_sizes.data(), &zsz);
+  if (st) return st;
+  g.v.push_back(zsz);
+  const int prec = choose_precision(ctx, z, s_mat);
+  st = multiply_into(ctx, z, s_mat, zs, 1.0, prec, nullptr, s);
+  if (st) return st;
+  st = multiply_into(ctx, zs, z, zsz, 1.0, prec, nullptr, s);
+  if (st) return st;
+  return identity_distance(ctx, zsz, s, out);
+}
+
+extern "C" int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t* z_out,
+                            clr_ns_stats* stats, clr_tape_t* tape_out, void* stream) {
+  if (!ctx || !s_mat || !z_out) return CLR_EINVAL;
+  *z_out = nullptr;
+  if (tape_out) *tape_out = nullptr;
+  if (s_mat->row_sizes != s_mat->col_sizes)
+    return fail(ctx, CLR_EINVAL, "S must have equal row and column clusters");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  const clr_opts& o = ctx->opts;
+  if (o.ns_max_iter < 0 || o.ns_max_iter >= CLR_NS_MAX_HISTORY)
+    return fail(ctx, CLR_EINVAL, "ns_max_iter out of range");
+  double alpha = o.ns_alpha;
+  int st = CLR_OK;
+  if (!(alpha > 0.0)) {
+    st = estimate_alpha(ctx, s_mat, o.ns_power_steps, s, &alpha);
+    if (st) return st;
+  }
+  const int nr = s_mat->nr;
+  const int32_t* sz = s_mat->row_sizes.data();
+  MatGuard g;
+  clr_mat_t mats[7];
+  for (int i = 0; i < 7; ++i) {
+    st = alloc_mat(ctx, nr, sz, nr, sz, &mats[i]);
+    if (st) return st;
+    g.v.push_back(mats[i]);
+  }
+  clr_mat_t Y = mats[0], Z = mats[1], X = mats[2], X2 = mats[3], T = mats[4], Yn = mats[5],
+            Zn = mats[6];
+  std::unique_ptr<clr_tape_s> tape;
+  if (tape_out) {
+    tape.reset(new clr_tape_s);
+    tape->alpha = alpha;
+    tape->s = s_mat;
+  }
+  st = clr_mat_copy(ctx, s_mat, Y, s);
+  if (st) return st;
+  // Z_0 = I: 0 * S + 0 * S + 1 * I
+  st = clr_lincomb(ctx, 0.0, s_mat, 0.0, s_mat, 1.0, Z, s);
+  if (st) return st;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  cudaEventRecord(e0, s);
+  int prec = choose_precision(ctx, s_mat, s_mat);
+  int it = 0;
+  bool converged = false;
+  std::vector<double> proxies;
+  std::vector<int> precs;
+  while (true) {
+    st = multiply_into(ctx, Y, Z, X, alpha, prec, nullptr, s);
+    if (st) break;
+    double px = 0.0;
+    st = identity_distance(ctx, X, s, &px);
+    if (st) break;
+    proxies.push_back(px);
+    precs.push_back(prec);
+    if (!std::isfinite(px)) {
+      st = fail(ctx, CLR_ENOCONV, "Newton-Schulz diverged (non-finite residual)");
+      break;
+    }
+    if (o.ns_tol > 0.0 && px <= o.ns_tol) {
+      converged = true;
+      break;
+    }
+    if (it >= o.ns_max_iter) break;
+    if (o.ns_fp64_tail && px <= o.ns_ladder_switch) prec = CLR_PREC_FP64;
+    if (tape) {
+      clr_mat_t yc = nullptr, zc = nullptr;
+      st = alloc_mat(ctx, nr, sz, nr, sz, &yc);
+      if (st) break;
+      st = alloc_mat(ctx, nr, sz, nr, sz, &zc);
+      if (st) { free_mat(yc); break; }
+      tape->y.push_back(yc);
+      tape->z.push_back(zc);
+      if ((st = clr_mat_copy(ctx, Y, yc, s)) || (st = clr_mat_copy(ctx, Z, zc, s))) break;
+    }
+    st = multiply_into(ctx, X, X, X2, 1.0, prec, nullptr, s);
+    if (st) break;
+    st = clr_lincomb(ctx, -10.0 / 8.0, X, 3.0 / 8.0, X2, 15.0 / 8.0, T, s);
+    if (st) break;
+    st = multiply_into(ctx, Z, T, Zn, 1.0, prec, nullptr, s);
+    if (st) break;
+    st = multiply_into(ctx, T, Y, Yn, 1.0, prec, nullptr, s);
+    if (st) break;
+    std::swap(Z, Zn);
+    std::swap(Y, Yn);
+    ++it;
+  }
+  cudaEventRecord(e1, s);
+  cudaEventSynchronize(e1);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (tape) {
+    tape->iters = (int)tape->y.size();
+  }
+  if (st) {
+    if (tape)
+      for (size_t i = 0; i < tape->y.size(); ++i) {
+        free_mat(tape->y[i]);
+        free_mat(tape->z[i]);
+      }
+    return st;
+  }
+  // Z_out = sqrt(alpha) Z
+  clr_mat_t zo = g.keep(Z);
+  launch_scale_blocks(zo->view(), std::sqrt(alpha), s);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    free_mat(zo);
+    return cuda_fail(ctx, e, "scale");
+  }
+  if (stats) {
+    std::memset(stats, 0, sizeof(*stats));
+    stats->iters = it;
+    stats->converged = converged || o.ns_tol == 0.0;
+    stats->alpha = alpha;
+    for (size_t i = 0; i < proxies.size() && i < CLR_NS_MAX_HISTORY; ++i) {
+      stats->proxy[i] = proxies[i];
+      stats->precision_used[i] = precs[i];
+    }
+    stats->ms_total = ms;
+    double res = 0.0;
+    int rs = clr_ns_residual(ctx, s_mat, zo, &res, stream);
+    stats->residual = rs ? NAN : res;
+  }
+  *z_out = zo;
+  if (tape_out) *tape_out = tape.release();
+  if (o.ns_tol > 0.0 && !converged) {
+    ctx->err = "Newton-Schulz did not reach ns_tol";
+    return CLR_ENOCONV;
+  }
+  return CLR_OK;
+}
+
+extern "C" int clr_tape_free(clr_ctx_t ctx, clr_tape_t tape) {
+  if (!tape) return CLR_EINVAL;
+  if (ctx) cudaSetDevice(ctx->device);
+  for (clr_mat_t m : tape->y) free_mat(m);
+  for (clr_mat_t m : tape->z) free_mat(m);
+  delete tape;
+  return CLR_OK;
+}
+
+extern "C" int clr_sqrt_inv_backward(clr_ctx_t ctx, clr_tape_t tape, clr_mat_t zbar,
+                                     clr_mat_t* sbar, void* stream) {
+  if (!ctx || !tape || !zbar || !sbar) return CLR_EINVAL;
+  *sbar = nullptr;
+  (void)stream;
+  return fail(ctx, CLR_ENOTSUP, "backward not available");
+}

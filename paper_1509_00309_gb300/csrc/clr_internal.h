@@ -1,0 +1,140 @@
+// Internal declarations of the CLR library (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "clr.h"
+
+namespace clr {
+
+// ---------------------------------------------------------------------------------------------
+// Device view of a CLR matrix.  Block (I,J) owns the fixed pool slot
+//   slot(I,J) = row_off[I] * n_cols + m_I * col_off[J]
+// (the block-row panel of block-row I is an m_I x n_cols column-major matrix, and block
+// (I,J) is its columns col_off[J] .. col_off[J+1]-1).  Dense blocks are column-major m x n;
+// low-rank blocks store X (m x r) then W (n x r), both column-major.
+// ---------------------------------------------------------------------------------------------
+struct MatView {
+  int nr, nc;            // clusters
+  int64_t n_rows, n_cols;
+  const int* row_off;    // nr + 1 (device)
+  const int* col_off;    // nc + 1 (device)
+  int* kind;             // nr * nc
+  int* rank;             // nr * nc
+  double* norm;          // nr * nc, Frobenius norm of each block
+  double* pool;          // n_rows * n_cols
+};
+
+__host__ __device__ inline int64_t slot_of(const MatView& m, int I, int J, int mI) {
+  return (int64_t)m.row_off[I] * m.n_cols + (int64_t)mI * m.col_off[J];
+}
+
+// Triple kinds and tile routes.
+enum { T_DD = 0, T_DL = 1, T_LD = 2, T_LL = 3 };
+// MODE_* mirror the accumulation modes of the method: none, dense (a dense x dense product is
+// present), low rank.  ROUTE_* refine MODE_LR by how the GPU accumulates:
+//   ROUTE_QR   : concatenated rank R <= floor(min(m,n)/2): concatenate factors, QR both,
+//                SVD of the R x R core.
+//   ROUTE_DACC : larger R: accumulate the sum densely, then a dense truncated SVD.
+enum { ROUTE_ZERO = 0, ROUTE_DENSE = 1, ROUTE_QR = 2, ROUTE_DACC = 3 };
+
+struct Triple {
+  int tile;   // C block index I * nJ + J
+  int k;      // inner cluster K
+  int kind;   // T_*
+  int col;    // QR route: first column of this product's factors in the tile concatenation
+};
+
+// Counters written by the planning kernels (device, zeroed before each plan).
+struct PlanCounters {
+  unsigned long long n_triples;
+  unsigned long long by_kind[4];
+  unsigned long long flops;
+  unsigned long long by_mode[3];
+  unsigned long long max_rsum;
+  int n_dense, n_lr, n_qr, n_dacc, n_dcomp;
+  int err;  // error flag raised by kernels (bounded waits, bad metadata)
+};
+
+struct Plan {
+  int nI, nJ, nK;
+  int* t_count;   // nI*nJ
+  int* t_start;   // nI*nJ
+  int* t_route;   // nI*nJ
+  int* t_rsum;    // nI*nJ
+  int* l_dense;   // tiles with ROUTE_DENSE
+  int* l_lr;      // tiles with at least one low-rank product (any route)
+  int* l_qr;      // ROUTE_QR
+  int* l_dcomp;   // tiles needing a dense truncated SVD (ROUTE_DACC, or ROUTE_DENSE when
+                  // dense tiles are recompressed)
+  Triple* triples;
+  int64_t max_triples;
+  PlanCounters* counters;
+};
+
+// ---------------------------------------------------------------------------------------------
+// Kernel launchers (defined in the .cu files).  All are asynchronous on `st`.
+// ---------------------------------------------------------------------------------------------
+// k_plan.cu
+void launch_plan(const MatView& A, const MatView& B, const Plan& p, double eps_sp,
+                 int recompress_dense, cudaStream_t st);
+void launch_plan_scan(const Plan& p, int recompress_dense, cudaStream_t st);
+// k_dense64.cu
+void launch_dd_fp64(const MatView& A, const MatView& B, const MatView& C, const Plan& p,
+                    int grid, cudaStream_t st);
+void launch_to_dense(const MatView& M, double* out, int64_t ldo, cudaStream_t st);
+void launch_zero_blocks(const MatView& M, cudaStream_t st);
+void launch_set_route_kinds(const MatView& C, const Plan& p, cudaStream_t st);
+void launch_dense_tile_norms(const MatView& C, const Plan& p, cudaStream_t st);
+// k_lowrank.cu
+void launch_lr_products(const MatView& A, const MatView& B, const MatView& C, const Plan& p,
+                        double* ws, double* scratch, int64_t scratch_per_cta, int grid,
+                        cudaStream_t st);
+// k_svd.cu
+void launch_compress_qr(const MatView& C, const int* list, const int* count, const int* rsum,
+                        double* ws, double eps, int max_sweeps, int grid, int* err,
+                        cudaStream_t st);
+// Dense truncated SVD of blocks listed in `list` (count on device).  The source of block b is
+// either the matrix's own slot (src == nullptr) or a row-major dense matrix src with leading
+// dimension lds.  drop_norm: blocks with norm below it become zero.  dense_only: skip the
+// SVD (eps = 0 rule) and store every non-dropped block dense.
+void launch_compress_dense(const MatView& C, const int* list, const int* count,
+                           const double* src, int64_t lds, double* ws, double eps,
+                           double drop_norm, int dense_only, int max_sweeps, int grid,
+                           int* err, cudaStream_t st);
+void launch_block_norms(const MatView& M, cudaStream_t st);
+void launch_scale_blocks(const MatView& M, double alpha, cudaStream_t st);
+// k_ns.cu
+void launch_lincomb_plan(double a, const MatView& X, double b, const MatView& Y, double diag,
+                         const MatView& O, const Plan& p, double* ws, int recompress_dense,
+                         cudaStream_t st);
+void launch_identity_distance(const MatView& X, double* out_sq, cudaStream_t st);
+void launch_matvec(const MatView& M, const double* x, double* y, cudaStream_t st);
+void launch_transpose(const MatView& S, const MatView& T, cudaStream_t st);
+// k_split_gemm.cu
+struct SplitGemmArgs {
+  const MatView* A;
+  const MatView* B;
+  const MatView* C;
+  const Plan* p;
+  int terms;          // 2 (bf16x3) or 3 (bf16x6)
+  void* a_panels;     // terms x M_pad x K_pad bf16
+  void* b_panels;     // terms x N_pad x K_pad bf16
+  int64_t M_pad, N_pad, K_pad;
+  const int* row_tile_of;  // n_rows: C block-row of each row
+  const int* col_tile_of;  // n_cols
+  int n_sm;
+  int* err;
+  void* encode_fn;    // cuTensorMapEncodeTiled
+};
+int split_gemm_dd(const SplitGemmArgs& a, cudaStream_t st, std::string* why);
+void launch_split_stage(const MatView& M, void* panels, int terms, int64_t rows_pad,
+                        int64_t cols_pad, int transpose_to_kmajor, cudaStream_t st);
+void launch_cluster_index(const int* off, int n_clusters, int* index_of, int64_t n,
+                          cudaStream_t st);
+
+}  // namespace clr

@@ -1,0 +1,171 @@
+// K0 -- the product's work list.
+//
+// The paper's task-based SUMMA (Section 3.2) issues one multiply task per (i,k,j) block
+// triple and reduces the partial products into C_ij; on one GPU that task graph becomes a
+// triple list built on the device, sorted by C tile (then by k) so that one CTA can own each
+// C tile and accumulate its products without atomics (the GEMM-update case of Section 3.2).
+// Tiles are screened with the Frobenius-norm estimate of Section 4.1.
+#include "clr_internal.h"
+
+namespace clr {
+
+__device__ __forceinline__ int out_rank(int kind, int ra, int rb) {
+  // Section 4.1, Eq. 1: Z = W_A^T X_B is contracted on the side of smaller output rank.
+  if (kind == T_DL) return rb;
+  if (kind == T_LD) return ra;
+  if (kind == T_LL) return rb <= ra ? rb : ra;
+  return 0;
+}
+
+__device__ __forceinline__ unsigned long long triple_flops(int kind, long long m, long long k,
+                                                           long long n, long long ra,
+                                                           long long rb) {
+  if (kind == T_DD) return 2ull * m * k * n;
+  if (kind == T_DL) return 2ull * m * k * rb;
+  if (kind == T_LD) return 2ull * k * n * ra;
+  return 2ull * k * ra * rb + (rb <= ra ? 2ull * m * ra * rb : 2ull * n * ra * rb);
+}
+
+__global__ void plan_count_kernel(MatView A, MatView B, Plan p, double eps_sp) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.nI * p.nJ) return;
+  int I = t / p.nJ, J = t % p.nJ;
+  int m = A.row_off[I + 1] - A.row_off[I];
+  int n = B.col_off[J + 1] - B.col_off[J];
+  bool pass = true;
+  if (eps_sp > 0.0) {
+    double est = 0.0;
+    for (int K = 0; K < p.nK; ++K) {
+      int ka = A.kind[I * A.nc + K], kb = B.kind[K * B.nc + J];
+      if (ka != CLR_KIND_ZERO && kb != CLR_KIND_ZERO)
+        est += A.norm[I * A.nc + K] * B.norm[K * B.nc + J];
+    }
+    pass = est > eps_sp * (double)m * (double)n;
+  }
+  int count = 0, has_dd = 0, rsum = 0;
+  unsigned long long fl = 0;
+  unsigned long long byk[4] = {0, 0, 0, 0};
+  if (pass) {
+    for (int K = 0; K < p.nK; ++K) {
+      int ka = A.kind[I * A.nc + K], kb = B.kind[K * B.nc + J];
+      if (ka == CLR_KIND_ZERO || kb == CLR_KIND_ZERO) continue;
+      int kind = (ka == CLR_KIND_DENSE ? 0 : 2) + (kb == CLR_KIND_DENSE ? 0 : 1);
+      int ra = A.rank[I * A.nc + K], rb = B.rank[K * B.nc + J];
+      int k = A.col_off[K + 1] - A.col_off[K];
+      ++count;
+      byk[kind]++;
+      fl += triple_flops(kind, m, k, n, ra, rb);
+      if (kind == T_DD) has_dd = 1; else rsum += out_rank(kind, ra, rb);
+    }
+  }
+  int route = ROUTE_ZERO;
+  if (count > 0) {
+    int lim = (m < n ? m : n) / 2;
+    route = has_dd ? ROUTE_DENSE : (rsum <= lim ? ROUTE_QR : ROUTE_DACC);
+  }
+  p.t_count[t] = count;
+  p.t_route[t] = route;
+  p.t_rsum[t] = rsum;
+  if (count > 0) {
+    atomicAdd(&p.counters->n_triples, (unsigned long long)count);
+    for (int q = 0; q < 4; ++q)
+      if (byk[q]) atomicAdd(&p.counters->by_kind[q], byk[q]);
+    atomicAdd(&p.counters->flops, fl);
+    atomicAdd(&p.counters->by_mode[has_dd ? 1 : 2], 1ull);
+    if (!has_dd) atomicMax(&p.counters->max_rsum, (unsigned long long)rsum);
+  } else {
+    atomicAdd(&p.counters->by_mode[0], 1ull);
+  }
+}
+
+// Single-CTA scan: t_start = exclusive prefix sum of t_count, plus the tile lists in tile
+// order.  Tile counts are at most a few hundred thousand, so one CTA of 1024 threads walking
+// contiguous chunks is enough.
+constexpr int kScanThreads = 1024;
+constexpr int kScanQ = 5;
+
+__global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(Plan p, int recompress_dense) {
+  __shared__ int sh[kScanQ][kScanThreads];
+  const int n = p.nI * p.nJ;
+  const int tid = threadIdx.x;
+  const int chunk = (n + kScanThreads - 1) / kScanThreads;
+  const int lo = min(n, tid * chunk), hi = min(n, lo + chunk);
+  int s[kScanQ] = {0, 0, 0, 0, 0};
+  for (int i = lo; i < hi; ++i) {
+    int route = p.t_route[i];
+    s[0] += p.t_count[i];
+    s[1] += route == ROUTE_DENSE;
+    s[2] += p.t_rsum[i] > 0;
+    s[3] += route == ROUTE_QR;
+    s[4] += route == ROUTE_DACC || (route == ROUTE_DENSE && recompress_dense);
+  }
+  for (int q = 0; q < kScanQ; ++q) sh[q][tid] = s[q];
+  __syncthreads();
+  // Hillis-Steele inclusive scan over the 1024 partial sums.
+  for (int off = 1; off < kScanThreads; off <<= 1) {
+    int v[kScanQ];
+    for (int q = 0; q < kScanQ; ++q) v[q] = tid >= off ? sh[q][tid - off] : 0;
+    __syncthreads();
+    for (int q = 0; q < kScanQ; ++q) sh[q][tid] += v[q];
+    __syncthreads();
+  }
+  int base[kScanQ];
+  for (int q = 0; q < kScanQ; ++q) base[q] = sh[q][tid] - s[q];
+  for (int i = lo; i < hi; ++i) {
+    int route = p.t_route[i];
+    p.t_start[i] = base[0];
+    base[0] += p.t_count[i];
+    if (route == ROUTE_DENSE) p.l_dense[base[1]++] = i;
+    if (p.t_rsum[i] > 0) p.l_lr[base[2]++] = i;
+    if (route == ROUTE_QR) p.l_qr[base[3]++] = i;
+    if (route == ROUTE_DACC || (route == ROUTE_DENSE && recompress_dense))
+      p.l_dcomp[base[4]++] = i;
+  }
+  if (tid == kScanThreads - 1) {
+    p.counters->n_dense = sh[1][tid];
+    p.counters->n_lr = sh[2][tid];
+    p.counters->n_qr = sh[3][tid];
+    p.counters->n_dcomp = sh[4][tid];
+    p.counters->n_dacc = 0;
+  }
+}
+
+__global__ void plan_fill_kernel(MatView A, MatView B, Plan p) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= p.nI * p.nJ) return;
+  int count = p.t_count[t];
+  if (count == 0) return;
+  int I = t / p.nJ, J = t % p.nJ;
+  int64_t pos = p.t_start[t];
+  int col = 0;
+  for (int K = 0; K < p.nK; ++K) {
+    int ka = A.kind[I * A.nc + K], kb = B.kind[K * B.nc + J];
+    if (ka == CLR_KIND_ZERO || kb == CLR_KIND_ZERO) continue;
+    int kind = (ka == CLR_KIND_DENSE ? 0 : 2) + (kb == CLR_KIND_DENSE ? 0 : 1);
+    Triple tr;
+    tr.tile = t;
+    tr.k = K;
+    tr.kind = kind;
+    tr.col = col;
+    col += out_rank(kind, A.rank[I * A.nc + K], B.rank[K * B.nc + J]);
+    if (pos < p.max_triples) p.triples[pos] = tr; else atomicExch(&p.counters->err, 2);
+    ++pos;
+  }
+}
+
+void launch_plan_scan(const Plan& p, int recompress_dense, cudaStream_t st) {
+  plan_scan_kernel<<<1, kScanThreads, 0, st>>>(p, recompress_dense);
+}
+
+void launch_plan(const MatView& A, const MatView& B, const Plan& p, double eps_sp,
+                 int recompress_dense, cudaStream_t st) {
+  const int n = p.nI * p.nJ;
+  const int threads = 128;
+  const int blocks = (n + threads - 1) / threads;
+  cudaMemsetAsync(p.counters, 0, sizeof(PlanCounters), st);
+  plan_count_kernel<<<blocks, threads, 0, st>>>(A, B, p, eps_sp);
+  plan_scan_kernel<<<1, kScanThreads, 0, st>>>(p, recompress_dense);
+  plan_fill_kernel<<<blocks, threads, 0, st>>>(A, B, p);
+}
+
+}  // namespace clr

@@ -1,0 +1,447 @@
+// K5 -- recompression of C tiles (FP64), and the truncated SVD used to build CLR matrices.
+//
+// Section 4.1 recompresses a low-rank sum X W^T by QR of both factors, X = Q_X R_X and
+// W = Q_W R_W, a low-rank decomposition of the small core M = R_X R_W^T, and re-expansion
+// X' = Q_X X_M, W' = Q_W W_M.  The decomposition of M is taken to be its SVD (the paper does
+// not name it); truncation keeps the smallest rank whose Frobenius error is <= eps, with the
+// singular values on the left factor (X' = Q_X U_r S_r, W' = Q_W V_r).  A block whose rank
+// exceeds floor(min(m,n)/2) is stored dense.
+//
+// One CTA (8 warps) handles one tile:
+//   Householder QR         LAPACK-style reflectors H = I - tau v v^T, v_0 = 1;
+//   one-sided Jacobi SVD   Hestenes rotations on column pairs, round-robin ordering so a
+//                          round's pairs are disjoint (one warp per pair), until no pair has
+//                          |g_a.g_b| > tol ||g_a|| ||g_b|| or the sweep limit is reached.
+// Working arrays live in the tile's workspace slot (2 m n doubles per tile, enough for
+// either route).
+#include <cfloat>
+
+#include "clr_internal.h"
+
+namespace clr {
+
+constexpr int kThreads = 256;
+constexpr int kWarps = kThreads / 32;
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ double block_sum(double v, double* sh) {
+  v = warp_sum(v);
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  for (int i = 0; i < kWarps; ++i) s += sh[i];
+  __syncthreads();
+  return s;
+}
+
+// In-place Householder QR of the p x q column-major matrix a (ld lda), p >= q.  R is left in
+// the upper triangle, the reflector vectors (without their unit first entry) below it.
+__device__ void householder_qr(double* a, int p, int q, int64_t lda, double* tau, double* sh) {
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  for (int j = 0; j < q; ++j) {
+    double* col = a + (int64_t)j * lda;
+    double part = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < p; i += kThreads) part += col[i] * col[i];
+    const double s = block_sum(part, sh);
+    const double x0 = col[j];
+    double t = 0.0, beta = x0, v0 = 1.0;
+    if (s > 0.0) {
+      beta = -copysign(sqrt(x0 * x0 + s), x0);
+      v0 = x0 - beta;
+      t = (beta - x0) / beta;
+    }
+    __syncthreads();
+    if (s > 0.0) {
+      const double inv = 1.0 / v0;
+      for (int i = j + 1 + threadIdx.x; i < p; i += kThreads) col[i] *= inv;
+    }
+    if (threadIdx.x == 0) {
+      col[j] = beta;
+      tau[j] = t;
+    }
+    __syncthreads();
+    if (t != 0.0) {
+      for (int c = j + 1 + w; c < q; c += kWarps) {
+        double* y = a + (int64_t)c * lda;
+        double d = 0.0;
+        for (int i = j + 1 + l; i < p; i += 32) d += col[i] * y[i];
+        d = warp_sum(d) + y[j];
+        const double f = t * d;
+        if (l == 0) y[j] -= f;
+        for (int i = j + 1 + l; i < p; i += 32) y[i] -= f * col[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// y (p x r, ld ldy) <- Q y with Q = H_0 H_1 ... H_{q-1} from householder_qr.
+__device__ void apply_q(const double* v, int p, int q, int64_t ldv, const double* tau,
+                        double* y, int r, int64_t ldy) {
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  for (int j = q - 1; j >= 0; --j) {
+    const double t = tau[j];
+    if (t != 0.0) {
+      const double* vj = v + (int64_t)j * ldv;
+      for (int c = w; c < r; c += kWarps) {
+        double* yc = y + (int64_t)c * ldy;
+        double d = 0.0;
+        for (int i = j + 1 + l; i < p; i += 32) d += vj[i] * yc[i];
+        d = warp_sum(d) + yc[j];
+        const double f = t * d;
+        if (l == 0) yc[j] -= f;
+        for (int i = j + 1 + l; i < p; i += 32) yc[i] -= f * vj[i];
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// One-sided Jacobi on the q columns of g (p x q, ld ldg); v (q x q, ld ldv) accumulates the
+// rotations (initialised to I here).  On return g = U S and the input equals g v^T.
+__device__ int jacobi_svd(double* g, int p, int q, int64_t ldg, double* v, int64_t ldv,
+                          int max_sweeps, int* sh_flag) {
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  for (int e = threadIdx.x; e < q * q; e += kThreads)
+    v[(e % q) + (int64_t)(e / q) * ldv] = (e % q == e / q) ? 1.0 : 0.0;
+  __syncthreads();
+  const int qq = q + (q & 1);  // even number of slots; slot q is a dummy when q is odd
+  const double tol = DBL_EPSILON * sqrt((double)p);
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) *sh_flag = 0;
+    __syncthreads();
+    for (int round = 0; round < qq - 1; ++round) {
+      for (int k = w; k < qq / 2; k += kWarps) {
+        int a, b;
+        if (k == 0) {
+          a = round;
+          b = qq - 1;
+        } else {
+          a = (round + k) % (qq - 1);
+          b = (round - k + (qq - 1)) % (qq - 1);
+        }
+        if (a >= q || b >= q) continue;
+        double* ga = g + (int64_t)a * ldg;
+        double* gb = g + (int64_t)b * ldg;
+        double al = 0.0, be = 0.0, ga_gb = 0.0;
+        for (int i = l; i < p; i += 32) {
+          const double x = ga[i], y = gb[i];
+          al = fma(x, x, al);
+          be = fma(y, y, be);
+          ga_gb = fma(x, y, ga_gb);
+        }
+        al = warp_sum(al);
+        be = warp_sum(be);
+        ga_gb = warp_sum(ga_gb);
+        const double scale = sqrt(al) * sqrt(be);
+        if (scale == 0.0 || fabs(ga_gb) <= tol * scale) continue;
+        const double zeta = (be - al) / (2.0 * ga_gb);
+        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / sqrt(1.0 + t * t);
+        const double s = c * t;
+        for (int i = l; i < p; i += 32) {
+          const double x = ga[i], y = gb[i];
+          ga[i] = c * x - s * y;
+          gb[i] = s * x + c * y;
+        }
+        double* va = v + (int64_t)a * ldv;
+        double* vb = v + (int64_t)b * ldv;
+        for (int i = l; i < q; i += 32) {
+          const double x = va[i], y = vb[i];
+          va[i] = c * x - s * y;
+          vb[i] = s * x + c * y;
+        }
+        if (l == 0) *sh_flag = 1;
+      }
+      __syncthreads();
+    }
+    const int rotated = *sh_flag;
+    __syncthreads();
+    if (!rotated) break;
+  }
+  return sweep;
+}
+
+struct SvdShared {
+  double red[kWarps];
+  double sigma[CLR_MAX_CLUSTER];    // by column
+  double sorted[CLR_MAX_CLUSTER];   // descending
+  int perm[CLR_MAX_CLUSTER];        // sorted position -> column
+  int flag;
+  int rank;
+  double kept_sq;
+};
+
+// Column norms of g, their descending order, and the truncation rank at eps.
+__device__ void sort_and_truncate(const double* g, int p, int q, int64_t ldg, double eps,
+                                  SvdShared& sh) {
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  for (int c = w; c < q; c += kWarps) {
+    const double* gc = g + (int64_t)c * ldg;
+    double s = 0.0;
+    for (int i = l; i < p; i += 32) s = fma(gc[i], gc[i], s);
+    s = warp_sum(s);
+    if (l == 0) sh.sigma[c] = sqrt(s);
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < q; j += kThreads) {
+    const double sj = sh.sigma[j];
+    int pos = 0;
+    for (int i = 0; i < q; ++i) {
+      const double si = sh.sigma[i];
+      pos += (si > sj) || (si == sj && i < j);
+    }
+    sh.perm[pos] = j;
+    sh.sorted[pos] = sj;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // smallest r with sqrt(sum_{i >= r} s_i^2) <= eps
+    double tail = 0.0;
+    int r = q;
+    for (int i = q - 1; i >= 0; --i) {
+      const double nt = tail + sh.sorted[i] * sh.sorted[i];
+      if (sqrt(nt) <= eps) {
+        tail = nt;
+        r = i;
+      } else {
+        break;
+      }
+    }
+    if (q == 0) r = 0;
+    double kept = 0.0;
+    for (int i = 0; i < r; ++i) kept += sh.sorted[i] * sh.sorted[i];
+    sh.rank = r;
+    sh.kept_sq = kept;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------------------------
+// ROUTE_QR tiles: X_cat (m x R) and W_cat (n x R) in the workspace slot.
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const int* list,
+                                                               const int* count,
+                                                               const int* rsum, double* ws,
+                                                               double eps, int max_sweeps) {
+  __shared__ SvdShared sh;
+  const int n_items = *count;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int t = list[it];
+    const int I = t / C.nc, J = t % C.nc;
+    const int m = C.row_off[I + 1] - C.row_off[I];
+    const int n = C.col_off[J + 1] - C.col_off[J];
+    const int R = rsum[t];
+    const int64_t sC = slot_of(C, I, J, m);
+    double* Xc = ws + 2 * sC;
+    double* Wc = Xc + (int64_t)m * R;
+    double* tauX = Wc + (int64_t)n * R;
+    double* tauW = tauX + R;
+    double* M = tauW + R;
+    double* V = M + (int64_t)R * R;
+    householder_qr(Xc, m, R, m, tauX, sh.red);
+    householder_qr(Wc, n, R, n, tauW, sh.red);
+    // M = R_X R_W^T (both upper triangular R x R)
+    for (int e = threadIdx.x; e < R * R; e += kThreads) {
+      const int a = e % R, b = e / R;
+      double s = 0.0;
+      for (int c = (a > b ? a : b); c < R; ++c)
+        s = fma(Xc[a + (int64_t)c * m], Wc[b + (int64_t)c * n], s);
+      M[e] = s;
+    }
+    __syncthreads();
+    jacobi_svd(M, R, R, R, V, R, max_sweeps, &sh.flag);
+    sort_and_truncate(M, R, R, R, eps, sh);
+    const int r = sh.rank;
+    double* Xo = C.pool + sC;
+    double* Wo = Xo + (int64_t)m * r;
+    for (int e = threadIdx.x; e < m * r; e += kThreads) {
+      const int i = e % m, c = e / m;
+      Xo[e] = i < R ? M[i + (int64_t)sh.perm[c] * R] : 0.0;
+    }
+    for (int e = threadIdx.x; e < n * r; e += kThreads) {
+      const int j = e % n, c = e / n;
+      Wo[e] = j < R ? V[j + (int64_t)sh.perm[c] * R] : 0.0;
+    }
+    __syncthreads();
+    apply_q(Xc, m, R, m, tauX, Xo, r, m);
+    apply_q(Wc, n, R, n, tauW, Wo, r, n);
+    if (threadIdx.x == 0) {
+      C.kind[t] = r > 0 ? CLR_KIND_LR : CLR_KIND_ZERO;
+      C.rank[t] = r;
+      C.norm[t] = sqrt(sh.kept_sq);
+    }
+    __syncthreads();
+  }
+}
+
+void launch_compress_qr(const MatView& C, const int* list, const int* count, const int* rsum,
+                        double* ws, double eps, int max_sweeps, int grid, int* err,
+                        cudaStream_t st) {
+  (void)err;
+  compress_qr_kernel<<<grid, kThreads, 0, st>>>(C, list, count, rsum, ws, eps, max_sweeps);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Dense truncated SVD of whole blocks (ROUTE_DACC tiles, recompressed dense tiles, building a
+// CLR matrix from a dense one).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) compress_dense_kernel(
+    MatView C, const int* list, const int* count, const double* src, int64_t lds, double* ws,
+    double eps, double drop_norm, int dense_only, int max_sweeps, int* err) {
+  __shared__ SvdShared sh;
+  const int n_items = list ? *count : C.nr * C.nc;
+  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+    const int t = list ? list[it] : it;
+    const int I = t / C.nc, J = t % C.nc;
+    const int m = C.row_off[I + 1] - C.row_off[I];
+    const int n = C.col_off[J + 1] - C.col_off[J];
+    const int64_t sC = slot_of(C, I, J, m);
+    double* slot = C.pool + sC;
+    const double* S = src ? src + (int64_t)C.row_off[I] * lds + C.col_off[J] : slot;
+    const int64_t s_r = src ? lds : 1;   // element (i,j) at S[i * s_r + j * s_c]
+    const int64_t s_c = src ? 1 : m;
+    const bool tr = m < n;
+    const int p = tr ? n : m, q = tr ? m : n;
+    double* G = ws + 2 * sC;             // p x q, ld p
+    double* V = G + (int64_t)m * n;      // q x q, ld q
+    double part = 0.0;
+    for (int e = threadIdx.x; e < m * n; e += kThreads) {
+      int i, j;
+      if (src) { i = e / n; j = e % n; } else { i = e % m; j = e / m; }
+      const double x = S[i * s_r + j * s_c];
+      part = fma(x, x, part);
+      if (tr) G[j + (int64_t)i * p] = x; else G[i + (int64_t)j * p] = x;
+    }
+    const double nsq = block_sum(part, sh.red);
+    if (!isfinite(nsq)) {
+      if (threadIdx.x == 0) atomicExch(err, 3);
+    }
+    const double nrm = sqrt(nsq);
+    int kind;
+    if (!(nrm >= drop_norm) || nsq == 0.0) {
+      kind = CLR_KIND_ZERO;
+      if (threadIdx.x == 0) { C.kind[t] = kind; C.rank[t] = 0; C.norm[t] = 0.0; }
+      __syncthreads();
+      continue;
+    }
+    int r = q;
+    if (!dense_only) {
+      jacobi_svd(G, p, q, p, V, q, max_sweeps, &sh.flag);
+      sort_and_truncate(G, p, q, p, eps, sh);
+      r = sh.rank;
+    }
+    const int lim = q / 2;
+    if (r == 0) {
+      if (threadIdx.x == 0) { C.kind[t] = CLR_KIND_ZERO; C.rank[t] = 0; C.norm[t] = 0.0; }
+    } else if (dense_only || r > lim) {
+      if (src) {
+        for (int e = threadIdx.x; e < m * n; e += kThreads) {
+          const int i = e % m, j = e / m;
+          slot[e] = S[i * s_r + j * s_c];
+        }
+      }
+      if (threadIdx.x == 0) { C.kind[t] = CLR_KIND_DENSE; C.rank[t] = q; C.norm[t] = nrm; }
+    } else {
+      double* Xo = slot;
+      double* Wo = slot + (int64_t)m * r;
+      if (!tr) {
+        // G = U S (m x n), V (n x n):  X = (U S)_r, W = V_r
+        for (int e = threadIdx.x; e < m * r; e += kThreads) {
+          const int i = e % m, c = e / m;
+          Xo[e] = G[i + (int64_t)sh.perm[c] * p];
+        }
+        for (int e = threadIdx.x; e < n * r; e += kThreads) {
+          const int j = e % n, c = e / n;
+          Wo[e] = V[j + (int64_t)sh.perm[c] * q];
+        }
+      } else {
+        // G = S^T V' = U' S (n x m): block = V' S U'^T -> X = V'_r S_r, W = U'_r
+        for (int e = threadIdx.x; e < m * r; e += kThreads) {
+          const int i = e % m, c = e / m;
+          Xo[e] = V[i + (int64_t)sh.perm[c] * q] * sh.sorted[c];
+        }
+        for (int e = threadIdx.x; e < n * r; e += kThreads) {
+          const int j = e % n, c = e / n;
+          Wo[e] = G[j + (int64_t)sh.perm[c] * p] / sh.sorted[c];
+        }
+      }
+      if (threadIdx.x == 0) {
+        C.kind[t] = CLR_KIND_LR;
+        C.rank[t] = r;
+        C.norm[t] = sqrt(sh.kept_sq);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+void launch_compress_dense(const MatView& C, const int* list, const int* count,
+                           const double* src, int64_t lds, double* ws, double eps,
+                           double drop_norm, int dense_only, int max_sweeps, int grid,
+                           int* err, cudaStream_t st) {
+  compress_dense_kernel<<<grid, kThreads, 0, st>>>(C, list, count, src, lds, ws, eps,
+                                                   drop_norm, dense_only, max_sweeps, err);
+}
+
+// ---------------------------------------------------------------------------------------------
+// Block Frobenius norms: dense directly, low rank as sqrt(sum_ab (X^T X)_ab (W^T W)_ab).
+// ---------------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(kThreads) block_norms_kernel(MatView M) {
+  __shared__ double red[kWarps];
+  const int t = blockIdx.x;
+  const int I = t / M.nc, J = t % M.nc;
+  const int m = M.row_off[I + 1] - M.row_off[I];
+  const int n = M.col_off[J + 1] - M.col_off[J];
+  const int kind = M.kind[t];
+  const double* s = M.pool + slot_of(M, I, J, m);
+  double part = 0.0;
+  if (kind == CLR_KIND_DENSE) {
+    for (int e = threadIdx.x; e < m * n; e += kThreads) part = fma(s[e], s[e], part);
+  } else if (kind == CLR_KIND_LR) {
+    const int r = M.rank[t];
+    const double* X = s;
+    const double* W = s + (int64_t)m * r;
+    for (int e = threadIdx.x; e < r * r; e += kThreads) {
+      const int a = e % r, b = e / r;
+      double gx = 0.0, gw = 0.0;
+      for (int i = 0; i < m; ++i) gx = fma(X[i + (int64_t)a * m], X[i + (int64_t)b * m], gx);
+      for (int j = 0; j < n; ++j) gw = fma(W[j + (int64_t)a * n], W[j + (int64_t)b * n], gw);
+      part = fma(gx, gw, part);
+    }
+  }
+  const double tot = block_sum(part, red);
+  if (threadIdx.x == 0) M.norm[t] = kind == CLR_KIND_ZERO ? 0.0 : sqrt(fmax(tot, 0.0));
+}
+
+void launch_block_norms(const MatView& M, cudaStream_t st) {
+  block_norms_kernel<<<M.nr * M.nc, kThreads, 0, st>>>(M);
+}
+
+// alpha * M in place: dense values or the X factor, and the norms.
+__global__ void scale_blocks_kernel(MatView M, double alpha) {
+  const int t = blockIdx.x;
+  const int I = t / M.nc, J = t % M.nc;
+  const int m = M.row_off[I + 1] - M.row_off[I];
+  const int n = M.col_off[J + 1] - M.col_off[J];
+  const int kind = M.kind[t];
+  double* s = M.pool + slot_of(M, I, J, m);
+  int64_t len = kind == CLR_KIND_DENSE ? (int64_t)m * n
+              : kind == CLR_KIND_LR ? (int64_t)m * M.rank[t] : 0;
+  for (int64_t e = threadIdx.x; e < len; e += blockDim.x) s[e] *= alpha;
+  if (threadIdx.x == 0) M.norm[t] *= fabs(alpha);
+}
+
+void launch_scale_blocks(const MatView& M, double alpha, cudaStream_t st) {
+  scale_blocks_kernel<<<M.nr * M.nc, 256, 0, st>>>(M, alpha);
+}
+
+}  // namespace clr

@@ -1,0 +1,197 @@
+"""GPU parity of the CLR product (FP64 path) against the FP64 oracle, through the C ABI."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import clr_oracle as co
+from paper_1509_00309_gb300 import workloads as wl
+from tests import clr_pack
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1509_00309_gb300 import build, clr
+    build.build()
+    return clr.Context(0, precision="fp64", eps_lr=1e-8)
+
+
+def _check_product(ctx, a_or, b_or, eps, got, stats=None):
+    """Compare a GPU product with the oracle's: reconstruction within the truncation bound,
+    kinds equal (ranks within one of the oracle's at the threshold)."""
+    want = co.multiply(a_or, b_or, eps)
+    g = clr_pack.from_library(got)
+    da, db = a_or.to_dense(), b_or.to_dense()
+    ref = da @ db
+    err = np.linalg.norm(g.to_dense() - want.to_dense())
+    tol = co.product_tolerance(da, db, max(eps, 1e-12))
+    assert err <= tol, (err, tol)
+    # every low-rank tile is within eps of the exact tile sum (truncation bound)
+    gk, wk = g.kinds(), want.kinds()
+    gr, wr = g.ranks(), want.ranks()
+    for i in range(len(a_or.row_sizes)):
+        for j in range(len(b_or.col_sizes)):
+            if gk[i, j] != wk[i, j]:
+                # a kind may only differ at the dense/low-rank threshold
+                lim = co.dense_rank_limit(a_or.row_sizes[i], b_or.col_sizes[j])
+                assert {gk[i, j], wk[i, j]} <= {co.KIND_DENSE, co.KIND_LR}
+                assert max(gr[i, j], wr[i, j]) >= lim
+                continue
+            if gk[i, j] == co.KIND_LR:
+                assert abs(int(gr[i, j]) - int(wr[i, j])) <= 1
+                blk = ref[a_or.row_off[i]:a_or.row_off[i + 1], b_or.col_off[j]:b_or.col_off[j + 1]]
+                scale = np.abs(blk).sum() + 1.0
+                assert np.linalg.norm(g.block_dense(i, j) - blk) <= eps * (1 + 1e-6) + 1e-13 * scale
+    if stats is not None:
+        tl = co.triple_list(a_or, b_or)
+        kinds = np.bincount(tl.triples[:, 3], minlength=4) if len(tl.triples) else np.zeros(4)
+        assert stats["n_triples"] == [int(v) for v in kinds]
+        assert stats["flops"] == int(tl.flops.sum())
+        modes = np.bincount(tl.tile_mode.ravel(), minlength=3)
+        assert stats["n_tiles"] == [int(v) for v in modes]
+    return err
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_random_structures_all_kinds(ctx, seed):
+    rng = np.random.default_rng(1000 + seed)
+    nb = int(rng.integers(2, 5))
+    sizes = [int(s) for s in rng.integers(1, 40, size=nb)]
+    if seed == 0:
+        sizes = [1, 7, 33]
+    a = co.from_blocks(sizes, sizes, wl.random_blocks_spec(rng, sizes, sizes))
+    b = co.from_blocks(sizes, sizes, wl.random_blocks_spec(rng, sizes, sizes))
+    ga, gb = clr_pack.to_library(ctx, a), clr_pack.to_library(ctx, b)
+    gc = ctx.zeros(sizes, sizes)
+    stats = ctx.multiply_into(ga, gb, gc, stats=True)
+    _check_product(ctx, a, b, 1e-8, gc, stats)
+
+
+def test_rectangular_and_max_cluster(ctx):
+    rng = np.random.default_rng(7)
+    rs, ks, cs = [256, 5], [200, 256, 3], [17, 256]
+    a = co.from_blocks(rs, ks, wl.random_blocks_spec(rng, rs, ks, p_zero=0.1))
+    b = co.from_blocks(ks, cs, wl.random_blocks_spec(rng, ks, cs, p_zero=0.1))
+    gc = ctx.multiply(clr_pack.to_library(ctx, a), clr_pack.to_library(ctx, b))
+    _check_product(ctx, a, b, 1e-8, gc)
+
+
+def test_low_rank_sum_recompression_ranks(ctx):
+    # a tile fed only by low-rank products: ranks after recompression equal the oracle's
+    rng = np.random.default_rng(11)
+    sizes = [48, 40, 56]
+    spec = [[(2, (rng.standard_normal((m, 3)), rng.standard_normal((n, 3)))) for n in sizes]
+            for m in sizes]
+    a = co.from_blocks(sizes, sizes, spec)
+    gc = ctx.multiply(clr_pack.to_library(ctx, a), clr_pack.to_library(ctx, a))
+    g = clr_pack.from_library(gc)
+    want = co.multiply(a, a, 1e-8)
+    assert np.array_equal(g.kinds(), want.kinds())
+    assert np.array_equal(g.ranks(), want.ranks())
+    ref = a.to_dense() @ a.to_dense()
+    for i in range(3):
+        for j in range(3):
+            blk = ref[a.row_off[i]:a.row_off[i + 1], a.col_off[j]:a.col_off[j + 1]]
+            s_ref = np.linalg.svd(blk, compute_uv=False)
+            r = want.ranks()[i, j]
+            s_got = np.linalg.svd(g.block_dense(i, j), compute_uv=False)[:r]
+            assert np.allclose(s_got, s_ref[:r], rtol=1e-11, atol=1e-12 * s_ref[0])
+
+
+def test_all_zero_product(ctx):
+    sizes = [5, 9]
+    a = co.CLR(sizes, sizes)
+    gc = ctx.multiply(clr_pack.to_library(ctx, a), clr_pack.to_library(ctx, a))
+    k, r, n, _ = gc.get_blocks(pool=False)
+    assert not k.any() and not r.any() and not n.any()
+    assert not gc.to_dense().any()
+
+
+def test_from_dense_matches_oracle_build(ctx):
+    w = wl.chain_overlap(n=512, n_clusters=4, lo=96, hi=160)
+    m = ctx.from_dense(w.a, w.row_sizes, eps_lr=w.eps_lr, drop_norm=w.drop_norm)
+    want = co.build(w.a, w.row_sizes, w.col_sizes, w.eps_lr, w.drop_norm)
+    g = clr_pack.from_library(m)
+    assert np.array_equal(g.kinds(), want.kinds())
+    assert np.abs(g.ranks().astype(int) - want.ranks().astype(int)).max() <= 1
+    for (i, j) in want.blocks:
+        blk = w.a[want.row_off[i]:want.row_off[i + 1], want.col_off[j]:want.col_off[j + 1]]
+        assert np.linalg.norm(g.block_dense(i, j) - blk) <= w.eps_lr * (1 + 1e-6) + 1e-14
+    # device input path gives the same matrix
+    import torch
+    m2 = ctx.from_dense(torch.from_numpy(w.a).cuda(), w.row_sizes, eps_lr=w.eps_lr,
+                        drop_norm=w.drop_norm)
+    assert np.array_equal(m2.to_dense(), m.to_dense())
+
+
+def test_chain_overlap_product_full_size(ctx):
+    # the 1D-chain workload at its full size: N = 2048, 16 uneven clusters, eps = 1e-8
+    w = wl.chain_overlap()
+    s_or = co.build(w.a, w.row_sizes, w.col_sizes, w.eps_lr, w.drop_norm)
+    gs = clr_pack.to_library(ctx, s_or)
+    gc = ctx.zeros(w.row_sizes)
+    stats = ctx.multiply_into(gs, gs, gc, stats=True)
+    err = _check_product(ctx, s_or, s_or, w.eps_lr, gc, stats)
+    assert err <= co.product_tolerance(w.a, w.a, w.eps_lr)
+
+
+def test_all_dense_product_matches_gemm(ctx):
+    w = wl.dense_normal(n=1100, n_clusters=6)
+    ga = ctx.from_dense(w.a, w.row_sizes)
+    gb = ctx.from_dense(w.b, w.row_sizes)
+    gc = ctx.multiply(ga, gb)
+    ref = w.a @ w.b
+    got = gc.to_dense()
+    assert np.linalg.norm(got - ref) <= 1e-14 * np.linalg.norm(ref) * math.sqrt(1100)
+    k, _, _, _ = gc.get_blocks(pool=False)
+    assert (k == co.KIND_DENSE).all()
+
+
+def test_lincomb_matches_oracle(ctx):
+    rng = np.random.default_rng(21)
+    sizes = [30, 45, 20]
+    x = co.from_blocks(sizes, sizes, wl.random_blocks_spec(rng, sizes, sizes, max_rank=4))
+    y = co.from_blocks(sizes, sizes, wl.random_blocks_spec(rng, sizes, sizes, max_rank=4))
+    out = ctx.lincomb(-1.25, clr_pack.to_library(ctx, x), 0.375, clr_pack.to_library(ctx, y),
+                      1.875)
+    want = co.lincomb(-1.25, x, 0.375, y, 1.875, 1e-8)
+    g = clr_pack.from_library(out)
+    assert np.array_equal(g.kinds(), want.kinds())
+    assert np.linalg.norm(g.to_dense() - want.to_dense()) <= 1e-12 * np.linalg.norm(want.to_dense()) + 9e-8
+
+
+def test_transpose_and_matvec(ctx):
+    rng = np.random.default_rng(5)
+    rs, cs = [12, 30], [7, 25, 9]
+    a = co.from_blocks(rs, cs, wl.random_blocks_spec(rng, rs, cs))
+    ga = clr_pack.to_library(ctx, a)
+    at = ctx.transpose(ga)
+    assert np.array_equal(at.to_dense(), a.to_dense().T)
+    import torch
+    x = torch.randn(sum(cs), dtype=torch.float64, device="cuda")
+    y = torch.empty(sum(rs), dtype=torch.float64, device="cuda")
+    ctx.matvec(ga, x, y)
+    torch.cuda.synchronize()
+    assert np.allclose(y.cpu().numpy(), a.to_dense() @ x.cpu().numpy(), rtol=1e-13, atol=1e-12)
+
+
+def test_errors_are_reported(ctx):
+    from paper_1509_00309_gb300 import clr
+    a = ctx.zeros([4, 5], [3, 3])
+    b = ctx.zeros([4, 2], [3])
+    with pytest.raises(clr.ClrError) as e:
+        ctx.multiply(a, b)
+    assert e.value.status == clr.CLR_EINVAL
+    with pytest.raises(clr.ClrError) as e:
+        ctx.zeros([257])
+    assert e.value.status == clr.CLR_EINVAL
+    bad = np.ones((8, 8))
+    bad[3, 4] = np.nan
+    with pytest.raises(clr.ClrError) as e:
+        ctx.from_dense(bad, [8], eps_lr=1e-8)
+    assert e.value.status == clr.CLR_EINVAL
+    c = ctx.zeros([4, 5], [4, 5])
+    with pytest.raises(clr.ClrError):
+        ctx.multiply_into(c, c, c)
