@@ -53,7 +53,7 @@ struct clr_ctx_s {
   void* encode_fn = nullptr;  // cuTensorMapEncodeTiled
   // workspaces (grow-only)
   DevBuf plan_ints, triples, counters, ws, scratch, small, panels_a, panels_b, index_rows,
-      index_cols;
+      index_cols, tile_flags;
   PlanCounters last_counters;
 };
 
@@ -304,7 +304,7 @@ extern "C" int clr_destroy(clr_ctx_t ctx) {
   cudaSetDevice(ctx->device);
   for (DevBuf* b : {&ctx->plan_ints, &ctx->triples, &ctx->counters, &ctx->ws, &ctx->scratch,
                     &ctx->small, &ctx->panels_a, &ctx->panels_b, &ctx->index_rows,
-                    &ctx->index_cols})
+                    &ctx->index_cols, &ctx->tile_flags})
     b->release();
   delete ctx;
   return CLR_OK;
@@ -595,6 +595,7 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
   CLR_CUDA(ctx->panels_b.ensure((size_t)terms * N_pad * K_pad * 2));
   CLR_CUDA(ctx->index_rows.ensure((size_t)c->n_rows * sizeof(int)));
   CLR_CUDA(ctx->index_cols.ensure((size_t)c->n_cols * sizeof(int)));
+  CLR_CUDA(ctx->tile_flags.ensure((size_t)(M_pad / 128) * (N_pad / 256)));
   MatView av = a->view(), bv = b->view(), cv = c->view();
   launch_split_stage(av, ctx->panels_a.p, terms, M_pad, K_pad, 1, s);
   launch_split_stage(bv, ctx->panels_b.p, terms, N_pad, K_pad, 0, s);
@@ -614,6 +615,7 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
   g.K_pad = K_pad;
   g.row_tile_of = (const int*)ctx->index_rows.p;
   g.col_tile_of = (const int*)ctx->index_cols.p;
+  g.tile_active = (unsigned char*)ctx->tile_flags.p;
   g.n_sm = ctx->n_sm;
   g.err = &p.counters->err;
   g.encode_fn = ctx->encode_fn;

@@ -127,6 +127,7 @@ struct SplitGemmArgs {
   int64_t M_pad, N_pad, K_pad;
   const int* row_tile_of;  // n_rows: C block-row of each row
   const int* col_tile_of;  // n_cols
+  unsigned char* tile_active;  // (M_pad/128) * (N_pad/256) flags
   int n_sm;
   int* err;
   void* encode_fn;    // cuTensorMapEncodeTiled

@@ -1,0 +1,116 @@
+"""GPU parity of the split-precision (bf16 terms on tcgen05 tensor cores) dense x dense tile
+products against the oracle: the exact value of the split product (oracle/split_oracle.py,
+which isolates the FP32 accumulation), the FP64 product at the product tolerance
+10 eps ||A||_F ||B||_F, and sampled tiles at the full 16384 size."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import clr_oracle as co
+from oracle import split_oracle as so
+from paper_1509_00309_gb300 import workloads as wl
+from tests import clr_pack
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    from paper_1509_00309_gb300 import build, clr
+    build.build()
+    return clr.Context(0, precision="bf16x3", eps_lr=1e-8)
+
+
+@pytest.fixture(scope="module")
+def dense_case():
+    # ragged against the 128 x 256 GEMM tiles and the 32-wide k chunks
+    return wl.dense_normal(n=1100, n_clusters=6, lo=128, hi=224, seed=77)
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "bf16x6"])
+def test_split_matches_exact_split_product(ctx, dense_case, mode):
+    w = dense_case
+    ctx.set_opts(precision=mode)
+    ga, gb = ctx.from_dense(w.a, w.row_sizes), ctx.from_dense(w.b, w.row_sizes)
+    gc = ctx.zeros(w.row_sizes)
+    st = ctx.multiply_into(ga, gb, gc, stats=True)
+    assert st["precision"] == mode
+    got = gc.to_dense()
+    want = so.split_product(w.a, w.b, mode)
+    # only FP32 accumulation separates the two: far below the 2^-16 effect of a dropped
+    # bf16x6 term pair and the 2^-8 effect of a wrong bf16x3 pair
+    assert np.linalg.norm(got - want) <= 2.0 ** -18 * np.linalg.norm(want)
+
+
+def test_bf16x6_meets_product_tolerance(ctx, dense_case):
+    w = dense_case
+    ctx.set_opts(precision="bf16x6")
+    gc = ctx.multiply(ctx.from_dense(w.a, w.row_sizes), ctx.from_dense(w.b, w.row_sizes))
+    err = np.linalg.norm(gc.to_dense() - w.a @ w.b)
+    assert err <= co.product_tolerance(w.a, w.b, 1e-8)
+
+
+@pytest.mark.parametrize("mode,rel", [("bf16x3", 2.0 ** -16), ("bf16x6", 2.0 ** -23)])
+def test_product_with_identity_returns_split_of_a(ctx, mode, rel):
+    # A I = A up to the split's truncation: |C - A| <= 2^-16 |A| (bf16x3), 2^-24-ish (bf16x6)
+    rng = np.random.default_rng(3)
+    sizes = [200, 56, 256, 17]
+    n = sum(sizes)
+    a = rng.standard_normal((n, n)) * np.exp(rng.uniform(-3, 3, (n, n)))
+    ctx.set_opts(precision=mode)
+    ga = ctx.from_dense(a, sizes)
+    gi = ctx.from_dense(np.eye(n), sizes)
+    got = ctx.multiply(ga, gi).to_dense()
+    assert np.all(np.abs(got - a) <= rel * np.abs(a) + 1e-300)
+
+
+def test_split_inside_mixed_clr_product(ctx):
+    # chain overlap: dense x dense products on the tensor cores, low-rank products in FP64
+    w = wl.chain_overlap()
+    s_or = co.build(w.a, w.row_sizes, w.col_sizes, w.eps_lr, w.drop_norm)
+    ctx.set_opts(precision="bf16x6")
+    gs = clr_pack.to_library(ctx, s_or)
+    gc = ctx.zeros(w.row_sizes)
+    st = ctx.multiply_into(gs, gs, gc, stats=True)
+    tl = co.triple_list(s_or, s_or)
+    assert st["n_triples"] == [int(v) for v in np.bincount(tl.triples[:, 3], minlength=4)]
+    want = co.multiply(s_or, s_or, w.eps_lr)
+    g = clr_pack.from_library(gc)
+    assert np.array_equal(g.kinds(), want.kinds())
+    err = np.linalg.norm(g.to_dense() - want.to_dense())
+    assert err <= co.product_tolerance(w.a, w.a, w.eps_lr)
+
+
+def test_full_size_sampled_tiles(ctx):
+    # the all-dense workload at full size (N = 16384, 96 uneven clusters, bf16x3), in the
+    # launch configuration the benchmark times; sampled C tiles against FP64 dot products
+    import torch
+    w = wl.dense_normal()
+    ctx.set_opts(precision="bf16x3")
+    ga = ctx.from_dense(w.a, w.row_sizes)
+    gb = ctx.from_dense(w.b, w.row_sizes)
+    gc = ctx.zeros(w.row_sizes)
+    ctx.multiply_into(ga, gb, gc)
+    out = torch.empty((w.n, w.n), dtype=torch.float64, device="cuda")
+    gc.to_dense(out)
+    torch.cuda.synchronize()
+    off = np.concatenate([[0], np.cumsum(w.row_sizes)])
+    rng = np.random.default_rng(5)
+    num, den, ab = 0.0, 0.0, 0.0
+    for _ in range(6):
+        i, j = rng.integers(0, 96, 2)
+        r0, r1, c0, c1 = off[i], off[i + 1], off[j], off[j + 1]
+        want = w.a[r0:r1] @ w.b[:, c0:c1]
+        got = out[r0:r1, c0:c1].cpu().numpy()
+        num += float(np.sum((got - want) ** 2))
+        den += float(np.sum(want ** 2))
+        ab += float(np.sum(np.linalg.norm(w.a[r0:r1], axis=1)[:, None] ** 2 *
+                           np.linalg.norm(w.b[:, c0:c1], axis=0)[None, :] ** 2))
+    # per-sample form of ||dC||_F <= 10 eps ||A||_F ||B||_F with eps = 1e-8:
+    # sum over sampled entries of dC^2 <= (10 eps)^2 * sum ||a_i||^2 ||b_j||^2
+    assert num <= (10 * 1e-8) ** 2 * ab
+    assert math.sqrt(num / den) < 3e-5
+    # the whole matrix: every block is dense
+    k, _, _, _ = gc.get_blocks(pool=False)
+    assert (k == co.KIND_DENSE).all()
