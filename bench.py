@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Benchmark of the CLR product (Calvin, Lewis & Valeev, Section 4.1) on one GB300.
+
+Workload: the all-dense CLR product C = A B with N = 16384 split into 96 uneven clusters
+(sizes U[128, 224] rescaled), A and B i.i.d. N(0,1) FP64 -- every block is dense, so the
+product is ordinary dense matrix multiplication (the eps -> 0 limit, Section 4.3), computed in
+split-precision bf16x3 on the tensor cores with FP32 accumulation in short segments and an
+FP64 epilogue.  A step is one whole CLR product through the library (triple list, staging of
+the bf16 term panels, the dense tile products, low-rank/recompression passes, norms).
+
+Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead, on a
+bounded sample of the same workload.  Multi-GPU runs (torchrun) are independent replicas:
+each rank multiplies its own matrices, nothing is exchanged between ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "CLR multiply TFLOP/s and ms per Newton–Schulz S^-1/2 iteration at stated error"
+
+# DRAM bytes (read + write) of one launch of the dense tile-product kernel, from one ncu capture
+# (profiles/split_gemm_dense16384_bf16x3.md), keyed by the kernel source's hash so the number
+# is dropped (traffic: null) as soon as the kernel changes.
+MEASURED_TRAFFIC = {
+    "54fe88e1c983:bf16x3:16384:96": 17250053120 + 4155058432,
+}
+PAIRS = {"bf16x3": 3, "bf16x6": 6}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16x3", choices=["bf16x3", "bf16x6", "fp64"])
+    ap.add_argument("--n", type=int, default=16384)
+    ap.add_argument("--clusters", type=int, default=96)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def workload(args, rank=0):
+    from paper_1509_00309_gb300 import workloads as wl
+    return wl.dense_normal(n=args.n, n_clusters=args.clusters, lo=128, hi=224,
+                           seed=wl.default_seed(1) + 1000 * rank)
+
+
+def config(args, extra=None):
+    c = {"workload": "all-dense CLR product N=%d, %d uneven clusters U[128,224], "
+                     "A,B ~ N(0,1) FP64" % (args.n, args.clusters),
+         "n": args.n, "clusters": args.clusters, "precision": args.prec,
+         "l2": "inputs larger than L2 (A, B 2.1 GB FP64 each + bf16 term panels); no flush",
+         "parallelism": "replicas"}
+    if extra:
+        c.update(extra)
+    return c
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return p, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, \
+            "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: str):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", self.gpu, "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(name)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_init(args):
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        local = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+        return dist.get_rank(), ws, local
+    return 0, 1, 0
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, ws):
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle sample (the cpu_baseline leg and the reference arm)
+# ------------------------------------------------------------------------------------------
+
+def oracle_sample(w, seconds: float):
+    """Time the FP64 oracle's CLR product on whole block rows of C (all of K and all column
+    clusters) until about ``seconds`` have elapsed.  Returns (flops, elapsed, rows_done)."""
+    import numpy as np
+
+    from oracle import clr_oracle as co
+    rs = w.row_sizes
+    off = np.concatenate([[0], np.cumsum(rs)])
+    spec_b = [[(co.KIND_DENSE, w.b[off[k]:off[k + 1], off[j]:off[j + 1]])
+               for j in range(len(rs))] for k in range(len(rs))]
+    b = co.from_blocks(rs, rs, spec_b)
+    flops, elapsed, rows = 0, 0.0, 0
+    while elapsed < seconds and rows < len(rs):
+        i = rows
+        spec_a = [[(co.KIND_DENSE, w.a[off[i]:off[i + 1], off[k]:off[k + 1]])
+                   for k in range(len(rs))]]
+        a = co.from_blocks([rs[i]], rs, spec_a)
+        t0 = time.perf_counter()
+        co.multiply(a, b, 0.0)
+        elapsed += time.perf_counter() - t0
+        flops += 2 * rs[i] * w.n * w.n
+        rows += 1
+    return flops, elapsed, rows
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args)
+    # each step a bounded oracle sample: the whole run stays within about a minute or two
+    per_step = max(2.0, 60.0 / max(1, args.steps))
+    for _ in range(args.warmup):
+        oracle_sample(w, 1.0)
+    fl, el = 0, 0.0
+    rows = 0
+    for _ in range(args.steps):
+        f, e, r = oracle_sample(w, per_step)
+        fl += f
+        el += e
+        rows += r
+    value = fl / el / 1e12
+    cores = os.cpu_count()
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+           "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": config(args, {"precision": "fp64 (CPU oracle)"}),
+           "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores,
+                            "kind": "oracle",
+                            "sample": "%d block rows of C (each: all 96 column clusters x all "
+                                      "96 inner clusters) per %d steps" % (rows, args.steps)},
+           "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ------------------------------------------------------------------------------------------
+# Our arm
+# ------------------------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    from paper_1509_00309_gb300 import build, clr
+    rank, ws, local = dist_init(args)
+    if ws == 1:
+        torch.cuda.set_device(0)
+    build.build()
+    ctx = clr.Context(torch.cuda.current_device(), precision=args.prec, eps_lr=1e-8)
+    w = workload(args, rank)
+    n = w.n
+    stream = torch.cuda.current_stream()
+    a_d = torch.from_numpy(w.a).cuda()
+    b_d = torch.from_numpy(w.b).cuda()
+    ga = ctx.from_dense(a_d, w.row_sizes)
+    gb = ctx.from_dense(b_d, w.row_sizes)
+    del a_d, b_d
+    gc = ctx.zeros(w.row_sizes)
+    stats = ctx.multiply_into(ga, gb, gc, stats=True)
+    alg_flops = float(stats["flops"])
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[0] \
+        if ws == 1 else str(local)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(gpu_index) as clk:
+        for _ in range(args.warmup):
+            ctx.multiply_into(ga, gb, gc)
+        torch.cuda.synchronize()
+        barrier(ws)
+        clk.lines.clear()
+        ctx.profile_enable(True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            ctx.multiply_into(ga, gb, gc)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier(ws)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    ms_total = max_over_ranks(e0.elapsed_time(e1), ws)
+    ms_step = ms_total / args.steps
+    value = alg_flops * ws * args.steps / (ms_total * 1e-3) / 1e12
+
+    # accuracy of this run's result on sampled tiles vs FP64 dot products
+    err = None
+    if rank == 0:
+        out = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        gc.to_dense(out)
+        torch.cuda.synchronize()
+        off = np.concatenate([[0], np.cumsum(w.row_sizes)])
+        rng = np.random.default_rng(5)
+        num = den = ab = 0.0
+        for _ in range(4):
+            i, j = rng.integers(0, len(w.row_sizes), 2)
+            r0, r1, c0, c1 = off[i], off[i + 1], off[j], off[j + 1]
+            want = w.a[r0:r1] @ w.b[:, c0:c1]
+            got = out[r0:r1, c0:c1].cpu().numpy()
+            num += float(np.sum((got - want) ** 2))
+            den += float(np.sum(want ** 2))
+            ab += float(np.sum(np.linalg.norm(w.a[r0:r1], axis=1)[:, None] ** 2 *
+                               np.linalg.norm(w.b[:, c0:c1], axis=0)[None, :] ** 2))
+        del out
+        err = {"rel_frob_sampled": math.sqrt(num / den),
+               "frob_over_normA_normB_sampled": math.sqrt(num / ab),
+               "bound_10eps_eps1e-8": 1e-7}
+
+    # roofline of the dominant kernel (the split dense tile-product kernel)
+    peaks, src = load_peaks()
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1509_00309_gb300", "csrc", "k_split_gemm.cu"), "rb") as f:
+        ksha = hashlib.sha256(f.read()).hexdigest()[:12]
+    traffic = MEASURED_TRAFFIC.get("%s:%s:%d:%d" % (ksha, args.prec, args.n, args.clusters))
+    gemm_ms = prof["ms_dense"] / max(1, prof["dense_launches"])
+    if args.prec in PAIRS:
+        pairs = PAIRS[args.prec]
+        achieved = alg_flops / (gemm_ms * 1e-3) / 1e12
+        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) / pairs
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": traffic,
+                # bf16 term panels of A and B read once, FP64 C written once
+                "algorithmic_bytes": (2 if pairs == 3 else 3) * 2 * (2 * n * n) + 8 * n * n,
+                "kernel": "split_gemm_kernel<%d>" % (2 if pairs == 3 else 3),
+                "kernel_ms": gemm_ms,
+                "peak_basis": "%s sustained bf16 %.1f TFLOP/s / %d term-pair products" % (
+                    src, peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]), pairs),
+                "tensor_tflops_issued": prof["dense_tensor_flops"] / max(1, prof["dense_launches"])
+                / (gemm_ms * 1e-3) / 1e12}
+    else:
+        roof = {"bound": "alu", "achieved": alg_flops / (gemm_ms * 1e-3) / 1e12,
+                "peak": None, "unit": "TFLOP/s", "frac": None, "traffic": None,
+                "kernel": "dd_fp64_kernel", "kernel_ms": gemm_ms}
+    phases = {k: prof[k] / args.steps for k in ("ms_plan", "ms_stage", "ms_dense",
+                                                "ms_lowrank", "ms_compress", "ms_finalize")}
+
+    # end to end through the C ABI with host buffers (pinned), copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        a_h = torch.from_numpy(w.a).pin_memory()
+        b_h = torch.from_numpy(w.b).pin_memory()
+        c_h = torch.empty((n, n), dtype=torch.float64).pin_memory()
+        e2e_steps = max(1, min(args.steps, 3))
+        torch.cuda.synchronize()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ha = ctx.from_dense(a_h, w.row_sizes)
+            hb = ctx.from_dense(b_h, w.row_sizes)
+            hc = ctx.multiply(ha, hb)
+            hc.to_dense(c_h)
+            ha.close()
+            hb.close()
+            hc.close()
+        torch.cuda.synchronize()
+        el = max_over_ranks(time.perf_counter() - t0, ws)
+        e2e = {"value": alg_flops * ws * e2e_steps / el / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8,
+               "ms_per_step": 1e3 * el / e2e_steps}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu:
+        fl, el, rows = oracle_sample(w, 15.0)
+        cpu = {"value": fl / el / 1e12, "unit": "TFLOP/s", "cores": os.cpu_count(),
+               "kind": "oracle",
+               "sample": "%d block rows of C (all 96 column clusters x all 96 inner clusters, "
+                         "%.1f GFLOP) of the same workload" % (rows, fl / 1e9)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": args.prec, "data": "synthetic",
+                "config": config(args, {"error": err, "phases_ms_per_step": phases,
+                                        "algorithmic_flops_per_step": alg_flops}),
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "gpu_launches": int(prof["launches"]), "clocks": clk.summary()}
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

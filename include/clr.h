@@ -209,6 +209,26 @@ int clr_sqrt_inv_backward(clr_ctx_t ctx, clr_tape_t tape, clr_mat_t zbar, clr_ma
                           void* stream);
 int clr_tape_free(clr_ctx_t ctx, clr_tape_t tape);
 
+/* ---- observability ------------------------------------------------------------------------
+ * With profiling on, every product records CUDA events on its stream at its phase boundaries
+ * and counts the kernels it launches.  clr_profile_read synchronises the device, converts the
+ * events to per-phase device times (ms, summed over products) and returns the totals;
+ * clr_profile_enable(ctx, 1) resets them. */
+typedef struct clr_profile {
+  int64_t products;            /* products recorded */
+  int64_t launches;            /* kernels launched by those products */
+  int64_t dense_launches;      /* launches of the dense x dense kernel */
+  double dense_tensor_flops;   /* tensor-core flops issued by the split dense kernel */
+  double ms_plan;              /* triple list: screen, count, scan, fill */
+  double ms_stage;             /* split-precision staging of operand panels */
+  double ms_dense;             /* dense x dense tile products */
+  double ms_lowrank;           /* low-rank tile products and accumulation */
+  double ms_compress;          /* recompression (QR + SVD) */
+  double ms_finalize;          /* norms and scaling */
+} clr_profile;
+int clr_profile_enable(clr_ctx_t ctx, int on);
+int clr_profile_read(clr_ctx_t ctx, clr_profile* out);
+
 /* y = A x for dense device vectors (x: n_cols, y: n_rows). */
 int clr_matvec(clr_ctx_t ctx, clr_mat_t a, const double* x, double* y, void* stream);
 

@@ -52,6 +52,14 @@ class ClrNsStats(C.Structure):
                 ("precision_used", C.c_int32 * NS_MAX_HISTORY), ("ms_total", C.c_double)]
 
 
+class ClrProfile(C.Structure):
+    _fields_ = [("products", C.c_int64), ("launches", C.c_int64),
+                ("dense_launches", C.c_int64), ("dense_tensor_flops", C.c_double),
+                ("ms_plan", C.c_double), ("ms_stage", C.c_double), ("ms_dense", C.c_double),
+                ("ms_lowrank", C.c_double), ("ms_compress", C.c_double),
+                ("ms_finalize", C.c_double)]
+
+
 _VP = C.c_void_p
 _SIGNATURES = {
     "clr_strerror": (C.c_char_p, [C.c_int]),
@@ -85,6 +93,8 @@ _SIGNATURES = {
     "clr_sqrt_inv_backward": (C.c_int, [_VP, _VP, _VP, C.POINTER(_VP), _VP]),
     "clr_tape_free": (C.c_int, [_VP, _VP]),
     "clr_matvec": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "clr_profile_enable": (C.c_int, [_VP, C.c_int]),
+    "clr_profile_read": (C.c_int, [_VP, C.POINTER(ClrProfile)]),
 }
 
 _LIB: Optional[C.CDLL] = None
@@ -180,8 +190,10 @@ class Matrix:
             self.ctx._check(load().clr_mat_to_dense(self.ctx.handle, self.handle, _ptr(host), m,
                                                     1, _stream(stream)))
             return host
-        self.ctx._check(load().clr_mat_to_dense(self.ctx.handle, self.handle, _ptr(out),
-                                                out.stride(0), 0, _stream(stream)))
+        on_host = isinstance(out, np.ndarray) or not out.is_cuda
+        ld = out.shape[1] if isinstance(out, np.ndarray) else out.stride(0)
+        self.ctx._check(load().clr_mat_to_dense(self.ctx.handle, self.handle, _ptr(out), ld,
+                                                int(on_host), _stream(stream)))
         return out
 
     def get_blocks(self, pool: bool = True, stream=None):
@@ -252,6 +264,15 @@ class Context:
             setattr(o, k, v)
         self._check(load().clr_set_opts(self.handle, C.byref(o)))
 
+    # observability -----------------------------------------------------------------------
+    def profile_enable(self, on: bool = True):
+        self._check(load().clr_profile_enable(self.handle, int(on)))
+
+    def profile_read(self) -> Dict:
+        p = ClrProfile()
+        self._check(load().clr_profile_read(self.handle, C.byref(p)))
+        return {f: getattr(p, f) for f, _ in ClrProfile._fields_}
+
     # matrices ------------------------------------------------------------------------------
     def zeros(self, row_sizes, col_sizes=None) -> Matrix:
         col_sizes = row_sizes if col_sizes is None else col_sizes
@@ -263,13 +284,18 @@ class Context:
 
     def from_dense(self, a, row_sizes, col_sizes=None, eps_lr: float = 0.0,
                    drop_norm: float = 0.0, stream=None) -> Matrix:
-        """``a``: row-major float64 torch CUDA tensor (device path) or numpy array (host)."""
+        """``a``: row-major float64 torch CUDA tensor (device path), or a numpy array / torch
+        CPU tensor (host path; pinned memory makes the upload fast)."""
         col_sizes = row_sizes if col_sizes is None else col_sizes
         rs, cs = _i32(row_sizes), _i32(col_sizes)
-        on_host = isinstance(a, np.ndarray)
-        if on_host:
+        on_host = isinstance(a, np.ndarray) or (hasattr(a, "is_cuda") and not a.is_cuda)
+        if isinstance(a, np.ndarray):
             a = np.ascontiguousarray(a, dtype=np.float64)
             lda = a.shape[1]
+        elif on_host:
+            if a.dtype != __import__("torch").float64 or a.stride(1) != 1:
+                raise ValueError("host tensor input must be row-major float64")
+            lda = a.stride(0)
         else:
             if a.dtype != __import__("torch").float64 or not a.is_cuda or a.stride(1) != 1:
                 raise ValueError("device input must be a row-major float64 CUDA tensor")

@@ -53,8 +53,13 @@ struct clr_ctx_s {
   void* encode_fn = nullptr;  // cuTensorMapEncodeTiled
   // workspaces (grow-only)
   DevBuf plan_ints, triples, counters, ws, scratch, small, panels_a, panels_b, index_rows,
-      index_cols, tile_flags;
+      index_cols, index_k, tile_flags, upload;
   PlanCounters last_counters;
+  // profiling: per-product phase events
+  bool prof_on = false;
+  std::vector<std::pair<cudaEvent_t, int>> prof_events;  // (event, phase that ENDS here)
+  std::vector<cudaEvent_t> event_pool;
+  clr_profile prof;
 };
 
 struct clr_mat_s {
@@ -64,6 +69,8 @@ struct clr_mat_s {
   std::vector<int> row_sizes, col_sizes, row_off, col_off;
   int* d_row_off = nullptr;
   int* d_col_off = nullptr;
+  int* d_row_idx = nullptr;  // cluster of every row
+  int* d_col_idx = nullptr;  // cluster of every column
   int* d_kind = nullptr;
   int* d_rank = nullptr;
   double* d_norm = nullptr;
@@ -130,6 +137,8 @@ void free_mat(clr_mat_t m) {
   if (!m) return;
   cudaFree(m->d_row_off);
   cudaFree(m->d_col_off);
+  cudaFree(m->d_row_idx);
+  cudaFree(m->d_col_idx);
   cudaFree(m->d_kind);
   cudaFree(m->d_rank);
   cudaFree(m->d_norm);
@@ -163,6 +172,8 @@ int alloc_mat(clr_ctx_t ctx, int nr, const int32_t* rs, int nc, const int32_t* c
   };
   A((void**)&m->d_row_off, (nr + 1) * sizeof(int));
   A((void**)&m->d_col_off, (nc + 1) * sizeof(int));
+  A((void**)&m->d_row_idx, (size_t)m->n_rows * sizeof(int));
+  A((void**)&m->d_col_idx, (size_t)m->n_cols * sizeof(int));
   A((void**)&m->d_kind, nb * sizeof(int));
   A((void**)&m->d_rank, nb * sizeof(int));
   A((void**)&m->d_norm, nb * sizeof(double));
@@ -173,6 +184,16 @@ int alloc_mat(clr_ctx_t ctx, int nr, const int32_t* rs, int nc, const int32_t* c
   if (e == cudaSuccess)
     e = cudaMemcpy(m->d_col_off, m->col_off.data(), (nc + 1) * sizeof(int),
                    cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    std::vector<int> ri(m->n_rows), ci(m->n_cols);
+    for (int i = 0; i < nr; ++i)
+      for (int r = m->row_off[i]; r < m->row_off[i + 1]; ++r) ri[r] = i;
+    for (int j = 0; j < nc; ++j)
+      for (int c = m->col_off[j]; c < m->col_off[j + 1]; ++c) ci[c] = j;
+    e = cudaMemcpy(m->d_row_idx, ri.data(), ri.size() * sizeof(int), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess)
+      e = cudaMemcpy(m->d_col_idx, ci.data(), ci.size() * sizeof(int), cudaMemcpyHostToDevice);
+  }
   if (e == cudaSuccess) e = cudaMemset(m->d_kind, 0, nb * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(m->d_rank, 0, nb * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(m->d_norm, 0, nb * sizeof(double));
@@ -212,6 +233,25 @@ int make_plan(clr_ctx_t ctx, int nI, int nJ, int nK, Plan* p) {
 }
 
 int grid_of(clr_ctx_t ctx, int per_sm) { return std::max(1, ctx->n_sm * per_sm); }
+
+enum { PH_START = -1, PH_PLAN = 0, PH_STAGE, PH_DENSE, PH_LOWRANK, PH_COMPRESS, PH_FINALIZE };
+
+void prof_mark(clr_ctx_t ctx, cudaStream_t s, int phase) {
+  if (!ctx->prof_on) return;
+  cudaEvent_t e;
+  if (!ctx->event_pool.empty()) {
+    e = ctx->event_pool.back();
+    ctx->event_pool.pop_back();
+  } else if (cudaEventCreate(&e) != cudaSuccess) {
+    return;
+  }
+  cudaEventRecord(e, s);
+  ctx->prof_events.push_back({e, phase});
+}
+
+void prof_launches(clr_ctx_t ctx, int n) {
+  if (ctx->prof_on) ctx->prof.launches += n;
+}
 
 constexpr int64_t kScratchPerCta =
     (int64_t)(CLR_MAX_CLUSTER / 2) * (CLR_MAX_CLUSTER / 2) +
@@ -302,9 +342,11 @@ extern "C" int clr_create(clr_ctx_t* out, int device, const clr_opts* opts) {
 extern "C" int clr_destroy(clr_ctx_t ctx) {
   if (!ctx) return CLR_EINVAL;
   cudaSetDevice(ctx->device);
+  for (auto& pe : ctx->prof_events) cudaEventDestroy(pe.first);
+  for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   for (DevBuf* b : {&ctx->plan_ints, &ctx->triples, &ctx->counters, &ctx->ws, &ctx->scratch,
                     &ctx->small, &ctx->panels_a, &ctx->panels_b, &ctx->index_rows,
-                    &ctx->index_cols, &ctx->tile_flags})
+                    &ctx->index_cols, &ctx->index_k, &ctx->tile_flags, &ctx->upload})
     b->release();
   delete ctx;
   return CLR_OK;
@@ -368,7 +410,7 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
   }
   cudaStream_t s = as_stream(stream);
   const double* src = a;
-  DevBuf staging;
+  DevBuf& staging = ctx->upload;
   if (a_on_host) {
     const size_t bytes = (size_t)m->n_rows * m->n_cols * sizeof(double);
     cudaError_t e = staging.ensure(bytes);
@@ -377,7 +419,6 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
                             m->n_cols * sizeof(double), m->n_rows, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
       free_mat(m);
-      staging.release();
       return cuda_fail(ctx, e, "from_dense upload");
     }
     src = (const double*)staging.p;
@@ -387,19 +428,24 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
   if (e == cudaSuccess) e = ctx->counters.ensure(sizeof(PlanCounters));
   if (e != cudaSuccess) {
     free_mat(m);
-    staging.release();
     return cuda_fail(ctx, e, "from_dense workspace");
   }
   PlanCounters* pc = (PlanCounters*)ctx->counters.p;
   cudaMemsetAsync(pc, 0, sizeof(PlanCounters), s);
-  launch_compress_dense(m->view(), nullptr, nullptr, src, lda, (double*)ctx->ws.p, eps_lr,
-                        drop_norm, eps_lr == 0.0 ? 1 : 0, ctx->opts.jacobi_max_sweeps,
-                        grid_of(ctx, 2), &pc->err, s);
+  if (eps_lr == 0.0) {
+    // every kept block is dense: a coalesced layout copy, then norms decide what is dropped
+    launch_rowmajor_to_pool(m->view(), m->d_row_idx, src, lda, s);
+    launch_block_norms_dense(m->view(), s);
+    launch_dense_kinds(m->view(), drop_norm, &pc->err, s);
+  } else {
+    launch_compress_dense(m->view(), nullptr, nullptr, src, lda, (double*)ctx->ws.p, eps_lr,
+                          drop_norm, 0, ctx->opts.jacobi_max_sweeps, grid_of(ctx, 2), &pc->err,
+                          s);
+  }
   e = cudaGetLastError();
   int errflag = 0;
   if (e == cudaSuccess) e = cudaMemcpyAsync(&errflag, &pc->err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  staging.release();
   if (e != cudaSuccess) {
     free_mat(m);
     return cuda_fail(ctx, e, "from_dense");
@@ -466,22 +512,21 @@ extern "C" int clr_mat_to_dense(clr_ctx_t ctx, clr_mat_t m, double* out, int64_t
   cudaSetDevice(ctx->device);
   cudaStream_t s = as_stream(stream);
   if (!out_on_host) {
-    launch_to_dense(m->view(), out, ldo, s);
+    launch_pool_to_rowmajor(m->view(), m->d_row_idx, m->d_col_idx, out, ldo, s);
     CLR_CHECK_LAUNCH("to_dense");
     return CLR_OK;
   }
-  DevBuf tmp;
+  DevBuf& tmp = ctx->upload;
   const size_t bytes = (size_t)m->n_rows * m->n_cols * sizeof(double);
   cudaError_t e = tmp.ensure(bytes);
   if (e == cudaSuccess) {
-    launch_to_dense(m->view(), (double*)tmp.p, m->n_cols, s);
+    launch_pool_to_rowmajor(m->view(), m->d_row_idx, m->d_col_idx, (double*)tmp.p, m->n_cols, s);
     e = cudaGetLastError();
   }
   if (e == cudaSuccess)
     e = cudaMemcpy2DAsync(out, ldo * sizeof(double), tmp.p, m->n_cols * sizeof(double),
                           m->n_cols * sizeof(double), m->n_rows, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  tmp.release();
   if (e != cudaSuccess) return cuda_fail(ctx, e, "to_dense");
   return CLR_OK;
 }
@@ -590,18 +635,22 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
   const int terms = prec == CLR_PREC_BF16X3 ? 2 : 3;
   const int64_t M_pad = (c->n_rows + 127) / 128 * 128;
   const int64_t N_pad = (c->n_cols + 255) / 256 * 256;
-  const int64_t K_pad = (a->n_cols + 63) / 64 * 64;
+  const int64_t K_pad = (a->n_cols + 127) / 128 * 128;  // staging tiles are 128 wide
   CLR_CUDA(ctx->panels_a.ensure((size_t)terms * M_pad * K_pad * 2));
   CLR_CUDA(ctx->panels_b.ensure((size_t)terms * N_pad * K_pad * 2));
   CLR_CUDA(ctx->index_rows.ensure((size_t)c->n_rows * sizeof(int)));
   CLR_CUDA(ctx->index_cols.ensure((size_t)c->n_cols * sizeof(int)));
+  CLR_CUDA(ctx->index_k.ensure((size_t)a->n_cols * sizeof(int)));
   CLR_CUDA(ctx->tile_flags.ensure((size_t)(M_pad / 128) * (N_pad / 256)));
   MatView av = a->view(), bv = b->view(), cv = c->view();
-  launch_split_stage(av, ctx->panels_a.p, terms, M_pad, K_pad, 1, s);
-  launch_split_stage(bv, ctx->panels_b.p, terms, N_pad, K_pad, 0, s);
-  launch_cluster_index(c->d_row_off, c->nr, (int*)ctx->index_rows.p, c->n_rows, s);
-  launch_cluster_index(c->d_col_off, c->nc, (int*)ctx->index_cols.p, c->n_cols, s);
+  const int* idx_m = c->d_row_idx;
+  const int* idx_n = c->d_col_idx;
+  const int* idx_k = a->d_col_idx;
+  launch_split_stage(av, idx_m, idx_k, ctx->panels_a.p, terms, M_pad, K_pad, 1, s);
+  launch_split_stage(bv, idx_k, idx_n, ctx->panels_b.p, terms, N_pad, K_pad, 0, s);
   CLR_CHECK_LAUNCH("split staging");
+  prof_launches(ctx, 2);
+  prof_mark(ctx, s, PH_STAGE);
   SplitGemmArgs g;
   g.A = &av;
   g.B = &bv;
@@ -613,8 +662,8 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
   g.M_pad = M_pad;
   g.N_pad = N_pad;
   g.K_pad = K_pad;
-  g.row_tile_of = (const int*)ctx->index_rows.p;
-  g.col_tile_of = (const int*)ctx->index_cols.p;
+  g.row_tile_of = idx_m;
+  g.col_tile_of = idx_n;
   g.tile_active = (unsigned char*)ctx->tile_flags.p;
   g.n_sm = ctx->n_sm;
   g.err = &p.counters->err;
@@ -623,6 +672,16 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
   int st = split_gemm_dd(g, s, &why);
   if (st) return fail(ctx, st, "split GEMM: " + why);
   CLR_CHECK_LAUNCH("split GEMM");
+  prof_launches(ctx, 2);  // tile flags + GEMM
+  if (ctx->prof_on) {
+    ctx->prof.dense_launches++;
+    // tensor flops issued: every active 128 x 256 tile runs the full K for each term pair;
+    // counted exactly for all-dense operands, an upper bound otherwise
+    const double pairs = terms == 2 ? 3.0 : 6.0;
+    ctx->prof.dense_tensor_flops += 2.0 * pairs * (double)c->n_rows * (double)c->n_cols *
+                                    (double)K_pad;
+  }
+  prof_mark(ctx, s, PH_DENSE);
   return CLR_OK;
 }
 
@@ -642,12 +701,18 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   CLR_CUDA(ctx->scratch.ensure((size_t)lr_grid * kScratchPerCta * sizeof(double)));
   MatView av = a->view(), bv = b->view(), cv = c->view();
   const clr_opts& o = ctx->opts;
+  prof_mark(ctx, s, PH_START);
   launch_plan(av, bv, p, o.eps_sp, o.recompress_dense, s);
   launch_set_route_kinds(cv, p, s);
   CLR_CHECK_LAUNCH("plan");
+  prof_launches(ctx, 4);
+  prof_mark(ctx, s, PH_PLAN);
   if (prec == CLR_PREC_FP64) {
     launch_dd_fp64(av, bv, cv, p, grid_of(ctx, 4), s);
     CLR_CHECK_LAUNCH("dense x dense (FP64)");
+    prof_launches(ctx, 1);
+    if (ctx->prof_on) ctx->prof.dense_launches++;
+    prof_mark(ctx, s, PH_DENSE);
   } else {
     st = run_split_dd(ctx, a, b, c, p, prec, s);
     if (st) return st;
@@ -655,17 +720,27 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   launch_lr_products(av, bv, cv, p, (double*)ctx->ws.p, (double*)ctx->scratch.p,
                      kScratchPerCta, lr_grid, s);
   CLR_CHECK_LAUNCH("low-rank products");
+  prof_launches(ctx, 1);
+  prof_mark(ctx, s, PH_LOWRANK);
   launch_compress_qr(cv, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->ws.p, o.eps_lr,
                      o.jacobi_max_sweeps, grid_of(ctx, 2), &p.counters->err, s);
   launch_compress_dense(cv, p.l_dcomp, &p.counters->n_dcomp, nullptr, 0, (double*)ctx->ws.p,
                         o.eps_lr, 0.0, 0, o.jacobi_max_sweeps, grid_of(ctx, 2),
                         &p.counters->err, s);
-  if (!o.recompress_dense) launch_dense_tile_norms(cv, p, s);
   CLR_CHECK_LAUNCH("recompression");
+  prof_launches(ctx, 2);
+  prof_mark(ctx, s, PH_COMPRESS);
+  if (!o.recompress_dense) {
+    launch_dense_tile_norms(cv, p, s);
+    prof_launches(ctx, 1);
+  }
   if (alpha != 1.0) {
     launch_scale_blocks(cv, alpha, s);
-    CLR_CHECK_LAUNCH("scale");
+    prof_launches(ctx, 1);
   }
+  CLR_CHECK_LAUNCH("finalize");
+  prof_mark(ctx, s, PH_FINALIZE);
+  if (ctx->prof_on) ctx->prof.products++;
   if (stats) {
     PlanCounters pc;
     CLR_CUDA(cudaMemcpyAsync(&pc, p.counters, sizeof(pc), cudaMemcpyDeviceToHost, s));
@@ -683,6 +758,43 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
 }
 
 }  // namespace
+
+extern "C" int clr_profile_enable(clr_ctx_t ctx, int on) {
+  if (!ctx) return CLR_EINVAL;
+  cudaSetDevice(ctx->device);
+  for (auto& pe : ctx->prof_events) ctx->event_pool.push_back(pe.first);
+  ctx->prof_events.clear();
+  std::memset(&ctx->prof, 0, sizeof(ctx->prof));
+  ctx->prof_on = on != 0;
+  return CLR_OK;
+}
+
+extern "C" int clr_profile_read(clr_ctx_t ctx, clr_profile* out) {
+  if (!ctx || !out) return CLR_EINVAL;
+  cudaSetDevice(ctx->device);
+  if (!ctx->prof_events.empty()) {
+    CLR_CUDA(cudaEventSynchronize(ctx->prof_events.back().first));
+    cudaEvent_t prev = nullptr;
+    for (auto& pe : ctx->prof_events) {
+      if (pe.second != PH_START && prev) {
+        float ms = 0.f;
+        CLR_CUDA(cudaEventElapsedTime(&ms, prev, pe.first));
+        double* slot = pe.second == PH_PLAN ? &ctx->prof.ms_plan
+                     : pe.second == PH_STAGE ? &ctx->prof.ms_stage
+                     : pe.second == PH_DENSE ? &ctx->prof.ms_dense
+                     : pe.second == PH_LOWRANK ? &ctx->prof.ms_lowrank
+                     : pe.second == PH_COMPRESS ? &ctx->prof.ms_compress
+                     : &ctx->prof.ms_finalize;
+        *slot += ms;
+      }
+      prev = pe.first;
+    }
+    for (auto& pe : ctx->prof_events) ctx->event_pool.push_back(pe.first);
+    ctx->prof_events.clear();
+  }
+  *out = ctx->prof;
+  return CLR_OK;
+}
 
 extern "C" int clr_multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c,
                                  double alpha, clr_product_stats* stats, void* stream) {

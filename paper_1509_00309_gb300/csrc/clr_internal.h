@@ -90,6 +90,12 @@ void launch_to_dense(const MatView& M, double* out, int64_t ldo, cudaStream_t st
 void launch_zero_blocks(const MatView& M, cudaStream_t st);
 void launch_set_route_kinds(const MatView& C, const Plan& p, cudaStream_t st);
 void launch_dense_tile_norms(const MatView& C, const Plan& p, cudaStream_t st);
+// k_layout.cu
+void launch_rowmajor_to_pool(const MatView& M, const int* row_idx, const double* src,
+                             int64_t lds, cudaStream_t st);
+void launch_dense_kinds(const MatView& M, double drop_norm, int* err, cudaStream_t st);
+void launch_pool_to_rowmajor(const MatView& M, const int* row_idx, const int* col_idx,
+                             double* out, int64_t ldo, cudaStream_t st);
 // k_lowrank.cu
 void launch_lr_products(const MatView& A, const MatView& B, const MatView& C, const Plan& p,
                         double* ws, double* scratch, int64_t scratch_per_cta, int grid,
@@ -107,6 +113,7 @@ void launch_compress_dense(const MatView& C, const int* list, const int* count,
                            double drop_norm, int dense_only, int max_sweeps, int grid,
                            int* err, cudaStream_t st);
 void launch_block_norms(const MatView& M, cudaStream_t st);
+void launch_block_norms_dense(const MatView& M, cudaStream_t st);
 void launch_scale_blocks(const MatView& M, double alpha, cudaStream_t st);
 // k_ns.cu
 void launch_lincomb_plan(double a, const MatView& X, double b, const MatView& Y, double diag,
@@ -133,8 +140,9 @@ struct SplitGemmArgs {
   void* encode_fn;    // cuTensorMapEncodeTiled
 };
 int split_gemm_dd(const SplitGemmArgs& a, cudaStream_t st, std::string* why);
-void launch_split_stage(const MatView& M, void* panels, int terms, int64_t rows_pad,
-                        int64_t cols_pad, int transpose_to_kmajor, cudaStream_t st);
+void launch_split_stage(const MatView& M, const int* row_idx, const int* col_idx, void* panels,
+                        int terms, int64_t rows_pad, int64_t cols_pad, int a_mode,
+                        cudaStream_t st);
 void launch_cluster_index(const int* off, int n_clusters, int* index_of, int64_t n,
                           cudaStream_t st);
 

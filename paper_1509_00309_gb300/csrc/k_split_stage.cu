@@ -12,96 +12,198 @@
 
 namespace clr {
 
-// Round a double to the nearest bf16 (ties to even), from the format's definition: 8
-// significant bits, exponent range of binary32, subnormal spacing 2^-133.
-__device__ __forceinline__ unsigned short bf16_bits_rn(double x) {
-  if (x == 0.0 || !isfinite(x)) {
-    const float f = (float)x;
-    return (unsigned short)(__float_as_uint(f) >> 16);
+// Round the value R * 2^s (R a signed integer, |R| < 2^62) to the nearest bf16, ties to
+// even, from the format's definition: 8 significant bits, exponent range of binary32, below
+// the smallest normal 2^-126 a fixed spacing of 2^-133.  Returns the bf16 bits and, in *Rr,
+// the rounded value in units of 2^s (exact), so the caller can form the residual R - Rr.
+// Integer operations only: FP64 arithmetic runs at a small fraction of the integer rate.
+__device__ __forceinline__ unsigned short round_bf16(long long R, int s, long long* Rr) {
+  if (R == 0) {
+    *Rr = 0;
+    return 0;
   }
-  int e = ilogb(x);
-  if (e < -126) e = -126;
-  const double r = rint(scalbn(x, 7 - e));
-  const float f = (float)scalbn(r, e - 7);
-  return (unsigned short)(__float_as_uint(f) >> 16);
-}
-
-__device__ __forceinline__ double bf16_bits_to_double(unsigned short b) {
-  return (double)__uint_as_float(((unsigned)b) << 16);
-}
-
-__device__ __forceinline__ int cluster_of(const int* off, int n, int x) {
-  int lo = 0, hi = n - 1;  // off[lo] <= x < off[hi+1]
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (off[mid] <= x) lo = mid; else hi = mid - 1;
+  const unsigned short sign = R < 0 ? 0x8000 : 0;
+  const unsigned long long mag = R < 0 ? (unsigned long long)(-R) : (unsigned long long)R;
+  const int msb = 63 - __clzll(mag);
+  int shift = msb - 7;
+  const int sub = -133 - s;
+  if (shift < sub) shift = sub;
+  unsigned long long q;
+  if (shift <= 0) {
+    q = mag;  // at most 8 significant bits: exact
+    shift = 0;
+  } else if (shift > 62) {
+    q = 0;
+  } else {
+    const unsigned long long rem = mag & ((1ull << shift) - 1);
+    const unsigned long long half = 1ull << (shift - 1);
+    q = mag >> shift;
+    if (rem > half || (rem == half && (q & 1))) ++q;
   }
-  return lo;
+  if (q == 0) {
+    *Rr = 0;
+    return sign;
+  }
+  const long long rr = (long long)(q << shift);
+  *Rr = R < 0 ? -rr : rr;
+  const int vexp = s + shift;
+  const int qb = 63 - __clzll(q);  // <= 8
+  const int E = qb + vexp;         // exponent of the leading bit
+  if (E < -126) return sign | (unsigned short)(q << (vexp + 133));  // subnormal
+  const unsigned mant = qb >= 7 ? (unsigned)(q >> (qb - 7)) & 0x7Fu
+                                : (unsigned)(q << (7 - qb)) & 0x7Fu;
+  return sign | (unsigned short)((E + 127) << 7) | (unsigned short)mant;
 }
 
-// One CTA stages a 32 (matrix rows) x 32 (matrix cols) tile.
-__global__ void __launch_bounds__(256) split_stage_kernel(MatView M, unsigned short* panels,
-                                                          int terms, int64_t rows_pad,
-                                                          int64_t cols_pad, int a_mode) {
-  __shared__ double tile[32][33];
-  // tile origin in matrix coordinates (r = matrix row, c = matrix col)
-  const int64_t prow_tiles = a_mode ? rows_pad / 32 : cols_pad / 32;  // along matrix rows
-  const int64_t r0 = (a_mode ? blockIdx.x % prow_tiles : blockIdx.x % prow_tiles) * 32;
-  const int64_t c0 = (int64_t)(blockIdx.x / prow_tiles) * 32;
-  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
-  // load: consecutive threads take consecutive matrix rows (column-major source)
-  for (int cc = ty; cc < 32; cc += 8) {
-    const int64_t r = r0 + tx, c = c0 + cc;
-    double v = 0.0;
-    if (r < M.n_rows && c < M.n_cols) {
-      const int R = cluster_of(M.row_off, M.nr, (int)r);
-      const int Cc = cluster_of(M.col_off, M.nc, (int)c);
-      if (M.kind[R * M.nc + Cc] == CLR_KIND_DENSE) {
-        const int mR = M.row_off[R + 1] - M.row_off[R];
-        v = M.pool[(int64_t)M.row_off[R] * M.n_cols + (r - M.row_off[R]) + c * mR];
-      }
+// a = a_0 + a_1 (+ a_2) + residual: successive round-to-nearest bf16 terms of a finite double.
+// Fast path (exponent of a in [-110, 126], so a_0 is a normal bf16): a_0 by adding the
+// rounding bias to the FP64 bit pattern and clearing the 45 low bits (carries into the exponent
+// are exact), the residual a - a_0 as an integer multiple of a's ulp; the lower terms, and the
+// whole split outside that range, by the generic integer rounding above.
+__device__ __forceinline__ void split_bf16(double x, int terms, unsigned short* out) {
+  const unsigned long long u = (unsigned long long)__double_as_longlong(x);
+  const int E = (int)((u >> 52) & 0x7FF);
+  if (E >= 1023 - 110 && E <= 1023 + 126) {
+    const unsigned long long u0 = (u + 0xFFFFFFFFFFFull + ((u >> 45) & 1ull)) & ~0x1FFFFFFFFFFFull;
+    const unsigned hi0 = (unsigned)(u0 >> 32);
+    const unsigned E0 = (hi0 >> 20) & 0x7FFu;
+    out[0] = (unsigned short)(((hi0 >> 16) & 0x8000u) | ((E0 - 896u) << 7) | ((hi0 >> 13) & 0x7Fu));
+    if (terms == 1) return;
+    const long long M = (long long)((u & 0xFFFFFFFFFFFFFull) | (1ull << 52));
+    const long long M0 = (long long)((u0 & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (E0 - E);
+    long long R = (u >> 63) ? M0 - M : M - M0;
+    const int s = E - 1075;
+    for (int t = 1; t < terms; ++t) {
+      long long rr;
+      out[t] = round_bf16(R, s, &rr);
+      R -= rr;
     }
+    return;
+  }
+  const long long bits = (long long)u;
+  const long long frac = bits & ((1ll << 52) - 1);
+  const long long M = E == 0 ? frac : (frac | (1ll << 52));
+  const int s = E == 0 ? -1074 : E - 1075;
+  long long R = bits < 0 ? -M : M;
+  for (int t = 0; t < terms; ++t) {
+    long long rr;
+    out[t] = round_bf16(R, s, &rr);
+    R -= rr;
+  }
+}
+
+// A panel: one CTA converts a 32 (rows) x 128 (k) tile.  The source block-row panels are
+// column-major (consecutive rows contiguous), the panel is row-major (consecutive k
+// contiguous), so the tile goes through shared memory; each thread then packs 4 consecutive
+// k of one row into one 8-byte store per term.
+constexpr int kTk = 128;
+
+__global__ void __launch_bounds__(256) split_stage_a_kernel(MatView M, const int* row_idx,
+                                                            const int* col_idx,
+                                                            unsigned short* panels, int terms,
+                                                            int64_t rows_pad, int64_t cols_pad) {
+  __shared__ double tile[32][kTk + 1];
+  const int64_t tiles_r = rows_pad / 32;
+  const int64_t r0 = (int64_t)(blockIdx.x % tiles_r) * 32;
+  const int64_t k0 = (int64_t)(blockIdx.x / tiles_r) * kTk;
+  const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
+  const int64_t r = r0 + tx;
+  int R = 0, mR = 1;
+  int64_t rbase = 0;
+  const bool rin = r < M.n_rows;
+  if (rin) {
+    R = row_idx[r];
+    mR = M.row_off[R + 1] - M.row_off[R];
+    rbase = (int64_t)M.row_off[R] * M.n_cols + (r - M.row_off[R]);
+  }
+  const int* kind_row = M.kind + (int64_t)R * M.nc;
+  for (int cc = ty; cc < kTk; cc += 8) {
+    const int64_t c = k0 + cc;
+    double v = 0.0;
+    if (rin && c < M.n_cols && kind_row[col_idx[c]] == CLR_KIND_DENSE) v = M.pool[rbase + c * mR];
     tile[tx][cc] = v;
   }
   __syncthreads();
   const int64_t plane = rows_pad * cols_pad;
-  if (a_mode) {
-    // panel[i][k] = A(i,k): consecutive threads write consecutive k
-    for (int rr = ty; rr < 32; rr += 8) {
-      const int64_t i = r0 + rr, k = c0 + tx;
-      if (i >= rows_pad || k >= cols_pad) continue;
-      double rest = tile[rr][tx];
-      for (int t = 0; t < terms; ++t) {
-        const unsigned short b = bf16_bits_rn(rest);
-        panels[t * plane + i * cols_pad + k] = b;
-        rest -= bf16_bits_to_double(b);
-      }
+  for (int rr = ty; rr < 32; rr += 8) {
+    const int64_t i = r0 + rr;
+    const int64_t k = k0 + 4 * tx;
+    unsigned long long packed[3] = {0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      unsigned short b[3];
+      split_bf16(tile[rr][4 * tx + q], terms, b);
+      for (int t = 0; t < terms; ++t) packed[t] |= (unsigned long long)b[t] << (16 * q);
     }
-  } else {
-    // panel[j][k] = B(k,j): rows of the panel are matrix columns; consecutive threads write
-    // consecutive k (matrix rows)
-    for (int cc = ty; cc < 32; cc += 8) {
-      const int64_t j = c0 + cc, k = r0 + tx;
-      if (j >= rows_pad || k >= cols_pad) continue;
-      double rest = tile[tx][cc];
-      for (int t = 0; t < terms; ++t) {
-        const unsigned short b = bf16_bits_rn(rest);
-        panels[t * plane + j * cols_pad + k] = b;
-        rest -= bf16_bits_to_double(b);
-      }
-    }
+    for (int t = 0; t < terms; ++t)
+      *reinterpret_cast<unsigned long long*>(panels + t * plane + i * cols_pad + k) = packed[t];
   }
 }
 
-void launch_split_stage(const MatView& M, void* panels, int terms, int64_t rows_pad,
-                        int64_t cols_pad, int a_mode, cudaStream_t st) {
-  // tiles cover the padded panel: A: rows_pad x cols_pad over (matrix rows, matrix cols);
-  // B: panel rows are matrix columns (rows_pad) and panel cols are matrix rows (cols_pad).
-  const int64_t along_rows = (a_mode ? rows_pad : cols_pad) / 32;
-  const int64_t along_cols = (a_mode ? cols_pad : rows_pad) / 32;
-  const int64_t n = along_rows * along_cols;
-  split_stage_kernel<<<(unsigned)n, 256, 0, st>>>(M, (unsigned short*)panels, terms, rows_pad,
-                                                   cols_pad, a_mode);
+// B panel: panel[j][k] = B(k, j).  Consecutive k are contiguous in both the source block-row
+// panels and the panel, so no transpose: each thread converts 4 consecutive k of one column.
+__global__ void __launch_bounds__(256) split_stage_b_kernel(MatView M, const int* row_idx,
+                                                            const int* col_idx,
+                                                            unsigned short* panels, int terms,
+                                                            int64_t rows_pad, int64_t cols_pad) {
+  const int64_t per_row = cols_pad / 4;                 // 4-wide groups along k
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= rows_pad * per_row) return;
+  const int64_t j = g / per_row;
+  const int64_t k = (g % per_row) * 4;
+  unsigned long long packed[3] = {0, 0, 0};
+  if (j < M.n_cols && k < M.n_rows) {
+    const int Cc = col_idx[j];
+    const int R0 = row_idx[k];
+    const int end0 = M.row_off[R0 + 1];
+    if (k + 3 < end0) {
+      // the 4 elements lie in one block: one kind lookup, contiguous source
+      if (M.kind[R0 * M.nc + Cc] == CLR_KIND_DENSE) {
+        const int mR = end0 - M.row_off[R0];
+        const double* src = M.pool + (int64_t)M.row_off[R0] * M.n_cols + (k - M.row_off[R0]) + j * mR;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          unsigned short b[3];
+          split_bf16(src[q], terms, b);
+          for (int t = 0; t < terms; ++t) packed[t] |= (unsigned long long)b[t] << (16 * q);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int64_t kk = k + q;
+        double v = 0.0;
+        if (kk < M.n_rows) {
+          const int R = row_idx[kk];
+          if (M.kind[R * M.nc + Cc] == CLR_KIND_DENSE) {
+            const int mR = M.row_off[R + 1] - M.row_off[R];
+            v = M.pool[(int64_t)M.row_off[R] * M.n_cols + (kk - M.row_off[R]) + j * mR];
+          }
+        }
+        unsigned short b[3];
+        split_bf16(v, terms, b);
+        for (int t = 0; t < terms; ++t) packed[t] |= (unsigned long long)b[t] << (16 * q);
+      }
+    }
+  }
+  const int64_t plane = rows_pad * cols_pad;
+  for (int t = 0; t < terms; ++t)
+    *reinterpret_cast<unsigned long long*>(panels + t * plane + j * cols_pad + k) = packed[t];
+}
+
+void launch_split_stage(const MatView& M, const int* row_idx, const int* col_idx, void* panels,
+                        int terms, int64_t rows_pad, int64_t cols_pad, int a_mode,
+                        cudaStream_t st) {
+  if (a_mode) {
+    const int64_t n = (rows_pad / 32) * (cols_pad / kTk);
+    split_stage_a_kernel<<<(unsigned)n, 256, 0, st>>>(M, row_idx, col_idx,
+                                                      (unsigned short*)panels, terms, rows_pad,
+                                                      cols_pad);
+  } else {
+    const int64_t n = rows_pad * (cols_pad / 4);
+    split_stage_b_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        M, row_idx, col_idx, (unsigned short*)panels, terms, rows_pad, cols_pad);
+  }
 }
 
 __global__ void cluster_index_kernel(const int* off, int n_clusters, int* index_of) {

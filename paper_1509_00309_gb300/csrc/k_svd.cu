@@ -422,6 +422,24 @@ __global__ void __launch_bounds__(kThreads) block_norms_kernel(MatView M) {
   if (threadIdx.x == 0) M.norm[t] = kind == CLR_KIND_ZERO ? 0.0 : sqrt(fmax(tot, 0.0));
 }
 
+// Frobenius norm of every block's slot read as a dense block (kinds not yet known).
+__global__ void __launch_bounds__(kThreads) block_norms_dense_kernel(MatView M) {
+  __shared__ double red[kWarps];
+  const int t = blockIdx.x;
+  const int I = t / M.nc, J = t % M.nc;
+  const int m = M.row_off[I + 1] - M.row_off[I];
+  const int n = M.col_off[J + 1] - M.col_off[J];
+  const double* s = M.pool + slot_of(M, I, J, m);
+  double part = 0.0;
+  for (int e = threadIdx.x; e < m * n; e += kThreads) part = fma(s[e], s[e], part);
+  const double tot = block_sum(part, red);
+  if (threadIdx.x == 0) M.norm[t] = sqrt(tot);
+}
+
+void launch_block_norms_dense(const MatView& M, cudaStream_t st) {
+  block_norms_dense_kernel<<<M.nr * M.nc, kThreads, 0, st>>>(M);
+}
+
 void launch_block_norms(const MatView& M, cudaStream_t st) {
   block_norms_kernel<<<M.nr * M.nc, kThreads, 0, st>>>(M);
 }

@@ -63,6 +63,14 @@ def test_product_with_identity_returns_split_of_a(ctx, mode, rel):
     gi = ctx.from_dense(np.eye(n), sizes)
     got = ctx.multiply(ga, gi).to_dense()
     assert np.all(np.abs(got - a) <= rel * np.abs(a) + 1e-300)
+    if mode == "bf16x3":
+        # where a_0 + a_1 is an FP32 value the tensor-core sum is exact, so the GPU's integer
+        # bf16 rounding must reproduce the oracle's terms bit for bit there
+        t = so.split_terms(a, 2)
+        s2 = t[0] + t[1]
+        exact = s2.astype(np.float32).astype(np.float64) == s2
+        assert exact.mean() > 0.99
+        assert np.array_equal(got[exact], s2[exact])
 
 
 def test_split_inside_mixed_clr_product(ctx):
