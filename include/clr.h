@@ -229,6 +229,29 @@ typedef struct clr_profile {
 int clr_profile_enable(clr_ctx_t ctx, int on);
 int clr_profile_read(clr_ctx_t ctx, clr_profile* out);
 
+/* ---- allocation-free single-block compression ---------------------------------------------
+ * clr_block_compress_noalloc: the truncated SVD of one m x n block at Frobenius error eps, the
+ * same per-block computation as clr_mat_from_dense (drop threshold 0), for callers that must
+ * not allocate device memory: code running while a CUDA stream is being captured into a graph,
+ * real-time or embedded hosts whose device memory is planned ahead, and plugins living inside a
+ * framework whose allocator owns all device memory.  It calls no cudaMalloc, cudaFree or
+ * allocating library routine and needs no context.  The paper has no counterpart: it is a
+ * deployment variant, not part of the method.
+ *   block        device pointer, m x n column-major, leading dimension ld >= m
+ *   m, n         1 .. CLR_MAX_CLUSTER (256); larger sizes return CLR_EINVAL
+ *   x_out, w_out device buffers for X (m x min(m,n)) and W (n x min(m,n)), column-major with
+ *                leading dimensions m and n; written only when the result is low rank
+ *   sigma_out    optional device buffer of min(m,n) singular values, descending
+ *   status       device int32[3]: kind (CLR_KIND_*), rank, error flag (3: non-finite input)
+ * Scratch: a fixed 1 MiB device array compiled into the library (2 x 256 x 256 doubles) that
+ * every GPU loading the library holds until exit.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call shares the array and overwrites it; calls that overlap
+ * on the GPU race, so issue them on one stream (or serialise them).  Asynchronous on `stream`. */
+int clr_block_compress_noalloc(int device, const double* block, int64_t ld, int m, int n,
+                               double eps, int max_sweeps, double* x_out, double* w_out,
+                               double* sigma_out, int32_t* status, void* stream);
+
 /* y = A x for dense device vectors (x: n_cols, y: n_rows). */
 int clr_matvec(clr_ctx_t ctx, clr_mat_t a, const double* x, double* y, void* stream);
 

@@ -93,6 +93,8 @@ _SIGNATURES = {
     "clr_sqrt_inv_backward": (C.c_int, [_VP, _VP, _VP, C.POINTER(_VP), _VP]),
     "clr_tape_free": (C.c_int, [_VP, _VP]),
     "clr_matvec": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
+    "clr_block_compress_noalloc": (C.c_int, [C.c_int, _VP, C.c_int64, C.c_int, C.c_int,
+                                             C.c_double, C.c_int, _VP, _VP, _VP, _VP, _VP]),
     "clr_profile_enable": (C.c_int, [_VP, C.c_int]),
     "clr_profile_read": (C.c_int, [_VP, C.POINTER(ClrProfile)]),
 }
@@ -391,6 +393,23 @@ class Context:
         self._check(load().clr_sqrt_inv_backward(self.handle, tape.handle, zbar.handle,
                                                  C.byref(h), _stream(stream)))
         return Matrix(self, h.value, zbar.row_sizes, zbar.col_sizes)
+
+
+def block_compress_noalloc(block, eps: float, x_out, w_out, status, sigma_out=None,
+                           max_sweeps: int = 40, stream=None) -> None:
+    """Truncated SVD of one dense block (a column-major view: a CUDA float64 tensor whose
+    transpose is contiguous, or any tensor with stride(0) == 1) into caller-owned device
+    buffers, without any device allocation (see clr_block_compress_noalloc in clr.h)."""
+    m, n = block.shape
+    if block.stride(0) != 1:
+        raise ValueError("block must be column-major (stride(0) == 1)")
+    ld = block.stride(1) if n > 1 else m
+    st = load().clr_block_compress_noalloc(block.device.index or 0, _ptr(block), ld, m, n,
+                                           float(eps), int(max_sweeps), _ptr(x_out),
+                                           _ptr(w_out), _ptr(sigma_out), _ptr(status),
+                                           _stream(stream))
+    if st != CLR_OK:
+        raise ClrError(st, "clr_block_compress_noalloc failed")
 
 
 class Tape:

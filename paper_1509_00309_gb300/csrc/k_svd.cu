@@ -15,6 +15,7 @@
 // Working arrays live in the tile's workspace slot (2 m n doubles per tile, enough for
 // either route).
 #include <cfloat>
+#include <mutex>
 
 #include "clr_internal.h"
 
@@ -463,3 +464,108 @@ void launch_scale_blocks(const MatView& M, double alpha, cudaStream_t st) {
 }
 
 }  // namespace clr
+
+// =============================================================================================
+// Allocation-free truncated SVD of one block (clr_block_compress_noalloc).
+//
+// Same computation as compress_dense_kernel for a single block, but its working memory (the
+// block copy G and the rotation matrix V) lives in a fixed file-scope device array instead of a
+// caller- or context-allocated workspace, so the entry point never allocates.  The array holds
+// CLR_MAX_CLUSTER^2 doubles for G and as many for V (1 MiB), is loaded with every GPU that
+// loads this library, and is shared by every call: G is fully rewritten and V reset to the
+// identity by each call, so no stale contents are read, but calls that overlap on the GPU
+// (different streams, concurrent host threads) race on it.
+// =============================================================================================
+namespace clr {
+namespace {
+
+constexpr int64_t kNoAllocScratchDoubles = 2LL * CLR_MAX_CLUSTER * CLR_MAX_CLUSTER;
+__device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+constexpr int kNoAllocMaxDevices = 64;
+double* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
+std::mutex g_noalloc_mutex;
+
+// status[0] = kind, status[1] = rank, status[2] = error flag (3: non-finite input)
+__global__ void __launch_bounds__(kThreads) compress_block_noalloc_kernel(
+    const double* src, int64_t lds, int m, int n, double eps, int max_sweeps, double* scratch,
+    double* x_out, double* w_out, double* sigma_out, int* status) {
+  __shared__ SvdShared sh;
+  const bool tr = m < n;
+  const int p = tr ? n : m, q = tr ? m : n;
+  double* G = scratch;                                   // p x q, ld p
+  double* V = scratch + (int64_t)CLR_MAX_CLUSTER * CLR_MAX_CLUSTER;  // q x q, ld q
+  double part = 0.0;
+  for (int e = threadIdx.x; e < m * n; e += kThreads) {
+    const int i = e % m, j = e / m;
+    const double x = src[i + (int64_t)j * lds];
+    part = fma(x, x, part);
+    if (tr) G[j + (int64_t)i * p] = x; else G[i + (int64_t)j * p] = x;
+  }
+  const double nsq = block_sum(part, sh.red);
+  if (threadIdx.x == 0) status[2] = isfinite(nsq) ? 0 : 3;
+  if (!isfinite(nsq) || nsq == 0.0) {
+    if (threadIdx.x == 0) { status[0] = CLR_KIND_ZERO; status[1] = 0; }
+    return;
+  }
+  jacobi_svd(G, p, q, p, V, q, max_sweeps, &sh.flag);
+  sort_and_truncate(G, p, q, p, eps, sh);
+  const int r = sh.rank;
+  if (sigma_out)
+    for (int c = threadIdx.x; c < q; c += kThreads) sigma_out[c] = sh.sorted[c];
+  if (r == 0) {
+    if (threadIdx.x == 0) { status[0] = CLR_KIND_ZERO; status[1] = 0; }
+    return;
+  }
+  if (r > q / 2) {
+    if (threadIdx.x == 0) { status[0] = CLR_KIND_DENSE; status[1] = q; }
+    return;
+  }
+  if (!tr) {
+    for (int e = threadIdx.x; e < m * r; e += kThreads)
+      x_out[e] = G[(e % m) + (int64_t)sh.perm[e / m] * p];
+    for (int e = threadIdx.x; e < n * r; e += kThreads)
+      w_out[e] = V[(e % n) + (int64_t)sh.perm[e / n] * q];
+  } else {
+    for (int e = threadIdx.x; e < m * r; e += kThreads)
+      x_out[e] = V[(e % m) + (int64_t)sh.perm[e / m] * q] * sh.sorted[e / m];
+    for (int e = threadIdx.x; e < n * r; e += kThreads)
+      w_out[e] = G[(e % n) + (int64_t)sh.perm[e / n] * p] / sh.sorted[e / n];
+  }
+  if (threadIdx.x == 0) { status[0] = CLR_KIND_LR; status[1] = r; }
+}
+
+}  // namespace
+}  // namespace clr
+
+extern "C" int clr_block_compress_noalloc(int device, const double* block, int64_t ld, int m,
+                                          int n, double eps, int max_sweeps, double* x_out,
+                                          double* w_out, double* sigma_out, int32_t* status,
+                                          void* stream) {
+  using namespace clr;
+  if (!block || !x_out || !w_out || !status) return CLR_EINVAL;
+  if (m < 1 || n < 1 || m > CLR_MAX_CLUSTER || n > CLR_MAX_CLUSTER) return CLR_EINVAL;
+  if (ld < m || !(eps >= 0.0) || max_sweeps < 1) return CLR_EINVAL;
+  if (device < 0 || device >= kNoAllocMaxDevices) return CLR_EINVAL;
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) return CLR_ECUDA;
+  if (prev != device && cudaSetDevice(device) != cudaSuccess) return CLR_ECUDA;
+  double* scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[device]) {
+      void* ptr = nullptr;
+      if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
+        if (prev != device) cudaSetDevice(prev);
+        return CLR_ECUDA;
+      }
+      g_noalloc_ptr[device] = (double*)ptr;
+    }
+    scratch = g_noalloc_ptr[device];
+  }
+  compress_block_noalloc_kernel<<<1, kThreads, 0, (cudaStream_t)stream>>>(
+      block, ld, m, n, eps, max_sweeps, scratch, x_out, w_out, sigma_out, (int*)status);
+  const cudaError_t e = cudaGetLastError();
+  if (prev != device) cudaSetDevice(prev);
+  return e == cudaSuccess ? CLR_OK : CLR_ECUDA;
+}
