@@ -1138,8 +1138,71 @@ extern "C" int clr_tape_free(clr_ctx_t ctx, clr_tape_t tape) {
 
 extern "C" int clr_sqrt_inv_backward(clr_ctx_t ctx, clr_tape_t tape, clr_mat_t zbar,
                                      clr_mat_t* sbar, void* stream) {
+  // Reverse sweep of Section 4.2's recurrences (alpha held constant; truncation treated as
+  // the identity, every adjoint product a CLR product at eps_lr):
+  //   Z_{n+1} = Z_n T_n      ->  Zb_n  = Zb_{n+1} T_n^T,       Tb_n  = Z_n^T Zb_{n+1}
+  //   Y_{n+1} = T_n Y_n      ->  Yb_n  = T_n^T Yb_{n+1},       Tb_n += Yb_{n+1} Y_n^T
+  //   T_n = (15I-10X+3X^2)/8 ->  Xb_n  = (-10 Tb_n + 3 (Tb_n X_n^T + X_n^T Tb_n)) / 8
+  //   X_n = alpha Y_n Z_n    ->  Yb_n += alpha Xb_n Z_n^T,     Zb_n += alpha Y_n^T Xb_n
+  // starting from Zb = sqrt(alpha) zbar (the output is sqrt(alpha) Z), Yb = 0; dL/dS = Yb_0.
   if (!ctx || !tape || !zbar || !sbar) return CLR_EINVAL;
   *sbar = nullptr;
-  (void)stream;
-  return fail(ctx, CLR_ENOTSUP, "backward not available");
+  if (!tape->s || zbar->row_sizes != tape->s->row_sizes ||
+      zbar->col_sizes != tape->s->col_sizes)
+    return fail(ctx, CLR_EINVAL, "zbar clusters differ from S");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  const int nr = tape->s->nr;
+  const int32_t* sz = tape->s->row_sizes.data();
+  MatGuard g;
+  enum { X, X2, T, TT, XT, YT, ZT, TB, XB, ZB, YB, ZBN, YBN, W1, W2, NW };
+  clr_mat_t m[NW];
+  for (int i = 0; i < NW; ++i) {
+    int st = alloc_mat(ctx, nr, sz, nr, sz, &m[i]);
+    if (st) return st;
+    g.v.push_back(m[i]);
+  }
+  const double alpha = tape->alpha;
+  const int prec = choose_precision(ctx, tape->s, tape->s);
+  auto mul = [&](clr_mat_t a, clr_mat_t b, clr_mat_t c, double sc) {
+    return multiply_into(ctx, a, b, c, sc, prec, nullptr, s);
+  };
+  auto tr = [&](clr_mat_t a, clr_mat_t t) {
+    launch_transpose(a->view(), t->view(), s);
+    return cudaGetLastError() == cudaSuccess ? CLR_OK : CLR_ECUDA;
+  };
+  int st = clr_lincomb(ctx, std::sqrt(alpha), zbar, 0.0, zbar, 0.0, m[ZB], s);
+  if (st) return st;
+  st = clr_lincomb(ctx, 0.0, zbar, 0.0, zbar, 0.0, m[YB], s);  // Yb = 0
+  if (st) return st;
+  for (int n = tape->iters - 1; n >= 0; --n) {
+    clr_mat_t Yn = tape->y[n], Zn = tape->z[n];
+    if ((st = mul(Yn, Zn, m[X], alpha))) return st;                           // X = a Y Z
+    if ((st = mul(m[X], m[X], m[X2], 1.0))) return st;                        // X^2
+    if ((st = clr_lincomb(ctx, -10.0 / 8.0, m[X], 3.0 / 8.0, m[X2], 15.0 / 8.0, m[T], s)))
+      return st;                                                               // T
+    if ((st = tr(m[T], m[TT])) || (st = tr(m[X], m[XT])) || (st = tr(Yn, m[YT])) ||
+        (st = tr(Zn, m[ZT])))
+      return st;
+    // Tb = Z^T Zb + Yb Y^T
+    if ((st = mul(m[ZT], m[ZB], m[W1], 1.0)) || (st = mul(m[YB], m[YT], m[W2], 1.0)) ||
+        (st = clr_lincomb(ctx, 1.0, m[W1], 1.0, m[W2], 0.0, m[TB], s)))
+      return st;
+    // Zb_n = Zb T^T ; Yb_n = T^T Yb
+    if ((st = mul(m[ZB], m[TT], m[ZBN], 1.0)) || (st = mul(m[TT], m[YB], m[YBN], 1.0))) return st;
+    // Xb = (-10 Tb + 3 (Tb X^T + X^T Tb)) / 8
+    if ((st = mul(m[TB], m[XT], m[W1], 1.0)) || (st = mul(m[XT], m[TB], m[W2], 1.0)) ||
+        (st = clr_lincomb(ctx, 1.0, m[W1], 1.0, m[W2], 0.0, m[X2], s)) ||
+        (st = clr_lincomb(ctx, -10.0 / 8.0, m[TB], 3.0 / 8.0, m[X2], 0.0, m[XB], s)))
+      return st;
+    // Yb_n += a Xb Z^T ; Zb_n += a Y^T Xb
+    if ((st = mul(m[XB], m[ZT], m[W1], alpha)) ||
+        (st = clr_lincomb(ctx, 1.0, m[YBN], 1.0, m[W1], 0.0, m[YB], s)))
+      return st;
+    if ((st = mul(m[YT], m[XB], m[W2], alpha)) ||
+        (st = clr_lincomb(ctx, 1.0, m[ZBN], 1.0, m[W2], 0.0, m[ZB], s)))
+      return st;
+  }
+  *sbar = g.keep(m[YB]);
+  return CLR_OK;
 }

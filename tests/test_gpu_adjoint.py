@@ -1,0 +1,74 @@
+"""GPU parity of the hand-written adjoint of the Newton–Schulz iteration (loss
+trace(W S^-1/2)) against the oracle's reverse sweep, the Daleckii–Krein eigen-gradient and
+finite differences."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import clr_oracle as co
+from paper_1509_00309_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def clr():
+    from paper_1509_00309_gb300 import build, clr
+    build.build()
+    return clr
+
+
+def test_adjoint_fixed_iterations_matches_oracle_reverse_sweep(clr):
+    w = wl.chain_overlap(n=384, n_clusters=3, lo=96, hi=160)
+    s = w.a
+    wmat = wl.symmetric_normal(3, s.shape[0])
+    alpha = co.alpha_estimate(s)
+    ctx = clr.Context(0, precision="fp64", eps_lr=1e-13, ns_tol=0.0, ns_max_iter=6,
+                      ns_alpha=alpha)
+    sm = ctx.from_dense(s, w.row_sizes, eps_lr=1e-13)
+    z, st, tape = ctx.sqrt_inv(sm, keep_tape=True)
+    assert st["iters"] == 6
+    zb = ctx.from_dense(np.ascontiguousarray(wmat.T), w.row_sizes, eps_lr=0.0)
+    g = ctx.sqrt_inv_backward(tape, zb).to_dense()
+    want = co.ns_adjoint_dense(s, wmat, alpha, 6)
+    assert np.linalg.norm(g - want) <= 1e-9 * np.linalg.norm(want)
+
+
+def test_adjoint_converged_matches_daleckii_krein(clr):
+    # the 3D lattice construction at N = 512 (4 x 4 x 2 sites x 16 points)
+    w = wl.adjoint_lattice(n_sites_shape=(4, 4, 2), min_points=32, max_points=128)
+    s, wmat = w.a, w.extra["w"]
+    ctx = clr.Context(0, precision="fp64", eps_lr=1e-10, ns_tol=1e-11, ns_max_iter=80)
+    sm = ctx.from_dense(s, w.row_sizes, eps_lr=1e-10)
+    z, st, tape = ctx.sqrt_inv(sm, keep_tape=True)
+    assert st["converged"]
+    zb = ctx.from_dense(np.ascontiguousarray(wmat.T), w.row_sizes, eps_lr=0.0)
+    g = ctx.sqrt_inv_backward(tape, zb).to_dense()
+    want = co.grad_trace_inv_sqrt(s, wmat)
+    assert np.linalg.norm(g - want) <= 1e-5 * np.linalg.norm(want)
+
+
+def test_autograd_function_vs_finite_differences(clr):
+    import torch
+    from paper_1509_00309_gb300.autograd import sqrt_inv
+    w = wl.chain_overlap(n=256, n_clusters=2, lo=96, hi=160)
+    ctx = clr.Context(0, precision="fp64", eps_lr=1e-12, ns_tol=1e-12, ns_max_iter=80)
+    s = torch.from_numpy(w.a).cuda().requires_grad_(True)
+    wm = torch.from_numpy(wl.symmetric_normal(5, 256)).cuda()
+    loss = torch.trace(wm @ sqrt_inv(s, ctx, w.row_sizes, eps_lr=1e-12))
+    loss.backward()
+    g = s.grad.cpu().numpy()
+
+    def f(mat):
+        z = sqrt_inv(torch.from_numpy(mat).cuda(), ctx, w.row_sizes, eps_lr=1e-12)
+        return float(torch.trace(wm @ z))
+
+    h = 1e-6
+    rng = np.random.default_rng(0)
+    for _ in range(3):
+        i, j = rng.integers(0, 256, 2)
+        e = np.zeros_like(w.a)
+        e[i, j] = h
+        fd = (f(w.a + e) - f(w.a - e)) / (2 * h)
+        assert abs(fd - g[i, j]) <= 1e-4 * max(1.0, abs(g[i, j])), (i, j, fd, g[i, j])
