@@ -24,7 +24,8 @@ namespace clr {
 constexpr int kThreads = 256;
 constexpr int kWarps = kThreads / 32;
 
-__device__ __forceinline__ double warp_sum(double v) {
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
@@ -106,15 +107,22 @@ __device__ void apply_q(const double* v, int p, int q, int64_t ldv, const double
 }
 
 // One-sided Jacobi on the q columns of g (p x q, ld ldg); v (q x q, ld ldv) accumulates the
-// rotations (initialised to I here).  On return g = U S and the input equals g v^T.
-__device__ int jacobi_svd(double* g, int p, int q, int64_t ldg, double* v, int64_t ldv,
-                          int max_sweeps, int* sh_flag) {
+// rotations (initialised to I here unless reset_v is false).  On return g = U S and the input
+// equals g v^T (times the initial v^T when v is not reset).  T is float or double; the
+// convergence threshold is the type's epsilon times sqrt(p) (times tol_scale).
+template <typename T>
+__device__ int jacobi_svd(T* g, int p, int q, int64_t ldg, T* v, int64_t ldv,
+                          int max_sweeps, int* sh_flag, bool reset_v = true,
+                          T tol_scale = T(1)) {
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
-  for (int e = threadIdx.x; e < q * q; e += kThreads)
-    v[(e % q) + (int64_t)(e / q) * ldv] = (e % q == e / q) ? 1.0 : 0.0;
-  __syncthreads();
+  if (reset_v) {
+    for (int e = threadIdx.x; e < q * q; e += kThreads)
+      v[(e % q) + (int64_t)(e / q) * ldv] = (e % q == e / q) ? T(1) : T(0);
+    __syncthreads();
+  }
   const int qq = q + (q & 1);  // even number of slots; slot q is a dummy when q is odd
-  const double tol = DBL_EPSILON * sqrt((double)p);
+  const T eps_t = sizeof(T) == 4 ? T(FLT_EPSILON) : T(DBL_EPSILON);
+  const T tol = eps_t * sqrt(T(p)) * tol_scale;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     if (threadIdx.x == 0) *sh_flag = 0;
@@ -130,11 +138,11 @@ __device__ int jacobi_svd(double* g, int p, int q, int64_t ldg, double* v, int64
           b = (round - k + (qq - 1)) % (qq - 1);
         }
         if (a >= q || b >= q) continue;
-        double* ga = g + (int64_t)a * ldg;
-        double* gb = g + (int64_t)b * ldg;
-        double al = 0.0, be = 0.0, ga_gb = 0.0;
+        T* ga = g + (int64_t)a * ldg;
+        T* gb = g + (int64_t)b * ldg;
+        T al = 0, be = 0, ga_gb = 0;
         for (int i = l; i < p; i += 32) {
-          const double x = ga[i], y = gb[i];
+          const T x = ga[i], y = gb[i];
           al = fma(x, x, al);
           be = fma(y, y, be);
           ga_gb = fma(x, y, ga_gb);
@@ -142,23 +150,23 @@ __device__ int jacobi_svd(double* g, int p, int q, int64_t ldg, double* v, int64
         al = warp_sum(al);
         be = warp_sum(be);
         ga_gb = warp_sum(ga_gb);
-        const double scale = sqrt(al) * sqrt(be);
-        if (scale == 0.0 || fabs(ga_gb) <= tol * scale) continue;
-        const double zeta = (be - al) / (2.0 * ga_gb);
-        const double t = copysign(1.0, zeta) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-        const double c = 1.0 / sqrt(1.0 + t * t);
-        const double s = c * t;
+        const T scale = sqrt(al) * sqrt(be);
+        if (scale == T(0) || fabs(ga_gb) <= tol * scale) continue;
+        const T zeta = (be - al) / (T(2) * ga_gb);
+        const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
+        const T c = T(1) / sqrt(T(1) + t * t);
+        const T sn = c * t;
         for (int i = l; i < p; i += 32) {
-          const double x = ga[i], y = gb[i];
-          ga[i] = c * x - s * y;
-          gb[i] = s * x + c * y;
+          const T x = ga[i], y = gb[i];
+          ga[i] = c * x - sn * y;
+          gb[i] = sn * x + c * y;
         }
-        double* va = v + (int64_t)a * ldv;
-        double* vb = v + (int64_t)b * ldv;
+        T* va = v + (int64_t)a * ldv;
+        T* vb = v + (int64_t)b * ldv;
         for (int i = l; i < q; i += 32) {
-          const double x = va[i], y = vb[i];
-          va[i] = c * x - s * y;
-          vb[i] = s * x + c * y;
+          const T x = va[i], y = vb[i];
+          va[i] = c * x - sn * y;
+          vb[i] = sn * x + c * y;
         }
         if (l == 0) *sh_flag = 1;
       }
@@ -226,6 +234,97 @@ __device__ void sort_and_truncate(const double* g, int p, int q, int64_t ldg, do
   __syncthreads();
 }
 
+// Read-only view of the p x q working matrix: element (i, j) = src[i * s_r + j * s_c], or of its
+// transpose when tr is set.
+struct SrcView {
+  const double* src;
+  int64_t s_r, s_c;
+  bool tr;
+  __device__ __forceinline__ double at(int i, int j) const {
+    return tr ? src[(int64_t)j * s_r + (int64_t)i * s_c] : src[(int64_t)i * s_r + (int64_t)j * s_c];
+  }
+};
+
+// Mixed-precision one-sided Jacobi SVD of the p x q (p >= q) matrix A given by `a`:
+//  1. FP32 sweeps on a copy (FP32 runs far faster than FP64 on this part) until converged at
+//     FP32 accuracy, accumulating V32;
+//  2. optional certified early exit: with the FP32 singular values sorted, if the Frobenius
+//     tail beyond `dense_h` exceeds eps by more than a bound on the FP32 backward error
+//     (2 (sweeps + 1) q u_32 ||A||_F), the eps-rank exceeds dense_h for certain: return 1;
+//  3. FP64 refinement: V = V32 orthonormalised in FP64 (modified Gram-Schmidt), G = A V in
+//     FP64, and FP64 sweeps continuing on (G, V) -- one to three sweeps from this start.
+// On return 0, g = U S and A = g v^T in FP64 (the same result as FP64 Jacobi from scratch, up
+// to rounding).  g (p x q doubles) also serves as the FP32 scratch (p q + q^2 floats).
+__device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, int max_sweeps,
+                         double eps, int dense_h, double fro, SvdShared& sh) {
+  float* g32 = reinterpret_cast<float*>(g);
+  float* v32 = g32 + (int64_t)p * q;
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  for (int e = threadIdx.x; e < p * q; e += kThreads) g32[e] = (float)a.at(e % p, e / p);
+  __syncthreads();
+  const int sw32 = jacobi_svd<float>(g32, p, q, p, v32, q, max_sweeps, &sh.flag, true, 4.0f);
+  if (dense_h >= 0) {
+    for (int c = w; c < q; c += kWarps) {
+      const float* gc = g32 + (int64_t)c * p;
+      double s2 = 0.0;
+      for (int i = l; i < p; i += 32) s2 = fma((double)gc[i], (double)gc[i], s2);
+      s2 = warp_sum(s2);
+      if (l == 0) sh.sigma[c] = s2;
+    }
+    __syncthreads();
+    // tail beyond dense_h of the sorted squared norms = total minus the dense_h largest
+    double mine_total = 0.0, mine_top = 0.0;
+    for (int c = threadIdx.x; c < q; c += kThreads) {
+      int above = 0;
+      for (int d = 0; d < q; ++d)
+        above += sh.sigma[d] > sh.sigma[c] || (sh.sigma[d] == sh.sigma[c] && d < c);
+      mine_total += sh.sigma[c];
+      if (above < dense_h) mine_top += sh.sigma[c];
+    }
+    const double total = block_sum(mine_total, sh.red);
+    const double top = block_sum(mine_top, sh.red);
+    if (threadIdx.x == 0) {
+      const double tail = sqrt(fmax(total - top, 0.0));
+      const double delta = 2.0 * (sw32 + 1) * q * (double)FLT_EPSILON * fro;
+      sh.flag = tail - delta > eps ? 1 : 0;
+    }
+    __syncthreads();
+    const int dense = sh.flag;
+    __syncthreads();
+    if (dense) return 1;
+  }
+  // FP64 refinement
+  for (int e = threadIdx.x; e < q * q; e += kThreads) v[e] = (double)v32[e];
+  __syncthreads();
+  for (int j = 0; j < q; ++j) {
+    double* vj = v + (int64_t)j * q;
+    double part = 0.0;
+    for (int i = threadIdx.x; i < q; i += kThreads) part = fma(vj[i], vj[i], part);
+    const double nrm = sqrt(block_sum(part, sh.red));
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int i = threadIdx.x; i < q; i += kThreads) vj[i] *= inv;
+    __syncthreads();
+    for (int k = j + 1 + w; k < q; k += kWarps) {
+      double* vk = v + (int64_t)k * q;
+      double d = 0.0;
+      for (int i = l; i < q; i += 32) d = fma(vj[i], vk[i], d);
+      d = warp_sum(d);
+      for (int i = l; i < q; i += 32) vk[i] = fma(-d, vj[i], vk[i]);
+    }
+    __syncthreads();
+  }
+  for (int e = threadIdx.x; e < p * q; e += kThreads) {
+    const int i = e % p, j = e / p;
+    const double* vj = v + (int64_t)j * q;
+    double s2 = 0.0;
+    for (int k = 0; k < q; ++k) s2 = fma(a.at(i, k), vj[k], s2);
+    g[e] = s2;
+  }
+  __syncthreads();
+  jacobi_svd<double>(g, p, q, p, v, q, max_sweeps, &sh.flag, false);
+  return 0;
+}
+
 // ---------------------------------------------------------------------------------------------
 // ROUTE_QR tiles: X_cat (m x R) and W_cat (n x R) in the workspace slot.
 // ---------------------------------------------------------------------------------------------
@@ -248,6 +347,7 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
     double* tauW = tauX + R;
     double* M = tauW + R;
     double* V = M + (int64_t)R * R;
+    double* G = V + (int64_t)R * R;
     householder_qr(Xc, m, R, m, tauX, sh.red);
     householder_qr(Wc, n, R, n, tauW, sh.red);
     // M = R_X R_W^T (both upper triangular R x R)
@@ -259,14 +359,17 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
       M[e] = s;
     }
     __syncthreads();
-    jacobi_svd(M, R, R, R, V, R, max_sweeps, &sh.flag);
-    sort_and_truncate(M, R, R, R, eps, sh);
+    {
+      SrcView mv{M, 1, R, false};
+      svd_mixed(mv, R, R, G, V, max_sweeps, eps, -1, 0.0, sh);
+    }
+    sort_and_truncate(G, R, R, R, eps, sh);
     const int r = sh.rank;
     double* Xo = C.pool + sC;
     double* Wo = Xo + (int64_t)m * r;
     for (int e = threadIdx.x; e < m * r; e += kThreads) {
       const int i = e % m, c = e / m;
-      Xo[e] = i < R ? M[i + (int64_t)sh.perm[c] * R] : 0.0;
+      Xo[e] = i < R ? G[i + (int64_t)sh.perm[c] * R] : 0.0;
     }
     for (int e = threadIdx.x; e < n * r; e += kThreads) {
       const int j = e % n, c = e / n;
@@ -312,7 +415,7 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
     const int64_t s_c = src ? 1 : m;
     const bool tr = m < n;
     const int p = tr ? n : m, q = tr ? m : n;
-    double* G = ws + 2 * sC;             // p x q, ld p
+    double* G = ws + 2 * sC;             // p x q, ld p (also the FP32 scratch)
     double* V = G + (int64_t)m * n;      // q x q, ld q
     double part = 0.0;
     for (int e = threadIdx.x; e < m * n; e += kThreads) {
@@ -320,7 +423,6 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
       if (src) { i = e / n; j = e % n; } else { i = e % m; j = e / m; }
       const double x = S[i * s_r + j * s_c];
       part = fma(x, x, part);
-      if (tr) G[j + (int64_t)i * p] = x; else G[i + (int64_t)j * p] = x;
     }
     const double nsq = block_sum(part, sh.red);
     if (!isfinite(nsq)) {
@@ -328,7 +430,7 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
     }
     const double nrm = sqrt(nsq);
     int kind;
-    if (!(nrm >= drop_norm) || nsq == 0.0) {
+    if (!(nrm >= drop_norm) || nsq == 0.0 || !isfinite(nsq)) {
       kind = CLR_KIND_ZERO;
       if (threadIdx.x == 0) { C.kind[t] = kind; C.rank[t] = 0; C.norm[t] = 0.0; }
       __syncthreads();
@@ -336,9 +438,12 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
     }
     int r = q;
     if (!dense_only) {
-      jacobi_svd(G, p, q, p, V, q, max_sweeps, &sh.flag);
-      sort_and_truncate(G, p, q, p, eps, sh);
-      r = sh.rank;
+      const SrcView view{S, s_r, s_c, tr};
+      const int early_dense = svd_mixed(view, p, q, G, V, max_sweeps, eps, q / 2, nrm, sh);
+      if (!early_dense) {
+        sort_and_truncate(G, p, q, p, eps, sh);
+        r = sh.rank;
+      }
     }
     const int lim = q / 2;
     if (r == 0) {
