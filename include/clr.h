@@ -63,6 +63,7 @@ extern "C" {
 typedef struct clr_ctx_s* clr_ctx_t;
 typedef struct clr_mat_s* clr_mat_t;
 typedef struct clr_tape_s* clr_tape_t;
+typedef struct clr_batch_s* clr_batch_t;
 
 /* Options of a context.  Fill with clr_opts_default() and override fields. */
 typedef struct clr_opts {
@@ -175,12 +176,37 @@ int clr_mat_free(clr_ctx_t ctx, clr_mat_t m);
  * clusters (else CLR_EINVAL).
  * clr_multiply: allocates C.  clr_multiply_into: C must have A's row clusters and B's column
  *   clusters and must not be A or B; no host synchronisation unless `stats` is non-NULL.
- * clr_multiply_batched: n independent products issued together on one stream. */
+ * clr_multiply_batched: n independent products in one CUDA graph launch (see clr_batch_*;
+ *   tuned when the precision is CLR_PREC_AUTO); the outputs are new handles for the caller. */
 int clr_multiply(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t* c, void* stream);
 int clr_multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double alpha,
                       clr_product_stats* stats, void* stream);
 int clr_multiply_batched(clr_ctx_t ctx, int n, const clr_mat_t* a, const clr_mat_t* b,
                          clr_mat_t* c, void* stream);
+
+/* ---- batched products in one CUDA graph, and the autotuner ------------------------------
+ * clr_batch_create: n independent products C_i = A_i B_i (uneven sizes, clusters and ranks),
+ *   product i truncated at eps[i] (eps NULL: the context's eps_lr).  Allocates the outputs, picks each product's launch configuration (with tune_on: the
+ *   autotuner measures every allowed precision -- the configured one, or under CLR_PREC_AUTO
+ *   each mode whose error model meets eps_lr -- times 1, 2 or 4 CTAs per SM for the low-rank
+ *   and recompression kernels, once per shape key, and keeps the fastest), runs each product
+ *   once to size its workspaces, and captures all of them into one CUDA graph whose products
+ *   run on up to 4 parallel branches with their own workspaces (longest-first assignment).
+ *   Synchronises `stream`.  The inputs must stay alive and unchanged while the batch exists.
+ * clr_batch_run: one graph launch computing every product on `stream` (replayable).
+ * clr_batch_output: the i-th output (owned by the batch until clr_batch_free).
+ * clr_batch_tuning: the chosen precision, CTAs per SM and branch of product i.
+ * clr_autotune_save / clr_autotune_load: the autotuner's cache as a text file (one line per
+ *   shape key: key precision ctas_per_sm ms); clr_autotune_entries: cache size. */
+int clr_batch_create(clr_ctx_t ctx, int n, const clr_mat_t* a, const clr_mat_t* b,
+                     const double* eps, int tune_on, void* stream, clr_batch_t* out);
+int clr_batch_run(clr_ctx_t ctx, clr_batch_t batch, void* stream);
+int clr_batch_output(clr_batch_t batch, int i, clr_mat_t* c);
+int clr_batch_tuning(clr_batch_t batch, int i, int* precision, int* ctas_per_sm, int* branch);
+int clr_batch_free(clr_ctx_t ctx, clr_batch_t batch);
+int clr_autotune_save(clr_ctx_t ctx, const char* path);
+int clr_autotune_load(clr_ctx_t ctx, const char* path);
+int clr_autotune_entries(clr_ctx_t ctx);
 
 /* ---- CLR linear combination (low-rank addition, Section 4.1, Eq. lr_addition) ------------
  * out = a X + b Y + diag I.  A block present in one operand only is scaled exactly; a block

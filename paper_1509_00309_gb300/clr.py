@@ -95,6 +95,16 @@ _SIGNATURES = {
     "clr_matvec": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "clr_block_compress_noalloc": (C.c_int, [C.c_int, _VP, C.c_int64, C.c_int, C.c_int,
                                              C.c_double, C.c_int, _VP, _VP, _VP, _VP, _VP]),
+    "clr_batch_create": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP, C.c_int, _VP,
+                                   C.POINTER(_VP)]),
+    "clr_batch_run": (C.c_int, [_VP, _VP, _VP]),
+    "clr_batch_output": (C.c_int, [_VP, C.c_int, C.POINTER(_VP)]),
+    "clr_batch_tuning": (C.c_int, [_VP, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                                   C.POINTER(C.c_int)]),
+    "clr_batch_free": (C.c_int, [_VP, _VP]),
+    "clr_autotune_save": (C.c_int, [_VP, C.c_char_p]),
+    "clr_autotune_load": (C.c_int, [_VP, C.c_char_p]),
+    "clr_autotune_entries": (C.c_int, [_VP]),
     "clr_profile_enable": (C.c_int, [_VP, C.c_int]),
     "clr_profile_read": (C.c_int, [_VP, C.POINTER(ClrProfile)]),
 }
@@ -354,6 +364,26 @@ class Context:
         self._check(load().clr_multiply_batched(self.handle, n, ah, bh, ch, _stream(stream)))
         return [Matrix(self, ch[i], a[i].row_sizes, b[i].col_sizes) for i in range(n)]
 
+    def batch(self, a: Sequence[Matrix], b: Sequence[Matrix], eps=None, tune: bool = True,
+              stream=None) -> "Batch":
+        n = len(a)
+        ah = (C.c_void_p * n)(*[m.handle for m in a])
+        bh = (C.c_void_p * n)(*[m.handle for m in b])
+        ep = None if eps is None else np.ascontiguousarray(np.asarray(eps, dtype=np.float64))
+        h = C.c_void_p()
+        self._check(load().clr_batch_create(self.handle, n, ah, bh, _ptr(ep), int(tune),
+                                            _stream(stream), C.byref(h)))
+        return Batch(self, h.value, list(a), list(b))
+
+    def autotune_save(self, path: str):
+        self._check(load().clr_autotune_save(self.handle, path.encode()))
+
+    def autotune_load(self, path: str):
+        self._check(load().clr_autotune_load(self.handle, path.encode()))
+
+    def autotune_entries(self) -> int:
+        return load().clr_autotune_entries(self.handle)
+
     def lincomb(self, a: float, x: Matrix, b: float, y: Matrix, diag: float = 0.0,
                 out: Optional[Matrix] = None, stream=None) -> Matrix:
         out = out if out is not None else self.zeros(x.row_sizes, x.col_sizes)
@@ -410,6 +440,44 @@ def block_compress_noalloc(block, eps: float, x_out, w_out, status, sigma_out=No
                                            _stream(stream))
     if st != CLR_OK:
         raise ClrError(st, "clr_block_compress_noalloc failed")
+
+
+class Batch:
+    """Products captured into one CUDA graph (clr_batch_*); outputs are owned by the batch."""
+
+    def __init__(self, ctx: Context, handle: int, a, b):
+        self.ctx = ctx
+        self.handle = handle
+        self._inputs = (a, b)   # inputs must outlive the batch
+        self.n = len(a)
+
+    def run(self, stream=None):
+        self.ctx._check(load().clr_batch_run(self.ctx.handle, self.handle, _stream(stream)))
+
+    def output(self, i: int) -> Matrix:
+        h = C.c_void_p()
+        self.ctx._check(load().clr_batch_output(self.handle, i, C.byref(h)))
+        a, b = self._inputs
+        m = Matrix(self.ctx, h.value, a[i].row_sizes, b[i].col_sizes)
+        m.close = lambda: None    # borrowed: freed with the batch
+        return m
+
+    def tuning(self, i: int):
+        p, c, br = C.c_int(), C.c_int(), C.c_int()
+        self.ctx._check(load().clr_batch_tuning(self.handle, i, C.byref(p), C.byref(c),
+                                                C.byref(br)))
+        return {"precision": PREC_NAME[p.value], "ctas_per_sm": c.value, "branch": br.value}
+
+    def close(self):
+        if self.handle:
+            load().clr_batch_free(self.ctx.handle, self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Tape:

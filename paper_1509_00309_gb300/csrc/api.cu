@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <memory>
 #include <new>
 #include <string>
@@ -44,6 +45,24 @@ struct DevBuf {
 
 }  // namespace
 
+// Device workspaces of one product in flight (grow-only).  Batched products captured into a
+// graph run on several branches, each with its own set.
+struct WorkSet {
+  DevBuf plan_ints, triples, counters, ws, scratch, panels_a, panels_b, tile_flags;
+  void release() {
+    for (DevBuf* b : {&plan_ints, &triples, &counters, &ws, &scratch, &panels_a, &panels_b,
+                      &tile_flags})
+      b->release();
+  }
+};
+
+// Tunable launch parameters of one product, chosen by the autotuner.
+struct Tuning {
+  int prec = CLR_PREC_FP64;
+  int lr_mult = 2;     // CTAs per SM of the low-rank product and recompression kernels
+  double eps = -1.0;   // truncation threshold of this product (< 0: the context's eps_lr)
+};
+
 struct clr_ctx_s {
   int device = 0;
   clr_opts opts;
@@ -52,8 +71,12 @@ struct clr_ctx_s {
   std::string err;
   void* encode_fn = nullptr;  // cuTensorMapEncodeTiled
   // workspaces (grow-only)
-  DevBuf plan_ints, triples, counters, ws, scratch, small, panels_a, panels_b, index_rows,
-      index_cols, index_k, tile_flags, upload;
+  std::vector<std::unique_ptr<WorkSet>> wsets;
+  WorkSet* cur = nullptr;  // workspace set used by the next product
+  DevBuf small, upload;
+  bool capturing = false;
+  // autotuner cache: shape key -> tuning and measured ms
+  std::map<std::string, std::pair<Tuning, double>> tune_cache;
   PlanCounters last_counters;
   // profiling: per-product phase events
   bool prof_on = false;
@@ -90,6 +113,8 @@ struct clr_mat_s {
     return v;
   }
 };
+
+struct clr_batch_s;
 
 struct clr_tape_s {
   double alpha = 0.0;
@@ -210,11 +235,11 @@ bool same_clusters(const std::vector<int>& a, const std::vector<int>& b) { retur
 // Grow the context workspaces needed by a plan over nI x nJ tiles and nK inner clusters.
 int make_plan(clr_ctx_t ctx, int nI, int nJ, int nK, Plan* p) {
   const size_t nt = (size_t)nI * nJ;
-  CLR_CUDA(ctx->plan_ints.ensure(8 * nt * sizeof(int)));
+  CLR_CUDA(ctx->cur->plan_ints.ensure(8 * nt * sizeof(int)));
   const int64_t max_tr = (int64_t)nt * nK;
-  CLR_CUDA(ctx->triples.ensure((size_t)max_tr * sizeof(Triple)));
-  CLR_CUDA(ctx->counters.ensure(sizeof(PlanCounters)));
-  int* base = (int*)ctx->plan_ints.p;
+  CLR_CUDA(ctx->cur->triples.ensure((size_t)max_tr * sizeof(Triple)));
+  CLR_CUDA(ctx->cur->counters.ensure(sizeof(PlanCounters)));
+  int* base = (int*)ctx->cur->plan_ints.p;
   p->nI = nI;
   p->nJ = nJ;
   p->nK = nK;
@@ -226,9 +251,9 @@ int make_plan(clr_ctx_t ctx, int nI, int nJ, int nK, Plan* p) {
   p->l_lr = base + 5 * nt;
   p->l_qr = base + 6 * nt;
   p->l_dcomp = base + 7 * nt;
-  p->triples = (Triple*)ctx->triples.p;
+  p->triples = (Triple*)ctx->cur->triples.p;
   p->max_triples = max_tr;
-  p->counters = (PlanCounters*)ctx->counters.p;
+  p->counters = (PlanCounters*)ctx->cur->counters.p;
   return CLR_OK;
 }
 
@@ -237,7 +262,7 @@ int grid_of(clr_ctx_t ctx, int per_sm) { return std::max(1, ctx->n_sm * per_sm);
 enum { PH_START = -1, PH_PLAN = 0, PH_STAGE, PH_DENSE, PH_LOWRANK, PH_COMPRESS, PH_FINALIZE };
 
 void prof_mark(clr_ctx_t ctx, cudaStream_t s, int phase) {
-  if (!ctx->prof_on) return;
+  if (!ctx->prof_on || ctx->capturing) return;
   cudaEvent_t e;
   if (!ctx->event_pool.empty()) {
     e = ctx->event_pool.back();
@@ -250,21 +275,22 @@ void prof_mark(clr_ctx_t ctx, cudaStream_t s, int phase) {
 }
 
 void prof_launches(clr_ctx_t ctx, int n) {
-  if (ctx->prof_on) ctx->prof.launches += n;
+  if (ctx->prof_on && !ctx->capturing) ctx->prof.launches += n;
 }
 
 constexpr int64_t kScratchPerCta =
     (int64_t)(CLR_MAX_CLUSTER / 2) * (CLR_MAX_CLUSTER / 2) +
     (int64_t)CLR_MAX_CLUSTER * (CLR_MAX_CLUSTER / 2);
 
-int choose_precision(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b) {
+int choose_precision(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, double eps_in = -1.0) {
   int prec = ctx->opts.precision;
   if (prec != CLR_PREC_AUTO) return prec;
   // A-priori statistical error model of the split products (relative RMS error of one
   // product term, including FP32 accumulation): bf16x3 ~ 2^-16.5, bf16x6 ~ 2^-23.  The
   // expected ||dC||_F is about u ||A||_F ||B||_F / sqrt(K); the product tolerance is
   // 10 eps ||A||_F ||B||_F.  Take the cheapest mode with a factor-4 margin.
-  const double eps = ctx->opts.eps_lr > 0 ? ctx->opts.eps_lr : 1e-8;
+  const double e0 = eps_in >= 0.0 ? eps_in : ctx->opts.eps_lr;
+  const double eps = e0 > 0 ? e0 : 1e-8;
   const double sk = std::sqrt((double)a->n_cols);
   if (std::ldexp(1.0, -16) * 0.6 / sk * 4.0 <= 10.0 * eps) return CLR_PREC_BF16X3;
   if (std::ldexp(1.0, -23) / sk * 4.0 <= 10.0 * eps) return CLR_PREC_BF16X6;
@@ -335,6 +361,8 @@ extern "C" int clr_create(clr_ctx_t* out, int device, const clr_opts* opts) {
                                        cudaEnableDefault, &q);
   if (e == cudaSuccess && q == cudaDriverEntryPointSuccess) ctx->encode_fn = fn;
   std::memset(&ctx->last_counters, 0, sizeof(ctx->last_counters));
+  ctx->wsets.emplace_back(new WorkSet);
+  ctx->cur = ctx->wsets[0].get();
   *out = ctx;
   return CLR_OK;
 }
@@ -344,10 +372,9 @@ extern "C" int clr_destroy(clr_ctx_t ctx) {
   cudaSetDevice(ctx->device);
   for (auto& pe : ctx->prof_events) cudaEventDestroy(pe.first);
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
-  for (DevBuf* b : {&ctx->plan_ints, &ctx->triples, &ctx->counters, &ctx->ws, &ctx->scratch,
-                    &ctx->small, &ctx->panels_a, &ctx->panels_b, &ctx->index_rows,
-                    &ctx->index_cols, &ctx->index_k, &ctx->tile_flags, &ctx->upload})
-    b->release();
+  for (auto& w : ctx->wsets) w->release();
+  ctx->small.release();
+  ctx->upload.release();
   delete ctx;
   return CLR_OK;
 }
@@ -424,13 +451,13 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
     src = (const double*)staging.p;
     lda = m->n_cols;
   }
-  cudaError_t e = ctx->ws.ensure(2 * (size_t)m->n_rows * m->n_cols * sizeof(double));
-  if (e == cudaSuccess) e = ctx->counters.ensure(sizeof(PlanCounters));
+  cudaError_t e = ctx->cur->ws.ensure(2 * (size_t)m->n_rows * m->n_cols * sizeof(double));
+  if (e == cudaSuccess) e = ctx->cur->counters.ensure(sizeof(PlanCounters));
   if (e != cudaSuccess) {
     free_mat(m);
     return cuda_fail(ctx, e, "from_dense workspace");
   }
-  PlanCounters* pc = (PlanCounters*)ctx->counters.p;
+  PlanCounters* pc = (PlanCounters*)ctx->cur->counters.p;
   cudaMemsetAsync(pc, 0, sizeof(PlanCounters), s);
   if (eps_lr == 0.0) {
     // every kept block is dense: a coalesced layout copy, then norms decide what is dropped
@@ -438,7 +465,7 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
     launch_block_norms_dense(m->view(), s);
     launch_dense_kinds(m->view(), drop_norm, &pc->err, s);
   } else {
-    launch_compress_dense(m->view(), nullptr, nullptr, src, lda, (double*)ctx->ws.p, eps_lr,
+    launch_compress_dense(m->view(), nullptr, nullptr, src, lda, (double*)ctx->cur->ws.p, eps_lr,
                           drop_norm, 0, ctx->opts.jacobi_max_sweeps, grid_of(ctx, 2), &pc->err,
                           s);
   }
@@ -636,18 +663,15 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
   const int64_t M_pad = (c->n_rows + 127) / 128 * 128;
   const int64_t N_pad = (c->n_cols + 255) / 256 * 256;
   const int64_t K_pad = (a->n_cols + 127) / 128 * 128;  // staging tiles are 128 wide
-  CLR_CUDA(ctx->panels_a.ensure((size_t)terms * M_pad * K_pad * 2));
-  CLR_CUDA(ctx->panels_b.ensure((size_t)terms * N_pad * K_pad * 2));
-  CLR_CUDA(ctx->index_rows.ensure((size_t)c->n_rows * sizeof(int)));
-  CLR_CUDA(ctx->index_cols.ensure((size_t)c->n_cols * sizeof(int)));
-  CLR_CUDA(ctx->index_k.ensure((size_t)a->n_cols * sizeof(int)));
-  CLR_CUDA(ctx->tile_flags.ensure((size_t)(M_pad / 128) * (N_pad / 256)));
+  CLR_CUDA(ctx->cur->panels_a.ensure((size_t)terms * M_pad * K_pad * 2));
+  CLR_CUDA(ctx->cur->panels_b.ensure((size_t)terms * N_pad * K_pad * 2));
+  CLR_CUDA(ctx->cur->tile_flags.ensure((size_t)(M_pad / 128) * (N_pad / 256)));
   MatView av = a->view(), bv = b->view(), cv = c->view();
   const int* idx_m = c->d_row_idx;
   const int* idx_n = c->d_col_idx;
   const int* idx_k = a->d_col_idx;
-  launch_split_stage(av, idx_m, idx_k, ctx->panels_a.p, terms, M_pad, K_pad, 1, s);
-  launch_split_stage(bv, idx_k, idx_n, ctx->panels_b.p, terms, N_pad, K_pad, 0, s);
+  launch_split_stage(av, idx_m, idx_k, ctx->cur->panels_a.p, terms, M_pad, K_pad, 1, s);
+  launch_split_stage(bv, idx_k, idx_n, ctx->cur->panels_b.p, terms, N_pad, K_pad, 0, s);
   CLR_CHECK_LAUNCH("split staging");
   prof_launches(ctx, 2);
   prof_mark(ctx, s, PH_STAGE);
@@ -657,14 +681,14 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
   g.C = &cv;
   g.p = &p;
   g.terms = terms;
-  g.a_panels = ctx->panels_a.p;
-  g.b_panels = ctx->panels_b.p;
+  g.a_panels = ctx->cur->panels_a.p;
+  g.b_panels = ctx->cur->panels_b.p;
   g.M_pad = M_pad;
   g.N_pad = N_pad;
   g.K_pad = K_pad;
   g.row_tile_of = idx_m;
   g.col_tile_of = idx_n;
-  g.tile_active = (unsigned char*)ctx->tile_flags.p;
+  g.tile_active = (unsigned char*)ctx->cur->tile_flags.p;
   g.n_sm = ctx->n_sm;
   g.err = &p.counters->err;
   g.encode_fn = ctx->encode_fn;
@@ -686,7 +710,9 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
 }
 
 int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double alpha,
-                  int prec, clr_product_stats* stats, cudaStream_t s) {
+                  const Tuning& tune, clr_product_stats* stats, cudaStream_t s) {
+  const int prec = tune.prec;
+  const double eps_lr = tune.eps >= 0.0 ? tune.eps : ctx->opts.eps_lr;
   if (!same_clusters(a->col_sizes, b->row_sizes))
     return fail(ctx, CLR_EINVAL, "inner clusters of A and B differ");
   if (!same_clusters(c->row_sizes, a->row_sizes) || !same_clusters(c->col_sizes, b->col_sizes))
@@ -696,9 +722,9 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   Plan p;
   int st = make_plan(ctx, a->nr, b->nc, a->nc, &p);
   if (st) return st;
-  CLR_CUDA(ctx->ws.ensure(2 * (size_t)c->n_rows * c->n_cols * sizeof(double)));
-  const int lr_grid = grid_of(ctx, 2);
-  CLR_CUDA(ctx->scratch.ensure((size_t)lr_grid * kScratchPerCta * sizeof(double)));
+  CLR_CUDA(ctx->cur->ws.ensure(2 * (size_t)c->n_rows * c->n_cols * sizeof(double)));
+  const int lr_grid = grid_of(ctx, tune.lr_mult);
+  CLR_CUDA(ctx->cur->scratch.ensure((size_t)lr_grid * kScratchPerCta * sizeof(double)));
   MatView av = a->view(), bv = b->view(), cv = c->view();
   const clr_opts& o = ctx->opts;
   prof_mark(ctx, s, PH_START);
@@ -717,16 +743,15 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
     st = run_split_dd(ctx, a, b, c, p, prec, s);
     if (st) return st;
   }
-  launch_lr_products(av, bv, cv, p, (double*)ctx->ws.p, (double*)ctx->scratch.p,
+  launch_lr_products(av, bv, cv, p, (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p,
                      kScratchPerCta, lr_grid, s);
   CLR_CHECK_LAUNCH("low-rank products");
   prof_launches(ctx, 1);
   prof_mark(ctx, s, PH_LOWRANK);
-  launch_compress_qr(cv, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->ws.p, o.eps_lr,
-                     o.jacobi_max_sweeps, grid_of(ctx, 2), &p.counters->err, s);
-  launch_compress_dense(cv, p.l_dcomp, &p.counters->n_dcomp, nullptr, 0, (double*)ctx->ws.p,
-                        o.eps_lr, 0.0, 0, o.jacobi_max_sweeps, grid_of(ctx, 2),
-                        &p.counters->err, s);
+  launch_compress_qr(cv, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p, eps_lr,
+                     o.jacobi_max_sweeps, lr_grid, &p.counters->err, s);
+  launch_compress_dense(cv, p.l_dcomp, &p.counters->n_dcomp, nullptr, 0, (double*)ctx->cur->ws.p,
+                        eps_lr, 0.0, 0, o.jacobi_max_sweeps, lr_grid, &p.counters->err, s);
   CLR_CHECK_LAUNCH("recompression");
   prof_launches(ctx, 2);
   prof_mark(ctx, s, PH_COMPRESS);
@@ -800,8 +825,9 @@ extern "C" int clr_multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_ma
                                  double alpha, clr_product_stats* stats, void* stream) {
   if (!ctx || !a || !b || !c) return CLR_EINVAL;
   cudaSetDevice(ctx->device);
-  return multiply_into(ctx, a, b, c, alpha, choose_precision(ctx, a, b), stats,
-                       as_stream(stream));
+  Tuning t;
+  t.prec = choose_precision(ctx, a, b);
+  return multiply_into(ctx, a, b, c, alpha, t, stats, as_stream(stream));
 }
 
 extern "C" int clr_multiply(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t* c,
@@ -812,30 +838,14 @@ extern "C" int clr_multiply(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t* 
   clr_mat_t out = nullptr;
   int st = alloc_mat(ctx, a->nr, a->row_sizes.data(), b->nc, b->col_sizes.data(), &out);
   if (st) return st;
-  st = multiply_into(ctx, a, b, out, 1.0, choose_precision(ctx, a, b), nullptr,
-                     as_stream(stream));
+  Tuning t;
+  t.prec = choose_precision(ctx, a, b);
+  st = multiply_into(ctx, a, b, out, 1.0, t, nullptr, as_stream(stream));
   if (st) {
     free_mat(out);
     return st;
   }
   *c = out;
-  return CLR_OK;
-}
-
-extern "C" int clr_multiply_batched(clr_ctx_t ctx, int n, const clr_mat_t* a,
-                                    const clr_mat_t* b, clr_mat_t* c, void* stream) {
-  if (!ctx || n < 0 || (n > 0 && (!a || !b || !c))) return CLR_EINVAL;
-  for (int i = 0; i < n; ++i) c[i] = nullptr;
-  for (int i = 0; i < n; ++i) {
-    int st = clr_multiply(ctx, a[i], b[i], &c[i], stream);
-    if (st) {
-      for (int j = 0; j < i; ++j) {
-        free_mat(c[j]);
-        c[j] = nullptr;
-      }
-      return st;
-    }
-  }
   return CLR_OK;
 }
 
@@ -855,13 +865,13 @@ extern "C" int clr_lincomb(clr_ctx_t ctx, double a, clr_mat_t x, double b, clr_m
   Plan p;
   int st = make_plan(ctx, x->nr, x->nc, 1, &p);
   if (st) return st;
-  CLR_CUDA(ctx->ws.ensure(2 * (size_t)x->n_rows * x->n_cols * sizeof(double)));
+  CLR_CUDA(ctx->cur->ws.ensure(2 * (size_t)x->n_rows * x->n_cols * sizeof(double)));
   const clr_opts& o = ctx->opts;
   MatView xv = x->view(), yv = y->view(), ov = out->view();
-  launch_lincomb_plan(a, xv, b, yv, diag, ov, p, (double*)ctx->ws.p, o.recompress_dense, s);
-  launch_compress_qr(ov, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->ws.p, o.eps_lr,
+  launch_lincomb_plan(a, xv, b, yv, diag, ov, p, (double*)ctx->cur->ws.p, o.recompress_dense, s);
+  launch_compress_qr(ov, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p, o.eps_lr,
                      o.jacobi_max_sweeps, grid_of(ctx, 2), &p.counters->err, s);
-  launch_compress_dense(ov, p.l_dcomp, &p.counters->n_dcomp, nullptr, 0, (double*)ctx->ws.p,
+  launch_compress_dense(ov, p.l_dcomp, &p.counters->n_dcomp, nullptr, 0, (double*)ctx->cur->ws.p,
                         o.eps_lr, 0.0, 0, o.jacobi_max_sweeps, grid_of(ctx, 2),
                         &p.counters->err, s);
   CLR_CHECK_LAUNCH("lincomb");
@@ -982,10 +992,11 @@ extern "C" int clr_ns_residual(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t z, doub
   st = alloc_mat(ctx, z->nr, z->row_sizes.data(), z->nc, z->col_sizes.data(), &zsz);
   if (st) return st;
   g.v.push_back(zsz);
-  const int prec = choose_precision(ctx, z, s_mat);
-  st = multiply_into(ctx, z, s_mat, zs, 1.0, prec, nullptr, s);
+  Tuning t;
+  t.prec = choose_precision(ctx, z, s_mat);
+  st = multiply_into(ctx, z, s_mat, zs, 1.0, t, nullptr, s);
   if (st) return st;
-  st = multiply_into(ctx, zs, z, zsz, 1.0, prec, nullptr, s);
+  st = multiply_into(ctx, zs, z, zsz, 1.0, t, nullptr, s);
   if (st) return st;
   return identity_distance(ctx, zsz, s, out);
 }
@@ -1034,13 +1045,15 @@ extern "C" int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t* z_out,
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
-  int prec = choose_precision(ctx, s_mat, s_mat);
+  Tuning tn;
+  tn.prec = choose_precision(ctx, s_mat, s_mat);
+  int& prec = tn.prec;
   int it = 0;
   bool converged = false;
   std::vector<double> proxies;
   std::vector<int> precs;
   while (true) {
-    st = multiply_into(ctx, Y, Z, X, alpha, prec, nullptr, s);
+    st = multiply_into(ctx, Y, Z, X, alpha, tn, nullptr, s);
     if (st) break;
     double px = 0.0;
     st = identity_distance(ctx, X, s, &px);
@@ -1067,13 +1080,13 @@ extern "C" int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t* z_out,
       tape->z.push_back(zc);
       if ((st = clr_mat_copy(ctx, Y, yc, s)) || (st = clr_mat_copy(ctx, Z, zc, s))) break;
     }
-    st = multiply_into(ctx, X, X, X2, 1.0, prec, nullptr, s);
+    st = multiply_into(ctx, X, X, X2, 1.0, tn, nullptr, s);
     if (st) break;
     st = clr_lincomb(ctx, -10.0 / 8.0, X, 3.0 / 8.0, X2, 15.0 / 8.0, T, s);
     if (st) break;
-    st = multiply_into(ctx, Z, T, Zn, 1.0, prec, nullptr, s);
+    st = multiply_into(ctx, Z, T, Zn, 1.0, tn, nullptr, s);
     if (st) break;
-    st = multiply_into(ctx, T, Y, Yn, 1.0, prec, nullptr, s);
+    st = multiply_into(ctx, T, Y, Yn, 1.0, tn, nullptr, s);
     if (st) break;
     std::swap(Z, Zn);
     std::swap(Y, Yn);
@@ -1163,9 +1176,10 @@ extern "C" int clr_sqrt_inv_backward(clr_ctx_t ctx, clr_tape_t tape, clr_mat_t z
     g.v.push_back(m[i]);
   }
   const double alpha = tape->alpha;
-  const int prec = choose_precision(ctx, tape->s, tape->s);
+  Tuning tn;
+  tn.prec = choose_precision(ctx, tape->s, tape->s);
   auto mul = [&](clr_mat_t a, clr_mat_t b, clr_mat_t c, double sc) {
-    return multiply_into(ctx, a, b, c, sc, prec, nullptr, s);
+    return multiply_into(ctx, a, b, c, sc, tn, nullptr, s);
   };
   auto tr = [&](clr_mat_t a, clr_mat_t t) {
     launch_transpose(a->view(), t->view(), s);
@@ -1205,4 +1219,299 @@ extern "C" int clr_sqrt_inv_backward(clr_ctx_t ctx, clr_tape_t tape, clr_mat_t z
   }
   *sbar = g.keep(m[YB]);
   return CLR_OK;
+}
+
+// =============================================================================================
+// Autotuner and batched products
+// =============================================================================================
+namespace {
+
+// Shape key of a product: sizes, cluster counts, block-kind counts of both operands and the
+// truncation threshold.  Reads the operands' kinds (synchronises the stream).
+int shape_key(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, double eps, cudaStream_t s,
+              std::string* key) {
+  std::vector<int> ka((size_t)a->nr * a->nc), kb((size_t)b->nr * b->nc);
+  CLR_CUDA(cudaMemcpyAsync(ka.data(), a->d_kind, ka.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLR_CUDA(cudaMemcpyAsync(kb.data(), b->d_kind, kb.size() * sizeof(int), cudaMemcpyDeviceToHost, s));
+  CLR_CUDA(cudaStreamSynchronize(s));
+  long long cnt[2][3] = {{0, 0, 0}, {0, 0, 0}};
+  for (int k : ka) cnt[0][k & 3 ? (k < 3 ? k : 0) : 0]++;
+  for (int k : kb) cnt[1][k & 3 ? (k < 3 ? k : 0) : 0]++;
+  char buf[256];
+  snprintf(buf, sizeof(buf), "%lldx%lldx%lld/%dx%dx%d/d%lld,%lld/l%lld,%lld/e%.3g/s%.3g",
+           (long long)a->n_rows, (long long)a->n_cols, (long long)b->n_cols, a->nr, a->nc, b->nc,
+           cnt[0][1], cnt[1][1], cnt[0][2], cnt[1][2], eps, ctx->opts.eps_sp);
+  *key = buf;
+  return CLR_OK;
+}
+
+// Candidate precisions: the configured one, or under CLR_PREC_AUTO every mode whose a-priori
+// error model meets the tolerance (FP64 always does).
+std::vector<int> precision_candidates(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, double eps) {
+  if (ctx->opts.precision != CLR_PREC_AUTO) return {ctx->opts.precision};
+  const int cheapest = choose_precision(ctx, a, b, eps);
+  std::vector<int> out;
+  if (cheapest == CLR_PREC_BF16X3) out.push_back(CLR_PREC_BF16X3);
+  if (cheapest != CLR_PREC_FP64) out.push_back(CLR_PREC_BF16X6);
+  out.push_back(CLR_PREC_FP64);
+  return out;
+}
+
+int time_product(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Tuning& t,
+                 cudaStream_t s, double* ms) {
+  int st = multiply_into(ctx, a, b, c, 1.0, t, nullptr, s);  // warm-up (also sizes workspaces)
+  if (st) return st;
+  cudaEvent_t e0, e1;
+  CLR_CUDA(cudaEventCreate(&e0));
+  CLR_CUDA(cudaEventCreate(&e1));
+  cudaEventRecord(e0, s);
+  st = multiply_into(ctx, a, b, c, 1.0, t, nullptr, s);
+  cudaEventRecord(e1, s);
+  cudaError_t e = cudaEventSynchronize(e1);
+  float f = 0.f;
+  if (e == cudaSuccess) e = cudaEventElapsedTime(&f, e0, e1);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st) return st;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "autotune timing");
+  *ms = f;
+  return CLR_OK;
+}
+
+// Fastest (precision, CTAs per SM) for this shape, measured once per shape key and cached.
+int autotune(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double eps,
+             cudaStream_t s, Tuning* out) {
+  std::string key;
+  int st = shape_key(ctx, a, b, eps, s, &key);
+  if (st) return st;
+  auto it = ctx->tune_cache.find(key);
+  if (it != ctx->tune_cache.end()) {
+    *out = it->second.first;
+    out->eps = eps;
+    return CLR_OK;
+  }
+  Tuning best;
+  double best_ms = -1.0;
+  for (int prec : precision_candidates(ctx, a, b, eps))
+    for (int mult : {1, 2, 4}) {
+      Tuning t;
+      t.prec = prec;
+      t.lr_mult = mult;
+      t.eps = eps;
+      double ms = 0.0;
+      st = time_product(ctx, a, b, c, t, s, &ms);
+      if (st) return st;
+      if (best_ms < 0.0 || ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+  ctx->tune_cache[key] = {best, best_ms};
+  *out = best;
+  return CLR_OK;
+}
+
+}  // namespace
+
+extern "C" int clr_autotune_save(clr_ctx_t ctx, const char* path) {
+  if (!ctx || !path) return CLR_EINVAL;
+  FILE* f = fopen(path, "w");
+  if (!f) return fail(ctx, CLR_EINVAL, "cannot open autotune file for writing");
+  for (auto& kv : ctx->tune_cache)
+    fprintf(f, "%s %d %d %.6f\n", kv.first.c_str(), kv.second.first.prec,
+            kv.second.first.lr_mult, kv.second.second);
+  fclose(f);
+  return CLR_OK;
+}
+
+extern "C" int clr_autotune_load(clr_ctx_t ctx, const char* path) {
+  if (!ctx || !path) return CLR_EINVAL;
+  FILE* f = fopen(path, "r");
+  if (!f) return fail(ctx, CLR_EINVAL, "cannot open autotune file");
+  char key[256];
+  int prec = 0, mult = 0;
+  double ms = 0.0;
+  int n = 0;
+  while (fscanf(f, "%255s %d %d %lf", key, &prec, &mult, &ms) == 4) {
+    if (prec < 0 || prec > 2 || mult < 1 || mult > 8) continue;
+    Tuning t;
+    t.prec = prec;
+    t.lr_mult = mult;
+    ctx->tune_cache[key] = {t, ms};
+    ++n;
+  }
+  fclose(f);
+  return n >= 0 ? CLR_OK : CLR_EINVAL;
+}
+
+extern "C" int clr_autotune_entries(clr_ctx_t ctx) {
+  return ctx ? (int)ctx->tune_cache.size() : CLR_EINVAL;
+}
+
+struct clr_batch_s {
+  int n = 0;
+  std::vector<clr_mat_t> a, b, c;
+  std::vector<Tuning> tune;
+  std::vector<int> branch;
+  std::vector<std::unique_ptr<WorkSet>> wsets;  // one per branch, owned by the batch
+  std::vector<cudaStream_t> streams;            // origin + branches
+  std::vector<cudaEvent_t> events;              // fork + joins
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  ~clr_batch_s() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    for (cudaEvent_t e : events) cudaEventDestroy(e);
+    for (cudaStream_t s : streams) cudaStreamDestroy(s);
+    for (auto& w : wsets) w->release();
+    for (clr_mat_t m : c) free_mat(m);
+  }
+};
+
+extern "C" int clr_batch_create(clr_ctx_t ctx, int n, const clr_mat_t* a, const clr_mat_t* b,
+                                const double* eps, int tune_on, void* stream, clr_batch_t* out) {
+  if (!ctx || n < 1 || !a || !b || !out) return CLR_EINVAL;
+  *out = nullptr;
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  std::unique_ptr<clr_batch_s> bt(new (std::nothrow) clr_batch_s);
+  if (!bt) return fail(ctx, CLR_ENOMEM, "host allocation");
+  bt->n = n;
+  for (int i = 0; i < n; ++i) {
+    if (!a[i] || !b[i]) return CLR_EINVAL;
+    if (a[i]->col_sizes != b[i]->row_sizes)
+      return fail(ctx, CLR_EINVAL, "batch: inner clusters of A and B differ");
+    bt->a.push_back(a[i]);
+    bt->b.push_back(b[i]);
+    clr_mat_t ci = nullptr;
+    int st = alloc_mat(ctx, a[i]->nr, a[i]->row_sizes.data(), b[i]->nc, b[i]->col_sizes.data(), &ci);
+    if (st) return st;
+    bt->c.push_back(ci);
+  }
+  // tuning (uncaptured, on the context's own workspaces)
+  WorkSet* saved = ctx->cur;
+  for (int i = 0; i < n; ++i) {
+    const double ei = eps ? eps[i] : ctx->opts.eps_lr;
+    if (!(ei >= 0.0)) return fail(ctx, CLR_EINVAL, "batch: eps must be >= 0");
+    Tuning t;
+    t.prec = choose_precision(ctx, a[i], b[i], ei);
+    t.eps = ei;
+    if (tune_on) {
+      int st = autotune(ctx, a[i], b[i], bt->c[i], ei, s, &t);
+      if (st) return st;
+    }
+    bt->tune.push_back(t);
+  }
+  // branches: longest-processing-time assignment on a dense-equivalent cost estimate
+  const int nb = std::min(n, 4);
+  std::vector<int> order(n);
+  for (int i = 0; i < n; ++i) order[i] = i;
+  auto cost = [&](int i) {
+    return (double)a[i]->n_rows * (double)a[i]->n_cols * (double)b[i]->n_cols;
+  };
+  std::sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+  std::vector<double> load(nb, 0.0);
+  bt->branch.assign(n, 0);
+  for (int i : order) {
+    const int br = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    bt->branch[i] = br;
+    load[br] += cost(i);
+  }
+  for (int br = 0; br < nb; ++br) bt->wsets.emplace_back(new WorkSet);
+  // size each branch's workspaces (and warm up) with one uncaptured run per product
+  for (int i = 0; i < n; ++i) {
+    ctx->cur = bt->wsets[bt->branch[i]].get();
+    int st = multiply_into(ctx, a[i], b[i], bt->c[i], 1.0, bt->tune[i], nullptr, s);
+    if (st) {
+      ctx->cur = saved;
+      return st;
+    }
+  }
+  ctx->cur = saved;
+  CLR_CUDA(cudaStreamSynchronize(s));
+  // capture every product into one graph: fork to nb branches, join on the origin stream
+  bt->streams.resize(nb + 1, nullptr);
+  for (auto& st : bt->streams) CLR_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+  bt->events.resize(nb + 1, nullptr);
+  for (auto& e : bt->events) CLR_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaStream_t origin = bt->streams[0];
+  CLR_CUDA(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+  ctx->capturing = true;
+  int st = CLR_OK;
+  cudaEventRecord(bt->events[0], origin);
+  for (int br = 0; br < nb; ++br) cudaStreamWaitEvent(bt->streams[br + 1], bt->events[0], 0);
+  for (int i = 0; i < n && !st; ++i) {
+    ctx->cur = bt->wsets[bt->branch[i]].get();
+    st = multiply_into(ctx, a[i], b[i], bt->c[i], 1.0, bt->tune[i], nullptr,
+                       bt->streams[bt->branch[i] + 1]);
+  }
+  for (int br = 0; br < nb; ++br) {
+    cudaEventRecord(bt->events[br + 1], bt->streams[br + 1]);
+    cudaStreamWaitEvent(origin, bt->events[br + 1], 0);
+  }
+  ctx->capturing = false;
+  ctx->cur = saved;
+  cudaError_t e = cudaStreamEndCapture(origin, &bt->graph);
+  if (st) return st;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch capture");
+  e = cudaGraphInstantiate(&bt->exec, bt->graph, 0);
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "batch graph instantiate");
+  *out = bt.release();
+  return CLR_OK;
+}
+
+extern "C" int clr_batch_run(clr_ctx_t ctx, clr_batch_t batch, void* stream) {
+  if (!ctx || !batch || !batch->exec) return CLR_EINVAL;
+  cudaSetDevice(ctx->device);
+  CLR_CUDA(cudaGraphLaunch(batch->exec, as_stream(stream)));
+  return CLR_OK;
+}
+
+extern "C" int clr_batch_output(clr_batch_t batch, int i, clr_mat_t* c) {
+  if (!batch || !c || i < 0 || i >= batch->n) return CLR_EINVAL;
+  *c = batch->c[i];
+  return CLR_OK;
+}
+
+extern "C" int clr_batch_tuning(clr_batch_t batch, int i, int* precision, int* lr_mult,
+                                int* branch) {
+  if (!batch || i < 0 || i >= batch->n) return CLR_EINVAL;
+  if (precision) *precision = batch->tune[i].prec;
+  if (lr_mult) *lr_mult = batch->tune[i].lr_mult;
+  if (branch) *branch = batch->branch[i];
+  return CLR_OK;
+}
+
+extern "C" int clr_batch_free(clr_ctx_t ctx, clr_batch_t batch) {
+  if (!batch) return CLR_EINVAL;
+  if (ctx) cudaSetDevice(ctx->device);
+  for (cudaStream_t s : batch->streams) cudaStreamSynchronize(s);
+  delete batch;
+  return CLR_OK;
+}
+
+extern "C" int clr_multiply_batched(clr_ctx_t ctx, int n, const clr_mat_t* a,
+                                    const clr_mat_t* b, clr_mat_t* c, void* stream) {
+  // one graph launch for all n products (tuned when precision is CLR_PREC_AUTO); the outputs
+  // are handed to the caller
+  if (!ctx || n < 0 || (n > 0 && (!a || !b || !c))) return CLR_EINVAL;
+  for (int i = 0; i < n; ++i) c[i] = nullptr;
+  if (n == 0) return CLR_OK;
+  clr_batch_t bt = nullptr;
+  int st = clr_batch_create(ctx, n, a, b, nullptr, ctx->opts.precision == CLR_PREC_AUTO, stream,
+                            &bt);
+  if (st) return st;
+  st = clr_batch_run(ctx, bt, stream);
+  if (st == CLR_OK) {
+    cudaError_t e = cudaStreamSynchronize(as_stream(stream));
+    if (e != cudaSuccess) st = cuda_fail(ctx, e, "batched products");
+  }
+  if (st == CLR_OK)
+    for (int i = 0; i < n; ++i) {
+      c[i] = bt->c[i];
+      bt->c[i] = nullptr;
+    }
+  bt->c.clear();
+  clr_batch_free(ctx, bt);
+  return st;
 }

@@ -456,11 +456,18 @@ int launch_terms(const SplitGemmArgs& a, const CUtensorMap& tmA, const CUtensorM
                  const Epi& epi, int n_m, int n_n, int num_k, cudaStream_t st,
                  std::string* why) {
   const uint32_t smem = Cfg<TERMS>::SMEM_TOTAL;
-  cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<TERMS>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) {
-    if (why) *why = cudaGetErrorString(e);
-    return CLR_ECUDA;
+  // set once per device (outside any stream capture the first time a product runs)
+  static bool attr_done[64] = {false};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64 || !attr_done[dev]) {
+    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<TERMS>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) {
+      if (why) *why = cudaGetErrorString(e);
+      return CLR_ECUDA;
+    }
+    if (dev >= 0 && dev < 64) attr_done[dev] = true;
   }
   const int grid = std::max(1, std::min(a.n_sm, n_m * n_n));
   split_gemm_kernel<TERMS><<<grid, THREADS, smem, st>>>(tmA, tmB, epi, n_m, n_n, num_k,
