@@ -50,6 +50,8 @@ def parse():
     ap.add_argument("--clusters", type=int, default=96)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-ns", action="store_true")
+    ap.add_argument("--ns-prec", default="bf16x6", choices=["bf16x3", "bf16x6", "fp64"])
     return ap.parse_args()
 
 
@@ -349,6 +351,29 @@ def run_ours(args):
                "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8,
                "ms_per_step": 1e3 * el / e2e_steps}
 
+    # Newton-Schulz S^-1/2 on the 1D-chain overlap matrix (N = 2048, 16 uneven clusters,
+    # eps_lr = 1e-8): ms per iteration to ||X_n - I||_F/sqrt(N) <= 1e-6, split-precision
+    # products with FP64 products once the proxy drops below 1e-3 (precision ladder)
+    ns = None
+    if not args.no_ns:
+        from paper_1509_00309_gb300 import workloads as wl
+        wn = wl.chain_overlap()
+        nctx = clr.Context(torch.cuda.current_device(), precision=args.ns_prec,
+                           eps_lr=wn.eps_lr, ns_tol=1e-6, ns_max_iter=60, ns_fp64_tail=1,
+                           ns_ladder_switch=1e-3)
+        sm = nctx.from_dense(torch.from_numpy(wn.a).cuda(), wn.row_sizes, eps_lr=wn.eps_lr,
+                             drop_norm=wn.drop_norm)
+        nctx.sqrt_inv(sm, allow_noconv=True)   # warm-up
+        torch.cuda.synchronize()
+        z, nst, _ = nctx.sqrt_inv(sm, allow_noconv=True)
+        it = max(1, nst["iters"])
+        ns = {"workload": "1D-chain overlap N=2048, 16 uneven clusters, eps_lr=1e-8",
+              "ms_per_iteration": nst["ms_total"] / it, "iterations": nst["iters"],
+              "converged": nst["converged"], "proxy_final": nst["proxy"][-1],
+              "residual_ZSZ_minus_I_rms": nst["residual"], "tol": 1e-6,
+              "precision": "%s, fp64 below proxy 1e-3" % args.ns_prec,
+              "z_blocks_zero_dense_lr": z.info()["n_blocks"]}
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         fl, el, rows = oracle_sample(w, 15.0)
@@ -364,7 +389,7 @@ def run_ours(args):
                 "dtype": args.prec, "data": "synthetic",
                 "config": config(args, {"error": err, "phases_ms_per_step": phases,
                                         "algorithmic_flops_per_step": alg_flops}),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ns": ns,
                 "gpu_launches": int(prof["launches"]), "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if ws > 1:

@@ -60,7 +60,8 @@ __device__ __forceinline__ unsigned short round_bf16(long long R, int s, long lo
 // rounding bias to the FP64 bit pattern and clearing the 45 low bits (carries into the exponent
 // are exact), the residual a - a_0 as an integer multiple of a's ulp; the lower terms, and the
 // whole split outside that range, by the generic integer rounding above.
-__device__ __forceinline__ void split_bf16(double x, int terms, unsigned short* out) {
+template <int TERMS>
+__device__ __forceinline__ void split_bf16(double x, unsigned short (&out)[TERMS]) {
   const unsigned long long u = (unsigned long long)__double_as_longlong(x);
   const int E = (int)((u >> 52) & 0x7FF);
   if (E >= 1023 - 110 && E <= 1023 + 126) {
@@ -68,12 +69,13 @@ __device__ __forceinline__ void split_bf16(double x, int terms, unsigned short* 
     const unsigned hi0 = (unsigned)(u0 >> 32);
     const unsigned E0 = (hi0 >> 20) & 0x7FFu;
     out[0] = (unsigned short)(((hi0 >> 16) & 0x8000u) | ((E0 - 896u) << 7) | ((hi0 >> 13) & 0x7Fu));
-    if (terms == 1) return;
+    if (TERMS == 1) return;
     const long long M = (long long)((u & 0xFFFFFFFFFFFFFull) | (1ull << 52));
     const long long M0 = (long long)((u0 & 0xFFFFFFFFFFFFFull) | (1ull << 52)) << (E0 - E);
     long long R = (u >> 63) ? M0 - M : M - M0;
     const int s = E - 1075;
-    for (int t = 1; t < terms; ++t) {
+#pragma unroll
+    for (int t = 1; t < TERMS; ++t) {
       long long rr;
       out[t] = round_bf16(R, s, &rr);
       R -= rr;
@@ -85,7 +87,8 @@ __device__ __forceinline__ void split_bf16(double x, int terms, unsigned short* 
   const long long M = E == 0 ? frac : (frac | (1ll << 52));
   const int s = E == 0 ? -1074 : E - 1075;
   long long R = bits < 0 ? -M : M;
-  for (int t = 0; t < terms; ++t) {
+#pragma unroll
+  for (int t = 0; t < TERMS; ++t) {
     long long rr;
     out[t] = round_bf16(R, s, &rr);
     R -= rr;
@@ -98,9 +101,10 @@ __device__ __forceinline__ void split_bf16(double x, int terms, unsigned short* 
 // k of one row into one 8-byte store per term.
 constexpr int kTk = 128;
 
+template <int TERMS>
 __global__ void __launch_bounds__(256) split_stage_a_kernel(MatView M, const int* row_idx,
                                                             const int* col_idx,
-                                                            unsigned short* panels, int terms,
+                                                            unsigned short* panels,
                                                             int64_t rows_pad, int64_t cols_pad) {
   __shared__ double tile[32][kTk + 1];
   const int64_t tiles_r = rows_pad / 32;
@@ -128,30 +132,37 @@ __global__ void __launch_bounds__(256) split_stage_a_kernel(MatView M, const int
   for (int rr = ty; rr < 32; rr += 8) {
     const int64_t i = r0 + rr;
     const int64_t k = k0 + 4 * tx;
-    unsigned long long packed[3] = {0, 0, 0};
+    unsigned long long packed[TERMS];
+#pragma unroll
+    for (int t = 0; t < TERMS; ++t) packed[t] = 0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-      unsigned short b[3];
-      split_bf16(tile[rr][4 * tx + q], terms, b);
-      for (int t = 0; t < terms; ++t) packed[t] |= (unsigned long long)b[t] << (16 * q);
+      unsigned short b[TERMS];
+      split_bf16<TERMS>(tile[rr][4 * tx + q], b);
+#pragma unroll
+      for (int t = 0; t < TERMS; ++t) packed[t] |= (unsigned long long)b[t] << (16 * q);
     }
-    for (int t = 0; t < terms; ++t)
+#pragma unroll
+    for (int t = 0; t < TERMS; ++t)
       *reinterpret_cast<unsigned long long*>(panels + t * plane + i * cols_pad + k) = packed[t];
   }
 }
 
 // B panel: panel[j][k] = B(k, j).  Consecutive k are contiguous in both the source block-row
 // panels and the panel, so no transpose: each thread converts 4 consecutive k of one column.
+template <int TERMS>
 __global__ void __launch_bounds__(256) split_stage_b_kernel(MatView M, const int* row_idx,
                                                             const int* col_idx,
-                                                            unsigned short* panels, int terms,
+                                                            unsigned short* panels,
                                                             int64_t rows_pad, int64_t cols_pad) {
   const int64_t per_row = cols_pad / 4;                 // 4-wide groups along k
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= rows_pad * per_row) return;
   const int64_t j = g / per_row;
   const int64_t k = (g % per_row) * 4;
-  unsigned long long packed[3] = {0, 0, 0};
+  unsigned long long packed[TERMS];
+#pragma unroll
+  for (int t = 0; t < TERMS; ++t) packed[t] = 0;
   if (j < M.n_cols && k < M.n_rows) {
     const int Cc = col_idx[j];
     const int R0 = row_idx[k];
@@ -163,9 +174,10 @@ __global__ void __launch_bounds__(256) split_stage_b_kernel(MatView M, const int
         const double* src = M.pool + (int64_t)M.row_off[R0] * M.n_cols + (k - M.row_off[R0]) + j * mR;
 #pragma unroll
         for (int q = 0; q < 4; ++q) {
-          unsigned short b[3];
-          split_bf16(src[q], terms, b);
-          for (int t = 0; t < terms; ++t) packed[t] |= (unsigned long long)b[t] << (16 * q);
+          unsigned short b[TERMS];
+          split_bf16<TERMS>(src[q], b);
+#pragma unroll
+          for (int t = 0; t < TERMS; ++t) packed[t] |= (unsigned long long)b[t] << (16 * q);
         }
       }
     } else {
@@ -180,29 +192,35 @@ __global__ void __launch_bounds__(256) split_stage_b_kernel(MatView M, const int
             v = M.pool[(int64_t)M.row_off[R] * M.n_cols + (kk - M.row_off[R]) + j * mR];
           }
         }
-        unsigned short b[3];
-        split_bf16(v, terms, b);
-        for (int t = 0; t < terms; ++t) packed[t] |= (unsigned long long)b[t] << (16 * q);
+        unsigned short b[TERMS];
+        split_bf16<TERMS>(v, b);
+#pragma unroll
+        for (int t = 0; t < TERMS; ++t) packed[t] |= (unsigned long long)b[t] << (16 * q);
       }
     }
   }
   const int64_t plane = rows_pad * cols_pad;
-  for (int t = 0; t < terms; ++t)
+#pragma unroll
+  for (int t = 0; t < TERMS; ++t)
     *reinterpret_cast<unsigned long long*>(panels + t * plane + j * cols_pad + k) = packed[t];
 }
 
 void launch_split_stage(const MatView& M, const int* row_idx, const int* col_idx, void* panels,
                         int terms, int64_t rows_pad, int64_t cols_pad, int a_mode,
                         cudaStream_t st) {
+  unsigned short* pn = (unsigned short*)panels;
   if (a_mode) {
-    const int64_t n = (rows_pad / 32) * (cols_pad / kTk);
-    split_stage_a_kernel<<<(unsigned)n, 256, 0, st>>>(M, row_idx, col_idx,
-                                                      (unsigned short*)panels, terms, rows_pad,
-                                                      cols_pad);
+    const unsigned n = (unsigned)((rows_pad / 32) * (cols_pad / kTk));
+    if (terms == 2)
+      split_stage_a_kernel<2><<<n, 256, 0, st>>>(M, row_idx, col_idx, pn, rows_pad, cols_pad);
+    else
+      split_stage_a_kernel<3><<<n, 256, 0, st>>>(M, row_idx, col_idx, pn, rows_pad, cols_pad);
   } else {
-    const int64_t n = rows_pad * (cols_pad / 4);
-    split_stage_b_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
-        M, row_idx, col_idx, (unsigned short*)panels, terms, rows_pad, cols_pad);
+    const unsigned n = (unsigned)((rows_pad * (cols_pad / 4) + 255) / 256);
+    if (terms == 2)
+      split_stage_b_kernel<2><<<n, 256, 0, st>>>(M, row_idx, col_idx, pn, rows_pad, cols_pad);
+    else
+      split_stage_b_kernel<3><<<n, 256, 0, st>>>(M, row_idx, col_idx, pn, rows_pad, cols_pad);
   }
 }
 
