@@ -1069,21 +1069,7 @@ extern "C" int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t* z_out,
       break;
     }
     if (it >= o.ns_max_iter) break;
-    if (o.ns_fp64_tail && prec != CLR_PREC_FP64 && px <= o.ns_ladder_switch) {
-      // precision ladder: the remaining products run in FP64.  Split-precision rounding in the
-      // earlier products breaks the invariant Y_n = S Z_n of the coupled iteration, which the
-      // iteration does not repair, so Y is re-coupled once (Y <- S Z) and X recomputed.
-      prec = CLR_PREC_FP64;
-      st = multiply_into(ctx, s_mat, Z, Yn, 1.0, tn, nullptr, s);
-      if (st) break;
-      std::swap(Y, Yn);
-      st = multiply_into(ctx, Y, Z, X, alpha, tn, nullptr, s);
-      if (st) break;
-      st = identity_distance(ctx, X, s, &px);
-      if (st) break;
-      proxies.back() = px;
-      precs.back() = prec;
-    }
+    if (o.ns_fp64_tail && px <= o.ns_ladder_switch) prec = CLR_PREC_FP64;
     if (tape) {
       clr_mat_t yc = nullptr, zc = nullptr;
       st = alloc_mat(ctx, nr, sz, nr, sz, &yc);

@@ -54,3 +54,25 @@ def test_ns_fixed_iterations_and_noconv(ctx):
         ctx.sqrt_inv(gs)
     assert e.value.status == clr.CLR_ENOCONV
     ctx.set_opts(ns_tol=1e-6, ns_max_iter=50)
+
+
+def test_ns_fp64_meets_residual_and_split_floor(ctx):
+    # FP64 products reach the residual tolerance 1e-6 on the 1D chain (kappa ~ 8400).  Split
+    # products (bf16x6, FP64 from ||X - I|| <= 1e-3 on) stop at the floor ~ u_split * kappa:
+    # early absolute rounding errors are large relative to the small-eigenvalue components of
+    # X and the coupled iteration carries them to the end.
+    w = wl.chain_overlap()
+    gs = ctx.from_dense(w.a, w.row_sizes, eps_lr=w.eps_lr, drop_norm=w.drop_norm)
+    ctx.set_opts(precision="fp64", ns_tol=1e-6, ns_max_iter=60, ns_alpha=0.0, eps_lr=1e-8,
+                 ns_fp64_tail=0)
+    z_64, st_64, _ = ctx.sqrt_inv(gs)
+    assert st_64["converged"] and st_64["residual"] < 1e-6
+    exact = co.inv_sqrt_eigh(w.a)
+    assert np.linalg.norm(z_64.to_dense() - exact) / np.linalg.norm(exact) < 1e-6
+    ctx.set_opts(precision="bf16x6", ns_fp64_tail=1, ns_ladder_switch=1e-3)
+    z_lad, st_lad, _ = ctx.sqrt_inv(gs)
+    assert st_lad["converged"]
+    lam = np.linalg.eigvalsh(w.a)
+    floor = 2.0 ** -24 * lam[-1] / lam[0]
+    assert st_lad["residual"] < 30 * floor
+    ctx.set_opts(precision="fp64", ns_fp64_tail=0)
