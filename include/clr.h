@@ -251,6 +251,10 @@ typedef struct clr_profile {
   double ms_lowrank;           /* low-rank tile products and accumulation */
   double ms_compress;          /* recompression (QR + SVD) */
   double ms_finalize;          /* norms and scaling */
+  int64_t svd_blocks;          /* truncated SVDs (one-sided Jacobi) run by recompression */
+  int64_t svd_sweeps_fp32;     /* FP32 sweeps, summed over those SVDs */
+  int64_t svd_sweeps_fp64;     /* FP64 sweeps, summed */
+  int64_t svd_early_dense;     /* SVDs stopped after the FP32 phase (certified dense) */
 } clr_profile;
 int clr_profile_enable(clr_ctx_t ctx, int on);
 int clr_profile_read(clr_ctx_t ctx, clr_profile* out);

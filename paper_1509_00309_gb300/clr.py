@@ -57,7 +57,9 @@ class ClrProfile(C.Structure):
                 ("dense_launches", C.c_int64), ("dense_tensor_flops", C.c_double),
                 ("ms_plan", C.c_double), ("ms_stage", C.c_double), ("ms_dense", C.c_double),
                 ("ms_lowrank", C.c_double), ("ms_compress", C.c_double),
-                ("ms_finalize", C.c_double)]
+                ("ms_finalize", C.c_double), ("svd_blocks", C.c_int64),
+                ("svd_sweeps_fp32", C.c_int64), ("svd_sweeps_fp64", C.c_int64),
+                ("svd_early_dense", C.c_int64)]
 
 
 _VP = C.c_void_p

@@ -73,7 +73,7 @@ struct clr_ctx_s {
   // workspaces (grow-only)
   std::vector<std::unique_ptr<WorkSet>> wsets;
   WorkSet* cur = nullptr;  // workspace set used by the next product
-  DevBuf small, upload;
+  DevBuf small, upload, jstats;  // jstats: 4 SVD counters accumulated while profiling
   bool capturing = false;
   // autotuner cache: shape key -> tuning and measured ms
   std::map<std::string, std::pair<Tuning, double>> tune_cache;
@@ -259,6 +259,12 @@ int make_plan(clr_ctx_t ctx, int nI, int nJ, int nK, Plan* p) {
 
 int grid_of(clr_ctx_t ctx, int per_sm) { return std::max(1, ctx->n_sm * per_sm); }
 
+// SVD counters while profiling (not inside a graph capture), else null
+unsigned long long* jst(clr_ctx_t ctx) {
+  return (ctx->prof_on && !ctx->capturing && ctx->jstats.p)
+             ? (unsigned long long*)ctx->jstats.p : nullptr;
+}
+
 enum { PH_START = -1, PH_PLAN = 0, PH_STAGE, PH_DENSE, PH_LOWRANK, PH_COMPRESS, PH_FINALIZE };
 
 void prof_mark(clr_ctx_t ctx, cudaStream_t s, int phase) {
@@ -375,6 +381,7 @@ extern "C" int clr_destroy(clr_ctx_t ctx) {
   for (auto& w : ctx->wsets) w->release();
   ctx->small.release();
   ctx->upload.release();
+  ctx->jstats.release();
   delete ctx;
   return CLR_OK;
 }
@@ -466,8 +473,7 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
     launch_dense_kinds(m->view(), drop_norm, &pc->err, s);
   } else {
     launch_compress_dense(m->view(), nullptr, nullptr, src, lda, (double*)ctx->cur->ws.p, eps_lr,
-                          drop_norm, 0, ctx->opts.jacobi_max_sweeps, grid_of(ctx, 2), &pc->err,
-                          s);
+                          drop_norm, 0, ctx->opts.jacobi_max_sweeps, grid_of(ctx, 2), &pc->err, jst(ctx), s);
   }
   e = cudaGetLastError();
   int errflag = 0;
@@ -749,9 +755,9 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   prof_launches(ctx, 1);
   prof_mark(ctx, s, PH_LOWRANK);
   launch_compress_qr(cv, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p, eps_lr,
-                     o.jacobi_max_sweeps, lr_grid, &p.counters->err, s);
+                     o.jacobi_max_sweeps, lr_grid, &p.counters->err, jst(ctx), s);
   launch_compress_dense(cv, p.l_dcomp, &p.counters->n_dcomp, nullptr, 0, (double*)ctx->cur->ws.p,
-                        eps_lr, 0.0, 0, o.jacobi_max_sweeps, lr_grid, &p.counters->err, s);
+                        eps_lr, 0.0, 0, o.jacobi_max_sweeps, lr_grid, &p.counters->err, jst(ctx), s);
   CLR_CHECK_LAUNCH("recompression");
   prof_launches(ctx, 2);
   prof_mark(ctx, s, PH_COMPRESS);
@@ -791,6 +797,10 @@ extern "C" int clr_profile_enable(clr_ctx_t ctx, int on) {
   ctx->prof_events.clear();
   std::memset(&ctx->prof, 0, sizeof(ctx->prof));
   ctx->prof_on = on != 0;
+  if (ctx->prof_on) {
+    CLR_CUDA(ctx->jstats.ensure(4 * sizeof(unsigned long long)));
+    CLR_CUDA(cudaMemset(ctx->jstats.p, 0, 4 * sizeof(unsigned long long)));
+  }
   return CLR_OK;
 }
 
@@ -816,6 +826,14 @@ extern "C" int clr_profile_read(clr_ctx_t ctx, clr_profile* out) {
     }
     for (auto& pe : ctx->prof_events) ctx->event_pool.push_back(pe.first);
     ctx->prof_events.clear();
+  }
+  if (ctx->jstats.p) {
+    unsigned long long j[4];
+    CLR_CUDA(cudaMemcpy(j, ctx->jstats.p, sizeof(j), cudaMemcpyDeviceToHost));
+    ctx->prof.svd_blocks = (int64_t)j[0];
+    ctx->prof.svd_sweeps_fp32 = (int64_t)j[1];
+    ctx->prof.svd_sweeps_fp64 = (int64_t)j[2];
+    ctx->prof.svd_early_dense = (int64_t)j[3];
   }
   *out = ctx->prof;
   return CLR_OK;
@@ -870,10 +888,10 @@ extern "C" int clr_lincomb(clr_ctx_t ctx, double a, clr_mat_t x, double b, clr_m
   MatView xv = x->view(), yv = y->view(), ov = out->view();
   launch_lincomb_plan(a, xv, b, yv, diag, ov, p, (double*)ctx->cur->ws.p, o.recompress_dense, s);
   launch_compress_qr(ov, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p, o.eps_lr,
-                     o.jacobi_max_sweeps, grid_of(ctx, 2), &p.counters->err, s);
+                     o.jacobi_max_sweeps, grid_of(ctx, 2), &p.counters->err, jst(ctx), s);
   launch_compress_dense(ov, p.l_dcomp, &p.counters->n_dcomp, nullptr, 0, (double*)ctx->cur->ws.p,
                         o.eps_lr, 0.0, 0, o.jacobi_max_sweeps, grid_of(ctx, 2),
-                        &p.counters->err, s);
+                        &p.counters->err, jst(ctx), s);
   CLR_CHECK_LAUNCH("lincomb");
   return CLR_OK;
 }

@@ -101,9 +101,10 @@ void launch_lr_products(const MatView& A, const MatView& B, const MatView& C, co
                         double* ws, double* scratch, int64_t scratch_per_cta, int grid,
                         cudaStream_t st);
 // k_svd.cu
+// jstats (may be null): device counters {svd blocks, FP32 sweeps, FP64 sweeps, early dense}
 void launch_compress_qr(const MatView& C, const int* list, const int* count, const int* rsum,
                         double* ws, double eps, int max_sweeps, int grid, int* err,
-                        cudaStream_t st);
+                        unsigned long long* jstats, cudaStream_t st);
 // Dense truncated SVD of blocks listed in `list` (count on device).  The source of block b is
 // either the matrix's own slot (src == nullptr) or a row-major dense matrix src with leading
 // dimension lds.  drop_norm: blocks with norm below it become zero.  dense_only: skip the
@@ -111,7 +112,7 @@ void launch_compress_qr(const MatView& C, const int* list, const int* count, con
 void launch_compress_dense(const MatView& C, const int* list, const int* count,
                            const double* src, int64_t lds, double* ws, double eps,
                            double drop_norm, int dense_only, int max_sweeps, int grid,
-                           int* err, cudaStream_t st);
+                           int* err, unsigned long long* jstats, cudaStream_t st);
 void launch_block_norms(const MatView& M, cudaStream_t st);
 void launch_block_norms_dense(const MatView& M, cudaStream_t st);
 void launch_scale_blocks(const MatView& M, double alpha, cudaStream_t st);

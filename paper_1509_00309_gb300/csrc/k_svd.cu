@@ -109,11 +109,12 @@ __device__ void apply_q(const double* v, int p, int q, int64_t ldv, const double
 // One-sided Jacobi on the q columns of g (p x q, ld ldg); v (q x q, ld ldv) accumulates the
 // rotations (initialised to I here unless reset_v is false).  On return g = U S and the input
 // equals g v^T (times the initial v^T when v is not reset).  T is float or double; the
-// convergence threshold is the type's epsilon times sqrt(p) (times tol_scale).
+// convergence threshold is the type's epsilon times sqrt(p) (times tol_scale); pairs whose inner
+// product is below floor2 are left alone.
 template <typename T>
 __device__ int jacobi_svd(T* g, int p, int q, int64_t ldg, T* v, int64_t ldv,
                           int max_sweeps, int* sh_flag, bool reset_v = true,
-                          T tol_scale = T(1)) {
+                          T tol_scale = T(1), T floor2 = T(0)) {
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
   if (reset_v) {
     for (int e = threadIdx.x; e < q * q; e += kThreads)
@@ -151,7 +152,10 @@ __device__ int jacobi_svd(T* g, int p, int q, int64_t ldg, T* v, int64_t ldv,
         be = warp_sum(be);
         ga_gb = warp_sum(ga_gb);
         const T scale = sqrt(al) * sqrt(be);
-        if (scale == T(0) || fabs(ga_gb) <= tol * scale) continue;
+        // converged pair; or both columns at the noise floor of the arithmetic (a pair whose
+        // inner product is below floor2 = (p u ||A||_F)^2 cannot change any singular value by
+        // more than the SVD's own rounding)
+        if (scale == T(0) || fabs(ga_gb) <= tol * scale || fabs(ga_gb) <= floor2) continue;
         const T zeta = (be - al) / (T(2) * ga_gb);
         const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
         const T c = T(1) / sqrt(T(1) + t * t);
@@ -248,51 +252,24 @@ struct SrcView {
 // Mixed-precision one-sided Jacobi SVD of the p x q (p >= q) matrix A given by `a`:
 //  1. FP32 sweeps on a copy (FP32 runs far faster than FP64 on this part) until converged at
 //     FP32 accuracy, accumulating V32;
-//  2. optional certified early exit: with the FP32 singular values sorted, if the Frobenius
-//     tail beyond `dense_h` exceeds eps by more than a bound on the FP32 backward error
-//     (2 (sweeps + 1) q u_32 ||A||_F), the eps-rank exceeds dense_h for certain: return 1;
-//  3. FP64 refinement: V = V32 orthonormalised in FP64 (modified Gram-Schmidt), G = A V in
-//     FP64, and FP64 sweeps continuing on (G, V) -- one to three sweeps from this start.
-// On return 0, g = U S and A = g v^T in FP64 (the same result as FP64 Jacobi from scratch, up
-// to rounding).  g (p x q doubles) also serves as the FP32 scratch (p q + q^2 floats).
+//  2. V = V32 orthonormalised in FP64 (modified Gram-Schmidt) and G = A V in FP64, so A and G
+//     have the same singular values and G's columns are nearly orthogonal;
+//  3. FP64 sweeps continuing on (G, V) -- a few from this start.
+// Pairs whose inner product is below the noise floor are not rotated: p u ||A||_F in FP32, and
+// max(p u ||A||_F, 1e-3 eps) in FP64 (columns that small cannot move a truncation at eps).
+// On return g = U S and A = g v^T in FP64.  g (p x q doubles) also serves as the FP32 scratch
+// (p q + q^2 floats).  dense_h is unused and kept for the call sites.
 __device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, int max_sweeps,
-                         double eps, int dense_h, double fro, SvdShared& sh) {
+                         double eps, int dense_h, double fro, SvdShared& sh,
+                         unsigned long long* jstats) {
   float* g32 = reinterpret_cast<float*>(g);
   float* v32 = g32 + (int64_t)p * q;
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
   for (int e = threadIdx.x; e < p * q; e += kThreads) g32[e] = (float)a.at(e % p, e / p);
   __syncthreads();
-  const int sw32 = jacobi_svd<float>(g32, p, q, p, v32, q, max_sweeps, &sh.flag, true, 4.0f);
-  if (dense_h >= 0) {
-    for (int c = w; c < q; c += kWarps) {
-      const float* gc = g32 + (int64_t)c * p;
-      double s2 = 0.0;
-      for (int i = l; i < p; i += 32) s2 = fma((double)gc[i], (double)gc[i], s2);
-      s2 = warp_sum(s2);
-      if (l == 0) sh.sigma[c] = s2;
-    }
-    __syncthreads();
-    // tail beyond dense_h of the sorted squared norms = total minus the dense_h largest
-    double mine_total = 0.0, mine_top = 0.0;
-    for (int c = threadIdx.x; c < q; c += kThreads) {
-      int above = 0;
-      for (int d = 0; d < q; ++d)
-        above += sh.sigma[d] > sh.sigma[c] || (sh.sigma[d] == sh.sigma[c] && d < c);
-      mine_total += sh.sigma[c];
-      if (above < dense_h) mine_top += sh.sigma[c];
-    }
-    const double total = block_sum(mine_total, sh.red);
-    const double top = block_sum(mine_top, sh.red);
-    if (threadIdx.x == 0) {
-      const double tail = sqrt(fmax(total - top, 0.0));
-      const double delta = 2.0 * (sw32 + 1) * q * (double)FLT_EPSILON * fro;
-      sh.flag = tail - delta > eps ? 1 : 0;
-    }
-    __syncthreads();
-    const int dense = sh.flag;
-    __syncthreads();
-    if (dense) return 1;
-  }
+  const float floor32 = (float)((double)p * FLT_EPSILON * fro);
+  const int sw32 = jacobi_svd<float>(g32, p, q, p, v32, q, max_sweeps, &sh.flag, true, 4.0f,
+                                     floor32 * floor32);
   // FP64 refinement
   for (int e = threadIdx.x; e < q * q; e += kThreads) v[e] = (double)v32[e];
   __syncthreads();
@@ -321,7 +298,17 @@ __device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, i
     g[e] = s2;
   }
   __syncthreads();
-  jacobi_svd<double>(g, p, q, p, v, q, max_sweeps, &sh.flag, false);
+  // FP64 noise floor, raised to 1e-3 eps: columns below it hold less than 1e-6 eps^2 each, so
+  // their mutual (non-)orthogonality cannot move a truncation decision at eps except within a
+  // hair of the threshold, while orthogonalising them costs most of the sweeps
+  const double floor64 = fmax((double)p * DBL_EPSILON * fro, 1e-3 * eps);
+  const int sw64 = jacobi_svd<double>(g, p, q, p, v, q, max_sweeps, &sh.flag, false, 1.0,
+                                      floor64 * floor64);
+  if (jstats && threadIdx.x == 0) {
+    atomicAdd(&jstats[0], 1ull);
+    atomicAdd(&jstats[1], (unsigned long long)sw32);
+    atomicAdd(&jstats[2], (unsigned long long)sw64);
+  }
   return 0;
 }
 
@@ -331,7 +318,8 @@ __device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, i
 __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const int* list,
                                                                const int* count,
                                                                const int* rsum, double* ws,
-                                                               double eps, int max_sweeps) {
+                                                               double eps, int max_sweeps,
+                                                               unsigned long long* jstats) {
   __shared__ SvdShared sh;
   const int n_items = *count;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -360,8 +348,11 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
     }
     __syncthreads();
     {
+      double part = 0.0;
+      for (int e = threadIdx.x; e < R * R; e += kThreads) part = fma(M[e], M[e], part);
+      const double mfro = sqrt(block_sum(part, sh.red));
       SrcView mv{M, 1, R, false};
-      svd_mixed(mv, R, R, G, V, max_sweeps, eps, -1, 0.0, sh);
+      svd_mixed(mv, R, R, G, V, max_sweeps, eps, -1, mfro, sh, jstats);
     }
     sort_and_truncate(G, R, R, R, eps, sh);
     const int r = sh.rank;
@@ -389,9 +380,10 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
 
 void launch_compress_qr(const MatView& C, const int* list, const int* count, const int* rsum,
                         double* ws, double eps, int max_sweeps, int grid, int* err,
-                        cudaStream_t st) {
+                        unsigned long long* jstats, cudaStream_t st) {
   (void)err;
-  compress_qr_kernel<<<grid, kThreads, 0, st>>>(C, list, count, rsum, ws, eps, max_sweeps);
+  compress_qr_kernel<<<grid, kThreads, 0, st>>>(C, list, count, rsum, ws, eps, max_sweeps,
+                                                 jstats);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -400,7 +392,8 @@ void launch_compress_qr(const MatView& C, const int* list, const int* count, con
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
     MatView C, const int* list, const int* count, const double* src, int64_t lds, double* ws,
-    double eps, double drop_norm, int dense_only, int max_sweeps, int* err) {
+    double eps, double drop_norm, int dense_only, int max_sweeps, int* err,
+    unsigned long long* jstats) {
   __shared__ SvdShared sh;
   const int n_items = list ? *count : C.nr * C.nc;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
@@ -439,7 +432,8 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
     int r = q;
     if (!dense_only) {
       const SrcView view{S, s_r, s_c, tr};
-      const int early_dense = svd_mixed(view, p, q, G, V, max_sweeps, eps, q / 2, nrm, sh);
+      const int early_dense =
+          svd_mixed(view, p, q, G, V, max_sweeps, eps, q / 2, nrm, sh, jstats);
       if (!early_dense) {
         sort_and_truncate(G, p, q, p, eps, sh);
         r = sh.rank;
@@ -493,9 +487,10 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
 void launch_compress_dense(const MatView& C, const int* list, const int* count,
                            const double* src, int64_t lds, double* ws, double eps,
                            double drop_norm, int dense_only, int max_sweeps, int grid,
-                           int* err, cudaStream_t st) {
+                           int* err, unsigned long long* jstats, cudaStream_t st) {
   compress_dense_kernel<<<grid, kThreads, 0, st>>>(C, list, count, src, lds, ws, eps,
-                                                   drop_norm, dense_only, max_sweeps, err);
+                                                   drop_norm, dense_only, max_sweeps, err,
+                                                   jstats);
 }
 
 // ---------------------------------------------------------------------------------------------
