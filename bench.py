@@ -139,14 +139,18 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def dist_init(args):
+def dist_init(backend=None):
+    """One process per GPU under torchrun (RANK / LOCAL_RANK / WORLD_SIZE / MASTER_* from the
+    environment).  Returns (rank, world_size, local_rank)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
         import torch
         import torch.distributed as dist
         local = int(os.environ.get("LOCAL_RANK", "0"))
-        torch.cuda.set_device(local)
-        dist.init_process_group("nccl")
+        if backend is None:
+            backend = "nccl"
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
         return dist.get_rank(), ws, local
     return 0, 1, 0
 
@@ -157,14 +161,20 @@ def barrier(ws):
         dist.barrier()
 
 
-def max_over_ranks(x, ws):
+def max_over_ranks(x, ws, device="cuda"):
+    """The slowest rank's value (timings are taken as the max over ranks)."""
     if ws == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_tflops(flops_per_rank_step, ws, steps, ms_max):
+    """Whole-job throughput: every rank's flops over the slowest rank's time."""
+    return flops_per_rank_step * ws * steps / (ms_max * 1e-3) / 1e12
 
 
 # ------------------------------------------------------------------------------------------
@@ -202,9 +212,9 @@ def run_reference(args):
         return
     w = workload(args)
     # each step a bounded oracle sample: the whole run stays within about a minute or two
-    per_step = max(2.0, 60.0 / max(1, args.steps))
+    per_step = getattr(args, "ref_seconds", None) or max(2.0, 60.0 / max(1, args.steps))
     for _ in range(args.warmup):
-        oracle_sample(w, 1.0)
+        oracle_sample(w, min(1.0, per_step))
     fl, el = 0, 0.0
     rows = 0
     for _ in range(args.steps):
@@ -237,7 +247,7 @@ def run_ours(args):
     import torch
 
     from paper_1509_00309_gb300 import build, clr
-    rank, ws, local = dist_init(args)
+    rank, ws, local = dist_init()
     if ws == 1:
         torch.cuda.set_device(0)
     build.build()
@@ -274,7 +284,7 @@ def run_ours(args):
     ctx.profile_enable(False)
     ms_total = max_over_ranks(e0.elapsed_time(e1), ws)
     ms_step = ms_total / args.steps
-    value = alg_flops * ws * args.steps / (ms_total * 1e-3) / 1e12
+    value = job_tflops(alg_flops, ws, args.steps, ms_total)
 
     # accuracy of this run's result on sampled tiles vs FP64 dot products
     err = None
