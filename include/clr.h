@@ -165,6 +165,11 @@ int clr_mat_shape(clr_mat_t m, int64_t* n_rows, int64_t* n_cols, int* n_rt, int*
 int clr_mat_copy(clr_ctx_t ctx, clr_mat_t src, clr_mat_t dst, void* stream);
 int clr_mat_transpose(clr_ctx_t ctx, clr_mat_t src, clr_mat_t* out, void* stream);
 int clr_mat_free(clr_ctx_t ctx, clr_mat_t m);
+/* Matrix storage comes from a process-wide caching allocator: freed buffers are kept (up to
+ * 64 GiB) and reused by later matrices of the same size.  clr_mem_trim returns the context
+ * device's cached buffers to CUDA; clr_mem_cached reports the bytes currently cached. */
+int clr_mem_trim(clr_ctx_t ctx);
+int64_t clr_mem_cached(void);
 
 /* ---- the CLR product (Section 4.1) --------------------------------------------------------
  * C = alpha * (A B): every C tile receives the tile products A_IK B_KJ with both blocks

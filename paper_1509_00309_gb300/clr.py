@@ -107,6 +107,8 @@ _SIGNATURES = {
     "clr_autotune_save": (C.c_int, [_VP, C.c_char_p]),
     "clr_autotune_load": (C.c_int, [_VP, C.c_char_p]),
     "clr_autotune_entries": (C.c_int, [_VP]),
+    "clr_mem_trim": (C.c_int, [_VP]),
+    "clr_mem_cached": (C.c_int64, []),
     "clr_profile_enable": (C.c_int, [_VP, C.c_int]),
     "clr_profile_read": (C.c_int, [_VP, C.POINTER(ClrProfile)]),
 }
@@ -277,6 +279,9 @@ class Context:
                 v = PREC[v]
             setattr(o, k, v)
         self._check(load().clr_set_opts(self.handle, C.byref(o)))
+
+    def mem_trim(self):
+        self._check(load().clr_mem_trim(self.handle))
 
     # observability -----------------------------------------------------------------------
     def profile_enable(self, on: bool = True):

@@ -11,6 +11,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -42,6 +43,84 @@ struct DevBuf {
     bytes = 0;
   }
 };
+
+// Process-wide caching allocator for matrix storage.  Freed buffers are kept per (device, size)
+// and handed to later allocations of the same size, so creating and freeing matrices in a loop
+// (products, uploads, temporaries of the NS driver) costs no cudaMalloc / cudaFree after the
+// first round.  At most kPoolCap bytes stay cached; clr_mem_trim releases a device's cache.
+class DevicePool {
+ public:
+  cudaError_t alloc(int dev, void** p, size_t bytes) {
+    bytes = std::max<size_t>(bytes, 16);
+    {
+      std::lock_guard<std::mutex> lock(mu_);
+      auto it = free_.find({dev, bytes});
+      if (it != free_.end() && !it->second.empty()) {
+        *p = it->second.back();
+        it->second.pop_back();
+        cached_ -= bytes;
+        return cudaSuccess;
+      }
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e == cudaErrorMemoryAllocation) {  // give the cache back and retry once
+      cudaGetLastError();
+      trim(dev);
+      e = cudaMalloc(p, bytes);
+    }
+    return e;
+  }
+  void release(int dev, void* p, size_t bytes) {
+    if (!p) return;
+    bytes = std::max<size_t>(bytes, 16);
+    {
+      std::lock_guard<std::mutex> lock(mu_);
+      if (cached_ + bytes <= kPoolCap) {
+        free_[{dev, bytes}].push_back(p);
+        cached_ += bytes;
+        return;
+      }
+    }
+    cudaFree(p);
+  }
+  void trim(int dev) {
+    std::vector<void*> drop;
+    {
+      std::lock_guard<std::mutex> lock(mu_);
+      for (auto it = free_.begin(); it != free_.end();) {
+        if (it->first.first == dev) {
+          for (void* p : it->second) {
+            drop.push_back(p);
+            cached_ -= it->first.second;
+          }
+          it = free_.erase(it);
+        } else {
+          ++it;
+        }
+      }
+    }
+    int prev = 0;
+    cudaGetDevice(&prev);
+    if (prev != dev) cudaSetDevice(dev);
+    for (void* p : drop) cudaFree(p);
+    if (prev != dev) cudaSetDevice(prev);
+  }
+  size_t cached() {
+    std::lock_guard<std::mutex> lock(mu_);
+    return cached_;
+  }
+
+ private:
+  static constexpr size_t kPoolCap = 64ull << 30;
+  std::mutex mu_;
+  std::map<std::pair<int, size_t>, std::vector<void*>> free_;
+  size_t cached_ = 0;
+};
+
+DevicePool& pool() {
+  static DevicePool* p = new DevicePool;  // never destroyed: matrices may outlive contexts
+  return *p;
+}
 
 }  // namespace
 
@@ -160,14 +239,16 @@ int check_sizes(clr_ctx_t ctx, int n, const int32_t* sizes, const char* what) {
 
 void free_mat(clr_mat_t m) {
   if (!m) return;
-  cudaFree(m->d_row_off);
-  cudaFree(m->d_col_off);
-  cudaFree(m->d_row_idx);
-  cudaFree(m->d_col_idx);
-  cudaFree(m->d_kind);
-  cudaFree(m->d_rank);
-  cudaFree(m->d_norm);
-  cudaFree(m->d_pool);
+  const size_t nb = (size_t)m->nr * m->nc;
+  DevicePool& pl = pool();
+  pl.release(m->device, m->d_row_off, (m->nr + 1) * sizeof(int));
+  pl.release(m->device, m->d_col_off, (m->nc + 1) * sizeof(int));
+  pl.release(m->device, m->d_row_idx, (size_t)m->n_rows * sizeof(int));
+  pl.release(m->device, m->d_col_idx, (size_t)m->n_cols * sizeof(int));
+  pl.release(m->device, m->d_kind, nb * sizeof(int));
+  pl.release(m->device, m->d_rank, nb * sizeof(int));
+  pl.release(m->device, m->d_norm, nb * sizeof(double));
+  pl.release(m->device, m->d_pool, (size_t)m->n_rows * m->n_cols * sizeof(double));
   delete m;
 }
 
@@ -193,7 +274,7 @@ int alloc_mat(clr_ctx_t ctx, int nr, const int32_t* rs, int nc, const int32_t* c
   const size_t nb = (size_t)nr * nc;
   cudaError_t e = cudaSuccess;
   auto A = [&](void** p, size_t b) {
-    if (e == cudaSuccess) e = cudaMalloc(p, std::max<size_t>(b, 16));
+    if (e == cudaSuccess) e = pool().alloc(ctx->device, p, b);
   };
   A((void**)&m->d_row_off, (nr + 1) * sizeof(int));
   A((void**)&m->d_col_off, (nc + 1) * sizeof(int));
@@ -411,6 +492,14 @@ extern "C" int clr_mat_create(clr_ctx_t ctx, int n_rt, const int32_t* rs, int n_
   return alloc_mat(ctx, n_rt, rs, n_ct, cs, out);
 }
 
+extern "C" int clr_mem_trim(clr_ctx_t ctx) {
+  if (!ctx) return CLR_EINVAL;
+  pool().trim(ctx->device);
+  return CLR_OK;
+}
+
+extern "C" int64_t clr_mem_cached(void) { return (int64_t)pool().cached(); }
+
 extern "C" int clr_mat_free(clr_ctx_t ctx, clr_mat_t m) {
   if (!m) return CLR_EINVAL;
   if (ctx) cudaSetDevice(ctx->device);
@@ -449,8 +538,11 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
     const size_t bytes = (size_t)m->n_rows * m->n_cols * sizeof(double);
     cudaError_t e = staging.ensure(bytes);
     if (e == cudaSuccess)
-      e = cudaMemcpy2DAsync(staging.p, m->n_cols * sizeof(double), a, lda * sizeof(double),
-                            m->n_cols * sizeof(double), m->n_rows, cudaMemcpyHostToDevice, s);
+      e = lda == m->n_cols
+              ? cudaMemcpyAsync(staging.p, a, bytes, cudaMemcpyHostToDevice, s)
+              : cudaMemcpy2DAsync(staging.p, m->n_cols * sizeof(double), a,
+                                  lda * sizeof(double), m->n_cols * sizeof(double), m->n_rows,
+                                  cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) {
       free_mat(m);
       return cuda_fail(ctx, e, "from_dense upload");
@@ -557,8 +649,11 @@ extern "C" int clr_mat_to_dense(clr_ctx_t ctx, clr_mat_t m, double* out, int64_t
     e = cudaGetLastError();
   }
   if (e == cudaSuccess)
-    e = cudaMemcpy2DAsync(out, ldo * sizeof(double), tmp.p, m->n_cols * sizeof(double),
-                          m->n_cols * sizeof(double), m->n_rows, cudaMemcpyDeviceToHost, s);
+    e = ldo == m->n_cols
+            ? cudaMemcpyAsync(out, tmp.p, bytes, cudaMemcpyDeviceToHost, s)
+            : cudaMemcpy2DAsync(out, ldo * sizeof(double), tmp.p, m->n_cols * sizeof(double),
+                                m->n_cols * sizeof(double), m->n_rows, cudaMemcpyDeviceToHost,
+                                s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "to_dense");
   return CLR_OK;

@@ -86,8 +86,6 @@ void launch_plan_scan(const Plan& p, int recompress_dense, cudaStream_t st);
 // k_dense64.cu
 void launch_dd_fp64(const MatView& A, const MatView& B, const MatView& C, const Plan& p,
                     int grid, cudaStream_t st);
-void launch_to_dense(const MatView& M, double* out, int64_t ldo, cudaStream_t st);
-void launch_zero_blocks(const MatView& M, cudaStream_t st);
 void launch_set_route_kinds(const MatView& C, const Plan& p, cudaStream_t st);
 void launch_dense_tile_norms(const MatView& C, const Plan& p, cudaStream_t st);
 // k_layout.cu
@@ -144,7 +142,5 @@ int split_gemm_dd(const SplitGemmArgs& a, cudaStream_t st, std::string* why);
 void launch_split_stage(const MatView& M, const int* row_idx, const int* col_idx, void* panels,
                         int terms, int64_t rows_pad, int64_t cols_pad, int a_mode,
                         cudaStream_t st);
-void launch_cluster_index(const int* off, int n_clusters, int* index_of, int64_t n,
-                          cudaStream_t st);
 
 }  // namespace clr

@@ -81,34 +81,6 @@ void launch_dd_fp64(const MatView& A, const MatView& B, const MatView& C, const 
   dd_fp64_kernel<<<grid, 256, 0, st>>>(A, B, C, p);
 }
 
-// Reconstruction of every block into a row-major dense matrix.
-__global__ void to_dense_kernel(MatView M, double* out, int64_t ldo) {
-  const int b = blockIdx.x;
-  const int I = b / M.nc, J = b % M.nc;
-  const int m = M.row_off[I + 1] - M.row_off[I];
-  const int n = M.col_off[J + 1] - M.col_off[J];
-  const int kind = M.kind[b];
-  const int r = M.rank[b];
-  const double* s = M.pool + slot_of(M, I, J, m);
-  double* o = out + (int64_t)M.row_off[I] * ldo + M.col_off[J];
-  for (int e = threadIdx.x; e < m * n; e += blockDim.x) {
-    const int i = e / n, j = e % n;
-    double v = 0.0;
-    if (kind == CLR_KIND_DENSE) {
-      v = s[i + (int64_t)j * m];
-    } else if (kind == CLR_KIND_LR) {
-      const double* X = s;
-      const double* W = s + (int64_t)m * r;
-      for (int c = 0; c < r; ++c) v = fma(X[i + (int64_t)c * m], W[j + (int64_t)c * n], v);
-    }
-    o[(int64_t)i * ldo + j] = v;
-  }
-}
-
-void launch_to_dense(const MatView& M, double* out, int64_t ldo, cudaStream_t st) {
-  to_dense_kernel<<<M.nr * M.nc, 256, 0, st>>>(M, out, ldo);
-}
-
 // After planning: kinds of tiles that get no contribution (zero) or a dense accumulation.
 __global__ void set_route_kinds_kernel(MatView C, Plan p) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -159,13 +131,6 @@ __global__ void __launch_bounds__(256) dense_tile_norms_kernel(MatView C, Plan p
 
 void launch_dense_tile_norms(const MatView& C, const Plan& p, cudaStream_t st) {
   dense_tile_norms_kernel<<<1024, 256, 0, st>>>(C, p);
-}
-
-void launch_zero_blocks(const MatView& M, cudaStream_t st) {
-  const int64_t nb = (int64_t)M.nr * M.nc;
-  cudaMemsetAsync(M.kind, 0, nb * sizeof(int), st);
-  cudaMemsetAsync(M.rank, 0, nb * sizeof(int), st);
-  cudaMemsetAsync(M.norm, 0, nb * sizeof(double), st);
 }
 
 }  // namespace clr

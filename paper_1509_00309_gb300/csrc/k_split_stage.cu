@@ -55,6 +55,55 @@ __device__ __forceinline__ unsigned short round_bf16(long long R, int s, long lo
   return sign | (unsigned short)((E + 127) << 7) | (unsigned short)mant;
 }
 
+// The same rounding for |R| < 2^46 with 32-bit operations: when R does not fit in 32 bits its 14
+// low bits are folded into a sticky bit (round to odd); the rounding position is then at least
+// 11 bits above that bit, so round-to-nearest-even is unchanged.
+__device__ __forceinline__ unsigned short round_bf16_32(long long R, int s, long long* Rr) {
+  if (R == 0) {
+    *Rr = 0;
+    return 0;
+  }
+  const unsigned short sign = R < 0 ? 0x8000 : 0;
+  const unsigned long long m = R < 0 ? (unsigned long long)(-R) : (unsigned long long)R;
+  int extra = 0;
+  unsigned m32;
+  if (m >> 32) {
+    m32 = (unsigned)(m >> 14) | ((m & 0x3FFFull) ? 1u : 0u);
+    extra = 14;
+  } else {
+    m32 = (unsigned)m;
+  }
+  const int s2 = s + extra;
+  const int msb = 31 - __clz(m32);
+  int shift = msb - 7;
+  const int sub = -133 - s2;
+  if (shift < sub) shift = sub;
+  unsigned q;
+  if (shift <= 0) {
+    q = m32;
+    shift = 0;
+  } else if (shift >= 32) {
+    q = (shift == 32 && m32 > 0x80000000u) ? 1u : 0u;
+  } else {
+    const unsigned rem = m32 & ((1u << shift) - 1u);
+    const unsigned half = 1u << (shift - 1);
+    q = m32 >> shift;
+    if (rem > half || (rem == half && (q & 1u))) ++q;
+  }
+  if (q == 0) {
+    *Rr = 0;
+    return sign;
+  }
+  const long long rr = (long long)((unsigned long long)q << (shift + extra));
+  *Rr = R < 0 ? -rr : rr;
+  const int vexp = s2 + shift;
+  const int qb = 31 - __clz(q);  // <= 8
+  const int E = qb + vexp;
+  if (E < -126) return sign | (unsigned short)(q << (vexp + 133));
+  const unsigned mant = qb >= 7 ? (q >> (qb - 7)) & 0x7Fu : (q << (7 - qb)) & 0x7Fu;
+  return sign | (unsigned short)((E + 127) << 7) | (unsigned short)mant;
+}
+
 // a = a_0 + a_1 (+ a_2) + residual: successive round-to-nearest bf16 terms of a finite double.
 // Fast path (exponent of a in [-110, 126], so a_0 is a normal bf16): a_0 by adding the
 // rounding bias to the FP64 bit pattern and clearing the 45 low bits (carries into the exponent
@@ -77,7 +126,7 @@ __device__ __forceinline__ void split_bf16(double x, unsigned short (&out)[TERMS
 #pragma unroll
     for (int t = 1; t < TERMS; ++t) {
       long long rr;
-      out[t] = round_bf16(R, s, &rr);
+      out[t] = round_bf16_32(R, s, &rr);  // |R| < 2^45 after a_0
       R -= rr;
     }
     return;
@@ -222,17 +271,6 @@ void launch_split_stage(const MatView& M, const int* row_idx, const int* col_idx
     else
       split_stage_b_kernel<3><<<n, 256, 0, st>>>(M, row_idx, col_idx, pn, rows_pad, cols_pad);
   }
-}
-
-__global__ void cluster_index_kernel(const int* off, int n_clusters, int* index_of) {
-  for (int I = blockIdx.x; I < n_clusters; I += gridDim.x)
-    for (int i = off[I] + threadIdx.x; i < off[I + 1]; i += blockDim.x) index_of[i] = I;
-}
-
-void launch_cluster_index(const int* off, int n_clusters, int* index_of, int64_t n,
-                          cudaStream_t st) {
-  (void)n;
-  cluster_index_kernel<<<n_clusters, 256, 0, st>>>(off, n_clusters, index_of);
 }
 
 }  // namespace clr

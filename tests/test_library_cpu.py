@@ -20,7 +20,7 @@ def lib():
 
 def header_functions(root):
     text = open(os.path.join(root, "include", "clr.h")).read()
-    return sorted(set(re.findall(r"^\s*(?:int|void|const char\*)\s+(clr_\w+)\s*\(", text,
+    return sorted(set(re.findall(r"^\s*(?:int64_t|int|void|const char\*)\s+(clr_\w+)\s*\(", text,
                                  re.M)))
 
 
