@@ -115,6 +115,10 @@ template <typename T>
 __device__ int jacobi_svd(T* g, int p, int q, int64_t ldg, T* v, int64_t ldv,
                           int max_sweeps, int* sh_flag, bool reset_v = true,
                           T tol_scale = T(1), T floor2 = T(0)) {
+  // Column norms squared, kept in shared memory: recomputed exactly at every sweep start and
+  // refreshed (fused into the rotation pass) for the two columns of every rotated pair, so a
+  // pair costs one inner product unless it is rotated.
+  __shared__ T nrm2[CLR_MAX_CLUSTER];
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
   if (reset_v) {
     for (int e = threadIdx.x; e < q * q; e += kThreads)
@@ -126,6 +130,13 @@ __device__ int jacobi_svd(T* g, int p, int q, int64_t ldg, T* v, int64_t ldv,
   const T tol = eps_t * sqrt(T(p)) * tol_scale;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
+    for (int c = w; c < q; c += kWarps) {
+      const T* gc = g + (int64_t)c * ldg;
+      T s2 = 0;
+      for (int i = l; i < p; i += 32) s2 = fma(gc[i], gc[i], s2);
+      s2 = warp_sum(s2);
+      if (l == 0) nrm2[c] = s2;
+    }
     if (threadIdx.x == 0) *sh_flag = 0;
     __syncthreads();
     for (int round = 0; round < qq - 1; ++round) {
@@ -139,32 +150,31 @@ __device__ int jacobi_svd(T* g, int p, int q, int64_t ldg, T* v, int64_t ldv,
           b = (round - k + (qq - 1)) % (qq - 1);
         }
         if (a >= q || b >= q) continue;
+        const T al = nrm2[a], be = nrm2[b];
+        const T scale = sqrt(al) * sqrt(be);
+        // both columns at the noise floor: |g_a . g_b| <= scale <= floor2, nothing to do
+        if (scale == T(0) || scale <= floor2) continue;
         T* ga = g + (int64_t)a * ldg;
         T* gb = g + (int64_t)b * ldg;
-        T al = 0, be = 0, ga_gb = 0;
-        for (int i = l; i < p; i += 32) {
-          const T x = ga[i], y = gb[i];
-          al = fma(x, x, al);
-          be = fma(y, y, be);
-          ga_gb = fma(x, y, ga_gb);
-        }
-        al = warp_sum(al);
-        be = warp_sum(be);
+        T ga_gb = 0;
+        for (int i = l; i < p; i += 32) ga_gb = fma(ga[i], gb[i], ga_gb);
         ga_gb = warp_sum(ga_gb);
-        const T scale = sqrt(al) * sqrt(be);
-        // converged pair; or both columns at the noise floor of the arithmetic (a pair whose
-        // inner product is below floor2 = (p u ||A||_F)^2 cannot change any singular value by
-        // more than the SVD's own rounding)
-        if (scale == T(0) || fabs(ga_gb) <= tol * scale || fabs(ga_gb) <= floor2) continue;
+        if (fabs(ga_gb) <= tol * scale || fabs(ga_gb) <= floor2) continue;
         const T zeta = (be - al) / (T(2) * ga_gb);
         const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
         const T c = T(1) / sqrt(T(1) + t * t);
         const T sn = c * t;
+        T na = 0, nb = 0;
         for (int i = l; i < p; i += 32) {
           const T x = ga[i], y = gb[i];
-          ga[i] = c * x - sn * y;
-          gb[i] = sn * x + c * y;
+          const T xa = c * x - sn * y, yb = sn * x + c * y;
+          ga[i] = xa;
+          gb[i] = yb;
+          na = fma(xa, xa, na);
+          nb = fma(yb, yb, nb);
         }
+        na = warp_sum(na);
+        nb = warp_sum(nb);
         T* va = v + (int64_t)a * ldv;
         T* vb = v + (int64_t)b * ldv;
         for (int i = l; i < q; i += 32) {
@@ -172,7 +182,11 @@ __device__ int jacobi_svd(T* g, int p, int q, int64_t ldg, T* v, int64_t ldv,
           va[i] = c * x - sn * y;
           vb[i] = sn * x + c * y;
         }
-        if (l == 0) *sh_flag = 1;
+        if (l == 0) {
+          nrm2[a] = na;
+          nrm2[b] = nb;
+          *sh_flag = 1;
+        }
       }
       __syncthreads();
     }
@@ -258,7 +272,16 @@ struct SrcView {
 // Pairs whose inner product is below the noise floor are not rotated: p u ||A||_F in FP32, and
 // max(p u ||A||_F, 1e-3 eps) in FP64 (columns that small cannot move a truncation at eps).
 // On return g = U S and A = g v^T in FP64.  g (p x q doubles) also serves as the FP32 scratch
-// (p q + q^2 floats).  dense_h is unused and kept for the call sites.
+// (p q + q^2 floats).
+//
+// Certified dense exit (dense_h >= 0): the block is stored dense when its eps-rank exceeds
+// dense_h, i.e. when the singular-value tail sqrt(sum_{i >= dense_h} s_i^2) exceeds eps.  After
+// the FP32 phase every sorted column norm c_i of G32 is within delta of s_i(A), with
+//   delta = 2 u32 ||A||_F (4 q sqrt(p) + p sqrt(q) + 2 s32 q + 1)
+// (backward error of s32 FP32 sweeps of rotations, the rounding of A to FP32, and the residual
+// non-orthogonality of G32's columns: pairs within 4 u32 sqrt(p) of orthogonal or below the FP32
+// noise floor).  So tail(A) >= tail(c) - sqrt(q - dense_h) delta, and when that exceeds eps the
+// FP64 phase could only confirm "dense": it is skipped and the function returns 1.
 __device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, int max_sweeps,
                          double eps, int dense_h, double fro, SvdShared& sh,
                          unsigned long long* jstats) {
@@ -270,6 +293,37 @@ __device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, i
   const float floor32 = (float)((double)p * FLT_EPSILON * fro);
   const int sw32 = jacobi_svd<float>(g32, p, q, p, v32, q, max_sweeps, &sh.flag, true, 4.0f,
                                      floor32 * floor32);
+  if (dense_h >= 0 && dense_h < q) {
+    for (int c = w; c < q; c += kWarps) {
+      const float* gc = g32 + (int64_t)c * p;
+      double s2 = 0.0;
+      for (int i = l; i < p; i += 32) s2 = fma((double)gc[i], (double)gc[i], s2);
+      s2 = warp_sum(s2);
+      if (l == 0) sh.sigma[c] = sqrt(s2);
+    }
+    __syncthreads();
+    double part = 0.0;
+    for (int j = threadIdx.x; j < q; j += kThreads) {
+      const double sj = sh.sigma[j];
+      int pos = 0;
+      for (int i = 0; i < q; ++i) {
+        const double si = sh.sigma[i];
+        pos += (si > sj) || (si == sj && i < j);
+      }
+      if (pos >= dense_h) part = fma(sj, sj, part);
+    }
+    const double tail = sqrt(block_sum(part, sh.red));
+    const double delta = 2.0 * FLT_EPSILON * fro *
+                         (4.0 * q * sqrt((double)p) + p * sqrt((double)q) + 2.0 * sw32 * q + 1.0);
+    if (tail - sqrt((double)(q - dense_h)) * delta > eps) {
+      if (jstats && threadIdx.x == 0) {
+        atomicAdd(&jstats[0], 1ull);
+        atomicAdd(&jstats[1], (unsigned long long)sw32);
+        atomicAdd(&jstats[3], 1ull);
+      }
+      return 1;
+    }
+  }
   // FP64 refinement
   for (int e = threadIdx.x; e < q * q; e += kThreads) v[e] = (double)v32[e];
   __syncthreads();
