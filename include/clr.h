@@ -81,7 +81,10 @@ typedef struct clr_opts {
                             ||X_n - I||_F / sqrt(N) <= ns_ladder_switch */
   double ns_ladder_switch;
   int jacobi_max_sweeps; /* one-sided Jacobi sweep limit (default 40) */
-  int reserved[8];
+  int ns_snapshot_iter;  /* k > 0: clr_sqrt_inv keeps copies of X_k, Y_k, Z_k, T_k of its k-th
+                            iteration (Section 5's rank distribution of 5th-iteration
+                            intermediates), read back with clr_ns_snapshot; 0 = off */
+  int reserved[7];
 } clr_opts;
 
 /* Summary of a CLR matrix (clr_mat_info). */
@@ -239,6 +242,12 @@ int clr_ns_residual(clr_ctx_t ctx, clr_mat_t s, clr_mat_t z, double* out, void* 
 int clr_sqrt_inv_backward(clr_ctx_t ctx, clr_tape_t tape, clr_mat_t zbar, clr_mat_t* sbar,
                           void* stream);
 int clr_tape_free(clr_ctx_t ctx, clr_tape_t tape);
+/* Intermediates of the k-th NS iteration (k = opts.ns_snapshot_iter, 1-based) of the last
+ * clr_sqrt_inv on this context: which = 0: X_k = alpha Y_{k-1} Z_{k-1}, 1: T_k, 2: Y_k = T_k
+ * Y_{k-1}, 3: Z_k = Z_{k-1} T_k (Z unscaled, before the final sqrt(alpha)).  Ownership passes
+ * to the caller (free with clr_mat_free); CLR_EINVAL when no such snapshot is held (snapshot
+ * off, the iteration not reached, or already taken).  Use clr_mat_info's rank histogram on it. */
+int clr_ns_snapshot(clr_ctx_t ctx, int which, clr_mat_t* out);
 
 /* ---- observability ------------------------------------------------------------------------
  * With profiling on, every product records CUDA events on its stream at its phase boundaries

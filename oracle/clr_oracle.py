@@ -449,16 +449,23 @@ class NSClrResult:
     iters: int
     proxy: List[float]
     converged: bool
+    # intermediates of iteration `snapshot_iter` (1-based): X_k = alpha Y_{k-1} Z_{k-1}, T_k,
+    # Y_k = T_k Y_{k-1}, Z_k = Z_{k-1} T_k (Z unscaled); empty when not requested or not reached
+    snapshot: Dict[str, CLR] = dataclasses.field(default_factory=dict)
 
 
 def ns_clr(s: CLR, alpha: float, eps: float, max_iter: int, tol: float = 0.0,
-           eps_sp: float = 0.0, recompress_dense: bool = False) -> NSClrResult:
+           eps_sp: float = 0.0, recompress_dense: bool = False,
+           snapshot_iter: int = 0) -> NSClrResult:
     """Newton–Schulz with every product a CLR product truncated at eps and T formed by the
-    CLR linear combination; X_n = alpha (Y_n Z_n) is truncated before it is scaled."""
+    CLR linear combination; X_n = alpha (Y_n Z_n) is truncated before it is scaled.  With
+    snapshot_iter = k > 0 the X, T, Y, Z of the k-th iteration are returned as well (the
+    intermediates whose block ranks Section 5 shows for the 5th iteration)."""
     n = s.shape[0]
     sizes = s.row_sizes
     y, z = s, identity(sizes)
     proxy: List[float] = []
+    snap: Dict[str, CLR] = {}
     it = 0
     converged = False
     while True:
@@ -475,7 +482,23 @@ def ns_clr(s: CLR, alpha: float, eps: float, max_iter: int, tol: float = 0.0,
         z, y = (multiply(z, t, eps, eps_sp, recompress_dense),
                 multiply(t, y, eps, eps_sp, recompress_dense))
         it += 1
-    return NSClrResult(scale(z, math.sqrt(alpha)), alpha, it, proxy, converged or tol == 0.0)
+        if it == snapshot_iter:
+            snap = {"X": x, "T": t, "Y": y, "Z": z}
+    return NSClrResult(scale(z, math.sqrt(alpha)), alpha, it, proxy, converged or tol == 0.0,
+                       snap)
+
+
+def rank_histogram(m: CLR, max_cluster: int = 256) -> np.ndarray:
+    """Block-rank histogram (Section 5's distribution of block ranks): entry 0 counts zero
+    blocks, entry r (1 <= r <= max_cluster/2) low-rank blocks of rank r, and the last entry
+    dense blocks (full rank)."""
+    h = np.zeros(max_cluster // 2 + 2, dtype=np.int64)
+    k, r = m.kinds(), m.ranks()
+    h[0] = int(np.sum(k == KIND_ZERO))
+    h[-1] = int(np.sum(k == KIND_DENSE))
+    lr = r[k == KIND_LR]
+    np.add.at(h, lr, 1)
+    return h
 
 
 def residual(s_dense: np.ndarray, z_scaled: np.ndarray) -> float:

@@ -30,7 +30,7 @@ class ClrOpts(C.Structure):
                 ("ns_tol", C.c_double), ("ns_alpha", C.c_double),
                 ("ns_power_steps", C.c_int), ("ns_fp64_tail", C.c_int),
                 ("ns_ladder_switch", C.c_double), ("jacobi_max_sweeps", C.c_int),
-                ("reserved", C.c_int * 8)]
+                ("ns_snapshot_iter", C.c_int), ("reserved", C.c_int * 7)]
 
 
 class ClrInfo(C.Structure):
@@ -94,6 +94,7 @@ _SIGNATURES = {
     "clr_ns_residual": (C.c_int, [_VP, _VP, _VP, C.POINTER(C.c_double), _VP]),
     "clr_sqrt_inv_backward": (C.c_int, [_VP, _VP, _VP, C.POINTER(_VP), _VP]),
     "clr_tape_free": (C.c_int, [_VP, _VP]),
+    "clr_ns_snapshot": (C.c_int, [_VP, C.c_int, C.POINTER(_VP)]),
     "clr_matvec": (C.c_int, [_VP, _VP, _VP, _VP, _VP]),
     "clr_block_compress_noalloc": (C.c_int, [C.c_int, _VP, C.c_int64, C.c_int, C.c_int,
                                              C.c_double, C.c_int, _VP, _VP, _VP, _VP, _VP]),
@@ -418,6 +419,13 @@ class Context:
                  "ms_total": st.ms_total, "status": status}
         return Matrix(self, z.value, s.row_sizes, s.col_sizes), stats, \
             (Tape(self, tape.value) if keep_tape else None)
+
+    def ns_snapshot(self, which: str, like: Matrix) -> Matrix:
+        """The X, T, Y or Z of the NS iteration named by the option ns_snapshot_iter, from
+        the last sqrt_inv on this context (ownership passes to the returned Matrix)."""
+        h = C.c_void_p()
+        self._check(load().clr_ns_snapshot(self.handle, "XTYZ".index(which), C.byref(h)))
+        return Matrix(self, h.value, like.row_sizes, like.col_sizes)
 
     def ns_residual(self, s: Matrix, z: Matrix, stream=None) -> float:
         out = C.c_double()

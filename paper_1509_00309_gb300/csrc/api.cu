@@ -162,6 +162,8 @@ struct clr_ctx_s {
   std::vector<std::pair<cudaEvent_t, int>> prof_events;  // (event, phase that ENDS here)
   std::vector<cudaEvent_t> event_pool;
   clr_profile prof;
+  // NS snapshot of one iteration: X, T, Y, Z (opts.ns_snapshot_iter)
+  clr_mat_t snap[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 struct clr_mat_s {
@@ -460,6 +462,10 @@ extern "C" int clr_destroy(clr_ctx_t ctx) {
   for (auto& pe : ctx->prof_events) cudaEventDestroy(pe.first);
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   for (auto& w : ctx->wsets) w->release();
+  for (clr_mat_t& m : ctx->snap) {
+    if (m) free_mat(m);
+    m = nullptr;
+  }
   ctx->small.release();
   ctx->upload.release();
   ctx->jstats.release();
@@ -1158,6 +1164,10 @@ extern "C" int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t* z_out,
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   cudaEventRecord(e0, s);
+  for (clr_mat_t& m : ctx->snap) {
+    if (m) free_mat(m);
+    m = nullptr;
+  }
   Tuning tn;
   tn.prec = choose_precision(ctx, s_mat, s_mat);
   int& prec = tn.prec;
@@ -1204,6 +1214,14 @@ extern "C" int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t* z_out,
     std::swap(Z, Zn);
     std::swap(Y, Yn);
     ++it;
+    if (it == o.ns_snapshot_iter) {
+      const clr_mat_t src[4] = {X, T, Y, Z};
+      for (int k = 0; k < 4 && !st; ++k) {
+        st = alloc_mat(ctx, nr, sz, nr, sz, &ctx->snap[k]);
+        if (!st) st = clr_mat_copy(ctx, src[k], ctx->snap[k], s);
+      }
+      if (st) break;
+    }
   }
   cudaEventRecord(e1, s);
   cudaEventSynchronize(e1);
@@ -1250,6 +1268,15 @@ extern "C" int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t* z_out,
     ctx->err = "Newton-Schulz did not reach ns_tol";
     return CLR_ENOCONV;
   }
+  return CLR_OK;
+}
+
+extern "C" int clr_ns_snapshot(clr_ctx_t ctx, int which, clr_mat_t* out) {
+  if (!ctx || !out || which < 0 || which > 3) return CLR_EINVAL;
+  *out = nullptr;
+  if (!ctx->snap[which]) return fail(ctx, CLR_EINVAL, "no NS snapshot held");
+  *out = ctx->snap[which];
+  ctx->snap[which] = nullptr;
   return CLR_OK;
 }
 

@@ -1,0 +1,79 @@
+"""Block-rank diagnostics of the Newton–Schulz iterates (Section 5, the distribution of block
+ranks of the 5th-iteration intermediates X, Y, Z, T and of the input S).
+
+    python -m paper_1509_00309_gb300.diagnostics --shape 8x8x4 --iter 5
+
+builds the 3D lattice overlap matrix (16 points per site, clusters of 64..256 points, eps_lr
+1e-6, drop 1e-10, eps_sp 1e-13) on the GPU, runs clr_sqrt_inv with the snapshot option and
+prints one JSON object: per matrix its block counts by kind and the rank histogram (entry 0:
+zero blocks, entry r: low-rank blocks of rank r, last entry: dense blocks), plus the NS timing
+and the SVD counters of the library's profile.  Everything runs through the C ABI."""
+import argparse
+import json
+import time
+from typing import Dict
+
+import numpy as np
+
+from . import clr
+from . import workloads as wl
+
+
+def histogram_summary(m: "clr.Matrix") -> Dict:
+    info = m.info()
+    h = np.asarray(info["rank_hist"], dtype=np.int64)
+    lr_ranks = np.repeat(np.arange(len(h) - 2) + 1, h[1:-1])
+    return {"zero": int(h[0]), "dense": int(h[-1]), "low_rank": int(h[1:-1].sum()),
+            "lr_rank_mean": float(lr_ranks.mean()) if lr_ranks.size else 0.0,
+            "lr_rank_max": int(lr_ranks.max()) if lr_ranks.size else 0,
+            "hist": {int(r): int(c) for r, c in enumerate(h) if c}}
+
+
+def ns_rank_distribution(ctx: "clr.Context", s: "clr.Matrix", k: int = 5) -> Dict:
+    """Run NS on s with the k-th iteration snapshot on; histograms of S and of X, T, Y, Z."""
+    ctx.set_opts(ns_snapshot_iter=k)
+    ctx.profile_enable(True)
+    t0 = time.time()
+    z, st, _ = ctx.sqrt_inv(s, allow_noconv=True)
+    wall = time.time() - t0
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    out = {"S": histogram_summary(s)}
+    for name in "XTYZ":
+        out[name + "_%d" % k] = histogram_summary(ctx.ns_snapshot(name, s))
+    out["Z_final"] = histogram_summary(z)
+    out["ns"] = {"iters": st["iters"], "residual": st["residual"], "wall_s": wall,
+                 "ms_per_iter": st["ms_total"] / max(1, st["iters"]),
+                 "proxy": st["proxy"], "status": st["status"]}
+    out["profile"] = {key: prof[key] for key in ("products", "ms_dense", "ms_lowrank",
+                                                  "ms_compress", "svd_blocks", "svd_sweeps_fp32",
+                                                  "svd_sweeps_fp64", "svd_early_dense")}
+    ctx.set_opts(ns_snapshot_iter=0)
+    return out
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--shape", default="8x8x4", help="lattice sites, e.g. 16x16x8 (N = 16 x sites)")
+    ap.add_argument("--iter", type=int, default=5)
+    ap.add_argument("--precision", default="fp64")
+    ap.add_argument("--max-iter", type=int, default=40)
+    ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--no-recompress-dense", action="store_true")
+    args = ap.parse_args()
+    import torch
+    shape = tuple(int(v) for v in args.shape.split("x"))
+    w = wl.lattice_overlap(shape=shape)
+    ctx = clr.Context(0, precision=args.precision, eps_lr=w.eps_lr, eps_sp=w.eps_sp,
+                      ns_tol=args.tol, ns_max_iter=args.max_iter,
+                      recompress_dense=0 if args.no_recompress_dense else 1)
+    s = ctx.from_dense(torch.from_numpy(w.a).cuda(), w.row_sizes, eps_lr=w.eps_lr,
+                       drop_norm=w.drop_norm)
+    out = {"workload": w.name, "n": w.n, "clusters": len(w.row_sizes),
+           "precision": args.precision, "recompress_dense": not args.no_recompress_dense}
+    out.update(ns_rank_distribution(ctx, s, args.iter))
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -100,3 +100,39 @@ def test_clr_ns_truncated_converges():
     ref = co.inv_sqrt_eigh(w.a)
     assert co.residual(w.a, c.z.to_dense()) < 1e-5
     assert np.linalg.norm(c.z.to_dense() - ref) / np.linalg.norm(ref) < 1e-4
+
+
+def test_clr_ns_snapshot_on_diagonal_follows_scalar_recurrence():
+    # S diagonal in three dense diagonal blocks, eps = 0: the k-th iteration's X, T, Y, Z are
+    # diagonal with the scalar recurrence x = alpha y z, t = f(x), z <- z t, y <- t y
+    lam = np.array([0.02, 0.5, 1.0, 2.0, 3.5, 5.0, 6.0, 8.0, 9.0])
+    sizes = [2, 4, 3]
+    s = co.build(np.diag(lam), sizes, sizes, 0.0)
+    alpha = 1.0 / 9.5
+    k = 3
+    res = co.ns_clr(s, alpha, 0.0, max_iter=6, snapshot_iter=k)
+    y, z = lam.copy(), np.ones_like(lam)
+    for _ in range(k):
+        x = alpha * y * z
+        t = (15.0 - 10.0 * x + 3.0 * x * x) / 8.0
+        z, y = z * t, t * y
+    for name, want in (("X", x), ("T", t), ("Y", y), ("Z", z)):
+        got = res.snapshot[name].to_dense()
+        assert np.allclose(got, np.diag(want), rtol=1e-14, atol=1e-15), name
+    assert co.ns_clr(s, alpha, 0.0, max_iter=2, snapshot_iter=k).snapshot == {}
+
+
+def test_rank_histogram_counts_kinds_and_ranks():
+    rng = np.random.default_rng(4)
+    sizes = [6, 5, 7]
+
+    def lr(m, n, r):
+        return (co.KIND_LR, (rng.standard_normal((m, r)), rng.standard_normal((n, r))))
+
+    spec = [[(co.KIND_DENSE, rng.standard_normal((6, 6))), lr(6, 5, 2), (co.KIND_ZERO, None)],
+            [lr(5, 6, 1), (co.KIND_DENSE, rng.standard_normal((5, 5))), lr(5, 7, 2)],
+            [(co.KIND_ZERO, None), lr(7, 5, 3), (co.KIND_ZERO, None)]]
+    h = co.rank_histogram(co.from_blocks(sizes, sizes, spec))
+    want = np.zeros(130, dtype=np.int64)
+    want[0], want[1], want[2], want[3], want[-1] = 3, 1, 2, 1, 2
+    assert np.array_equal(h, want)
