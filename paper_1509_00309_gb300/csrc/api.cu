@@ -342,6 +342,13 @@ int make_plan(clr_ctx_t ctx, int nI, int nJ, int nK, Plan* p) {
 
 int grid_of(clr_ctx_t ctx, int per_sm) { return std::max(1, ctx->n_sm * per_sm); }
 
+int max_cluster(clr_mat_t m) {
+  int c = 0;
+  for (int v : m->row_sizes) c = std::max(c, v);
+  for (int v : m->col_sizes) c = std::max(c, v);
+  return c;
+}
+
 // SVD counters while profiling (not inside a graph capture), else null
 unsigned long long* jst(clr_ctx_t ctx) {
   return (ctx->prof_on && !ctx->capturing && ctx->jstats.p)
@@ -370,6 +377,11 @@ void prof_launches(clr_ctx_t ctx, int n) {
 constexpr int64_t kScratchPerCta =
     (int64_t)(CLR_MAX_CLUSTER / 2) * (CLR_MAX_CLUSTER / 2) +
     (int64_t)CLR_MAX_CLUSTER * (CLR_MAX_CLUSTER / 2);
+// Per-CTA scratch shared by the low-rank product kernel and (after it, on the same stream) the
+// recompression kernels' mixed-precision SVD.
+inline int64_t scratch_per_cta() {
+  return kScratchPerCta > kSvdScratchPerCta ? kScratchPerCta : kSvdScratchPerCta;
+}
 
 int choose_precision(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, double eps_in = -1.0) {
   int prec = ctx->opts.precision;
@@ -557,6 +569,8 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
     lda = m->n_cols;
   }
   cudaError_t e = ctx->cur->ws.ensure(2 * (size_t)m->n_rows * m->n_cols * sizeof(double));
+  if (e == cudaSuccess)
+    e = ctx->cur->scratch.ensure((size_t)grid_of(ctx, 2) * scratch_per_cta() * sizeof(double));
   if (e == cudaSuccess) e = ctx->cur->counters.ensure(sizeof(PlanCounters));
   if (e != cudaSuccess) {
     free_mat(m);
@@ -570,8 +584,9 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
     launch_block_norms_dense(m->view(), s);
     launch_dense_kinds(m->view(), drop_norm, &pc->err, s);
   } else {
-    launch_compress_dense(m->view(), nullptr, nullptr, src, lda, (double*)ctx->cur->ws.p, eps_lr,
-                          drop_norm, 0, ctx->opts.jacobi_max_sweeps, grid_of(ctx, 2), &pc->err, jst(ctx), s);
+    launch_compress_dense(m->view(), nullptr, nullptr, src, lda, (double*)ctx->cur->ws.p,
+                          (double*)ctx->cur->scratch.p, max_cluster(m), eps_lr, drop_norm, 0,
+                          ctx->opts.jacobi_max_sweeps, grid_of(ctx, 2), &pc->err, jst(ctx), s);
   }
   e = cudaGetLastError();
   int errflag = 0;
@@ -831,7 +846,7 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   if (st) return st;
   CLR_CUDA(ctx->cur->ws.ensure(2 * (size_t)c->n_rows * c->n_cols * sizeof(double)));
   const int lr_grid = grid_of(ctx, tune.lr_mult);
-  CLR_CUDA(ctx->cur->scratch.ensure((size_t)lr_grid * kScratchPerCta * sizeof(double)));
+  CLR_CUDA(ctx->cur->scratch.ensure((size_t)lr_grid * scratch_per_cta() * sizeof(double)));
   MatView av = a->view(), bv = b->view(), cv = c->view();
   const clr_opts& o = ctx->opts;
   prof_mark(ctx, s, PH_START);
@@ -855,10 +870,12 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   CLR_CHECK_LAUNCH("low-rank products");
   prof_launches(ctx, 1);
   prof_mark(ctx, s, PH_LOWRANK);
-  launch_compress_qr(cv, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p, eps_lr,
-                     o.jacobi_max_sweeps, lr_grid, &p.counters->err, jst(ctx), s);
+  launch_compress_qr(cv, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p,
+                     (double*)ctx->cur->scratch.p, max_cluster(c), eps_lr, o.jacobi_max_sweeps,
+                     lr_grid, &p.counters->err, jst(ctx), s);
   launch_compress_dense(cv, p.l_dcomp, &p.counters->n_dcomp, nullptr, 0, (double*)ctx->cur->ws.p,
-                        eps_lr, 0.0, 0, o.jacobi_max_sweeps, lr_grid, &p.counters->err, jst(ctx), s);
+                        (double*)ctx->cur->scratch.p, max_cluster(c), eps_lr, 0.0, 0,
+                        o.jacobi_max_sweeps, lr_grid, &p.counters->err, jst(ctx), s);
   CLR_CHECK_LAUNCH("recompression");
   prof_launches(ctx, 2);
   prof_mark(ctx, s, PH_COMPRESS);
@@ -985,14 +1002,17 @@ extern "C" int clr_lincomb(clr_ctx_t ctx, double a, clr_mat_t x, double b, clr_m
   int st = make_plan(ctx, x->nr, x->nc, 1, &p);
   if (st) return st;
   CLR_CUDA(ctx->cur->ws.ensure(2 * (size_t)x->n_rows * x->n_cols * sizeof(double)));
+  const int grid = grid_of(ctx, 2);
+  CLR_CUDA(ctx->cur->scratch.ensure((size_t)grid * scratch_per_cta() * sizeof(double)));
   const clr_opts& o = ctx->opts;
   MatView xv = x->view(), yv = y->view(), ov = out->view();
   launch_lincomb_plan(a, xv, b, yv, diag, ov, p, (double*)ctx->cur->ws.p, o.recompress_dense, s);
-  launch_compress_qr(ov, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p, o.eps_lr,
-                     o.jacobi_max_sweeps, grid_of(ctx, 2), &p.counters->err, jst(ctx), s);
+  launch_compress_qr(ov, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p,
+                     (double*)ctx->cur->scratch.p, max_cluster(out), o.eps_lr,
+                     o.jacobi_max_sweeps, grid, &p.counters->err, jst(ctx), s);
   launch_compress_dense(ov, p.l_dcomp, &p.counters->n_dcomp, nullptr, 0, (double*)ctx->cur->ws.p,
-                        o.eps_lr, 0.0, 0, o.jacobi_max_sweeps, grid_of(ctx, 2),
-                        &p.counters->err, jst(ctx), s);
+                        (double*)ctx->cur->scratch.p, max_cluster(out), o.eps_lr, 0.0, 0,
+                        o.jacobi_max_sweeps, grid, &p.counters->err, jst(ctx), s);
   CLR_CHECK_LAUNCH("lincomb");
   return CLR_OK;
 }

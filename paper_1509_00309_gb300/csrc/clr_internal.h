@@ -100,17 +100,23 @@ void launch_lr_products(const MatView& A, const MatView& B, const MatView& C, co
                         cudaStream_t st);
 // k_svd.cu
 // jstats (may be null): device counters {svd blocks, FP32 sweeps, FP64 sweeps, early dense}
+// svd_scratch: grid x kSvdScratchPerCta doubles (FP32 working copies and an FP64 q x q factor
+// of the mixed-precision SVD).
+constexpr int64_t kSvdScratchPerCta = (int64_t)2 * CLR_MAX_CLUSTER * CLR_MAX_CLUSTER;
+// max_cluster: the largest row or column cluster of C (sizes the shared-memory request).
 void launch_compress_qr(const MatView& C, const int* list, const int* count, const int* rsum,
-                        double* ws, double eps, int max_sweeps, int grid, int* err,
-                        unsigned long long* jstats, cudaStream_t st);
+                        double* ws, double* svd_scratch, int max_cluster, double eps,
+                        int max_sweeps, int grid, int* err, unsigned long long* jstats,
+                        cudaStream_t st);
 // Dense truncated SVD of blocks listed in `list` (count on device).  The source of block b is
 // either the matrix's own slot (src == nullptr) or a row-major dense matrix src with leading
 // dimension lds.  drop_norm: blocks with norm below it become zero.  dense_only: skip the
 // SVD (eps = 0 rule) and store every non-dropped block dense.
 void launch_compress_dense(const MatView& C, const int* list, const int* count,
-                           const double* src, int64_t lds, double* ws, double eps,
-                           double drop_norm, int dense_only, int max_sweeps, int grid,
-                           int* err, unsigned long long* jstats, cudaStream_t st);
+                           const double* src, int64_t lds, double* ws, double* svd_scratch,
+                           int max_cluster, double eps, double drop_norm, int dense_only,
+                           int max_sweeps, int grid, int* err, unsigned long long* jstats,
+                           cudaStream_t st);
 void launch_block_norms(const MatView& M, cudaStream_t st);
 void launch_block_norms_dense(const MatView& M, cudaStream_t st);
 void launch_scale_blocks(const MatView& M, double alpha, cudaStream_t st);

@@ -12,8 +12,8 @@
 //   one-sided Jacobi SVD   Hestenes rotations on column pairs, round-robin ordering so a
 //                          round's pairs are disjoint (one warp per pair), until no pair has
 //                          |g_a.g_b| > tol ||g_a|| ||g_b|| or the sweep limit is reached.
-// Working arrays live in the tile's workspace slot (2 m n doubles per tile, enough for
-// either route).
+// FP64 working arrays live in the tile's workspace slot (2 m n doubles per tile, enough for
+// either route); the FP32 copies of the mixed-precision SVD in a per-CTA scratch.
 #include <cfloat>
 #include <mutex>
 
@@ -21,7 +21,7 @@
 
 namespace clr {
 
-constexpr int kThreads = 256;
+constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 
 template <typename T>
@@ -106,8 +106,81 @@ __device__ void apply_q(const double* v, int p, int q, int64_t ldv, const double
   }
 }
 
+// Per-pair arithmetic of the Jacobi sweeps.  FP64 runs at 1/64 of the FP32 rate on this part
+// and each FP64 instruction of a warp occupies its sub-partition's FP64 pipe for many cycles,
+// so the scalar steps avoid FP64 square roots and most divisions: the tests compare squares,
+// the rotation's tangent t is found in FP32 from zeta (its accuracy only sets how far one
+// rotation reduces the pair's inner product) and c = (1 + t^2)^-1/2 is refined in FP64 by two
+// Newton steps from the FP32 seed, so that c^2 + s^2 = 1 to FP64 rounding and the rotation is
+// orthogonal.
+// In FP32 the hardware approximations (a few ulp) serve throughout: the FP32 stages only find
+// rotations that the FP64 stages apply and refine.
+__device__ __forceinline__ float rt_sqrt(float x) {
+  return x > 0.f ? (x <= FLT_MAX ? x * rsqrtf(x) : x) : 0.f;
+}
+
+__device__ __forceinline__ bool pair_below_floor(float al, float be, float f2) {
+  const float s = rt_sqrt(al * be);
+  return s == 0.f || s <= f2;
+}
+__device__ __forceinline__ bool pair_below_floor(double al, double be, double f2) {
+  const double p2 = al * be;
+  return p2 == 0.0 || p2 <= f2 * f2;
+}
+
+// |g| <= tol |g_a| |g_b| or |g| <= floor2
+__device__ __forceinline__ bool pair_converged(float al, float be, float g, float tol, float f2) {
+  const float s = rt_sqrt(al * be);
+  return fabsf(g) <= tol * s || fabsf(g) <= f2;
+}
+__device__ __forceinline__ bool pair_converged(double al, double be, double g, double tol,
+                                               double f2) {
+  const double g2 = g * g;
+  return g2 <= tol * tol * (al * be) || g2 <= f2 * f2;
+}
+
+// Rutishauser's rotation: zeta = (b - a) / 2g, t = sign(zeta) / (|zeta| + sqrt(1 + zeta^2)),
+// c = 1 / sqrt(1 + t^2), s = c t.
+// (for |zeta| > 2^40, where zeta^2 may overflow, the asymptote 1 / (2 zeta))
+__device__ __forceinline__ float tangent_of(float zeta) {
+  if (fabsf(zeta) > 0x1p40f) return __fdividef(0.5f, zeta);
+  return copysignf(__fdividef(1.f, fabsf(zeta) + rt_sqrt(1.f + zeta * zeta)), zeta);
+}
+__device__ __forceinline__ float rot_tangent(float d, float g) {
+  return tangent_of(__fdividef(d, 2.f * g));
+}
+__device__ __forceinline__ void rotation(float al, float be, float g, float& c, float& s,
+                                         float& t) {
+  t = rot_tangent(be - al, g);
+  c = rsqrtf(1.f + t * t);
+  s = c * t;
+}
+__device__ __forceinline__ void rotation(double al, double be, double g, double& c, double& s,
+                                         double& t) {
+  // zeta in FP64 (the operands may lie far outside the FP32 range).  For a large angle
+  // (|cos| > 1e-3: the first sweeps of a fresh start, nearly parallel columns) the tangent in
+  // FP64, since a rotation that is off by u32 there leaves a leak that is large relative to the
+  // smaller column; for the small angles of a refinement in FP32 where |zeta| < 2^100, else its
+  // asymptote 1 / (2 zeta).
+  const double zeta = (be - al) / (2.0 * g);
+  if (g * g > 1e-6 * (al * be)) {
+    t = copysign(1.0 / (fabs(zeta) + sqrt(fma(zeta, zeta, 1.0))), zeta);
+  } else if (fabs(zeta) < 0x1p100) {
+    t = (double)tangent_of((float)zeta);
+  } else {
+    t = 0.5 / zeta;
+  }
+  const double u = fma(t, t, 1.0);
+  double r = (double)rsqrtf((float)u);
+  r = r * fma(-0.5 * u, r * r, 1.5);
+  r = r * fma(-0.5 * u, r * r, 1.5);
+  c = r;
+  s = r * t;
+}
+
 // One-sided Jacobi on the q columns of g (p x q, ld ldg); v (q x q, ld ldv) accumulates the
-// rotations (initialised to I here unless reset_v is false).  On return g = U S and the input
+// rotations (initialised to I here unless reset_v is false; not accumulated when v is null).
+// On return g = U S and the input
 // equals g v^T (times the initial v^T when v is not reset).  T is float or double; the
 // convergence threshold is the type's epsilon times sqrt(p) (times tol_scale); pairs whose inner
 // product is below floor2 are left alone.
@@ -120,7 +193,7 @@ __device__ int jacobi_svd(T* g, int p, int q, int64_t ldg, T* v, int64_t ldv,
   // pair costs one inner product unless it is rotated.
   __shared__ T nrm2[CLR_MAX_CLUSTER];
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
-  if (reset_v) {
+  if (reset_v && v) {
     for (int e = threadIdx.x; e < q * q; e += kThreads)
       v[(e % q) + (int64_t)(e / q) * ldv] = (e % q == e / q) ? T(1) : T(0);
     __syncthreads();
@@ -146,41 +219,76 @@ __device__ int jacobi_svd(T* g, int p, int q, int64_t ldg, T* v, int64_t ldv,
           a = round;
           b = qq - 1;
         } else {
-          a = (round + k) % (qq - 1);
-          b = (round - k + (qq - 1)) % (qq - 1);
+          a = round + k;
+          if (a >= qq - 1) a -= qq - 1;
+          b = round - k;
+          if (b < 0) b += qq - 1;
         }
         if (a >= q || b >= q) continue;
         const T al = nrm2[a], be = nrm2[b];
-        const T scale = sqrt(al) * sqrt(be);
-        // both columns at the noise floor: |g_a . g_b| <= scale <= floor2, nothing to do
-        if (scale == T(0) || scale <= floor2) continue;
+        // both columns at the noise floor: |g_a . g_b| <= |g_a| |g_b| <= floor2, nothing to do
+        if (pair_below_floor(al, be, floor2)) continue;
         T* ga = g + (int64_t)a * ldg;
         T* gb = g + (int64_t)b * ldg;
+        // FP64 (global memory): the two columns stay in registers between the inner product
+        // and the rotation; FP32 (shared memory): re-read
+        constexpr int kPer = sizeof(T) == 8 ? CLR_MAX_CLUSTER / 32 : 1;
+        T xa[kPer], xb[kPer];
         T ga_gb = 0;
-        for (int i = l; i < p; i += 32) ga_gb = fma(ga[i], gb[i], ga_gb);
-        ga_gb = warp_sum(ga_gb);
-        if (fabs(ga_gb) <= tol * scale || fabs(ga_gb) <= floor2) continue;
-        const T zeta = (be - al) / (T(2) * ga_gb);
-        const T t = copysign(T(1), zeta) / (fabs(zeta) + sqrt(T(1) + zeta * zeta));
-        const T c = T(1) / sqrt(T(1) + t * t);
-        const T sn = c * t;
-        T na = 0, nb = 0;
-        for (int i = l; i < p; i += 32) {
-          const T x = ga[i], y = gb[i];
-          const T xa = c * x - sn * y, yb = sn * x + c * y;
-          ga[i] = xa;
-          gb[i] = yb;
-          na = fma(xa, xa, na);
-          nb = fma(yb, yb, nb);
+        if constexpr (sizeof(T) == 8) {
+#pragma unroll
+          for (int j = 0; j < kPer; ++j) {
+            if (32 * j >= p) break;
+            const int i = l + 32 * j;
+            xa[j] = i < p ? ga[i] : T(0);
+            xb[j] = i < p ? gb[i] : T(0);
+            ga_gb = fma(xa[j], xb[j], ga_gb);
+          }
+        } else {
+          for (int i = l; i < p; i += 32) ga_gb = fma(ga[i], gb[i], ga_gb);
         }
-        na = warp_sum(na);
-        nb = warp_sum(nb);
-        T* va = v + (int64_t)a * ldv;
-        T* vb = v + (int64_t)b * ldv;
-        for (int i = l; i < q; i += 32) {
-          const T x = va[i], y = vb[i];
-          va[i] = c * x - sn * y;
-          vb[i] = sn * x + c * y;
+        ga_gb = warp_sum(ga_gb);
+        if (pair_converged(al, be, ga_gb, tol, floor2)) continue;
+        T c, sn, t;
+        rotation(al, be, ga_gb, c, sn, t);
+        if constexpr (sizeof(T) == 8) {
+#pragma unroll
+          for (int j = 0; j < kPer; ++j) {
+            if (32 * j >= p) break;
+            const int i = l + 32 * j;
+            if (i < p) {
+              ga[i] = c * xa[j] - sn * xb[j];
+              gb[i] = sn * xa[j] + c * xb[j];
+            }
+          }
+        } else {
+          for (int i = l; i < p; i += 32) {
+            const T x = ga[i], y = gb[i];
+            ga[i] = c * x - sn * y;
+            gb[i] = sn * x + c * y;
+          }
+        }
+        // new squared norms: a - t g and b + t g exactly; recomputed from the rotated columns
+        // when the update cancels (a column losing more than 63/64 of its square)
+        T na = al - t * ga_gb, nb = be + t * ga_gb;
+        if (!(na > al * T(0.015625)) || !(nb > be * T(0.015625))) {
+          __syncwarp();
+          T sa = 0, sb = 0;
+          for (int i = l; i < p; i += 32) {
+            sa = fma(ga[i], ga[i], sa);
+            sb = fma(gb[i], gb[i], sb);
+          }
+          na = warp_sum(sa);
+          nb = warp_sum(sb);
+        }
+        if (v) {
+          T* va = v + (int64_t)a * ldv;
+          T* vb = v + (int64_t)b * ldv;
+          for (int i = l; i < q; i += 32) {
+            const T x = va[i], y = vb[i];
+            va[i] = c * x - sn * y;
+            vb[i] = sn * x + c * y;
+          }
         }
         if (l == 0) {
           nrm2[a] = na;
@@ -203,6 +311,7 @@ struct SvdShared {
   double sorted[CLR_MAX_CLUSTER];   // descending
   int perm[CLR_MAX_CLUSTER];        // sorted position -> column
   int flag;
+  int v_tracked;  // svd_mixed: 1 when v holds the right singular vectors (else recover_right)
   int rank;
   double kept_sq;
 };
@@ -263,30 +372,132 @@ struct SrcView {
   }
 };
 
-// Mixed-precision one-sided Jacobi SVD of the p x q (p >= q) matrix A given by `a`:
-//  1. FP32 sweeps on a copy (FP32 runs far faster than FP64 on this part) until converged at
-//     FP32 accuracy, accumulating V32;
-//  2. V = V32 orthonormalised in FP64 (modified Gram-Schmidt) and G = A V in FP64, so A and G
-//     have the same singular values and G's columns are nearly orthogonal;
-//  3. FP64 sweeps continuing on (G, V) -- a few from this start.
-// Pairs whose inner product is below the noise floor are not rotated: p u ||A||_F in FP32, and
-// max(p u ||A||_F, 1e-3 eps) in FP64 (columns that small cannot move a truncation at eps).
-// On return g = U S and A = g v^T in FP64.  g (p x q doubles) also serves as the FP32 scratch
-// (p q + q^2 floats).
+// v (q x q, ld q) <- the columns of the FP32 matrix v32 orthonormalised in FP64 (modified
+// Gram-Schmidt).
+__device__ void orthonormalise_fp64(const float* v32, double* v, int q, SvdShared& sh) {
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  for (int e = threadIdx.x; e < q * q; e += kThreads) v[e] = (double)v32[e];
+  __syncthreads();
+  for (int j = 0; j < q; ++j) {
+    double* vj = v + (int64_t)j * q;
+    double part = 0.0;
+    for (int i = threadIdx.x; i < q; i += kThreads) part = fma(vj[i], vj[i], part);
+    const double nrm = sqrt(block_sum(part, sh.red));
+    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    for (int i = threadIdx.x; i < q; i += kThreads) vj[i] *= inv;
+    __syncthreads();
+    for (int k = j + 1 + w; k < q; k += kWarps) {
+      double* vk = v + (int64_t)k * q;
+      double d = 0.0;
+      for (int i = l; i < q; i += 32) d = fma(vj[i], vk[i], d);
+      d = warp_sum(d);
+      for (int i = l; i < q; i += 32) vk[i] = fma(-d, vj[i], vk[i]);
+    }
+    __syncthreads();
+  }
+}
+
+// g (p x q, ld p) = A v in FP64.
+__device__ void project_fp64(const SrcView& a, int p, int q, const double* v, double* g) {
+  for (int e = threadIdx.x; e < p * q; e += kThreads) {
+    const int i = e % p, j = e / p;
+    const double* vj = v + (int64_t)j * q;
+    double s2 = 0.0;
+    for (int k = 0; k < q; ++k) s2 = fma(a.at(i, k), vj[k], s2);
+    g[e] = s2;
+  }
+  __syncthreads();
+}
+
+// y (q x r, ld q) = A^T G_r in FP64, G_r the r kept columns of g (p x q, ld p) in the order
+// perm; with G_r = U_r S_r this is V_r S_r^2.
+__device__ void recover_right(const SrcView& a, int p, int q, const double* g, const int* perm,
+                              int r, double* y) {
+  for (int e = threadIdx.x; e < q * r; e += kThreads) {
+    const int j = e % q, c = e / q;
+    const double* gc = g + (int64_t)perm[c] * p;
+    double s2 = 0.0;
+    for (int k = 0; k < p; ++k) s2 = fma(a.at(k, j), gc[k], s2);
+    y[e] = s2;
+  }
+  __syncthreads();
+}
+
+// m (rows x q, ld ldm) <- m w in FP64 with the q x q factor w given row-major (wt[k q + c] =
+// w(k, c)), row by row in place: one warp per row, the row held in registers (8 entries per
+// lane) and broadcast by shuffles, 8 output columns per lane (consecutive lanes read
+// consecutive entries of wt).
+__device__ void right_multiply_fp64(double* m, int rows, int64_t ldm, int q, const double* wt) {
+  constexpr int kPer = CLR_MAX_CLUSTER / 32;
+  const int wp = threadIdx.x / 32, l = threadIdx.x % 32;
+  for (int i = wp; i < rows; i += kWarps) {
+    double r[kPer], acc[kPer];
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      const int k = l + 32 * j;
+      r[j] = k < q ? m[i + (int64_t)k * ldm] : 0.0;
+      acc[j] = 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kPer; ++j) {
+      if (32 * j >= q) break;
+      for (int kk = 0; kk < 32; ++kk) {
+        const int k = 32 * j + kk;
+        const double rk = __shfl_sync(0xffffffffu, r[j], kk);
+        if (k >= q) break;
+#pragma unroll
+        for (int o = 0; o < kPer; ++o) {
+          const int c = l + 32 * o;
+          if (c < q) acc[o] = fma(rk, wt[(int64_t)k * q + c], acc[o]);
+        }
+      }
+    }
+    __syncwarp();
+#pragma unroll
+    for (int o = 0; o < kPer; ++o) {
+      const int c = l + 32 * o;
+      if (c < q) m[i + (int64_t)c * ldm] = acc[o];
+    }
+  }
+  __syncthreads();
+}
+
+// Mixed-precision one-sided Jacobi SVD of the p x q (p >= q) matrix A given by `a`.  FP64 runs
+// at a small fraction of the FP32 rate on this part, so the rotations are found in FP32 and only
+// applied, once per stage, in FP64:
+//  1. FP32 sweeps on a copy of A until converged at FP32 accuracy, accumulating V1;
+//  2. V = V1 orthonormalised in FP64 (modified Gram-Schmidt) and G = A V in FP64.  G's columns
+//     are orthogonal to FP32 accuracy relative to ||A||; the part of the spectrum below
+//     u32 ||A|| is still unresolved (it was rounding noise in the FP32 copy of A);
+//  3. FP32 sweeps on a copy of G, whose columns are rounded relative to their own norms, so
+//     the small columns are resolved against each other and against the large ones; V2
+//     orthonormalised in FP64 and G <- G V2;
+//  4. FP64 sweeps continuing on G -- a quadratically convergent clean-up from there.  The
+//     rotations are not accumulated: for kept columns G_r = U_r S_r the right factor is
+//     V_r = A^T G_r S_r^-2 (recover_right), and G_r (A^T G_r S_r^-2)^T = P A with P the
+//     orthogonal projector onto span(G_r), so rounding in V_r is scaled back by S_r.
+// Pairs whose inner product is below the noise floor are not rotated: p u ||A||_F in FP32 on A,
+// and max(p u ||A||_F, 1e-3 eps) on G (columns that small cannot move a truncation at eps).
+// On return g = U S in FP64, and v the right factor when sh.v_tracked (else workspace).  sc:
+// kSvdScratchPerCta doubles; sm32:
+// sm_cap floats of shared memory for the FP32 copies (used where they fit).
 //
 // Certified dense exit (dense_h >= 0): the block is stored dense when its eps-rank exceeds
 // dense_h, i.e. when the singular-value tail sqrt(sum_{i >= dense_h} s_i^2) exceeds eps.  After
-// the FP32 phase every sorted column norm c_i of G32 is within delta of s_i(A), with
+// stage 1 every sorted column norm c_i of G32 is within delta of s_i(A), with
 //   delta = 2 u32 ||A||_F (4 q sqrt(p) + p sqrt(q) + 2 s32 q + 1)
 // (backward error of s32 FP32 sweeps of rotations, the rounding of A to FP32, and the residual
 // non-orthogonality of G32's columns: pairs within 4 u32 sqrt(p) of orthogonal or below the FP32
 // noise floor).  So tail(A) >= tail(c) - sqrt(q - dense_h) delta, and when that exceeds eps the
-// FP64 phase could only confirm "dense": it is skipped and the function returns 1.
-__device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, int max_sweeps,
-                         double eps, int dense_h, double fro, SvdShared& sh,
-                         unsigned long long* jstats) {
-  float* g32 = reinterpret_cast<float*>(g);
-  float* v32 = g32 + (int64_t)p * q;
+// later stages could only confirm "dense": they are skipped and the function returns 1.
+__device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, double* sc,
+                         float* sm32, int sm_cap, int max_sweeps, double eps, int dense_h,
+                         double fro, SvdShared& sh, unsigned long long* jstats) {
+  // FP32 copies in shared memory where they fit (sm_cap floats), else in the scratch
+  const int64_t pq = (int64_t)p * q;
+  float* g32 = pq <= sm_cap ? sm32 : reinterpret_cast<float*>(sc);
+  float* v32 = pq + (int64_t)q * q <= sm_cap ? sm32 + pq : reinterpret_cast<float*>(sc) + pq;
+  double* v2 = sc + (int64_t)CLR_MAX_CLUSTER * CLR_MAX_CLUSTER;  // after p q + q^2 floats
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
   for (int e = threadIdx.x; e < p * q; e += kThreads) g32[e] = (float)a.at(e % p, e / p);
   __syncthreads();
@@ -324,43 +535,38 @@ __device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, i
       return 1;
     }
   }
-  // FP64 refinement
-  for (int e = threadIdx.x; e < q * q; e += kThreads) v[e] = (double)v32[e];
-  __syncthreads();
-  for (int j = 0; j < q; ++j) {
-    double* vj = v + (int64_t)j * q;
-    double part = 0.0;
-    for (int i = threadIdx.x; i < q; i += kThreads) part = fma(vj[i], vj[i], part);
-    const double nrm = sqrt(block_sum(part, sh.red));
-    const double inv = nrm > 0.0 ? 1.0 / nrm : 0.0;
-    for (int i = threadIdx.x; i < q; i += kThreads) vj[i] *= inv;
-    __syncthreads();
-    for (int k = j + 1 + w; k < q; k += kWarps) {
-      double* vk = v + (int64_t)k * q;
-      double d = 0.0;
-      for (int i = l; i < q; i += 32) d = fma(vj[i], vk[i], d);
-      d = warp_sum(d);
-      for (int i = l; i < q; i += 32) vk[i] = fma(-d, vj[i], vk[i]);
-    }
-    __syncthreads();
-  }
-  for (int e = threadIdx.x; e < p * q; e += kThreads) {
-    const int i = e % p, j = e / p;
-    const double* vj = v + (int64_t)j * q;
-    double s2 = 0.0;
-    for (int k = 0; k < q; ++k) s2 = fma(a.at(i, k), vj[k], s2);
-    g[e] = s2;
-  }
-  __syncthreads();
+  orthonormalise_fp64(v32, v, q, sh);
+  project_fp64(a, p, q, v, g);
   // FP64 noise floor, raised to 1e-3 eps: columns below it hold less than 1e-6 eps^2 each, so
   // their mutual (non-)orthogonality cannot move a truncation decision at eps except within a
   // hair of the threshold, while orthogonalising them costs most of the sweeps
   const double floor64 = fmax((double)p * DBL_EPSILON * fro, 1e-3 * eps);
-  const int sw64 = jacobi_svd<double>(g, p, q, p, v, q, max_sweeps, &sh.flag, false, 1.0,
-                                      floor64 * floor64);
+  for (int e = threadIdx.x; e < p * q; e += kThreads) g32[e] = (float)g[e];
+  __syncthreads();
+  const float floor_g = (float)floor64;
+  const int sw32b = jacobi_svd<float>(g32, p, q, p, v32, q, max_sweeps, &sh.flag, true, 4.0f,
+                                      floor_g * floor_g);
+  // The FP64 sweeps rotate G alone when eps is well above the noise floor: the right factor
+  // of the kept columns is then recovered from A and G afterwards (recover_right), a p q r
+  // product instead of 4 q flops per rotation.  Near the floor (eps < 1e3 p u ||A||_F) kept
+  // columns may lie below it, unorthogonalised, where that recovery is not a projection: V is
+  // accumulated instead.
+  const bool track_v = floor64 > 1e-3 * eps;
+  if (sw32b > 0) {
+    orthonormalise_fp64(v32, v2, q, sh);
+    // V2 row-major into the scratch's first half (the FP32 copies there are dead now)
+    double* v2t = sc;
+    for (int e = threadIdx.x; e < q * q; e += kThreads) v2t[e] = v2[e / q + (int64_t)(e % q) * q];
+    __syncthreads();
+    right_multiply_fp64(g, p, p, q, v2t);
+    if (track_v) right_multiply_fp64(v, q, q, q, v2t);
+  }
+  if (threadIdx.x == 0) sh.v_tracked = track_v ? 1 : 0;
+  const int sw64 = jacobi_svd<double>(g, p, q, p, track_v ? v : nullptr, q, max_sweeps,
+                                      &sh.flag, false, 1.0, floor64 * floor64);
   if (jstats && threadIdx.x == 0) {
     atomicAdd(&jstats[0], 1ull);
-    atomicAdd(&jstats[1], (unsigned long long)sw32);
+    atomicAdd(&jstats[1], (unsigned long long)(sw32 + sw32b));
     atomicAdd(&jstats[2], (unsigned long long)sw64);
   }
   return 0;
@@ -372,9 +578,13 @@ __device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, i
 __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const int* list,
                                                                const int* count,
                                                                const int* rsum, double* ws,
-                                                               double eps, int max_sweeps,
+                                                               double* svd_scratch,
+                                                               int sm_cap, double eps,
+                                                               int max_sweeps,
                                                                unsigned long long* jstats) {
   __shared__ SvdShared sh;
+  extern __shared__ float dyn32[];
+  double* sc = svd_scratch + (int64_t)blockIdx.x * kSvdScratchPerCta;
   const int n_items = *count;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int t = list[it];
@@ -406,10 +616,16 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
       for (int e = threadIdx.x; e < R * R; e += kThreads) part = fma(M[e], M[e], part);
       const double mfro = sqrt(block_sum(part, sh.red));
       SrcView mv{M, 1, R, false};
-      svd_mixed(mv, R, R, G, V, max_sweeps, eps, -1, mfro, sh, jstats);
+      svd_mixed(mv, R, R, G, V, sc, dyn32, sm_cap, max_sweeps, eps, -1, mfro, sh, jstats);
     }
     sort_and_truncate(G, R, R, R, eps, sh);
     const int r = sh.rank;
+    const bool tracked = sh.v_tracked;
+    if (!tracked) {
+      // V_r S_r^2 = M^T G_r into V (M is still intact)
+      SrcView mv{M, 1, R, false};
+      recover_right(mv, R, R, G, sh.perm, r, V);
+    }
     double* Xo = C.pool + sC;
     double* Wo = Xo + (int64_t)m * r;
     for (int e = threadIdx.x; e < m * r; e += kThreads) {
@@ -418,7 +634,9 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
     }
     for (int e = threadIdx.x; e < n * r; e += kThreads) {
       const int j = e % n, c = e / n;
-      Wo[e] = j < R ? V[j + (int64_t)sh.perm[c] * R] : 0.0;
+      Wo[e] = j >= R ? 0.0
+              : tracked ? V[j + (int64_t)sh.perm[c] * R]
+                        : V[j + (int64_t)c * R] / (sh.sorted[c] * sh.sorted[c]);
     }
     __syncthreads();
     apply_q(Xc, m, R, m, tauX, Xo, r, m);
@@ -432,12 +650,53 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
   }
 }
 
+// Launch shape of a recompression kernel: shared memory for the FP32 copies of the largest
+// SVD it may run (need_floats), capped by the opt-in limit, and as many CTAs per SM as that
+// leaves room for (at most 2), within the caller's grid (the scratch is sized for it).
+struct SvdLaunchCfg {
+  int grid;
+  size_t dyn;
+  int cap;
+};
+
+template <typename K>
+SvdLaunchCfg svd_launch_cfg(K kernel, int64_t need_floats, int grid_max, bool* attr_done) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int n_sm = 1, optin = 0, per_sm = 0;
+  cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  cudaFuncAttributes fa;
+  cudaFuncGetAttributes(&fa, kernel);
+  const int64_t avail = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
+  int64_t want = need_floats * (int64_t)sizeof(float);
+  if (want > avail) want = avail;
+  if (want < 0) want = 0;
+  // set once per device (outside any stream capture the first time a product runs)
+  if (dev >= 0 && dev < 64 && !attr_done[dev]) {
+    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail);
+    attr_done[dev] = true;
+  }
+  const int64_t per_cta = want + (int64_t)fa.sharedSizeBytes + 1024;
+  int ctas = per_cta > 0 ? (int)(per_sm / per_cta) : 2;
+  ctas = ctas < 1 ? 1 : (ctas > 2 ? 2 : ctas);
+  int grid = n_sm * ctas;
+  if (grid > grid_max) grid = grid_max;
+  if (grid < 1) grid = 1;
+  return {grid, (size_t)want, (int)(want / (int64_t)sizeof(float))};
+}
+
 void launch_compress_qr(const MatView& C, const int* list, const int* count, const int* rsum,
-                        double* ws, double eps, int max_sweeps, int grid, int* err,
-                        unsigned long long* jstats, cudaStream_t st) {
+                        double* ws, double* svd_scratch, int max_cluster, double eps,
+                        int max_sweeps, int grid, int* err, unsigned long long* jstats,
+                        cudaStream_t st) {
   (void)err;
-  compress_qr_kernel<<<grid, kThreads, 0, st>>>(C, list, count, rsum, ws, eps, max_sweeps,
-                                                 jstats);
+  static bool attr_done[64] = {false};
+  const int64_t r = max_cluster / 2;  // core size R <= floor(min(m, n) / 2)
+  const SvdLaunchCfg cfg = svd_launch_cfg(compress_qr_kernel, 2 * r * r, grid, attr_done);
+  compress_qr_kernel<<<cfg.grid, kThreads, cfg.dyn, st>>>(C, list, count, rsum, ws, svd_scratch,
+                                                         cfg.cap, eps, max_sweeps, jstats);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -446,9 +705,11 @@ void launch_compress_qr(const MatView& C, const int* list, const int* count, con
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
     MatView C, const int* list, const int* count, const double* src, int64_t lds, double* ws,
-    double eps, double drop_norm, int dense_only, int max_sweeps, int* err,
-    unsigned long long* jstats) {
+    double* svd_scratch, int sm_cap, double eps, double drop_norm, int dense_only,
+    int max_sweeps, int* err, unsigned long long* jstats) {
   __shared__ SvdShared sh;
+  extern __shared__ float dyn32[];
+  double* sc = svd_scratch + (int64_t)blockIdx.x * kSvdScratchPerCta;
   const int n_items = list ? *count : C.nr * C.nc;
   for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
     const int t = list ? list[it] : it;
@@ -462,7 +723,7 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
     const int64_t s_c = src ? 1 : m;
     const bool tr = m < n;
     const int p = tr ? n : m, q = tr ? m : n;
-    double* G = ws + 2 * sC;             // p x q, ld p (also the FP32 scratch)
+    double* G = ws + 2 * sC;             // p x q, ld p
     double* V = G + (int64_t)m * n;      // q x q, ld q
     double part = 0.0;
     for (int e = threadIdx.x; e < m * n; e += kThreads) {
@@ -487,7 +748,8 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
     if (!dense_only) {
       const SrcView view{S, s_r, s_c, tr};
       const int early_dense =
-          svd_mixed(view, p, q, G, V, max_sweeps, eps, q / 2, nrm, sh, jstats);
+          svd_mixed(view, p, q, G, V, sc, dyn32, sm_cap, max_sweeps, eps, q / 2, nrm, sh,
+                    jstats);
       if (!early_dense) {
         sort_and_truncate(G, p, q, p, eps, sh);
         r = sh.rank;
@@ -505,23 +767,31 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
       }
       if (threadIdx.x == 0) { C.kind[t] = CLR_KIND_DENSE; C.rank[t] = q; C.norm[t] = nrm; }
     } else {
+      // Y = A^T G_r (q x r) into V before the slot (possibly the source) is overwritten, or
+      // Y = V_r S_r^2 from the accumulated V
+      const SrcView view{S, s_r, s_c, tr};
+      const bool tracked = sh.v_tracked;
+      if (!tracked) recover_right(view, p, q, G, sh.perm, r, V);
       double* Xo = slot;
       double* Wo = slot + (int64_t)m * r;
       if (!tr) {
-        // G = U S (m x n), V (n x n):  X = (U S)_r, W = V_r
+        // G = U S (m x n), Y = V S^2:  X = (U S)_r, W = V_r
         for (int e = threadIdx.x; e < m * r; e += kThreads) {
           const int i = e % m, c = e / m;
           Xo[e] = G[i + (int64_t)sh.perm[c] * p];
         }
         for (int e = threadIdx.x; e < n * r; e += kThreads) {
           const int j = e % n, c = e / n;
-          Wo[e] = V[j + (int64_t)sh.perm[c] * q];
+          Wo[e] = tracked ? V[j + (int64_t)sh.perm[c] * q]
+                          : V[j + (int64_t)c * q] / (sh.sorted[c] * sh.sorted[c]);
         }
       } else {
-        // G = S^T V' = U' S (n x m): block = V' S U'^T -> X = V'_r S_r, W = U'_r
+        // G = U' S (n x m) of the transposed block, Y = V' S^2 (m x r): block = V' S U'^T ->
+        // X = V'_r S_r = Y S^-1, W = U'_r = G_r S^-1
         for (int e = threadIdx.x; e < m * r; e += kThreads) {
           const int i = e % m, c = e / m;
-          Xo[e] = V[i + (int64_t)sh.perm[c] * q] * sh.sorted[c];
+          Xo[e] = tracked ? V[i + (int64_t)sh.perm[c] * q] * sh.sorted[c]
+                          : V[i + (int64_t)c * q] / sh.sorted[c];
         }
         for (int e = threadIdx.x; e < n * r; e += kThreads) {
           const int j = e % n, c = e / n;
@@ -539,12 +809,17 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
 }
 
 void launch_compress_dense(const MatView& C, const int* list, const int* count,
-                           const double* src, int64_t lds, double* ws, double eps,
-                           double drop_norm, int dense_only, int max_sweeps, int grid,
-                           int* err, unsigned long long* jstats, cudaStream_t st) {
-  compress_dense_kernel<<<grid, kThreads, 0, st>>>(C, list, count, src, lds, ws, eps,
-                                                   drop_norm, dense_only, max_sweeps, err,
-                                                   jstats);
+                           const double* src, int64_t lds, double* ws, double* svd_scratch,
+                           int max_cluster, double eps, double drop_norm, int dense_only,
+                           int max_sweeps, int grid, int* err, unsigned long long* jstats,
+                           cudaStream_t st) {
+  static bool attr_done[64] = {false};
+  const int64_t c = max_cluster;
+  const SvdLaunchCfg cfg =
+      svd_launch_cfg(compress_dense_kernel, dense_only ? 0 : 2 * c * c, grid, attr_done);
+  compress_dense_kernel<<<cfg.grid, kThreads, cfg.dyn, st>>>(C, list, count, src, lds, ws,
+                                                            svd_scratch, cfg.cap, eps, drop_norm,
+                                                            dense_only, max_sweeps, err, jstats);
 }
 
 // ---------------------------------------------------------------------------------------------
