@@ -866,7 +866,7 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
     if (st) return st;
   }
   launch_lr_products(av, bv, cv, p, (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p,
-                     kScratchPerCta, lr_grid, s);
+                     kScratchPerCta, prec != CLR_PREC_FP64, lr_grid, s);
   CLR_CHECK_LAUNCH("low-rank products");
   prof_launches(ctx, 1);
   prof_mark(ctx, s, PH_LOWRANK);

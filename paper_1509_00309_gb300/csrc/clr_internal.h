@@ -95,9 +95,10 @@ void launch_dense_kinds(const MatView& M, double drop_norm, int* err, cudaStream
 void launch_pool_to_rowmajor(const MatView& M, const int* row_idx, const int* col_idx,
                              double* out, int64_t ldo, cudaStream_t st);
 // k_lowrank.cu
+// dense_by_gemm: DENSE and DACC tiles were fully summed by the split GEMM (skip them).
 void launch_lr_products(const MatView& A, const MatView& B, const MatView& C, const Plan& p,
-                        double* ws, double* scratch, int64_t scratch_per_cta, int grid,
-                        cudaStream_t st);
+                        double* ws, double* scratch, int64_t scratch_per_cta, int dense_by_gemm,
+                        int grid, cudaStream_t st);
 // k_svd.cu
 // jstats (may be null): device counters {svd blocks, FP32 sweeps, FP64 sweeps, early dense}
 // svd_scratch: grid x kSvdScratchPerCta doubles (FP32 working copies and an FP64 q x q factor

@@ -13,6 +13,8 @@
 //                added as X_t W_t^T;
 //   ROUTE_DACC   the concatenated rank exceeds floor(min(m,n)/2), so the sum is accumulated
 //                densely (from zero) and K5 takes a dense truncated SVD.
+// With split precision (dense_by_gemm) the tensor-core GEMM sums all contributions of DENSE and
+// DACC tiles, and this kernel only builds the ROUTE_QR concatenations.
 #include "clr_internal.h"
 
 namespace clr {
@@ -44,7 +46,8 @@ constexpr int64_t kZElems = (int64_t)(CLR_MAX_CLUSTER / 2) * (CLR_MAX_CLUSTER / 
 
 __global__ void __launch_bounds__(256) lr_products_kernel(MatView A, MatView B, MatView C,
                                                           Plan p, double* ws, double* scratch,
-                                                          int64_t scratch_per_cta) {
+                                                          int64_t scratch_per_cta,
+                                                          int dense_by_gemm) {
   double* scrZ = scratch + (int64_t)blockIdx.x * scratch_per_cta;
   double* scrF = scrZ + kZElems;
   const int n_lr = p.counters->n_lr;
@@ -54,6 +57,9 @@ __global__ void __launch_bounds__(256) lr_products_kernel(MatView A, MatView B, 
     const int m = C.row_off[I + 1] - C.row_off[I];
     const int n = C.col_off[J + 1] - C.col_off[J];
     const int route = p.t_route[t];
+    // with split precision the tensor-core GEMM has already summed every contribution of the
+    // densely accumulated tiles (low-rank operand blocks staged as X W^T)
+    if (dense_by_gemm && (route == ROUTE_DENSE || route == ROUTE_DACC)) continue;
     const int R = p.t_rsum[t];
     const int64_t sC = slot_of(C, I, J, m);
     double* D = C.pool + sC;
@@ -132,9 +138,10 @@ __global__ void __launch_bounds__(256) lr_products_kernel(MatView A, MatView B, 
 }
 
 void launch_lr_products(const MatView& A, const MatView& B, const MatView& C, const Plan& p,
-                        double* ws, double* scratch, int64_t scratch_per_cta, int grid,
-                        cudaStream_t st) {
-  lr_products_kernel<<<grid, 256, 0, st>>>(A, B, C, p, ws, scratch, scratch_per_cta);
+                        double* ws, double* scratch, int64_t scratch_per_cta, int dense_by_gemm,
+                        int grid, cudaStream_t st) {
+  lr_products_kernel<<<grid, 256, 0, st>>>(A, B, C, p, ws, scratch, scratch_per_cta,
+                                           dense_by_gemm);
 }
 
 }  // namespace clr

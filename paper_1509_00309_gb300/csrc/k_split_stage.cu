@@ -1,8 +1,10 @@
 // Split-precision staging: the dense blocks of an operand are written as bf16 term panels for
 // the tensor-core products (the FP64 value a is split as a = a_0 + a_1 (+ a_2) + residual with
 // a_0 = bf16(a), a_1 = bf16(a - a_0), a_2 = bf16(a - a_0 - a_1); every difference is exact in
-// FP64).  Non-dense blocks are written as zeros, so a dense GEMM over the panels computes
-// exactly the dense x dense part of the CLR product.
+// FP64).  Low-rank blocks are written as their reconstruction X W^T and zero blocks as zeros,
+// so a dense GEMM over the panels computes the whole sum sum_K A_IK B_KJ of every C tile that
+// is accumulated densely (route DENSE or DACC); low-rank C tiles (route QR) keep the
+// factorised products of Section 4.1.
 //
 // Panel layout (K-major for the MMA): for A, panel[t][i][k] = A(i, k), rows_pad x cols_pad;
 // for B, panel[t][j][k] = B(k, j).  Padding is zero.
@@ -144,6 +146,26 @@ __device__ __forceinline__ void split_bf16(double x, unsigned short (&out)[TERMS
   }
 }
 
+// Value (i, j) of block (R, Cc) of M in FP64: the stored entry of a dense block, the
+// reconstruction sum_t X(i, t) W(j, t) of a low-rank one (so dense C tiles take their low-rank
+// contributions on the tensor cores too), 0 for a zero block.
+__device__ __forceinline__ double block_value(const MatView& M, int R, int Cc, int64_t i,
+                                              int64_t j) {
+  const int64_t t = (int64_t)R * M.nc + Cc;
+  const int kind = M.kind[t];
+  if (kind == CLR_KIND_ZERO) return 0.0;
+  const int mR = M.row_off[R + 1] - M.row_off[R];
+  const double* slot = M.pool + (int64_t)M.row_off[R] * M.n_cols + (int64_t)mR * M.col_off[Cc];
+  if (kind == CLR_KIND_DENSE) return slot[i + j * mR];
+  const int nC = M.col_off[Cc + 1] - M.col_off[Cc];
+  const int r = M.rank[t];
+  const double* x = slot + i;
+  const double* w = slot + (int64_t)mR * r + j;
+  double v = 0.0;
+  for (int q = 0; q < r; ++q) v = fma(x[(int64_t)q * mR], w[(int64_t)q * nC], v);
+  return v;
+}
+
 // A panel: one CTA converts a 32 (rows) x 128 (k) tile.  The source block-row panels are
 // column-major (consecutive rows contiguous), the panel is row-major (consecutive k
 // contiguous), so the tile goes through shared memory; each thread then packs 4 consecutive
@@ -161,19 +183,16 @@ __global__ void __launch_bounds__(256) split_stage_a_kernel(MatView M, const int
   const int64_t k0 = (int64_t)(blockIdx.x / tiles_r) * kTk;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
   const int64_t r = r0 + tx;
-  int R = 0, mR = 1;
-  int64_t rbase = 0;
   const bool rin = r < M.n_rows;
-  if (rin) {
-    R = row_idx[r];
-    mR = M.row_off[R + 1] - M.row_off[R];
-    rbase = (int64_t)M.row_off[R] * M.n_cols + (r - M.row_off[R]);
-  }
-  const int* kind_row = M.kind + (int64_t)R * M.nc;
+  const int R = rin ? row_idx[r] : 0;
+  const int64_t i = rin ? r - M.row_off[R] : 0;
   for (int cc = ty; cc < kTk; cc += 8) {
     const int64_t c = k0 + cc;
     double v = 0.0;
-    if (rin && c < M.n_cols && kind_row[col_idx[c]] == CLR_KIND_DENSE) v = M.pool[rbase + c * mR];
+    if (rin && c < M.n_cols) {
+      const int Cc = col_idx[c];
+      v = block_value(M, R, Cc, i, c - M.col_off[Cc]);
+    }
     tile[tx][cc] = v;
   }
   __syncthreads();
@@ -216,9 +235,10 @@ __global__ void __launch_bounds__(256) split_stage_b_kernel(MatView M, const int
     const int Cc = col_idx[j];
     const int R0 = row_idx[k];
     const int end0 = M.row_off[R0 + 1];
-    if (k + 3 < end0) {
-      // the 4 elements lie in one block: one kind lookup, contiguous source
-      if (M.kind[R0 * M.nc + Cc] == CLR_KIND_DENSE) {
+    const int kind0 = M.kind[R0 * M.nc + Cc];
+    if (k + 3 < end0 && kind0 != CLR_KIND_LR) {
+      // the 4 elements lie in one dense or zero block: contiguous source
+      if (kind0 == CLR_KIND_DENSE) {
         const int mR = end0 - M.row_off[R0];
         const double* src = M.pool + (int64_t)M.row_off[R0] * M.n_cols + (k - M.row_off[R0]) + j * mR;
 #pragma unroll
@@ -236,10 +256,7 @@ __global__ void __launch_bounds__(256) split_stage_b_kernel(MatView M, const int
         double v = 0.0;
         if (kk < M.n_rows) {
           const int R = row_idx[kk];
-          if (M.kind[R * M.nc + Cc] == CLR_KIND_DENSE) {
-            const int mR = M.row_off[R + 1] - M.row_off[R];
-            v = M.pool[(int64_t)M.row_off[R] * M.n_cols + (kk - M.row_off[R]) + j * mR];
-          }
+          v = block_value(M, R, Cc, kk - M.row_off[R], j - M.col_off[Cc]);
         }
         unsigned short b[TERMS];
         split_bf16<TERMS>(v, b);
