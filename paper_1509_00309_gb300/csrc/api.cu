@@ -850,7 +850,12 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   MatView av = a->view(), bv = b->view(), cv = c->view();
   const clr_opts& o = ctx->opts;
   prof_mark(ctx, s, PH_START);
-  launch_plan(av, bv, p, o.eps_sp, o.recompress_dense, s);
+  // split precision: densely accumulated low-rank sums go to the tensor-core GEMM where its
+  // error bound u sum_K ||A_IK|| ||B_KJ|| stays below eps / 16 (u: 2^-15 bf16x3, 2^-22 bf16x6)
+  const double u_split = prec == CLR_PREC_BF16X3 ? std::ldexp(1.0, -15)
+                         : prec == CLR_PREC_BF16X6 ? std::ldexp(1.0, -22) : 0.0;
+  const double dacc_bound = u_split > 0.0 ? eps_lr / (16.0 * u_split) : 0.0;
+  launch_plan(av, bv, p, o.eps_sp, o.recompress_dense, dacc_bound, s);
   launch_set_route_kinds(cv, p, s);
   CLR_CHECK_LAUNCH("plan");
   prof_launches(ctx, 4);

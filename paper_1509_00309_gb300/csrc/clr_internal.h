@@ -39,8 +39,11 @@ enum { T_DD = 0, T_DL = 1, T_LD = 2, T_LL = 3 };
 // present), low rank.  ROUTE_* refine MODE_LR by how the GPU accumulates:
 //   ROUTE_QR   : concatenated rank R <= floor(min(m,n)/2): concatenate factors, QR both,
 //                SVD of the R x R core.
-//   ROUTE_DACC : larger R: accumulate the sum densely, then a dense truncated SVD.
-enum { ROUTE_ZERO = 0, ROUTE_DENSE = 1, ROUTE_QR = 2, ROUTE_DACC = 3 };
+//   ROUTE_DACC : larger R: accumulate the sum densely (FP64), then a dense truncated SVD.
+//   ROUTE_DACC_G: as ROUTE_DACC, the dense sum formed by the split-precision tensor-core GEMM;
+//                only where the split error bound u sum_K ||A_IK|| ||B_KJ|| is below eps/16, so
+//                the rank found by the SVD is that of the FP64 sum.
+enum { ROUTE_ZERO = 0, ROUTE_DENSE = 1, ROUTE_QR = 2, ROUTE_DACC = 3, ROUTE_DACC_G = 4 };
 
 struct Triple {
   int tile;   // C block index I * nJ + J
@@ -81,7 +84,7 @@ struct Plan {
 // ---------------------------------------------------------------------------------------------
 // k_plan.cu
 void launch_plan(const MatView& A, const MatView& B, const Plan& p, double eps_sp,
-                 int recompress_dense, cudaStream_t st);
+                 int recompress_dense, double gemm_dacc_bound, cudaStream_t st);
 void launch_plan_scan(const Plan& p, int recompress_dense, cudaStream_t st);
 // k_dense64.cu
 void launch_dd_fp64(const MatView& A, const MatView& B, const MatView& C, const Plan& p,

@@ -14,7 +14,7 @@
 //   ROUTE_DACC   the concatenated rank exceeds floor(min(m,n)/2), so the sum is accumulated
 //                densely (from zero) and K5 takes a dense truncated SVD.
 // With split precision (dense_by_gemm) the tensor-core GEMM sums all contributions of DENSE and
-// DACC tiles, and this kernel only builds the ROUTE_QR concatenations.
+// DACC_G tiles; this kernel builds the ROUTE_QR concatenations and the FP64 DACC sums.
 #include "clr_internal.h"
 
 namespace clr {
@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(256) lr_products_kernel(MatView A, MatView B, 
     const int route = p.t_route[t];
     // with split precision the tensor-core GEMM has already summed every contribution of the
     // densely accumulated tiles (low-rank operand blocks staged as X W^T)
-    if (dense_by_gemm && (route == ROUTE_DENSE || route == ROUTE_DACC)) continue;
+    if ((dense_by_gemm && route == ROUTE_DENSE) || route == ROUTE_DACC_G) continue;
     const int R = p.t_rsum[t];
     const int64_t sC = slot_of(C, I, J, m);
     double* D = C.pool + sC;

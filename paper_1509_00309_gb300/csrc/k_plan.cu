@@ -26,21 +26,25 @@ __device__ __forceinline__ unsigned long long triple_flops(int kind, long long m
   return 2ull * k * ra * rb + (rb <= ra ? 2ull * m * ra * rb : 2ull * n * ra * rb);
 }
 
-__global__ void plan_count_kernel(MatView A, MatView B, Plan p, double eps_sp) {
+// gemm_dacc_bound > 0 (split precision): a tile that would be accumulated densely in FP64
+// (ROUTE_DACC) is summed by the tensor-core GEMM instead (ROUTE_DACC_G) when its norm estimate
+// sum_K ||A_IK|| ||B_KJ|| is at most gemm_dacc_bound = eps / (16 u_split).
+__global__ void plan_count_kernel(MatView A, MatView B, Plan p, double eps_sp,
+                                  double gemm_dacc_bound) {
   int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= p.nI * p.nJ) return;
   int I = t / p.nJ, J = t % p.nJ;
   int m = A.row_off[I + 1] - A.row_off[I];
   int n = B.col_off[J + 1] - B.col_off[J];
   bool pass = true;
-  if (eps_sp > 0.0) {
-    double est = 0.0;
+  double est = 0.0;
+  if (eps_sp > 0.0 || gemm_dacc_bound > 0.0) {
     for (int K = 0; K < p.nK; ++K) {
       int ka = A.kind[I * A.nc + K], kb = B.kind[K * B.nc + J];
       if (ka != CLR_KIND_ZERO && kb != CLR_KIND_ZERO)
         est += A.norm[I * A.nc + K] * B.norm[K * B.nc + J];
     }
-    pass = est > eps_sp * (double)m * (double)n;
+    if (eps_sp > 0.0) pass = est > eps_sp * (double)m * (double)n;
   }
   int count = 0, has_dd = 0, rsum = 0;
   unsigned long long fl = 0;
@@ -62,6 +66,8 @@ __global__ void plan_count_kernel(MatView A, MatView B, Plan p, double eps_sp) {
   if (count > 0) {
     int lim = (m < n ? m : n) / 2;
     route = has_dd ? ROUTE_DENSE : (rsum <= lim ? ROUTE_QR : ROUTE_DACC);
+    if (route == ROUTE_DACC && gemm_dacc_bound > 0.0 && est <= gemm_dacc_bound)
+      route = ROUTE_DACC_G;
   }
   p.t_count[t] = count;
   p.t_route[t] = route;
@@ -97,7 +103,8 @@ __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(Plan p, int rec
     s[1] += route == ROUTE_DENSE;
     s[2] += p.t_rsum[i] > 0;
     s[3] += route == ROUTE_QR;
-    s[4] += route == ROUTE_DACC || (route == ROUTE_DENSE && recompress_dense);
+    s[4] += route == ROUTE_DACC || route == ROUTE_DACC_G ||
+            (route == ROUTE_DENSE && recompress_dense);
   }
   for (int q = 0; q < kScanQ; ++q) sh[q][tid] = s[q];
   __syncthreads();
@@ -118,7 +125,8 @@ __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(Plan p, int rec
     if (route == ROUTE_DENSE) p.l_dense[base[1]++] = i;
     if (p.t_rsum[i] > 0) p.l_lr[base[2]++] = i;
     if (route == ROUTE_QR) p.l_qr[base[3]++] = i;
-    if (route == ROUTE_DACC || (route == ROUTE_DENSE && recompress_dense))
+    if (route == ROUTE_DACC || route == ROUTE_DACC_G ||
+        (route == ROUTE_DENSE && recompress_dense))
       p.l_dcomp[base[4]++] = i;
   }
   if (tid == kScanThreads - 1) {
@@ -158,12 +166,12 @@ void launch_plan_scan(const Plan& p, int recompress_dense, cudaStream_t st) {
 }
 
 void launch_plan(const MatView& A, const MatView& B, const Plan& p, double eps_sp,
-                 int recompress_dense, cudaStream_t st) {
+                 int recompress_dense, double gemm_dacc_bound, cudaStream_t st) {
   const int n = p.nI * p.nJ;
   const int threads = 128;
   const int blocks = (n + threads - 1) / threads;
   cudaMemsetAsync(p.counters, 0, sizeof(PlanCounters), st);
-  plan_count_kernel<<<blocks, threads, 0, st>>>(A, B, p, eps_sp);
+  plan_count_kernel<<<blocks, threads, 0, st>>>(A, B, p, eps_sp, gemm_dacc_bound);
   plan_scan_kernel<<<1, kScanThreads, 0, st>>>(p, recompress_dense);
   plan_fill_kernel<<<blocks, threads, 0, st>>>(A, B, p);
 }

@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int64_t col = col0 + j;
           if (col < epi.n_cols) {
             const int J = epi.col_tile_of[col];
-            if (route_row[J] == ROUTE_DENSE || route_row[J] == ROUTE_DACC)
+            if (route_row[J] == ROUTE_DENSE || route_row[J] == ROUTE_DACC_G)
               epi.pool[rowbase + col * mI] = (double)hi[j];
           }
         }
@@ -414,8 +414,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-// GEMM tile t is active when it overlaps at least one densely accumulated C tile (route DENSE
-// or DACC).
+// GEMM tile t is active when it overlaps at least one C tile the GEMM sums (route DENSE or
+// DACC_G).
 __global__ void tile_active_kernel(const int* row_tile_of, const int* col_tile_of, int nc,
                                    const int* t_route, int n_m, int n_n, int64_t n_rows,
                                    int64_t n_cols, unsigned char* active) {
@@ -432,7 +432,7 @@ __global__ void tile_active_kernel(const int* row_tile_of, const int* col_tile_o
     for (int I = i0; I <= i1 && !on; ++I)
       for (int J = j0; J <= j1; ++J)
         if (t_route[(int64_t)I * nc + J] == ROUTE_DENSE ||
-            t_route[(int64_t)I * nc + J] == ROUTE_DACC) {
+            t_route[(int64_t)I * nc + J] == ROUTE_DACC_G) {
           on = 1;
           break;
         }

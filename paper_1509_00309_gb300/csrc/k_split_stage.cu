@@ -2,9 +2,9 @@
 // the tensor-core products (the FP64 value a is split as a = a_0 + a_1 (+ a_2) + residual with
 // a_0 = bf16(a), a_1 = bf16(a - a_0), a_2 = bf16(a - a_0 - a_1); every difference is exact in
 // FP64).  Low-rank blocks are written as their reconstruction X W^T and zero blocks as zeros,
-// so a dense GEMM over the panels computes the whole sum sum_K A_IK B_KJ of every C tile that
-// is accumulated densely (route DENSE or DACC); low-rank C tiles (route QR) keep the
-// factorised products of Section 4.1.
+// so a dense GEMM over the panels computes the whole sum sum_K A_IK B_KJ of the C tiles it
+// serves (route DENSE or DACC_G); low-rank C tiles (route QR) keep the factorised products of
+// Section 4.1.
 //
 // Panel layout (K-major for the MMA): for A, panel[t][i][k] = A(i, k), rows_pad x cols_pad;
 // for B, panel[t][j][k] = B(k, j).  Padding is zero.

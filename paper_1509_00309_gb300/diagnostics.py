@@ -1,10 +1,11 @@
 """Block-rank diagnostics of the Newton–Schulz iterates (Section 5, the distribution of block
 ranks of the 5th-iteration intermediates X, Y, Z, T and of the input S).
 
-    python -m paper_1509_00309_gb300.diagnostics --shape 8x8x4 --iter 5
+    python -m paper_1509_00309_gb300.diagnostics --shape 8x8x4 --iter 5 [--matrix coulomb]
 
 builds the 3D lattice overlap matrix (16 points per site, clusters of 64..256 points, eps_lr
-1e-6, drop 1e-10, eps_sp 1e-13) on the GPU, runs clr_sqrt_inv with the snapshot option and
+1e-6, drop 1e-10, eps_sp 1e-13), or the Coulomb-like erf(r)/r matrix on the same lattice, on
+the GPU, runs clr_sqrt_inv with the snapshot option and
 prints one JSON object: per matrix its block counts by kind and the rank histogram (entry 0:
 zero blocks, entry r: low-rank blocks of rank r, last entry: dense blocks), plus the NS timing
 and the SVD counters of the library's profile.  Everything runs through the C ABI."""
@@ -60,10 +61,12 @@ def main() -> None:
     ap.add_argument("--max-iter", type=int, default=40)
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-recompress-dense", action="store_true")
+    ap.add_argument("--matrix", default="overlap", choices=["overlap", "coulomb"])
     args = ap.parse_args()
     import torch
     shape = tuple(int(v) for v in args.shape.split("x"))
-    w = wl.lattice_overlap(shape=shape)
+    w = wl.lattice_overlap(shape=shape) if args.matrix == "overlap" else \
+        wl.lattice_coulomb(shape=shape)
     ctx = clr.Context(0, precision=args.precision, eps_lr=w.eps_lr, eps_sp=w.eps_sp,
                       ns_tol=args.tol, ns_max_iter=args.max_iter,
                       recompress_dense=0 if args.no_recompress_dense else 1)

@@ -1,7 +1,8 @@
 """Seeded synthetic inputs for the CLR product and the Newton–Schulz S^-1/2 iteration.
 
 This module only draws random numbers and evaluates the kernel functions that DEFINE the
-input matrices (Gaussian overlap-like kernels on jittered point sets, i.i.d. normal entries).
+input matrices (Gaussian overlap-like and erf(r)/r Coulomb-like kernels on jittered point sets,
+i.i.d. normal entries).
 It holds none of the method's arithmetic (no compression, no product, no iteration), so the
 CUDA path and the FP64 oracle can both take their inputs from here.
 
@@ -94,6 +95,30 @@ def gaussian_kernel_matrix(points: np.ndarray, width: float, diag_shift: float,
         lo, hi = max(r0, c0), min(r0 + pr.shape[0], c0 + pc.shape[0])
         for g in range(lo, hi):
             out[g - r0, g - c0] += diag_shift
+    return out
+
+
+def coulomb_kernel_matrix(points: np.ndarray, beta: float, diag_shift: float,
+                          chunk: int = 2048) -> np.ndarray:
+    """V_ij = erf(beta r_ij) / r_ij (2 beta / sqrt(pi) at r = 0) + diag_shift * delta_ij: the
+    Coulomb interaction of unit Gaussian charges (a positive definite, slowly decaying kernel:
+    no block is negligible, far blocks are low rank).  Evaluated in row chunks."""
+    from scipy.special import erf
+    pts = np.ascontiguousarray(points, dtype=np.float64)
+    n = pts.shape[0]
+    out = np.empty((n, n), dtype=np.float64)
+    for a in range(0, n, chunk):
+        b = min(a + chunk, n)
+        d2 = np.zeros((b - a, n), dtype=np.float64)
+        for ax in range(pts.shape[1]):
+            diff = pts[a:b, ax][:, None] - pts[None, :, ax]
+            d2 += diff * diff
+        r = np.sqrt(d2)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            v = erf(beta * r) / r
+        v[r == 0.0] = 2.0 * beta / np.sqrt(np.pi)
+        out[a:b] = v
+    out[np.diag_indices(n)] += diag_shift
     return out
 
 
@@ -209,6 +234,30 @@ def lattice_overlap(shape=(16, 16, 8), points_per_site: int = 16, spacing: float
     sizes = [len(g) * points_per_site for g in groups]
     s = gaussian_kernel_matrix(pts, width, diag_shift)
     return Workload("lattice_overlap_n%d" % pts.shape[0], sizes, sizes, s, None, eps_lr,
+                    drop_norm, eps_sp, extra={"points": pts})
+
+
+def lattice_coulomb(shape=(8, 8, 4), points_per_site: int = 16, spacing: float = 0.5,
+                    jitter: float = 0.1, beta: float = 1.0, diag_shift: float = 2e-2,
+                    min_points: int = 64, max_points: int = 256, eps_lr: float = 1e-6,
+                    drop_norm: float = 1e-10, eps_sp: float = 1e-13,
+                    seed: int = default_seed(5)) -> Workload:
+    """Coulomb-like matrix on the jittered 3D lattice of ``lattice_overlap`` (the paper's second
+    matrix V, which has no block sparsity, only block-rank sparsity): V_ij = erf(r_ij)/r_ij +
+    2e-2 delta_ij (condition number ~1e5 at 8x8x4 sites), clusters of 64..256 points by
+    bisection, eps_lr 1e-6."""
+    rng = np.random.default_rng(seed)
+    pts = lattice_points(rng, shape, spacing, points_per_site, jitter)
+    sites = pts.reshape(-1, points_per_site, 3).mean(axis=1)
+    groups = bisection_site_groups(rng, sites, max(1, min_points // points_per_site),
+                                   max(1, max_points // points_per_site))
+    order = np.concatenate([np.concatenate([np.arange(g * points_per_site,
+                                                      (g + 1) * points_per_site)
+                                            for g in grp]) for grp in groups])
+    pts = pts[order]
+    sizes = [len(g) * points_per_site for g in groups]
+    v = coulomb_kernel_matrix(pts, beta, diag_shift)
+    return Workload("lattice_coulomb_n%d" % pts.shape[0], sizes, sizes, v, None, eps_lr,
                     drop_norm, eps_sp, extra={"points": pts})
 
 
