@@ -34,7 +34,7 @@ METRIC = "CLR multiply TFLOP/s and ms per Newton–Schulz S^-1/2 iteration at st
 # (profiles/split_gemm_dense16384_bf16x3.md), keyed by the kernel source's hash so the number
 # is dropped (traffic: null) as soon as the kernel changes.
 MEASURED_TRAFFIC = {
-    "48908297d0c2:bf16x3:16384:96": 17269268736 + 4191840000,
+    "fdcf6f56594b:bf16x3:16384:96": 17209188608 + 3477965312,
 }
 PAIRS = {"bf16x3": 3, "bf16x6": 6}
 
@@ -388,40 +388,18 @@ def run_ours(args):
                            "%s, fp64 below proxy 1e-3" % args.ns_prec,
               "z_blocks_zero_dense_lr": z.info()["n_blocks"]}
 
-    # Newton-Schulz on the 3D lattice overlap matrix (16 points per jittered lattice site,
-    # clusters of 64..256 points, eps_lr = 1e-6, drop 1e-10, eps_sp = 1e-13), FP64 products,
+    # Newton-Schulz on the 3D lattice matrices (16 points per jittered lattice site, clusters
+    # of 64..256 points, eps_lr = 1e-6, drop 1e-10, eps_sp = 1e-13), FP64 products,
     # dense-accumulated tiles re-tested for low rank; with the block-rank distribution of the
-    # 5th-iteration intermediates X, T, Y, Z (Section 5)
-    ns_lat = None
+    # 5th-iteration intermediates X, T, Y, Z (Section 5).  The overlap-like S has block
+    # sparsity; the Coulomb-like V (erf(r)/r) has only block-rank sparsity (Section 4.2).
+    ns_lat = ns_coul = None
     if not args.no_ns and args.ns_lattice != "none":
-        from paper_1509_00309_gb300 import diagnostics, workloads as wl
+        from paper_1509_00309_gb300 import workloads as wl
         shape = tuple(int(v) for v in args.ns_lattice.split("x"))
-        wl3 = wl.lattice_overlap(shape=shape)
-        lctx = clr.Context(torch.cuda.current_device(), precision="fp64", eps_lr=wl3.eps_lr,
-                           eps_sp=wl3.eps_sp, ns_tol=1e-6, ns_max_iter=40, recompress_dense=1)
-        sl = lctx.from_dense(torch.from_numpy(wl3.a).cuda(), wl3.row_sizes, eps_lr=wl3.eps_lr,
-                             drop_norm=wl3.drop_norm)
-        lctx.set_opts(ns_max_iter=1, ns_tol=0.0)
-        lctx.sqrt_inv(sl, allow_noconv=True)   # warm-up: workspaces
-        lctx.set_opts(ns_max_iter=40, ns_tol=1e-6)
-        torch.cuda.synchronize()
-        d = diagnostics.ns_rank_distribution(lctx, sl, 5)
-        it = max(1, d["ns"]["iters"])
-        ns_lat = {"workload": "3D lattice overlap %s sites x 16 points, N=%d, %d clusters of "
-                              "64..256, eps_lr=1e-6" % (args.ns_lattice, wl3.n,
-                                                        len(wl3.row_sizes)),
-                  "ms_per_iteration": d["ns"]["ms_per_iter"], "iterations": d["ns"]["iters"],
-                  "proxy_final": d["ns"]["proxy"][-1],
-                  "residual_ZSZ_minus_I_rms": d["ns"]["residual"], "tol": 1e-6,
-                  "precision": "fp64", "recompress_dense": True,
-                  "phases_ms_total": {k: d["profile"][k] for k in
-                                      ("ms_dense", "ms_lowrank", "ms_compress")},
-                  "svd": {k: d["profile"][k] for k in ("svd_blocks", "svd_sweeps_fp32",
-                                                        "svd_sweeps_fp64", "svd_early_dense")},
-                  "rank_distribution_iter5": {
-                      k: {f: d[k][f] for f in ("zero", "dense", "low_rank", "lr_rank_mean",
-                                               "lr_rank_max")}
-                      for k in ("S", "X_5", "T_5", "Y_5", "Z_5", "Z_final")}}
+        ns_lat = lattice_ns(clr, wl.lattice_overlap(shape=shape), args.ns_lattice, "overlap")
+        ns_coul = lattice_ns(clr, wl.lattice_coulomb(shape=shape), args.ns_lattice,
+                             "Coulomb-like erf(r)/r")
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -439,12 +417,41 @@ def run_ours(args):
                 "config": config(args, {"error": err, "phases_ms_per_step": phases,
                                         "algorithmic_flops_per_step": alg_flops}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ns": ns,
-                "ns_lattice": ns_lat,
+                "ns_lattice": ns_lat, "ns_coulomb": ns_coul,
                 "gpu_launches": int(prof["launches"]), "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def lattice_ns(clr, w, shape_txt, what):
+    """NS to ||X - I||_F/sqrt(N) <= 1e-6 on one lattice matrix, through the C ABI."""
+    import torch
+    from paper_1509_00309_gb300 import diagnostics
+    ctx = clr.Context(torch.cuda.current_device(), precision="fp64", eps_lr=w.eps_lr,
+                      eps_sp=w.eps_sp, ns_tol=1e-6, ns_max_iter=40, recompress_dense=1)
+    sm = ctx.from_dense(torch.from_numpy(w.a).cuda(), w.row_sizes, eps_lr=w.eps_lr,
+                        drop_norm=w.drop_norm)
+    ctx.set_opts(ns_max_iter=1, ns_tol=0.0)
+    ctx.sqrt_inv(sm, allow_noconv=True)   # warm-up: workspaces
+    ctx.set_opts(ns_max_iter=40, ns_tol=1e-6)
+    torch.cuda.synchronize()
+    d = diagnostics.ns_rank_distribution(ctx, sm, 5)
+    return {"workload": "3D lattice %s matrix, %s sites x 16 points, N=%d, %d clusters of "
+                        "64..256, eps_lr=1e-6" % (what, shape_txt, w.n, len(w.row_sizes)),
+            "ms_per_iteration": d["ns"]["ms_per_iter"], "iterations": d["ns"]["iters"],
+            "proxy_final": d["ns"]["proxy"][-1],
+            "residual_ZSZ_minus_I_rms": d["ns"]["residual"], "tol": 1e-6,
+            "precision": "fp64", "recompress_dense": True,
+            "phases_ms_total": {k: d["profile"][k] for k in
+                                ("ms_dense", "ms_lowrank", "ms_compress")},
+            "svd": {k: d["profile"][k] for k in ("svd_blocks", "svd_sweeps_fp32",
+                                                  "svd_sweeps_fp64", "svd_early_dense")},
+            "rank_distribution_iter5": {
+                k: {f: d[k][f] for f in ("zero", "dense", "low_rank", "lr_rank_mean",
+                                         "lr_rank_max")}
+                for k in ("S", "X_5", "T_5", "Y_5", "Z_5", "Z_final")}}
 
 
 def main():

@@ -107,7 +107,9 @@ typedef struct clr_product_stats {
   int64_t n_tiles[3];       /* C tiles accumulated as: none, dense, low rank */
   int64_t max_rank_sum;     /* largest concatenated rank of a low-rank C tile */
   int32_t precision;        /* precision used for dense x dense products */
-  int32_t pad;
+  int32_t n_tiles_tensor;   /* C tiles summed entirely by the tensor-core GEMM (split precision:
+                               tiles with a dense x dense product, and densely accumulated
+                               low-rank sums within the split error bound) */
 } clr_product_stats;
 
 /* Newton–Schulz statistics (clr_sqrt_inv). */

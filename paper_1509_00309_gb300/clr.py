@@ -43,7 +43,8 @@ class ClrInfo(C.Structure):
 
 class ClrProductStats(C.Structure):
     _fields_ = [("n_triples", C.c_int64 * 4), ("flops", C.c_int64), ("n_tiles", C.c_int64 * 3),
-                ("max_rank_sum", C.c_int64), ("precision", C.c_int32), ("pad", C.c_int32)]
+                ("max_rank_sum", C.c_int64), ("precision", C.c_int32),
+                ("n_tiles_tensor", C.c_int32)]
 
 
 class ClrNsStats(C.Structure):
@@ -361,7 +362,8 @@ class Context:
         if not stats:
             return None
         return {"n_triples": list(s.n_triples), "flops": s.flops, "n_tiles": list(s.n_tiles),
-                "max_rank_sum": s.max_rank_sum, "precision": PREC_NAME[s.precision]}
+                "max_rank_sum": s.max_rank_sum, "precision": PREC_NAME[s.precision],
+                "n_tiles_tensor": s.n_tiles_tensor}
 
     def multiply_batched(self, a: Sequence[Matrix], b: Sequence[Matrix],
                          stream=None) -> List[Matrix]:

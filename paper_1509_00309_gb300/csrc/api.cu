@@ -905,6 +905,8 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
     for (int q = 0; q < 3; ++q) stats->n_tiles[q] = (int64_t)pc.by_mode[q];
     stats->max_rank_sum = (int64_t)pc.max_rsum;
     stats->precision = prec;
+    stats->n_tiles_tensor =
+        prec == CLR_PREC_FP64 ? 0 : (int32_t)(pc.by_mode[1] + pc.n_gemm_dacc);
     if (pc.err == 1) return fail(ctx, CLR_ETIMEOUT, "a device-side wait timed out");
     if (pc.err) return fail(ctx, CLR_EINVAL, "device reported bad data (flag " + std::to_string(pc.err) + ")");
   }

@@ -59,6 +59,7 @@ struct PlanCounters {
   unsigned long long flops;
   unsigned long long by_mode[3];
   unsigned long long max_rsum;
+  unsigned long long n_gemm_dacc;  // tiles routed ROUTE_DACC_G
   int n_dense, n_lr, n_qr, n_dacc, n_dcomp;
   int err;  // error flag raised by kernels (bounded waits, bad metadata)
 };

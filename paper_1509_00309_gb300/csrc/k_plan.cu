@@ -66,8 +66,10 @@ __global__ void plan_count_kernel(MatView A, MatView B, Plan p, double eps_sp,
   if (count > 0) {
     int lim = (m < n ? m : n) / 2;
     route = has_dd ? ROUTE_DENSE : (rsum <= lim ? ROUTE_QR : ROUTE_DACC);
-    if (route == ROUTE_DACC && gemm_dacc_bound > 0.0 && est <= gemm_dacc_bound)
+    if (route == ROUTE_DACC && gemm_dacc_bound > 0.0 && est <= gemm_dacc_bound) {
       route = ROUTE_DACC_G;
+      atomicAdd(&p.counters->n_gemm_dacc, 1ull);
+    }
   }
   p.t_count[t] = count;
   p.t_route[t] = route;

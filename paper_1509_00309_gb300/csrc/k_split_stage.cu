@@ -146,19 +146,15 @@ __device__ __forceinline__ void split_bf16(double x, unsigned short (&out)[TERMS
   }
 }
 
-// Value (i, j) of block (R, Cc) of M in FP64: the stored entry of a dense block, the
-// reconstruction sum_t X(i, t) W(j, t) of a low-rank one (so dense C tiles take their low-rank
-// contributions on the tensor cores too), 0 for a zero block.
-__device__ __forceinline__ double block_value(const MatView& M, int R, int Cc, int64_t i,
-                                              int64_t j) {
+// Entry (i, j) of the low-rank block (R, Cc) of M in FP64: its reconstruction
+// sum_t X(i, t) W(j, t) (so dense C tiles take their low-rank contributions on the tensor cores
+// too).  Dense and zero blocks are read directly by the callers.
+__device__ __noinline__ double lr_value(const MatView& M, int R, int Cc, int64_t i, int64_t j) {
   const int64_t t = (int64_t)R * M.nc + Cc;
-  const int kind = M.kind[t];
-  if (kind == CLR_KIND_ZERO) return 0.0;
   const int mR = M.row_off[R + 1] - M.row_off[R];
-  const double* slot = M.pool + (int64_t)M.row_off[R] * M.n_cols + (int64_t)mR * M.col_off[Cc];
-  if (kind == CLR_KIND_DENSE) return slot[i + j * mR];
   const int nC = M.col_off[Cc + 1] - M.col_off[Cc];
   const int r = M.rank[t];
+  const double* slot = M.pool + (int64_t)M.row_off[R] * M.n_cols + (int64_t)mR * M.col_off[Cc];
   const double* x = slot + i;
   const double* w = slot + (int64_t)mR * r + j;
   double v = 0.0;
@@ -183,15 +179,25 @@ __global__ void __launch_bounds__(256) split_stage_a_kernel(MatView M, const int
   const int64_t k0 = (int64_t)(blockIdx.x / tiles_r) * kTk;
   const int tx = threadIdx.x % 32, ty = threadIdx.x / 32;  // 32 x 8
   const int64_t r = r0 + tx;
+  int R = 0, mR = 1;
+  int64_t rbase = 0;
   const bool rin = r < M.n_rows;
-  const int R = rin ? row_idx[r] : 0;
-  const int64_t i = rin ? r - M.row_off[R] : 0;
+  if (rin) {
+    R = row_idx[r];
+    mR = M.row_off[R + 1] - M.row_off[R];
+    rbase = (int64_t)M.row_off[R] * M.n_cols + (r - M.row_off[R]);
+  }
+  const int* kind_row = M.kind + (int64_t)R * M.nc;
   for (int cc = ty; cc < kTk; cc += 8) {
     const int64_t c = k0 + cc;
     double v = 0.0;
     if (rin && c < M.n_cols) {
       const int Cc = col_idx[c];
-      v = block_value(M, R, Cc, i, c - M.col_off[Cc]);
+      const int kind = kind_row[Cc];
+      if (kind == CLR_KIND_DENSE)
+        v = M.pool[rbase + c * mR];
+      else if (kind == CLR_KIND_LR)
+        v = lr_value(M, R, Cc, r - M.row_off[R], c - M.col_off[Cc]);
     }
     tile[tx][cc] = v;
   }
@@ -256,7 +262,13 @@ __global__ void __launch_bounds__(256) split_stage_b_kernel(MatView M, const int
         double v = 0.0;
         if (kk < M.n_rows) {
           const int R = row_idx[kk];
-          v = block_value(M, R, Cc, kk - M.row_off[R], j - M.col_off[Cc]);
+          const int kind = M.kind[R * M.nc + Cc];
+          if (kind == CLR_KIND_DENSE) {
+            const int mR = M.row_off[R + 1] - M.row_off[R];
+            v = M.pool[(int64_t)M.row_off[R] * M.n_cols + (kk - M.row_off[R]) + j * mR];
+          } else if (kind == CLR_KIND_LR) {
+            v = lr_value(M, R, Cc, kk - M.row_off[R], j - M.col_off[Cc]);
+          }
         }
         unsigned short b[TERMS];
         split_bf16<TERMS>(v, b);

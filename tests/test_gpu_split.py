@@ -122,3 +122,39 @@ def test_full_size_sampled_tiles(ctx):
     # the whole matrix: every block is dense
     k, _, _, _ = gc.get_blocks(pool=False)
     assert (k == co.KIND_DENSE).all()
+
+
+def test_low_rank_sums_on_tensor_cores_follow_error_bound(ctx):
+    # Dense diagonal blocks, low-rank off-diagonal blocks of rank 13 (3 clusters): an
+    # off-diagonal C tile gets DL, LD and LL products of concatenated rank 39 > min/2, so it is
+    # accumulated densely.  With the off-diagonal blocks scaled to 1e-10 its split error bound
+    # u sum_K ||A_IK|| ||B_KJ|| is below eps/16 and the tensor-core GEMM sums it; at scale 1 the
+    # low-rank products stay in FP64.  Either way the result matches the oracle.
+    from tests.test_gpu_product import _check_product
+    rng = np.random.default_rng(21)
+    sizes = [64, 80, 72]
+    eps = 1e-8
+    for scale, want_gemm in ((1e-10, True), (1.0, False)):
+        def spec():
+            out = []
+            for i, m in enumerate(sizes):
+                row = []
+                for j, n in enumerate(sizes):
+                    if i == j:
+                        row.append((co.KIND_DENSE, rng.standard_normal((m, n))))
+                    else:
+                        row.append((co.KIND_LR, (scale * rng.standard_normal((m, 13)),
+                                                 rng.standard_normal((n, 13)))))
+                out.append(row)
+            return out
+        a_or = co.from_blocks(sizes, sizes, spec())
+        b_or = co.from_blocks(sizes, sizes, spec())
+        ctx.set_opts(precision="bf16x3", eps_lr=eps)
+        gc = ctx.zeros(sizes)
+        st = ctx.multiply_into(clr_pack.to_library(ctx, a_or), clr_pack.to_library(ctx, b_or),
+                               gc, stats=True)
+        # diagonal tiles hold a dense x dense product (tensor cores in both cases); the six
+        # off-diagonal tiles are densely accumulated low-rank sums
+        assert st["n_tiles_tensor"] == (9 if want_gemm else 3)
+        _check_product(ctx, a_or, b_or, eps, gc)
+    ctx.set_opts(precision="bf16x3", eps_lr=1e-8)
