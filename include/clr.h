@@ -271,9 +271,17 @@ typedef struct clr_profile {
   int64_t svd_sweeps_fp32;     /* FP32 sweeps, summed over those SVDs */
   int64_t svd_sweeps_fp64;     /* FP64 sweeps, summed */
   int64_t svd_early_dense;     /* SVDs stopped after the FP32 phase (certified dense) */
+  double svd_flops_fp64;       /* algorithmic FP64 flops of recompression: QR 2(m+n)R^2, core
+                                  products, orthonormalisations 2q^3, projections 2pq^2, Jacobi
+                                  4pq^2 per FP64 sweep, factor recovery / re-expansion */
+  double svd_flops_fp32;       /* algorithmic FP32 flops: Jacobi 4pq^2 per FP32 sweep */
 } clr_profile;
 int clr_profile_enable(clr_ctx_t ctx, int on);
 int clr_profile_read(clr_ctx_t ctx, clr_profile* out);
+/* FP64 FMA throughput of `device` measured by a short kernel of independent FMA chains on every
+ * SM (the roofline of the FP64 arithmetic in recompression): *tflops = 2 x FMAs / second.
+ * Synchronises the device. */
+int clr_probe_fp64_rate(int device, double* tflops);
 
 /* ---- allocation-free single-block compression ---------------------------------------------
  * clr_block_compress_noalloc: the truncated SVD of one m x n block at Frobenius error eps, the

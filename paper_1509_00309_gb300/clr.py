@@ -60,7 +60,8 @@ class ClrProfile(C.Structure):
                 ("ms_lowrank", C.c_double), ("ms_compress", C.c_double),
                 ("ms_finalize", C.c_double), ("svd_blocks", C.c_int64),
                 ("svd_sweeps_fp32", C.c_int64), ("svd_sweeps_fp64", C.c_int64),
-                ("svd_early_dense", C.c_int64)]
+                ("svd_early_dense", C.c_int64), ("svd_flops_fp64", C.c_double),
+                ("svd_flops_fp32", C.c_double)]
 
 
 _VP = C.c_void_p
@@ -113,6 +114,7 @@ _SIGNATURES = {
     "clr_mem_cached": (C.c_int64, []),
     "clr_profile_enable": (C.c_int, [_VP, C.c_int]),
     "clr_profile_read": (C.c_int, [_VP, C.POINTER(ClrProfile)]),
+    "clr_probe_fp64_rate": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
 }
 
 _LIB: Optional[C.CDLL] = None
@@ -440,6 +442,15 @@ class Context:
         self._check(load().clr_sqrt_inv_backward(self.handle, tape.handle, zbar.handle,
                                                  C.byref(h), _stream(stream)))
         return Matrix(self, h.value, zbar.row_sizes, zbar.col_sizes)
+
+
+def probe_fp64_rate(device: int = 0) -> float:
+    """Measured FP64 FMA throughput of the device in TFLOP/s (clr_probe_fp64_rate)."""
+    out = C.c_double()
+    st = load().clr_probe_fp64_rate(int(device), C.byref(out))
+    if st != CLR_OK:
+        raise ClrError(st, "clr_probe_fp64_rate failed")
+    return out.value
 
 
 def block_compress_noalloc(block, eps: float, x_out, w_out, status, sigma_out=None,

@@ -152,7 +152,7 @@ struct clr_ctx_s {
   // workspaces (grow-only)
   std::vector<std::unique_ptr<WorkSet>> wsets;
   WorkSet* cur = nullptr;  // workspace set used by the next product
-  DevBuf small, upload, jstats;  // jstats: 4 SVD counters accumulated while profiling
+  DevBuf small, upload, jstats;  // jstats: 6 SVD counters accumulated while profiling
   bool capturing = false;
   // autotuner cache: shape key -> tuning and measured ms
   std::map<std::string, std::pair<Tuning, double>> tune_cache;
@@ -923,8 +923,8 @@ extern "C" int clr_profile_enable(clr_ctx_t ctx, int on) {
   std::memset(&ctx->prof, 0, sizeof(ctx->prof));
   ctx->prof_on = on != 0;
   if (ctx->prof_on) {
-    CLR_CUDA(ctx->jstats.ensure(4 * sizeof(unsigned long long)));
-    CLR_CUDA(cudaMemset(ctx->jstats.p, 0, 4 * sizeof(unsigned long long)));
+    CLR_CUDA(ctx->jstats.ensure(6 * sizeof(unsigned long long)));
+    CLR_CUDA(cudaMemset(ctx->jstats.p, 0, 6 * sizeof(unsigned long long)));
   }
   return CLR_OK;
 }
@@ -953,12 +953,14 @@ extern "C" int clr_profile_read(clr_ctx_t ctx, clr_profile* out) {
     ctx->prof_events.clear();
   }
   if (ctx->jstats.p) {
-    unsigned long long j[4];
+    unsigned long long j[6];
     CLR_CUDA(cudaMemcpy(j, ctx->jstats.p, sizeof(j), cudaMemcpyDeviceToHost));
     ctx->prof.svd_blocks = (int64_t)j[0];
     ctx->prof.svd_sweeps_fp32 = (int64_t)j[1];
     ctx->prof.svd_sweeps_fp64 = (int64_t)j[2];
     ctx->prof.svd_early_dense = (int64_t)j[3];
+    ctx->prof.svd_flops_fp64 = (double)j[4];
+    ctx->prof.svd_flops_fp32 = (double)j[5];
   }
   *out = ctx->prof;
   return CLR_OK;

@@ -531,6 +531,7 @@ __device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, d
         atomicAdd(&jstats[0], 1ull);
         atomicAdd(&jstats[1], (unsigned long long)sw32);
         atomicAdd(&jstats[3], 1ull);
+        atomicAdd(&jstats[5], 4ull * p * q * q * sw32);
       }
       return 1;
     }
@@ -565,9 +566,15 @@ __device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, d
   const int sw64 = jacobi_svd<double>(g, p, q, p, track_v ? v : nullptr, q, max_sweeps,
                                       &sh.flag, false, 1.0, floor64 * floor64);
   if (jstats && threadIdx.x == 0) {
+    // algorithmic flops: Jacobi 4 p q^2 per sweep, orthonormalisation 2 q^3, products 2 p q^2
+    const unsigned long long pq2 = (unsigned long long)p * q * q, q3 = (unsigned long long)q * q * q;
+    unsigned long long f64 = 2 * q3 + 2 * pq2 + 4 * pq2 * sw64;
+    if (sw32b > 0) f64 += 2 * q3 + 2 * pq2 + (track_v ? 2 * q3 : 0);
     atomicAdd(&jstats[0], 1ull);
     atomicAdd(&jstats[1], (unsigned long long)(sw32 + sw32b));
     atomicAdd(&jstats[2], (unsigned long long)sw64);
+    atomicAdd(&jstats[4], f64);
+    atomicAdd(&jstats[5], 4 * pq2 * (unsigned long long)(sw32 + sw32b));
   }
   return 0;
 }
@@ -641,6 +648,13 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
     __syncthreads();
     apply_q(Xc, m, R, m, tauX, Xo, r, m);
     apply_q(Wc, n, R, n, tauW, Wo, r, n);
+    if (jstats && threadIdx.x == 0) {
+      // Householder QRs 2(m+n)R^2, core R_X R_W^T (2/3)R^3, recovery 2R^2 r (when not
+      // accumulated), re-expansion 4(m+n)R r
+      const unsigned long long mn = (unsigned long long)(m + n), RR = (unsigned long long)R * R;
+      atomicAdd(&jstats[4], 2 * mn * RR + 2 * RR * R / 3 + (tracked ? 0 : 2 * RR * r) +
+                                4 * mn * R * r);
+    }
     if (threadIdx.x == 0) {
       C.kind[t] = r > 0 ? CLR_KIND_LR : CLR_KIND_ZERO;
       C.rank[t] = r;
@@ -772,6 +786,8 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
       const SrcView view{S, s_r, s_c, tr};
       const bool tracked = sh.v_tracked;
       if (!tracked) recover_right(view, p, q, G, sh.perm, r, V);
+      if (jstats && threadIdx.x == 0 && !tracked)
+        atomicAdd(&jstats[4], 2ull * p * q * r);
       double* Xo = slot;
       double* Wo = slot + (int64_t)m * r;
       if (!tr) {

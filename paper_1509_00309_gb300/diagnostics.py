@@ -48,7 +48,8 @@ def ns_rank_distribution(ctx: "clr.Context", s: "clr.Matrix", k: int = 5) -> Dic
                  "proxy": st["proxy"], "status": st["status"]}
     out["profile"] = {key: prof[key] for key in ("products", "ms_dense", "ms_lowrank",
                                                   "ms_compress", "svd_blocks", "svd_sweeps_fp32",
-                                                  "svd_sweeps_fp64", "svd_early_dense")}
+                                                  "svd_sweeps_fp64", "svd_early_dense",
+                                                  "svd_flops_fp64", "svd_flops_fp32")}
     ctx.set_opts(ns_snapshot_iter=0)
     return out
 
