@@ -41,7 +41,10 @@ def ns_rank_distribution(ctx: "clr.Context", s: "clr.Matrix", k: int = 5) -> Dic
     ctx.profile_enable(False)
     out = {"S": histogram_summary(s)}
     for name in "XTYZ":
-        out[name + "_%d" % k] = histogram_summary(ctx.ns_snapshot(name, s))
+        try:
+            out[name + "_%d" % k] = histogram_summary(ctx.ns_snapshot(name, s))
+        except clr.ClrError:   # the iteration was not reached
+            out[name + "_%d" % k] = None
     out["Z_final"] = histogram_summary(z)
     out["ns"] = {"iters": st["iters"], "residual": st["residual"], "wall_s": wall,
                  "ms_per_iter": st["ms_total"] / max(1, st["iters"]),
