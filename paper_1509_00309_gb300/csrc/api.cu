@@ -127,10 +127,10 @@ DevicePool& pool() {
 // Device workspaces of one product in flight (grow-only).  Batched products captured into a
 // graph run on several branches, each with its own set.
 struct WorkSet {
-  DevBuf plan_ints, triples, counters, ws, scratch, panels_a, panels_b, tile_flags;
+  DevBuf plan_ints, triples, counters, ws, scratch, panels_a, panels_b, tile_flags, order;
   void release() {
     for (DevBuf* b : {&plan_ints, &triples, &counters, &ws, &scratch, &panels_a, &panels_b,
-                      &tile_flags})
+                      &tile_flags, &order})
       b->release();
   }
 };
@@ -318,7 +318,7 @@ bool same_clusters(const std::vector<int>& a, const std::vector<int>& b) { retur
 // Grow the context workspaces needed by a plan over nI x nJ tiles and nK inner clusters.
 int make_plan(clr_ctx_t ctx, int nI, int nJ, int nK, Plan* p) {
   const size_t nt = (size_t)nI * nJ;
-  CLR_CUDA(ctx->cur->plan_ints.ensure(8 * nt * sizeof(int)));
+  CLR_CUDA(ctx->cur->plan_ints.ensure(10 * nt * sizeof(int)));
   const int64_t max_tr = (int64_t)nt * nK;
   CLR_CUDA(ctx->cur->triples.ensure((size_t)max_tr * sizeof(Triple)));
   CLR_CUDA(ctx->cur->counters.ensure(sizeof(PlanCounters)));
@@ -334,6 +334,10 @@ int make_plan(clr_ctx_t ctx, int nI, int nJ, int nK, Plan* p) {
   p->l_lr = base + 5 * nt;
   p->l_qr = base + 6 * nt;
   p->l_dcomp = base + 7 * nt;
+  p->l_qr_s = base + 8 * nt;
+  p->l_dcomp_s = base + 9 * nt;
+  p->row_off = nullptr;
+  p->col_off = nullptr;
   p->triples = (Triple*)ctx->cur->triples.p;
   p->max_triples = max_tr;
   p->counters = (PlanCounters*)ctx->cur->counters.p;
@@ -584,9 +588,28 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
     launch_block_norms_dense(m->view(), s);
     launch_dense_kinds(m->view(), drop_norm, &pc->err, s);
   } else {
-    launch_compress_dense(m->view(), nullptr, nullptr, src, lda, (double*)ctx->cur->ws.p,
-                          (double*)ctx->cur->scratch.p, max_cluster(m), eps_lr, drop_norm, 0,
-                          ctx->opts.jacobi_max_sweeps, grid_of(ctx, 2), &pc->err, jst(ctx), s);
+    // blocks visited largest first (SVD cost ~ m n min(m, n)), so the dynamic distribution
+    // ends with the small ones
+    std::vector<int> order(m->nr * m->nc);
+    for (int t = 0; t < (int)order.size(); ++t) order[t] = t;
+    auto cost = [&](int t) {
+      const int64_t a = m->row_sizes[t / m->nc], b = m->col_sizes[t % m->nc];
+      return a * b * std::min(a, b);
+    };
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+    e = ctx->cur->order.ensure(order.size() * sizeof(int));
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(ctx->cur->order.p, order.data(), order.size() * sizeof(int),
+                          cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) {
+      free_mat(m);
+      return cuda_fail(ctx, e, "from_dense order");
+    }
+    launch_compress_dense(m->view(), nullptr, nullptr, (const int*)ctx->cur->order.p, src, lda,
+                          (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p, max_cluster(m),
+                          eps_lr, drop_norm, 0, ctx->opts.jacobi_max_sweeps, grid_of(ctx, 2),
+                          &pc->err, &pc->sched[2], jst(ctx), s);
   }
   e = cudaGetLastError();
   int errflag = 0;
@@ -844,6 +867,8 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   Plan p;
   int st = make_plan(ctx, a->nr, b->nc, a->nc, &p);
   if (st) return st;
+  p.row_off = c->d_row_off;
+  p.col_off = c->d_col_off;
   CLR_CUDA(ctx->cur->ws.ensure(2 * (size_t)c->n_rows * c->n_cols * sizeof(double)));
   const int lr_grid = grid_of(ctx, tune.lr_mult);
   CLR_CUDA(ctx->cur->scratch.ensure((size_t)lr_grid * scratch_per_cta() * sizeof(double)));
@@ -875,12 +900,13 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   CLR_CHECK_LAUNCH("low-rank products");
   prof_launches(ctx, 1);
   prof_mark(ctx, s, PH_LOWRANK);
-  launch_compress_qr(cv, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p,
+  launch_compress_qr(cv, p.l_qr_s, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p,
                      (double*)ctx->cur->scratch.p, max_cluster(c), eps_lr, o.jacobi_max_sweeps,
-                     lr_grid, &p.counters->err, jst(ctx), s);
-  launch_compress_dense(cv, p.l_dcomp, &p.counters->n_dcomp, nullptr, 0, (double*)ctx->cur->ws.p,
-                        (double*)ctx->cur->scratch.p, max_cluster(c), eps_lr, 0.0, 0,
-                        o.jacobi_max_sweeps, lr_grid, &p.counters->err, jst(ctx), s);
+                     lr_grid, &p.counters->err, &p.counters->sched[1], jst(ctx), s);
+  launch_compress_dense(cv, p.l_dcomp_s, &p.counters->n_dcomp, nullptr, nullptr, 0,
+                        (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p, max_cluster(c),
+                        eps_lr, 0.0, 0, o.jacobi_max_sweeps, lr_grid, &p.counters->err,
+                        &p.counters->sched[2], jst(ctx), s);
   CLR_CHECK_LAUNCH("recompression");
   prof_launches(ctx, 2);
   prof_mark(ctx, s, PH_COMPRESS);
@@ -1010,18 +1036,22 @@ extern "C" int clr_lincomb(clr_ctx_t ctx, double a, clr_mat_t x, double b, clr_m
   Plan p;
   int st = make_plan(ctx, x->nr, x->nc, 1, &p);
   if (st) return st;
+  p.row_off = out->d_row_off;
+  p.col_off = out->d_col_off;
   CLR_CUDA(ctx->cur->ws.ensure(2 * (size_t)x->n_rows * x->n_cols * sizeof(double)));
   const int grid = grid_of(ctx, 2);
   CLR_CUDA(ctx->cur->scratch.ensure((size_t)grid * scratch_per_cta() * sizeof(double)));
   const clr_opts& o = ctx->opts;
   MatView xv = x->view(), yv = y->view(), ov = out->view();
   launch_lincomb_plan(a, xv, b, yv, diag, ov, p, (double*)ctx->cur->ws.p, o.recompress_dense, s);
-  launch_compress_qr(ov, p.l_qr, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p,
+  launch_compress_qr(ov, p.l_qr_s, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p,
                      (double*)ctx->cur->scratch.p, max_cluster(out), o.eps_lr,
-                     o.jacobi_max_sweeps, grid, &p.counters->err, jst(ctx), s);
-  launch_compress_dense(ov, p.l_dcomp, &p.counters->n_dcomp, nullptr, 0, (double*)ctx->cur->ws.p,
-                        (double*)ctx->cur->scratch.p, max_cluster(out), o.eps_lr, 0.0, 0,
-                        o.jacobi_max_sweeps, grid, &p.counters->err, jst(ctx), s);
+                     o.jacobi_max_sweeps, grid, &p.counters->err, &p.counters->sched[1],
+                     jst(ctx), s);
+  launch_compress_dense(ov, p.l_dcomp_s, &p.counters->n_dcomp, nullptr, nullptr, 0,
+                        (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p, max_cluster(out),
+                        o.eps_lr, 0.0, 0, o.jacobi_max_sweeps, grid, &p.counters->err,
+                        &p.counters->sched[2], jst(ctx), s);
   CLR_CHECK_LAUNCH("lincomb");
   return CLR_OK;
 }

@@ -45,6 +45,16 @@ enum { T_DD = 0, T_DL = 1, T_LD = 2, T_LL = 3 };
 //                the rank found by the SVD is that of the FP64 sum.
 enum { ROUTE_ZERO = 0, ROUTE_DENSE = 1, ROUTE_QR = 2, ROUTE_DACC = 3, ROUTE_DACC_G = 4 };
 
+// Dynamic distribution of a tile list over a persistent grid: the CTA's next item index from
+// a launch-wide counter (zeroed before the launch), so that CTAs that drew cheap tiles take
+// more of them (tile costs vary with the cube of the cluster size).
+__device__ __forceinline__ int next_item(int* counter, int* sh_slot) {
+  __syncthreads();
+  if (threadIdx.x == 0) *sh_slot = atomicAdd(counter, 1);
+  __syncthreads();
+  return *sh_slot;
+}
+
 struct Triple {
   int tile;   // C block index I * nJ + J
   int k;      // inner cluster K
@@ -61,6 +71,7 @@ struct PlanCounters {
   unsigned long long max_rsum;
   unsigned long long n_gemm_dacc;  // tiles routed ROUTE_DACC_G
   int n_dense, n_lr, n_qr, n_dacc, n_dcomp;
+  int sched[4];   // work counters of the tile-list kernels (next_item), zeroed with the plan
   int err;  // error flag raised by kernels (bounded waits, bad metadata)
 };
 
@@ -75,6 +86,10 @@ struct Plan {
   int* l_qr;      // ROUTE_QR
   int* l_dcomp;   // tiles needing a dense truncated SVD (ROUTE_DACC, or ROUTE_DENSE when
                   // dense tiles are recompressed)
+  int* l_qr_s;    // l_qr and l_dcomp reordered by decreasing recompression cost (plan_scan)
+  int* l_dcomp_s;
+  const int* row_off;  // C's cluster offsets (device), for those costs
+  const int* col_off;
   Triple* triples;
   int64_t max_triples;
   PlanCounters* counters;
@@ -102,26 +117,28 @@ void launch_pool_to_rowmajor(const MatView& M, const int* row_idx, const int* co
 // dense_by_gemm: DENSE and DACC tiles were fully summed by the split GEMM (skip them).
 void launch_lr_products(const MatView& A, const MatView& B, const MatView& C, const Plan& p,
                         double* ws, double* scratch, int64_t scratch_per_cta, int dense_by_gemm,
-                        int grid, cudaStream_t st);
+                        int grid, cudaStream_t st);  // uses p.counters->sched[0]
 // k_svd.cu
 // jstats (may be null): device counters {svd blocks, FP32 sweeps, FP64 sweeps, early dense}
 // svd_scratch: grid x kSvdScratchPerCta doubles (FP32 working copies and an FP64 q x q factor
 // of the mixed-precision SVD).
 constexpr int64_t kSvdScratchPerCta = (int64_t)2 * CLR_MAX_CLUSTER * CLR_MAX_CLUSTER;
 // max_cluster: the largest row or column cluster of C (sizes the shared-memory request).
+// sched: a zeroed work counter (dynamic tile distribution).
 void launch_compress_qr(const MatView& C, const int* list, const int* count, const int* rsum,
                         double* ws, double* svd_scratch, int max_cluster, double eps,
-                        int max_sweeps, int grid, int* err, unsigned long long* jstats,
-                        cudaStream_t st);
+                        int max_sweeps, int grid, int* err, int* sched,
+                        unsigned long long* jstats, cudaStream_t st);
 // Dense truncated SVD of blocks listed in `list` (count on device).  The source of block b is
 // either the matrix's own slot (src == nullptr) or a row-major dense matrix src with leading
 // dimension lds.  drop_norm: blocks with norm below it become zero.  dense_only: skip the
 // SVD (eps = 0 rule) and store every non-dropped block dense.
+// order (list == nullptr only, may be null): the order in which all blocks are visited.
 void launch_compress_dense(const MatView& C, const int* list, const int* count,
-                           const double* src, int64_t lds, double* ws, double* svd_scratch,
-                           int max_cluster, double eps, double drop_norm, int dense_only,
-                           int max_sweeps, int grid, int* err, unsigned long long* jstats,
-                           cudaStream_t st);
+                           const int* order, const double* src, int64_t lds, double* ws,
+                           double* svd_scratch, int max_cluster, double eps, double drop_norm,
+                           int dense_only, int max_sweeps, int grid, int* err, int* sched,
+                           unsigned long long* jstats, cudaStream_t st);
 void launch_block_norms(const MatView& M, cudaStream_t st);
 void launch_block_norms_dense(const MatView& M, cudaStream_t st);
 void launch_scale_blocks(const MatView& M, double alpha, cudaStream_t st);

@@ -48,10 +48,12 @@ __global__ void __launch_bounds__(256) lr_products_kernel(MatView A, MatView B, 
                                                           Plan p, double* ws, double* scratch,
                                                           int64_t scratch_per_cta,
                                                           int dense_by_gemm) {
+  __shared__ int sh_next;
   double* scrZ = scratch + (int64_t)blockIdx.x * scratch_per_cta;
   double* scrF = scrZ + kZElems;
   const int n_lr = p.counters->n_lr;
-  for (int li = blockIdx.x; li < n_lr; li += gridDim.x) {
+  int* sched = &p.counters->sched[0];
+  for (int li = next_item(sched, &sh_next); li < n_lr; li = next_item(sched, &sh_next)) {
     const int t = p.l_lr[li];
     const int I = t / p.nJ, J = t % p.nJ;
     const int m = C.row_off[I + 1] - C.row_off[I];

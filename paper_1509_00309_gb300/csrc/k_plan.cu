@@ -91,6 +91,23 @@ __global__ void plan_count_kernel(MatView A, MatView B, Plan p, double eps_sp,
 // contiguous chunks is enough.
 constexpr int kScanThreads = 1024;
 constexpr int kScanQ = 5;
+constexpr int kCostBuckets = 32;
+
+// log2 bucket of a tile's recompression cost (which = 0: QR route, 1: dense SVD)
+__device__ __forceinline__ int cost_bucket(const Plan& p, int t, int which) {
+  const int I = t / p.nJ, J = t % p.nJ;
+  const long long m = p.row_off[I + 1] - p.row_off[I];
+  const long long n = p.col_off[J + 1] - p.col_off[J];
+  long long c;
+  if (which == 0) {
+    const long long R = p.t_rsum[t];
+    c = (m + n) * R * R + R * R * R;
+  } else {
+    c = m * n * (m < n ? m : n);
+  }
+  const int b = c > 0 ? 63 - __clzll(c) : 0;
+  return b < kCostBuckets ? b : kCostBuckets - 1;
+}
 
 __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(Plan p, int recompress_dense) {
   __shared__ int sh[kScanQ][kScanThreads];
@@ -137,6 +154,35 @@ __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(Plan p, int rec
     p.counters->n_qr = sh[3][tid];
     p.counters->n_dcomp = sh[4][tid];
     p.counters->n_dacc = 0;
+  }
+  // The recompression lists again, largest cost first (longest-processing-time order for the
+  // dynamically distributed SVD kernels): a counting sort on log2 of the cost, m n min(m, n)
+  // for a dense SVD, (m + n) R^2 for a QR route.  The order within a bucket is immaterial:
+  // every tile is recompressed independently.
+  __syncthreads();
+  const int n_qr = sh[3][kScanThreads - 1], n_dc = sh[4][kScanThreads - 1];
+  __shared__ int bcount[2][kCostBuckets], boff[2][kCostBuckets];
+  if (tid < 2 * kCostBuckets) (&bcount[0][0])[tid] = 0;
+  __syncthreads();
+  for (int i = tid; i < n_qr + n_dc; i += kScanThreads) {
+    const int which = i < n_qr ? 0 : 1;
+    const int t = which == 0 ? p.l_qr[i] : p.l_dcomp[i - n_qr];
+    atomicAdd(&bcount[which][cost_bucket(p, t, which)], 1);
+  }
+  __syncthreads();
+  if (tid < 2) {
+    int acc = 0;
+    for (int b = kCostBuckets - 1; b >= 0; --b) {
+      boff[tid][b] = acc;
+      acc += bcount[tid][b];
+    }
+  }
+  __syncthreads();
+  for (int i = tid; i < n_qr + n_dc; i += kScanThreads) {
+    const int which = i < n_qr ? 0 : 1;
+    const int t = which == 0 ? p.l_qr[i] : p.l_dcomp[i - n_qr];
+    const int pos = atomicAdd(&boff[which][cost_bucket(p, t, which)], 1);
+    (which == 0 ? p.l_qr_s : p.l_dcomp_s)[pos] = t;
   }
 }
 

@@ -587,13 +587,14 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
                                                                const int* rsum, double* ws,
                                                                double* svd_scratch,
                                                                int sm_cap, double eps,
-                                                               int max_sweeps,
+                                                               int max_sweeps, int* sched,
                                                                unsigned long long* jstats) {
   __shared__ SvdShared sh;
+  __shared__ int sh_next;
   extern __shared__ float dyn32[];
   double* sc = svd_scratch + (int64_t)blockIdx.x * kSvdScratchPerCta;
   const int n_items = *count;
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
+  for (int it = next_item(sched, &sh_next); it < n_items; it = next_item(sched, &sh_next)) {
     const int t = list[it];
     const int I = t / C.nc, J = t % C.nc;
     const int m = C.row_off[I + 1] - C.row_off[I];
@@ -703,14 +704,14 @@ SvdLaunchCfg svd_launch_cfg(K kernel, int64_t need_floats, int grid_max, bool* a
 
 void launch_compress_qr(const MatView& C, const int* list, const int* count, const int* rsum,
                         double* ws, double* svd_scratch, int max_cluster, double eps,
-                        int max_sweeps, int grid, int* err, unsigned long long* jstats,
-                        cudaStream_t st) {
+                        int max_sweeps, int grid, int* err, int* sched,
+                        unsigned long long* jstats, cudaStream_t st) {
   (void)err;
   static bool attr_done[64] = {false};
   const int64_t r = max_cluster / 2;  // core size R <= floor(min(m, n) / 2)
   const SvdLaunchCfg cfg = svd_launch_cfg(compress_qr_kernel, 2 * r * r, grid, attr_done);
   compress_qr_kernel<<<cfg.grid, kThreads, cfg.dyn, st>>>(C, list, count, rsum, ws, svd_scratch,
-                                                         cfg.cap, eps, max_sweeps, jstats);
+                                                         cfg.cap, eps, max_sweeps, sched, jstats);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -718,15 +719,16 @@ void launch_compress_qr(const MatView& C, const int* list, const int* count, con
 // CLR matrix from a dense one).
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
-    MatView C, const int* list, const int* count, const double* src, int64_t lds, double* ws,
-    double* svd_scratch, int sm_cap, double eps, double drop_norm, int dense_only,
-    int max_sweeps, int* err, unsigned long long* jstats) {
+    MatView C, const int* list, const int* count, const int* order, const double* src,
+    int64_t lds, double* ws, double* svd_scratch, int sm_cap, double eps, double drop_norm,
+    int dense_only, int max_sweeps, int* err, int* sched, unsigned long long* jstats) {
   __shared__ SvdShared sh;
+  __shared__ int sh_next;
   extern __shared__ float dyn32[];
   double* sc = svd_scratch + (int64_t)blockIdx.x * kSvdScratchPerCta;
   const int n_items = list ? *count : C.nr * C.nc;
-  for (int it = blockIdx.x; it < n_items; it += gridDim.x) {
-    const int t = list ? list[it] : it;
+  for (int it = next_item(sched, &sh_next); it < n_items; it = next_item(sched, &sh_next)) {
+    const int t = list ? list[it] : (order ? order[it] : it);
     const int I = t / C.nc, J = t % C.nc;
     const int m = C.row_off[I + 1] - C.row_off[I];
     const int n = C.col_off[J + 1] - C.col_off[J];
@@ -825,17 +827,18 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
 }
 
 void launch_compress_dense(const MatView& C, const int* list, const int* count,
-                           const double* src, int64_t lds, double* ws, double* svd_scratch,
-                           int max_cluster, double eps, double drop_norm, int dense_only,
-                           int max_sweeps, int grid, int* err, unsigned long long* jstats,
-                           cudaStream_t st) {
+                           const int* order, const double* src, int64_t lds, double* ws,
+                           double* svd_scratch, int max_cluster, double eps, double drop_norm,
+                           int dense_only, int max_sweeps, int grid, int* err, int* sched,
+                           unsigned long long* jstats, cudaStream_t st) {
   static bool attr_done[64] = {false};
   const int64_t c = max_cluster;
   const SvdLaunchCfg cfg =
       svd_launch_cfg(compress_dense_kernel, dense_only ? 0 : 2 * c * c, grid, attr_done);
-  compress_dense_kernel<<<cfg.grid, kThreads, cfg.dyn, st>>>(C, list, count, src, lds, ws,
+  compress_dense_kernel<<<cfg.grid, kThreads, cfg.dyn, st>>>(C, list, count, order, src, lds, ws,
                                                             svd_scratch, cfg.cap, eps, drop_norm,
-                                                            dense_only, max_sweeps, err, jstats);
+                                                            dense_only, max_sweeps, err, sched,
+                                                            jstats);
 }
 
 // ---------------------------------------------------------------------------------------------
