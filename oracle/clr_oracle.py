@@ -155,14 +155,61 @@ def compress_block(m_blk: np.ndarray, eps: float, drop_norm: float = 0.0) -> Blo
     return Block(KIND_LR, x=u[:, :r] * s[:r], w=vt[:r].T.copy())
 
 
+def compress_block_rrqr(m_blk: np.ndarray, eps: float, drop_norm: float = 0.0) -> Block:
+    """Compress one block the way Section 4.1 builds X and W: a rank-revealing QR with column
+    pivoting (Businger-Golub: at every step the remaining column of largest norm), M P = Q R,
+    truncated at the smallest r whose trailing block has ||R_22||_F <= eps (the Frobenius error
+    of X W^T, since Q is orthogonal); X = Q_r, W = P R_r^T.  Dense when r > floor(min(m,n)/2),
+    zero when r = 0 or ||M||_F < drop_norm.  Written out step by step (no LAPACK pivoting), so
+    the pivot order is the definition's."""
+    m, n = m_blk.shape
+    if m == 0 or n == 0:
+        return ZERO
+    if float(np.linalg.norm(m_blk)) < drop_norm:
+        return ZERO
+    a = np.array(m_blk, dtype=np.float64, copy=True)
+    perm = np.arange(n)
+    q = np.eye(m)
+    k = min(m, n)
+    r = k
+    for j in range(k):
+        tail = a[j:, j:]
+        if math.sqrt(float(np.sum(tail * tail))) <= eps:
+            r = j
+            break
+        norms = np.sum(a[j:, j:] ** 2, axis=0)
+        c = j + int(np.argmax(norms))          # first maximum
+        a[:, [j, c]] = a[:, [c, j]]
+        perm[[j, c]] = perm[[c, j]]
+        x = a[j:, j]
+        alpha = -math.copysign(float(np.linalg.norm(x)), float(x[0]) if x[0] != 0 else 1.0)
+        v = x.copy()
+        v[0] -= alpha
+        vn = float(v @ v)
+        if vn > 0.0:
+            h = np.eye(m - j) - 2.0 * np.outer(v, v) / vn
+            a[j:, :] = h @ a[j:, :]
+            q[:, j:] = q[:, j:] @ h
+    if r == 0:
+        return ZERO
+    if r > dense_rank_limit(m, n):
+        return Block(KIND_DENSE, d=np.array(m_blk, dtype=np.float64, copy=True))
+    w = np.zeros((n, r))
+    w[perm, :] = np.triu(a[:r, :]).T
+    return Block(KIND_LR, x=q[:, :r].copy(), w=w)
+
+
 def build(dense: np.ndarray, row_sizes: Sequence[int], col_sizes: Sequence[int], eps: float,
-          drop_norm: float = 0.0) -> CLR:
-    """CLR form of a dense matrix: every block compressed with ``compress_block``."""
+          drop_norm: float = 0.0, rrqr: bool = False) -> CLR:
+    """CLR form of a dense matrix: every block compressed with ``compress_block`` (truncated
+    SVD, the minimal rank) or, with ``rrqr``, ``compress_block_rrqr`` (the paper's
+    rank-revealing QR)."""
     out = CLR(row_sizes, col_sizes)
+    comp = compress_block_rrqr if rrqr else compress_block
     for i in range(len(out.row_sizes)):
         for j in range(len(out.col_sizes)):
             blk = dense[out.row_off[i]:out.row_off[i + 1], out.col_off[j]:out.col_off[j + 1]]
-            out.set(i, j, compress_block(blk, eps, drop_norm))
+            out.set(i, j, comp(blk, eps, drop_norm))
     return out
 
 

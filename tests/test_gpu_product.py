@@ -195,3 +195,31 @@ def test_errors_are_reported(ctx):
     c = ctx.zeros([4, 5], [4, 5])
     with pytest.raises(clr.ClrError):
         ctx.multiply_into(c, c, c)
+
+
+def test_build_svd_shared_memory_placements(ctx):
+    # clusters of 256 (FP32 copies of the SVD in global scratch), 200 (G32 in shared memory,
+    # V32 in scratch) and 37 (both in shared memory), on a smooth kernel whose blocks need
+    # both FP32 stages and the FP64 clean-up to reach eps = 1e-8
+    sizes = [256, 200, 37]
+    n = sum(sizes)
+    r = np.linspace(0.0, 0.02 * n, n) + np.random.default_rng(3).uniform(-0.004, 0.004, n)
+    a = np.exp(-(r[:, None] - r[None, :]) ** 2 / 2.0) + 1e-3 * np.eye(n)
+    eps = 1e-8
+    m = ctx.from_dense(a, sizes, eps_lr=eps)
+    want = co.build(a, sizes, sizes, eps)
+    g = clr_pack.from_library(m)
+    gk, wk, gr, wr = g.kinds(), want.kinds(), g.ranks(), want.ranks()
+    assert (wk == co.KIND_LR).sum() >= 4
+    for i in range(3):
+        for j in range(3):
+            blk = a[want.row_off[i]:want.row_off[i + 1], want.col_off[j]:want.col_off[j + 1]]
+            if gk[i, j] != wk[i, j]:
+                lim = co.dense_rank_limit(sizes[i], sizes[j])
+                assert max(gr[i, j], wr[i, j]) >= lim
+                continue
+            if gk[i, j] == co.KIND_LR:
+                assert abs(int(gr[i, j]) - int(wr[i, j])) <= 1
+                assert np.linalg.norm(g.block_dense(i, j) - blk) <= eps * (1 + 1e-6)
+            elif gk[i, j] == co.KIND_DENSE:
+                assert np.array_equal(g.block_dense(i, j), blk)

@@ -89,3 +89,51 @@ def test_build_and_reconstruct_block_errors():
             blk = a[c.row_off[i]:c.row_off[i + 1], c.col_off[j]:c.col_off[j + 1]]
             assert np.linalg.norm(blk - c.block_dense(i, j)) <= 1e-6 * (1 + 1e-9)
     assert np.linalg.norm(c.to_dense() - a) <= 3e-6
+
+
+def test_rrqr_build_error_rank_and_exact_low_rank():
+    rng = np.random.default_rng(12)
+    eps = 1e-8
+    # exact rank 6 (generic): the pivoted QR's trailing block vanishes after 6 steps
+    a = rng.standard_normal((30, 6)) @ rng.standard_normal((6, 25))
+    b = co.compress_block_rrqr(a, eps)
+    assert b.kind == co.KIND_LR and b.rank == 6
+    assert np.linalg.norm(b.x @ b.w.T - a) <= 1e-12 * np.linalg.norm(a)
+    assert np.allclose(b.x.T @ b.x, np.eye(6), atol=1e-13)         # X = Q_r orthonormal
+    # graded spectrum: error <= eps and rank >= the SVD's minimal rank
+    u, _ = np.linalg.qr(rng.standard_normal((40, 40)))
+    v, _ = np.linalg.qr(rng.standard_normal((32, 32)))
+    s = 10.0 ** (-0.5 * np.arange(32))
+    g = (u[:, :32] * s) @ v.T
+    for e in (1e-4, 1e-6):
+        br = co.compress_block_rrqr(g, e)
+        bs = co.compress_block(g, e)
+        assert br.kind == co.KIND_LR
+        assert np.linalg.norm(br.x @ br.w.T - g) <= e * (1 + 1e-9)
+        assert br.rank >= bs.rank
+    # dense and zero rules as for the SVD build
+    assert co.compress_block_rrqr(rng.standard_normal((8, 8)), eps).kind == co.KIND_DENSE
+    assert co.compress_block_rrqr(np.full((4, 5), 1e-12), 1e-8).kind == co.KIND_ZERO
+
+
+def test_rrqr_matches_lapack_pivoted_qr_rank():
+    # the step-by-step pivoted QR selects the same columns as LAPACK's xGEQP3 on generic input,
+    # so the truncation ranks agree
+    from scipy.linalg import qr
+    rng = np.random.default_rng(13)
+    for trial in range(5):
+        m, n = rng.integers(10, 40, size=2)
+        k = min(m, n)
+        s = 10.0 ** (-rng.uniform(0.2, 0.8) * np.arange(k))
+        u, _ = np.linalg.qr(rng.standard_normal((m, k)))
+        v, _ = np.linalg.qr(rng.standard_normal((n, k)))
+        g = (u * s) @ v.T
+        _, r_l, piv = qr(g, pivoting=True, mode="economic")
+        tails = [np.linalg.norm(r_l[j:, j:]) for j in range(k)] + [0.0]
+        want = next(j for j in range(k + 1) if tails[j] <= 1e-7)
+        b = co.compress_block_rrqr(g, 1e-7)
+        got = b.rank if b.kind == co.KIND_LR else (0 if b.kind == co.KIND_ZERO else -1)
+        if b.kind == co.KIND_DENSE:
+            assert want > co.dense_rank_limit(m, n)
+        else:
+            assert got == want
