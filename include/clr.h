@@ -84,7 +84,11 @@ typedef struct clr_opts {
   int ns_snapshot_iter;  /* k > 0: clr_sqrt_inv keeps copies of X_k, Y_k, Z_k, T_k of its k-th
                             iteration (Section 5's rank distribution of 5th-iteration
                             intermediates), read back with clr_ns_snapshot; 0 = off */
-  int reserved[7];
+  int build_rrqr;        /* 1: clr_mat_from_dense builds low-rank blocks by rank-revealing QR
+                            (greedy column pivoting, truncated at ||R_22||_F <= eps_lr; the
+                            paper's construction, Section 4.1) instead of the truncated SVD
+                            (the minimal rank for the same error) */
+  int reserved[6];
 } clr_opts;
 
 /* Summary of a CLR matrix (clr_mat_info). */

@@ -30,7 +30,8 @@ class ClrOpts(C.Structure):
                 ("ns_tol", C.c_double), ("ns_alpha", C.c_double),
                 ("ns_power_steps", C.c_int), ("ns_fp64_tail", C.c_int),
                 ("ns_ladder_switch", C.c_double), ("jacobi_max_sweeps", C.c_int),
-                ("ns_snapshot_iter", C.c_int), ("reserved", C.c_int * 7)]
+                ("ns_snapshot_iter", C.c_int), ("build_rrqr", C.c_int),
+                ("reserved", C.c_int * 6)]
 
 
 class ClrInfo(C.Structure):

@@ -608,8 +608,9 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
     }
     launch_compress_dense(m->view(), nullptr, nullptr, (const int*)ctx->cur->order.p, src, lda,
                           (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p, max_cluster(m),
-                          eps_lr, drop_norm, 0, ctx->opts.jacobi_max_sweeps, grid_of(ctx, 2),
-                          &pc->err, &pc->sched[2], jst(ctx), s);
+                          eps_lr, drop_norm, 0, ctx->opts.build_rrqr ? 1 : 0,
+                          ctx->opts.jacobi_max_sweeps, grid_of(ctx, 2), &pc->err, &pc->sched[2],
+                          jst(ctx), s);
   }
   e = cudaGetLastError();
   int errflag = 0;
@@ -905,7 +906,7 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
                      lr_grid, &p.counters->err, &p.counters->sched[1], jst(ctx), s);
   launch_compress_dense(cv, p.l_dcomp_s, &p.counters->n_dcomp, nullptr, nullptr, 0,
                         (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p, max_cluster(c),
-                        eps_lr, 0.0, 0, o.jacobi_max_sweeps, lr_grid, &p.counters->err,
+                        eps_lr, 0.0, 0, 0, o.jacobi_max_sweeps, lr_grid, &p.counters->err,
                         &p.counters->sched[2], jst(ctx), s);
   CLR_CHECK_LAUNCH("recompression");
   prof_launches(ctx, 2);
@@ -1050,7 +1051,7 @@ extern "C" int clr_lincomb(clr_ctx_t ctx, double a, clr_mat_t x, double b, clr_m
                      jst(ctx), s);
   launch_compress_dense(ov, p.l_dcomp_s, &p.counters->n_dcomp, nullptr, nullptr, 0,
                         (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p, max_cluster(out),
-                        o.eps_lr, 0.0, 0, o.jacobi_max_sweeps, grid, &p.counters->err,
+                        o.eps_lr, 0.0, 0, 0, o.jacobi_max_sweeps, grid, &p.counters->err,
                         &p.counters->sched[2], jst(ctx), s);
   CLR_CHECK_LAUNCH("lincomb");
   return CLR_OK;

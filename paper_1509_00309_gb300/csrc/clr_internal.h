@@ -134,11 +134,12 @@ void launch_compress_qr(const MatView& C, const int* list, const int* count, con
 // dimension lds.  drop_norm: blocks with norm below it become zero.  dense_only: skip the
 // SVD (eps = 0 rule) and store every non-dropped block dense.
 // order (list == nullptr only, may be null): the order in which all blocks are visited.
+// rrqr: truncate by rank-revealing QR instead of the SVD.
 void launch_compress_dense(const MatView& C, const int* list, const int* count,
                            const int* order, const double* src, int64_t lds, double* ws,
                            double* svd_scratch, int max_cluster, double eps, double drop_norm,
-                           int dense_only, int max_sweeps, int grid, int* err, int* sched,
-                           unsigned long long* jstats, cudaStream_t st);
+                           int dense_only, int rrqr, int max_sweeps, int grid, int* err,
+                           int* sched, unsigned long long* jstats, cudaStream_t st);
 void launch_block_norms(const MatView& M, cudaStream_t st);
 void launch_block_norms_dense(const MatView& M, cudaStream_t st);
 void launch_scale_blocks(const MatView& M, double alpha, cudaStream_t st);

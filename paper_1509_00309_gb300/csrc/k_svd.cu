@@ -715,13 +715,110 @@ void launch_compress_qr(const MatView& C, const int* list, const int* count, con
 }
 
 // ---------------------------------------------------------------------------------------------
+// Rank-revealing QR of one block (the paper's construction of X and W, Section 4.1): Householder
+// QR with greedy column pivoting (at step j the remaining column of largest norm over rows
+// j..m-1, first maximum; the norms are recomputed exactly every step), stopped at the first j
+// whose trailing block has ||R_22||_F <= eps.  g: m x n work copy (ld m); on return its upper
+// trapezoid holds R, the reflectors lie below the diagonal (v_0 = 1), tau in sh.sorted and the
+// column order in sh.perm.  Returns the rank r.
+// ---------------------------------------------------------------------------------------------
+__device__ int rrqr_block(const double* S, int64_t s_r, int64_t s_c, int m, int n, double eps,
+                          double* g, SvdShared& sh) {
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  for (int e = threadIdx.x; e < m * n; e += kThreads) {
+    const int i = e % m, j = e / m;
+    g[e] = S[i * s_r + j * s_c];
+  }
+  for (int c = threadIdx.x; c < n; c += kThreads) sh.perm[c] = c;
+  __syncthreads();
+  const int k = m < n ? m : n;
+  int r = k;
+  for (int j = 0; j < k; ++j) {
+    for (int c = j + w; c < n; c += kWarps) {
+      const double* gc = g + (int64_t)c * m;
+      double s2 = 0.0;
+      for (int i = j + l; i < m; i += 32) s2 = fma(gc[i], gc[i], s2);
+      s2 = warp_sum(s2);
+      if (l == 0) sh.sigma[c] = s2;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double tot = 0.0, best = -1.0;
+      int arg = j;
+      for (int c = j; c < n; ++c) {
+        tot += sh.sigma[c];
+        if (sh.sigma[c] > best) { best = sh.sigma[c]; arg = c; }
+      }
+      sh.kept_sq = tot;
+      sh.flag = arg;
+    }
+    __syncthreads();
+    if (sqrt(sh.kept_sq) <= eps) {
+      r = j;
+      break;
+    }
+    const int piv = sh.flag;
+    if (piv != j) {
+      double* a = g + (int64_t)j * m;
+      double* b = g + (int64_t)piv * m;
+      for (int i = threadIdx.x; i < m; i += kThreads) {
+        const double t = a[i];
+        a[i] = b[i];
+        b[i] = t;
+      }
+      if (threadIdx.x == 0) {
+        const int t = sh.perm[j];
+        sh.perm[j] = sh.perm[piv];
+        sh.perm[piv] = t;
+      }
+    }
+    __syncthreads();
+    // Householder reflector of column j below the diagonal (as householder_qr)
+    double* col = g + (int64_t)j * m;
+    double part = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < m; i += kThreads) part += col[i] * col[i];
+    const double s = block_sum(part, sh.red);
+    const double x0 = col[j];
+    double t = 0.0, beta = x0, v0 = 1.0;
+    if (s > 0.0) {
+      beta = -copysign(sqrt(x0 * x0 + s), x0);
+      v0 = x0 - beta;
+      t = (beta - x0) / beta;
+    }
+    __syncthreads();
+    if (s > 0.0) {
+      const double inv = 1.0 / v0;
+      for (int i = j + 1 + threadIdx.x; i < m; i += kThreads) col[i] *= inv;
+    }
+    if (threadIdx.x == 0) {
+      col[j] = beta;
+      sh.sorted[j] = t;
+    }
+    __syncthreads();
+    if (t != 0.0) {
+      for (int c = j + 1 + w; c < n; c += kWarps) {
+        double* y = g + (int64_t)c * m;
+        double d = 0.0;
+        for (int i = j + 1 + l; i < m; i += 32) d += col[i] * y[i];
+        d = warp_sum(d) + y[j];
+        const double f = t * d;
+        if (l == 0) y[j] -= f;
+        for (int i = j + 1 + l; i < m; i += 32) y[i] -= f * col[i];
+      }
+    }
+    __syncthreads();
+  }
+  return r;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Dense truncated SVD of whole blocks (ROUTE_DACC tiles, recompressed dense tiles, building a
 // CLR matrix from a dense one).
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
     MatView C, const int* list, const int* count, const int* order, const double* src,
     int64_t lds, double* ws, double* svd_scratch, int sm_cap, double eps, double drop_norm,
-    int dense_only, int max_sweeps, int* err, int* sched, unsigned long long* jstats) {
+    int dense_only, int rrqr, int max_sweeps, int* err, int* sched, unsigned long long* jstats) {
   __shared__ SvdShared sh;
   __shared__ int sh_next;
   extern __shared__ float dyn32[];
@@ -761,7 +858,32 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
       continue;
     }
     int r = q;
-    if (!dense_only) {
+    if (rrqr && !dense_only) {
+      r = rrqr_block(S, s_r, s_c, m, n, eps, G, sh);
+      if (r > 0 && r <= q / 2) {
+        // X = Q_r (the first r columns of H_0 ... H_{r-1}), W = P R_r^T
+        double* Xo = slot;
+        double* Wo = slot + (int64_t)m * r;
+        for (int e = threadIdx.x; e < m * r; e += kThreads) Xo[e] = (e % m == e / m) ? 1.0 : 0.0;
+        __syncthreads();
+        apply_q(G, m, r, m, sh.sorted, Xo, r, m);
+        double part = 0.0;
+        for (int e = threadIdx.x; e < n * r; e += kThreads) {
+          const int c = e % n, i = e / n;
+          const double v = c >= i ? G[i + (int64_t)c * m] : 0.0;
+          Wo[sh.perm[c] + (int64_t)i * n] = v;
+          part = fma(v, v, part);
+        }
+        const double kept = block_sum(part, sh.red);
+        if (threadIdx.x == 0) {
+          C.kind[t] = CLR_KIND_LR;
+          C.rank[t] = r;
+          C.norm[t] = sqrt(kept);
+        }
+        __syncthreads();
+        continue;
+      }
+    } else if (!dense_only) {
       const SrcView view{S, s_r, s_c, tr};
       const int early_dense =
           svd_mixed(view, p, q, G, V, sc, dyn32, sm_cap, max_sweeps, eps, q / 2, nrm, sh,
@@ -829,16 +951,16 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
 void launch_compress_dense(const MatView& C, const int* list, const int* count,
                            const int* order, const double* src, int64_t lds, double* ws,
                            double* svd_scratch, int max_cluster, double eps, double drop_norm,
-                           int dense_only, int max_sweeps, int grid, int* err, int* sched,
-                           unsigned long long* jstats, cudaStream_t st) {
+                           int dense_only, int rrqr, int max_sweeps, int grid, int* err,
+                           int* sched, unsigned long long* jstats, cudaStream_t st) {
   static bool attr_done[64] = {false};
   const int64_t c = max_cluster;
   const SvdLaunchCfg cfg =
       svd_launch_cfg(compress_dense_kernel, dense_only ? 0 : 2 * c * c, grid, attr_done);
   compress_dense_kernel<<<cfg.grid, kThreads, cfg.dyn, st>>>(C, list, count, order, src, lds, ws,
                                                             svd_scratch, cfg.cap, eps, drop_norm,
-                                                            dense_only, max_sweeps, err, sched,
-                                                            jstats);
+                                                            dense_only, rrqr, max_sweeps, err,
+                                                            sched, jstats);
 }
 
 // ---------------------------------------------------------------------------------------------

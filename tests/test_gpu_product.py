@@ -223,3 +223,33 @@ def test_build_svd_shared_memory_placements(ctx):
                 assert np.linalg.norm(g.block_dense(i, j) - blk) <= eps * (1 + 1e-6)
             elif gk[i, j] == co.KIND_DENSE:
                 assert np.array_equal(g.block_dense(i, j), blk)
+
+
+def test_rrqr_build_matches_oracle(ctx):
+    # the paper's construction (Section 4.1): rank-revealing QR with greedy column pivoting,
+    # truncated at ||R_22||_F <= eps; ranks as the oracle's step-by-step pivoted QR (within one
+    # where a pivot is decided by rounding), errors within eps, never below the SVD's rank
+    w = wl.chain_overlap(n=640, n_clusters=5, lo=96, hi=160)
+    eps = 1e-8
+    ctx.set_opts(build_rrqr=1)
+    try:
+        m = ctx.from_dense(w.a, w.row_sizes, eps_lr=eps, drop_norm=w.drop_norm)
+    finally:
+        ctx.set_opts(build_rrqr=0)
+    want = co.build(w.a, w.row_sizes, w.col_sizes, eps, w.drop_norm, rrqr=True)
+    svd = co.build(w.a, w.row_sizes, w.col_sizes, eps, w.drop_norm)
+    g = clr_pack.from_library(m)
+    gk, wk, gr, wr = g.kinds(), want.kinds(), g.ranks(), want.ranks()
+    assert (wk == co.KIND_LR).sum() >= 6
+    for (i, j) in want.blocks:
+        blk = w.a[want.row_off[i]:want.row_off[i + 1], want.col_off[j]:want.col_off[j + 1]]
+        if gk[i, j] != wk[i, j]:
+            lim = co.dense_rank_limit(blk.shape[0], blk.shape[1])
+            assert max(gr[i, j], wr[i, j]) >= lim
+            continue
+        if gk[i, j] == co.KIND_LR:
+            assert abs(int(gr[i, j]) - int(wr[i, j])) <= 1
+            assert gr[i, j] >= svd.ranks()[i, j]
+            assert np.linalg.norm(g.block_dense(i, j) - blk) <= eps * (1 + 1e-6)
+            x = g.blocks[(i, j)].x
+            assert np.allclose(x.T @ x, np.eye(x.shape[1]), atol=1e-12)   # X = Q_r
