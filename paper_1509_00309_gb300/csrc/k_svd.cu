@@ -7,13 +7,16 @@
 // singular values on the left factor (X' = Q_X U_r S_r, W' = Q_W V_r).  A block whose rank
 // exceeds floor(min(m,n)/2) is stored dense.
 //
-// One CTA (8 warps) handles one tile:
+// One CTA (16 warps) handles one tile at a time, taking tiles from a launch-wide counter:
 //   Householder QR         LAPACK-style reflectors H = I - tau v v^T, v_0 = 1;
 //   one-sided Jacobi SVD   Hestenes rotations on column pairs, round-robin ordering so a
 //                          round's pairs are disjoint (one warp per pair), until no pair has
-//                          |g_a.g_b| > tol ||g_a|| ||g_b|| or the sweep limit is reached.
+//                          |g_a.g_b| > tol ||g_a|| ||g_b|| or the sweep limit is reached
+//                          (mixed FP32/FP64 stages, svd_mixed);
+//   rank-revealing QR      the paper's construction for building from dense (option).
 // FP64 working arrays live in the tile's workspace slot (2 m n doubles per tile, enough for
-// either route); the FP32 copies of the mixed-precision SVD in a per-CTA scratch.
+// either route); the FP32 copies of the mixed-precision SVD in shared memory where they fit,
+// else in a per-CTA scratch.
 #include <cfloat>
 #include <mutex>
 
