@@ -2,6 +2,7 @@
 ranks of the 5th-iteration intermediates X, Y, Z, T and of the input S).
 
     python -m paper_1509_00309_gb300.diagnostics --shape 8x8x4 --iter 5 [--matrix coulomb]
+    python -m paper_1509_00309_gb300.diagnostics --adjoint --shape 8x8x8 --max-iter 20
 
 builds the 3D lattice overlap matrix (16 points per site, clusters of 64..256 points, eps_lr
 1e-6, drop 1e-10, eps_sp 1e-13), or the Coulomb-like erf(r)/r matrix on the same lattice, on
@@ -57,6 +58,31 @@ def ns_rank_distribution(ctx: "clr.Context", s: "clr.Matrix", k: int = 5) -> Dic
     return out
 
 
+def adjoint_run(shape, precision: str = "fp64", iters: int = 20, eps: float = 1e-8) -> Dict:
+    """The differentiation configuration: loss = trace(W S^-1/2) on the 3D lattice overlap
+    matrix (eps_lr = 1e-8, 20 checkpointed NS iterations), gradient dL/dS by the hand-written
+    adjoint (clr_sqrt_inv_backward); device times of the forward and backward sweeps."""
+    import torch
+    w = wl.adjoint_lattice(n_sites_shape=shape)
+    ctx = clr.Context(0, precision=precision, eps_lr=eps, ns_tol=0.0, ns_max_iter=iters)
+    s = ctx.from_dense(torch.from_numpy(w.a).cuda(), w.row_sizes, eps_lr=eps)
+    zb = ctx.from_dense(torch.from_numpy(np.ascontiguousarray(w.extra["w"].T)).cuda(),
+                        w.row_sizes, eps_lr=0.0)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    ev[0].record()
+    z, st, tape = ctx.sqrt_inv(s, keep_tape=True)
+    ev[1].record()
+    g = ctx.sqrt_inv_backward(tape, zb)
+    ev[2].record()
+    torch.cuda.synchronize()
+    gi = g.info()
+    return {"workload": w.name, "n": w.n, "clusters": len(w.row_sizes), "eps_lr": eps,
+            "iterations": st["iters"], "residual": st["residual"],
+            "ms_forward": ev[0].elapsed_time(ev[1]), "ms_backward": ev[1].elapsed_time(ev[2]),
+            "grad_frob": gi["frob_norm"], "grad_blocks": gi["n_blocks"]}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--shape", default="8x8x4", help="lattice sites, e.g. 16x16x8 (N = 16 x sites)")
@@ -66,9 +92,15 @@ def main() -> None:
     ap.add_argument("--tol", type=float, default=1e-6)
     ap.add_argument("--no-recompress-dense", action="store_true")
     ap.add_argument("--matrix", default="overlap", choices=["overlap", "coulomb"])
+    ap.add_argument("--adjoint", action="store_true",
+                    help="time forward + adjoint of trace(W S^-1/2) instead (eps_lr 1e-8, "
+                         "--max-iter iterations)")
     args = ap.parse_args()
     import torch
     shape = tuple(int(v) for v in args.shape.split("x"))
+    if args.adjoint:
+        print(json.dumps(adjoint_run(shape, args.precision, min(args.max_iter, 40))))
+        return
     w = wl.lattice_overlap(shape=shape) if args.matrix == "overlap" else \
         wl.lattice_coulomb(shape=shape)
     ctx = clr.Context(0, precision=args.precision, eps_lr=w.eps_lr, eps_sp=w.eps_sp,

@@ -72,3 +72,37 @@ def test_autograd_function_vs_finite_differences(clr):
         e[i, j] = h
         fd = (f(w.a + e) - f(w.a - e)) / (2 * h)
         assert abs(fd - g[i, j]) <= 1e-4 * max(1.0, abs(g[i, j])), (i, j, fd, g[i, j])
+
+
+@pytest.mark.parametrize("eps", [1e-8, 0.0])
+def test_adjoint_lattice_finite_differences_32_entries(clr, eps):
+    # the differentiation configuration scaled to N = 512 (4x4x2 sites x 16 points): 20
+    # Newton-Schulz iterations at eps_lr, gradient of trace(W S^-1/2) by the adjoint against
+    # central differences (h = 1e-6) on 32 seeded entries.  With eps = 1e-8 the truncation noise
+    # in L (~1e-8) limits the difference quotient to ~1e-2 absolute: tolerance
+    # max(1e-2 |g|, 1e-3); exact arithmetic (eps = 0, dense tiles): 1e-6 relative.
+    w = wl.adjoint_lattice(n_sites_shape=(4, 4, 2), min_points=32, max_points=128)
+    s, wmat = w.a, w.extra["w"]
+    alpha = co.alpha_estimate(s)
+    ctx = clr.Context(0, precision="fp64", eps_lr=eps, ns_tol=0.0, ns_max_iter=20,
+                      ns_alpha=alpha)
+
+    def loss(mat, tape=False):
+        sm = ctx.from_dense(mat, w.row_sizes, eps_lr=eps)
+        z, st, tp = ctx.sqrt_inv(sm, keep_tape=tape)
+        assert st["iters"] == 20
+        return float(np.sum(wmat * z.to_dense().T)), z, tp   # trace(W Z)
+
+    _, z, tape = loss(s, tape=True)
+    zb = ctx.from_dense(np.ascontiguousarray(wmat.T), w.row_sizes, eps_lr=0.0)
+    g = ctx.sqrt_inv_backward(tape, zb).to_dense()
+    h = 1e-6
+    rng = np.random.default_rng(44)
+    worst = 0.0
+    for i, j in rng.integers(0, w.n, size=(32, 2)):
+        e = np.zeros_like(s)
+        e[i, j] = h
+        fd = (loss(s + e)[0] - loss(s - e)[0]) / (2 * h)
+        tol = max(1e-2 * abs(g[i, j]), 1e-3) if eps > 0 else 1e-6 * max(1.0, abs(g[i, j]))
+        assert abs(fd - g[i, j]) <= tol, (i, j, fd, g[i, j])
+        worst = max(worst, abs(fd - g[i, j]))
