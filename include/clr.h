@@ -236,7 +236,8 @@ int clr_lincomb(clr_ctx_t ctx, double a, clr_mat_t x, double b, clr_mat_t y, dou
  * product at the context's eps_lr / eps_sp; T is formed by clr_lincomb.  Synchronises
  * `stream` once per iteration to read the convergence scalar.  Returns CLR_ENOCONV (with *z
  * still set) when ns_tol > 0 is not reached.  With `tape` non-NULL the iterates (Y_n, Z_n)
- * are kept for clr_sqrt_inv_backward (checkpointed every iteration). */
+ * are kept for clr_sqrt_inv_backward (checkpointed every iteration); the tape owns copies of
+ * everything it needs, so S may be freed before the backward call. */
 int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s, clr_mat_t* z, clr_ns_stats* stats,
                  clr_tape_t* tape, void* stream);
 /* ||alpha Z S Z - I||_F / sqrt(N) for z = sqrt(alpha) Z (two CLR products); synchronises. */

@@ -200,7 +200,9 @@ struct clr_batch_s;
 struct clr_tape_s {
   double alpha = 0.0;
   int iters = 0;
-  clr_mat_t s = nullptr;                        // borrowed
+  std::vector<int> sizes;                       // S's clusters (S itself is not kept: the
+                                                // caller may free it before the backward)
+  int prec = CLR_PREC_FP64;                     // precision of the adjoint products
   std::vector<clr_mat_t> y, z;                  // owned: Y_n, Z_n before update n
 };
 
@@ -1213,7 +1215,8 @@ extern "C" int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t* z_out,
   if (tape_out) {
     tape.reset(new clr_tape_s);
     tape->alpha = alpha;
-    tape->s = s_mat;
+    tape->sizes = s_mat->row_sizes;
+    tape->prec = choose_precision(ctx, s_mat, s_mat);
   }
   st = clr_mat_copy(ctx, s_mat, Y, s);
   if (st) return st;
@@ -1360,13 +1363,12 @@ extern "C" int clr_sqrt_inv_backward(clr_ctx_t ctx, clr_tape_t tape, clr_mat_t z
   // starting from Zb = sqrt(alpha) zbar (the output is sqrt(alpha) Z), Yb = 0; dL/dS = Yb_0.
   if (!ctx || !tape || !zbar || !sbar) return CLR_EINVAL;
   *sbar = nullptr;
-  if (!tape->s || zbar->row_sizes != tape->s->row_sizes ||
-      zbar->col_sizes != tape->s->col_sizes)
+  if (tape->sizes.empty() || zbar->row_sizes != tape->sizes || zbar->col_sizes != tape->sizes)
     return fail(ctx, CLR_EINVAL, "zbar clusters differ from S");
   cudaSetDevice(ctx->device);
   cudaStream_t s = as_stream(stream);
-  const int nr = tape->s->nr;
-  const int32_t* sz = tape->s->row_sizes.data();
+  const int nr = (int)tape->sizes.size();
+  const int32_t* sz = tape->sizes.data();
   MatGuard g;
   enum { X, X2, T, TT, XT, YT, ZT, TB, XB, ZB, YB, ZBN, YBN, W1, W2, NW };
   clr_mat_t m[NW];
@@ -1377,7 +1379,7 @@ extern "C" int clr_sqrt_inv_backward(clr_ctx_t ctx, clr_tape_t tape, clr_mat_t z
   }
   const double alpha = tape->alpha;
   Tuning tn;
-  tn.prec = choose_precision(ctx, tape->s, tape->s);
+  tn.prec = tape->prec;
   auto mul = [&](clr_mat_t a, clr_mat_t b, clr_mat_t c, double sc) {
     return multiply_into(ctx, a, b, c, sc, tn, nullptr, s);
   };
