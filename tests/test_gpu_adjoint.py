@@ -98,11 +98,19 @@ def test_adjoint_lattice_finite_differences_32_entries(clr, eps):
     g = ctx.sqrt_inv_backward(tape, zb).to_dense()
     h = 1e-6
     rng = np.random.default_rng(44)
-    worst = 0.0
-    for i, j in rng.integers(0, w.n, size=(32, 2)):
+
+    def central(i, j, step):
         e = np.zeros_like(s)
-        e[i, j] = h
-        fd = (loss(s + e)[0] - loss(s - e)[0]) / (2 * h)
-        tol = max(1e-2 * abs(g[i, j]), 1e-3) if eps > 0 else 1e-6 * max(1.0, abs(g[i, j]))
+        e[i, j] = step
+        return (loss(s + e)[0] - loss(s - e)[0]) / (2 * step)
+
+    for i, j in rng.integers(0, w.n, size=(32, 2)):
+        fd = central(i, j, h)
+        if eps > 0:
+            tol = max(1e-2 * abs(g[i, j]), 1e-3)
+        else:
+            # exact arithmetic: 1e-6 relative plus the difference quotient's own O(h^2) error,
+            # estimated by Richardson from the step 2h (|fd(h) - fd(2h)| / 3); the small
+            # eigenvalues (1e-2) make the third derivative large enough for that term to matter
+            tol = 1e-6 * max(1.0, abs(g[i, j])) + abs(fd - central(i, j, 2 * h)) / 3 * 1.5
         assert abs(fd - g[i, j]) <= tol, (i, j, fd, g[i, j])
-        worst = max(worst, abs(fd - g[i, j]))
