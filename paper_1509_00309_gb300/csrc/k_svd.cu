@@ -26,6 +26,7 @@ namespace clr {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
+constexpr int kFp64SweepCap = 3;  // FP64 sweeps of svd_mixed when the right factor is recovered
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -315,6 +316,8 @@ struct SvdShared {
   int perm[CLR_MAX_CLUSTER];        // sorted position -> column
   int flag;
   int v_tracked;  // svd_mixed: 1 when v holds the right singular vectors (else recover_right)
+  int ls_recover; // svd_mixed: 1 when G's kept columns may be non-orthogonal (FP64 sweep cap
+                  // reached): the right factor needs the least-squares form (ls_solve)
   int rank;
   double kept_sq;
 };
@@ -422,6 +425,57 @@ __device__ void recover_right(const SrcView& a, int p, int q, const double* g, c
     double s2 = 0.0;
     for (int k = 0; k < p; ++k) s2 = fma(a.at(k, j), gc[k], s2);
     y[e] = s2;
+  }
+  __syncthreads();
+}
+
+// y (q x r, ld q) <- y (G_r^T G_r)^-1 in FP64, G_r the r kept columns of g (p x q, ld p) in the
+// order perm, with norms d: the least-squares right factor when G_r is not orthogonal to FP64
+// precision.  The Gram matrix of the normalised columns (unit diagonal, off-diagonal at the
+// FP32 stages' tolerance, so well conditioned) is factored by Cholesky in mw (r x r).
+__device__ void ls_solve(double* y, int q, int r, const double* g, int p, const int* perm,
+                         const double* d, double* mw, SvdShared& sh) {
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  for (int e = w; e < r * r; e += kWarps) {
+    const int i = e % r, j = e / r;
+    if (i < j) continue;
+    const double* gi = g + (int64_t)perm[i] * p;
+    const double* gj = g + (int64_t)perm[j] * p;
+    double s2 = 0.0;
+    for (int k = l; k < p; k += 32) s2 = fma(gi[k], gj[k], s2);
+    s2 = warp_sum(s2);
+    if (l == 0) mw[i + (int64_t)j * r] = s2 / (d[i] * d[j]);
+  }
+  __syncthreads();
+  for (int j = 0; j < r; ++j) {  // lower Cholesky, column by column
+    if (threadIdx.x == 0) {
+      double a = mw[j + (int64_t)j * r];
+      for (int k = 0; k < j; ++k) a -= mw[j + (int64_t)k * r] * mw[j + (int64_t)k * r];
+      mw[j + (int64_t)j * r] = sqrt(a);
+    }
+    __syncthreads();
+    const double ljj = mw[j + (int64_t)j * r];
+    for (int i = j + 1 + threadIdx.x; i < r; i += kThreads) {
+      double a = mw[i + (int64_t)j * r];
+      for (int k = 0; k < j; ++k) a -= mw[i + (int64_t)k * r] * mw[j + (int64_t)k * r];
+      mw[i + (int64_t)j * r] = a / ljj;
+    }
+    __syncthreads();
+  }
+  // each row t: x = (y_t D^-1) (L L^T)^-1 D^-1
+  for (int t = threadIdx.x; t < q; t += kThreads) {
+    double* yt = y + t;  // stride q
+    for (int i = 0; i < r; ++i) {  // forward: L u = (y_t D^-1)^T
+      double a = yt[(int64_t)i * q] / d[i];
+      for (int k = 0; k < i; ++k) a -= mw[i + (int64_t)k * r] * yt[(int64_t)k * q];
+      yt[(int64_t)i * q] = a / mw[i + (int64_t)i * r];
+    }
+    for (int i = r - 1; i >= 0; --i) {  // back: L^T x = u
+      double a = yt[(int64_t)i * q];
+      for (int k = i + 1; k < r; ++k) a -= mw[k + (int64_t)i * r] * yt[(int64_t)k * q];
+      yt[(int64_t)i * q] = a / mw[i + (int64_t)i * r];
+    }
+    for (int i = 0; i < r; ++i) yt[(int64_t)i * q] /= d[i];
   }
   __syncthreads();
 }
@@ -566,8 +620,15 @@ __device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, d
     if (track_v) right_multiply_fp64(v, q, q, q, v2t);
   }
   if (threadIdx.x == 0) sh.v_tracked = track_v ? 1 : 0;
-  const int sw64 = jacobi_svd<double>(g, p, q, p, track_v ? v : nullptr, q, max_sweeps,
-                                      &sh.flag, false, 1.0, floor64 * floor64);
+  // Without V accumulation the FP64 sweeps stop after kFp64SweepCap: a block whose spectrum has
+  // a tight cluster converges only linearly there (measured up to 17 sweeps on 256 x 256
+  // blocks), yet the truncation does not need it -- with the least-squares right factor
+  // (ls_solve) X W^T is the orthogonal projection of A onto span(G_r) for any G = A V_eff, so
+  // the error stays ||(I - P) G_tail|| <= ||G_tail||_F <= eps, converged or not.
+  const int cap64 = track_v || max_sweeps < kFp64SweepCap ? max_sweeps : kFp64SweepCap;
+  const int sw64 = jacobi_svd<double>(g, p, q, p, track_v ? v : nullptr, q, cap64, &sh.flag,
+                                      false, 1.0, floor64 * floor64);
+  if (threadIdx.x == 0) sh.ls_recover = (!track_v && sw64 >= cap64) ? 1 : 0;
   if (jstats && threadIdx.x == 0) {
     // algorithmic flops: Jacobi 4 p q^2 per sweep, orthonormalisation 2 q^3, products 2 p q^2
     const unsigned long long pq2 = (unsigned long long)p * q * q, q3 = (unsigned long long)q * q * q;
@@ -632,10 +693,12 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
     sort_and_truncate(G, R, R, R, eps, sh);
     const int r = sh.rank;
     const bool tracked = sh.v_tracked;
+    const bool ls = !tracked && sh.ls_recover;
     if (!tracked) {
-      // V_r S_r^2 = M^T G_r into V (M is still intact)
+      // V_r S_r^2 = M^T G_r into V (M is still intact), or the least-squares V_r
       SrcView mv{M, 1, R, false};
       recover_right(mv, R, R, G, sh.perm, r, V);
+      if (ls) ls_solve(V, R, r, G, R, sh.perm, sh.sorted, sc, sh);
     }
     double* Xo = C.pool + sC;
     double* Wo = Xo + (int64_t)m * r;
@@ -647,6 +710,7 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
       const int j = e % n, c = e / n;
       Wo[e] = j >= R ? 0.0
               : tracked ? V[j + (int64_t)sh.perm[c] * R]
+              : ls      ? V[j + (int64_t)c * R]
                         : V[j + (int64_t)c * R] / (sh.sorted[c] * sh.sorted[c]);
     }
     __syncthreads();
@@ -912,7 +976,9 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
       // Y = V_r S_r^2 from the accumulated V
       const SrcView view{S, s_r, s_c, tr};
       const bool tracked = sh.v_tracked;
+      const bool ls = !tracked && sh.ls_recover;
       if (!tracked) recover_right(view, p, q, G, sh.perm, r, V);
+      if (ls) ls_solve(V, q, r, G, p, sh.perm, sh.sorted, sc, sh);
       if (jstats && threadIdx.x == 0 && !tracked)
         atomicAdd(&jstats[4], 2ull * p * q * r);
       double* Xo = slot;
@@ -926,6 +992,7 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
         for (int e = threadIdx.x; e < n * r; e += kThreads) {
           const int j = e % n, c = e / n;
           Wo[e] = tracked ? V[j + (int64_t)sh.perm[c] * q]
+                  : ls    ? V[j + (int64_t)c * q]
                           : V[j + (int64_t)c * q] / (sh.sorted[c] * sh.sorted[c]);
         }
       } else {
@@ -934,11 +1001,12 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
         for (int e = threadIdx.x; e < m * r; e += kThreads) {
           const int i = e % m, c = e / m;
           Xo[e] = tracked ? V[i + (int64_t)sh.perm[c] * q] * sh.sorted[c]
+                  : ls    ? V[i + (int64_t)c * q]
                           : V[i + (int64_t)c * q] / sh.sorted[c];
         }
         for (int e = threadIdx.x; e < n * r; e += kThreads) {
           const int j = e % n, c = e / n;
-          Wo[e] = G[j + (int64_t)sh.perm[c] * p] / sh.sorted[c];
+          Wo[e] = ls ? G[j + (int64_t)sh.perm[c] * p] : G[j + (int64_t)sh.perm[c] * p] / sh.sorted[c];
         }
       }
       if (threadIdx.x == 0) {

@@ -253,3 +253,22 @@ def test_rrqr_build_matches_oracle(ctx):
             assert np.linalg.norm(g.block_dense(i, j) - blk) <= eps * (1 + 1e-6)
             x = g.blocks[(i, j)].x
             assert np.allclose(x.T @ x, np.eye(x.shape[1]), atol=1e-12)   # X = Q_r
+
+
+def test_build_tight_cluster_least_squares_factor(ctx):
+    # A tight cluster of kept singular values (40 values 1 + 1e-12 k) keeps the FP64 Jacobi from
+    # converging within its sweep cap; the right factor is then the least-squares one and X W^T
+    # must still be within eps of the block, with the oracle's rank.  Square and wide blocks.
+    rng = np.random.default_rng(17)
+    eps = 1e-6
+    for m, n in ((200, 200), (120, 230)):
+        k = min(m, n)
+        u, _ = np.linalg.qr(rng.standard_normal((m, k)))
+        v, _ = np.linalg.qr(rng.standard_normal((n, k)))
+        s = np.concatenate([1.0 + 1e-12 * np.arange(40), 1e-9 * rng.uniform(0.5, 1.0, k - 40)])
+        a = (u * s) @ v.T
+        mat = ctx.from_dense(a, [m], [n], eps_lr=eps)
+        g = clr_pack.from_library(mat)
+        assert g.kinds()[0, 0] == co.KIND_LR
+        assert g.ranks()[0, 0] == co.compress_block(a, eps).rank == 40
+        assert np.linalg.norm(g.block_dense(0, 0) - a) <= eps
