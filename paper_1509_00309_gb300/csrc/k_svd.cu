@@ -26,7 +26,7 @@ namespace clr {
 
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
-constexpr int kFp64SweepCap = 3;  // FP64 sweeps of svd_mixed when the right factor is recovered
+constexpr int kFp64SweepCap = 1;  // FP64 sweeps of svd_mixed when the right factor is recovered
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -620,11 +620,13 @@ __device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, d
     if (track_v) right_multiply_fp64(v, q, q, q, v2t);
   }
   if (threadIdx.x == 0) sh.v_tracked = track_v ? 1 : 0;
-  // Without V accumulation the FP64 sweeps stop after kFp64SweepCap: a block whose spectrum has
-  // a tight cluster converges only linearly there (measured up to 17 sweeps on 256 x 256
-  // blocks), yet the truncation does not need it -- with the least-squares right factor
-  // (ls_solve) X W^T is the orthogonal projection of A onto span(G_r) for any G = A V_eff, so
-  // the error stays ||(I - P) G_tail|| <= ||G_tail||_F <= eps, converged or not.
+  // Without V accumulation the FP64 sweeps stop after kFp64SweepCap: one sweep takes the pairs'
+  // cosines from the FP32 stages' ~1e-5 to ~1e-10 (quadratic step), which fixes the column
+  // norms (the truncation) to ~1e-20 relative; a block whose spectrum has a tight cluster would
+  // converge only linearly (measured up to 17 sweeps on 256 x 256 blocks), and the truncation
+  // does not need it -- with the least-squares right factor (ls_solve) X W^T is the orthogonal
+  // projection of A onto span(G_r) for any G = A V_eff, so the error stays
+  // ||(I - P) G_tail|| <= ||G_tail||_F <= eps, converged or not.
   const int cap64 = track_v || max_sweeps < kFp64SweepCap ? max_sweeps : kFp64SweepCap;
   const int sw64 = jacobi_svd<double>(g, p, q, p, track_v ? v : nullptr, q, cap64, &sh.flag,
                                       false, 1.0, floor64 * floor64);
