@@ -348,6 +348,18 @@ int make_plan(clr_ctx_t ctx, int nI, int nJ, int nK, Plan* p) {
 
 int grid_of(clr_ctx_t ctx, int per_sm) { return std::max(1, ctx->n_sm * per_sm); }
 
+// Device address of page-locked (pinned or registered) host memory, or null for pageable
+// memory: kernels may then read or write it directly.
+const double* host_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (at.type != cudaMemoryTypeHost || !at.devicePointer) return nullptr;
+  return (const double*)at.devicePointer;
+}
+
 int max_cluster(clr_mat_t m) {
   int c = 0;
   for (int v : m->row_sizes) c = std::max(c, v);
@@ -558,7 +570,18 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
   cudaStream_t s = as_stream(stream);
   const double* src = a;
   DevBuf& staging = ctx->upload;
-  if (a_on_host) {
+  // Page-locked host input read once (the dense path): the layout kernel reads it in place
+  // through the host-device link (on Grace-Blackwell, NVLink-C2C), with no staging copy.  The
+  // SVD path reads each block many times and stages it in device memory first.
+  bool direct = false;
+  if (a_on_host && eps_lr == 0.0) {
+    const double* dp = host_device_ptr(a);
+    if (dp) {
+      src = dp;
+      direct = true;
+    }
+  }
+  if (a_on_host && !direct) {
     const size_t bytes = (size_t)m->n_rows * m->n_cols * sizeof(double);
     cudaError_t e = staging.ensure(bytes);
     if (e == cudaSuccess)
@@ -686,6 +709,14 @@ extern "C" int clr_mat_to_dense(clr_ctx_t ctx, clr_mat_t m, double* out, int64_t
   if (!out_on_host) {
     launch_pool_to_rowmajor(m->view(), m->d_row_idx, m->d_col_idx, out, ldo, s);
     CLR_CHECK_LAUNCH("to_dense");
+    return CLR_OK;
+  }
+  if (double* dp = const_cast<double*>(host_device_ptr(out))) {
+    // page-locked output: written in place through the host-device link
+    launch_pool_to_rowmajor(m->view(), m->d_row_idx, m->d_col_idx, dp, ldo, s);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "to_dense");
     return CLR_OK;
   }
   DevBuf& tmp = ctx->upload;
