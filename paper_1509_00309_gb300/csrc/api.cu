@@ -159,7 +159,15 @@ struct clr_ctx_s {
   PlanCounters last_counters;
   // profiling: per-product phase events
   bool prof_on = false;
-  std::vector<std::pair<cudaEvent_t, int>> prof_events;  // (event, phase that ENDS here)
+  struct ProfEvent {
+    cudaEvent_t e;
+    int phase;       // the phase that ENDS here
+    cudaStream_t s;  // phases are timed between consecutive events of the same stream
+  };
+  std::vector<ProfEvent> prof_events;
+  // NS runs its two independent products of an iteration concurrently on a side stream
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<cudaEvent_t> event_pool;
   clr_profile prof;
   // NS snapshot of one iteration: X, T, Y, Z (opts.ns_snapshot_iter)
@@ -348,6 +356,29 @@ int make_plan(clr_ctx_t ctx, int nI, int nJ, int nK, Plan* p) {
 
 int grid_of(clr_ctx_t ctx, int per_sm) { return std::max(1, ctx->n_sm * per_sm); }
 
+// A side stream (and a second workspace set) ordered after `s`: work issued on ctx->side
+// between fork_side and join_side runs concurrently with work issued on `s`.
+int fork_side(clr_ctx_t ctx, cudaStream_t s) {
+  if (ctx->wsets.size() < 2) ctx->wsets.emplace_back(new WorkSet);
+  if (!ctx->side && cudaStreamCreateWithFlags(&ctx->side, cudaStreamNonBlocking) != cudaSuccess)
+    return CLR_ECUDA;
+  if (!ctx->ev_fork && cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess)
+    return CLR_ECUDA;
+  if (!ctx->ev_join && cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return CLR_ECUDA;
+  if (cudaEventRecord(ctx->ev_fork, s) != cudaSuccess ||
+      cudaStreamWaitEvent(ctx->side, ctx->ev_fork, 0) != cudaSuccess)
+    return CLR_ECUDA;
+  return CLR_OK;
+}
+
+int join_side(clr_ctx_t ctx, cudaStream_t s) {
+  if (cudaEventRecord(ctx->ev_join, ctx->side) != cudaSuccess ||
+      cudaStreamWaitEvent(s, ctx->ev_join, 0) != cudaSuccess)
+    return CLR_ECUDA;
+  return CLR_OK;
+}
+
 // Device address of page-locked (pinned or registered) host memory, or null for pageable
 // memory: kernels may then read or write it directly.
 const double* host_device_ptr(const void* p) {
@@ -385,7 +416,7 @@ void prof_mark(clr_ctx_t ctx, cudaStream_t s, int phase) {
     return;
   }
   cudaEventRecord(e, s);
-  ctx->prof_events.push_back({e, phase});
+  ctx->prof_events.push_back({e, phase, s});
 }
 
 void prof_launches(clr_ctx_t ctx, int n) {
@@ -489,7 +520,10 @@ extern "C" int clr_create(clr_ctx_t* out, int device, const clr_opts* opts) {
 extern "C" int clr_destroy(clr_ctx_t ctx) {
   if (!ctx) return CLR_EINVAL;
   cudaSetDevice(ctx->device);
-  for (auto& pe : ctx->prof_events) cudaEventDestroy(pe.first);
+  for (auto& pe : ctx->prof_events) cudaEventDestroy(pe.e);
+  if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
   for (auto& w : ctx->wsets) w->release();
   for (clr_mat_t& m : ctx->snap) {
@@ -978,7 +1012,7 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
 extern "C" int clr_profile_enable(clr_ctx_t ctx, int on) {
   if (!ctx) return CLR_EINVAL;
   cudaSetDevice(ctx->device);
-  for (auto& pe : ctx->prof_events) ctx->event_pool.push_back(pe.first);
+  for (auto& pe : ctx->prof_events) ctx->event_pool.push_back(pe.e);
   ctx->prof_events.clear();
   std::memset(&ctx->prof, 0, sizeof(ctx->prof));
   ctx->prof_on = on != 0;
@@ -993,23 +1027,24 @@ extern "C" int clr_profile_read(clr_ctx_t ctx, clr_profile* out) {
   if (!ctx || !out) return CLR_EINVAL;
   cudaSetDevice(ctx->device);
   if (!ctx->prof_events.empty()) {
-    CLR_CUDA(cudaEventSynchronize(ctx->prof_events.back().first));
-    cudaEvent_t prev = nullptr;
+    CLR_CUDA(cudaDeviceSynchronize());
+    std::map<cudaStream_t, cudaEvent_t> prev;  // last event per stream
     for (auto& pe : ctx->prof_events) {
-      if (pe.second != PH_START && prev) {
+      auto it = prev.find(pe.s);
+      if (pe.phase != PH_START && it != prev.end()) {
         float ms = 0.f;
-        CLR_CUDA(cudaEventElapsedTime(&ms, prev, pe.first));
-        double* slot = pe.second == PH_PLAN ? &ctx->prof.ms_plan
-                     : pe.second == PH_STAGE ? &ctx->prof.ms_stage
-                     : pe.second == PH_DENSE ? &ctx->prof.ms_dense
-                     : pe.second == PH_LOWRANK ? &ctx->prof.ms_lowrank
-                     : pe.second == PH_COMPRESS ? &ctx->prof.ms_compress
+        CLR_CUDA(cudaEventElapsedTime(&ms, it->second, pe.e));
+        double* slot = pe.phase == PH_PLAN ? &ctx->prof.ms_plan
+                     : pe.phase == PH_STAGE ? &ctx->prof.ms_stage
+                     : pe.phase == PH_DENSE ? &ctx->prof.ms_dense
+                     : pe.phase == PH_LOWRANK ? &ctx->prof.ms_lowrank
+                     : pe.phase == PH_COMPRESS ? &ctx->prof.ms_compress
                      : &ctx->prof.ms_finalize;
         *slot += ms;
       }
-      prev = pe.first;
+      prev[pe.s] = pe.e;
     }
-    for (auto& pe : ctx->prof_events) ctx->event_pool.push_back(pe.first);
+    for (auto& pe : ctx->prof_events) ctx->event_pool.push_back(pe.e);
     ctx->prof_events.clear();
   }
   if (ctx->jstats.p) {
@@ -1301,10 +1336,19 @@ extern "C" int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t* z_out,
     if (st) break;
     st = clr_lincomb(ctx, -10.0 / 8.0, X, 3.0 / 8.0, X2, 15.0 / 8.0, T, s);
     if (st) break;
-    st = multiply_into(ctx, Z, T, Zn, 1.0, tn, nullptr, s);
+    // Z T and T Y are independent: T Y runs on the side stream with the second workspace set,
+    // so that the SMs one product's longest tiles leave idle take the other's work
+    st = fork_side(ctx, s);
     if (st) break;
-    st = multiply_into(ctx, T, Y, Yn, 1.0, tn, nullptr, s);
-    if (st) break;
+    {
+      WorkSet* saved = ctx->cur;
+      ctx->cur = ctx->wsets[1].get();
+      st = multiply_into(ctx, T, Y, Yn, 1.0, tn, nullptr, ctx->side);
+      ctx->cur = saved;
+    }
+    if (!st) st = multiply_into(ctx, Z, T, Zn, 1.0, tn, nullptr, s);
+    const int sj = join_side(ctx, s);
+    if (st || (st = sj)) break;
     std::swap(Z, Zn);
     std::swap(Y, Yn);
     ++it;
