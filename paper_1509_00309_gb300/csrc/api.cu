@@ -886,7 +886,7 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
   launch_split_stage(av, idx_m, idx_k, ctx->cur->panels_a.p, terms, M_pad, K_pad, 1, s);
   launch_split_stage(bv, idx_k, idx_n, ctx->cur->panels_b.p, terms, N_pad, K_pad, 0, s);
   CLR_CHECK_LAUNCH("split staging");
-  prof_launches(ctx, 2);
+  prof_launches(ctx, 4);  // dense and low-rank passes for both operands
   prof_mark(ctx, s, PH_STAGE);
   SplitGemmArgs g;
   g.A = &av;

@@ -1,10 +1,10 @@
 // Split-precision staging: the dense blocks of an operand are written as bf16 term panels for
 // the tensor-core products (the FP64 value a is split as a = a_0 + a_1 (+ a_2) + residual with
 // a_0 = bf16(a), a_1 = bf16(a - a_0), a_2 = bf16(a - a_0 - a_1); every difference is exact in
-// FP64).  Low-rank blocks are written as their reconstruction X W^T and zero blocks as zeros,
-// so a dense GEMM over the panels computes the whole sum sum_K A_IK B_KJ of the C tiles it
-// serves (route DENSE or DACC_G); low-rank C tiles (route QR) keep the factorised products of
-// Section 4.1.
+// FP64).  The dense pass writes dense blocks and zeros elsewhere; a second pass writes each
+// low-rank block as its reconstruction X W^T, so a dense GEMM over the panels computes the whole
+// sum sum_K A_IK B_KJ of the C tiles it serves (route DENSE or DACC_G), while low-rank C tiles
+// (route QR) keep the factorised products of Section 4.1.
 //
 // Panel layout (K-major for the MMA): for A, panel[t][i][k] = A(i, k), rows_pad x cols_pad;
 // for B, panel[t][j][k] = B(k, j).  Padding is zero.
@@ -146,22 +146,6 @@ __device__ __forceinline__ void split_bf16(double x, unsigned short (&out)[TERMS
   }
 }
 
-// Entry (i, j) of the low-rank block (R, Cc) of M in FP64: its reconstruction
-// sum_t X(i, t) W(j, t) (so dense C tiles take their low-rank contributions on the tensor cores
-// too).  Dense and zero blocks are read directly by the callers.
-__device__ __noinline__ double lr_value(const MatView& M, int R, int Cc, int64_t i, int64_t j) {
-  const int64_t t = (int64_t)R * M.nc + Cc;
-  const int mR = M.row_off[R + 1] - M.row_off[R];
-  const int nC = M.col_off[Cc + 1] - M.col_off[Cc];
-  const int r = M.rank[t];
-  const double* slot = M.pool + (int64_t)M.row_off[R] * M.n_cols + (int64_t)mR * M.col_off[Cc];
-  const double* x = slot + i;
-  const double* w = slot + (int64_t)mR * r + j;
-  double v = 0.0;
-  for (int q = 0; q < r; ++q) v = fma(x[(int64_t)q * mR], w[(int64_t)q * nC], v);
-  return v;
-}
-
 // A panel: one CTA converts a 32 (rows) x 128 (k) tile.  The source block-row panels are
 // column-major (consecutive rows contiguous), the panel is row-major (consecutive k
 // contiguous), so the tile goes through shared memory; each thread then packs 4 consecutive
@@ -191,14 +175,7 @@ __global__ void __launch_bounds__(256) split_stage_a_kernel(MatView M, const int
   for (int cc = ty; cc < kTk; cc += 8) {
     const int64_t c = k0 + cc;
     double v = 0.0;
-    if (rin && c < M.n_cols) {
-      const int Cc = col_idx[c];
-      const int kind = kind_row[Cc];
-      if (kind == CLR_KIND_DENSE)
-        v = M.pool[rbase + c * mR];
-      else if (kind == CLR_KIND_LR)
-        v = lr_value(M, R, Cc, r - M.row_off[R], c - M.col_off[Cc]);
-    }
+    if (rin && c < M.n_cols && kind_row[col_idx[c]] == CLR_KIND_DENSE) v = M.pool[rbase + c * mR];
     tile[tx][cc] = v;
   }
   __syncthreads();
@@ -241,10 +218,9 @@ __global__ void __launch_bounds__(256) split_stage_b_kernel(MatView M, const int
     const int Cc = col_idx[j];
     const int R0 = row_idx[k];
     const int end0 = M.row_off[R0 + 1];
-    const int kind0 = M.kind[R0 * M.nc + Cc];
-    if (k + 3 < end0 && kind0 != CLR_KIND_LR) {
-      // the 4 elements lie in one dense or zero block: contiguous source
-      if (kind0 == CLR_KIND_DENSE) {
+    if (k + 3 < end0) {
+      // the 4 elements lie in one block: one kind lookup, contiguous source
+      if (M.kind[R0 * M.nc + Cc] == CLR_KIND_DENSE) {
         const int mR = end0 - M.row_off[R0];
         const double* src = M.pool + (int64_t)M.row_off[R0] * M.n_cols + (k - M.row_off[R0]) + j * mR;
 #pragma unroll
@@ -262,12 +238,9 @@ __global__ void __launch_bounds__(256) split_stage_b_kernel(MatView M, const int
         double v = 0.0;
         if (kk < M.n_rows) {
           const int R = row_idx[kk];
-          const int kind = M.kind[R * M.nc + Cc];
-          if (kind == CLR_KIND_DENSE) {
+          if (M.kind[R * M.nc + Cc] == CLR_KIND_DENSE) {
             const int mR = M.row_off[R + 1] - M.row_off[R];
             v = M.pool[(int64_t)M.row_off[R] * M.n_cols + (kk - M.row_off[R]) + j * mR];
-          } else if (kind == CLR_KIND_LR) {
-            v = lr_value(M, R, Cc, kk - M.row_off[R], j - M.col_off[Cc]);
           }
         }
         unsigned short b[TERMS];
@@ -281,6 +254,36 @@ __global__ void __launch_bounds__(256) split_stage_b_kernel(MatView M, const int
 #pragma unroll
   for (int t = 0; t < TERMS; ++t)
     *reinterpret_cast<unsigned long long*>(panels + t * plane + j * cols_pad + k) = packed[t];
+}
+
+// Low-rank blocks into the panels: one CTA per block of M (blocks of another kind return at
+// once), entry (i, j) = sum_t X(i, t) W(j, t) in FP64, then split as the dense pass does.
+// a_mode: panel[t][row][k] = A(row, k); else panel[t][col][k] = B(k, col).
+template <int TERMS>
+__global__ void __launch_bounds__(256) split_stage_lr_kernel(MatView M, unsigned short* panels,
+                                                             int64_t rows_pad, int64_t cols_pad,
+                                                             int a_mode) {
+  const int b = blockIdx.x;
+  if (M.kind[b] != CLR_KIND_LR) return;
+  const int R = b / M.nc, Cc = b % M.nc;
+  const int mR = M.row_off[R + 1] - M.row_off[R];
+  const int nC = M.col_off[Cc + 1] - M.col_off[Cc];
+  const int r = M.rank[b];
+  const double* x = M.pool + (int64_t)M.row_off[R] * M.n_cols + (int64_t)mR * M.col_off[Cc];
+  const double* w = x + (int64_t)mR * r;
+  const int64_t plane = rows_pad * cols_pad;
+  for (int e = threadIdx.x; e < mR * nC; e += blockDim.x) {
+    const int i = a_mode ? e / nC : e % mR;  // consecutive threads along the panel's k
+    const int j = a_mode ? e % nC : e / mR;
+    double v = 0.0;
+    for (int q = 0; q < r; ++q) v = fma(x[i + (int64_t)q * mR], w[j + (int64_t)q * nC], v);
+    unsigned short t[TERMS];
+    split_bf16<TERMS>(v, t);
+    const int64_t row = M.row_off[R] + i, col = M.col_off[Cc] + j;
+    const int64_t off = a_mode ? row * cols_pad + col : col * cols_pad + row;
+#pragma unroll
+    for (int k = 0; k < TERMS; ++k) panels[k * plane + off] = t[k];
+  }
 }
 
 void launch_split_stage(const MatView& M, const int* row_idx, const int* col_idx, void* panels,
@@ -300,6 +303,11 @@ void launch_split_stage(const MatView& M, const int* row_idx, const int* col_idx
     else
       split_stage_b_kernel<3><<<n, 256, 0, st>>>(M, row_idx, col_idx, pn, rows_pad, cols_pad);
   }
+  const unsigned nb = (unsigned)(M.nr * M.nc);
+  if (terms == 2)
+    split_stage_lr_kernel<2><<<nb, 256, 0, st>>>(M, pn, rows_pad, cols_pad, a_mode);
+  else
+    split_stage_lr_kernel<3><<<nb, 256, 0, st>>>(M, pn, rows_pad, cols_pad, a_mode);
 }
 
 }  // namespace clr
