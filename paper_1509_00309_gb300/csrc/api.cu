@@ -391,12 +391,6 @@ const double* host_device_ptr(const void* p) {
   return (const double*)at.devicePointer;
 }
 
-int max_cluster(clr_mat_t m) {
-  int c = 0;
-  for (int v : m->row_sizes) c = std::max(c, v);
-  for (int v : m->col_sizes) c = std::max(c, v);
-  return c;
-}
 
 // SVD counters while profiling (not inside a graph capture), else null
 unsigned long long* jst(clr_ctx_t ctx) {
@@ -666,7 +660,7 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
       return cuda_fail(ctx, e, "from_dense order");
     }
     launch_compress_dense(m->view(), nullptr, nullptr, (const int*)ctx->cur->order.p, src, lda,
-                          (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p, max_cluster(m),
+                          (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p,
                           eps_lr, drop_norm, 0, ctx->opts.build_rrqr ? 1 : 0,
                           ctx->opts.jacobi_max_sweeps, grid_of(ctx, 2), &pc->err, &pc->sched[2],
                           jst(ctx), s);
@@ -969,10 +963,10 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   prof_launches(ctx, 1);
   prof_mark(ctx, s, PH_LOWRANK);
   launch_compress_qr(cv, p.l_qr_s, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p,
-                     (double*)ctx->cur->scratch.p, max_cluster(c), eps_lr, o.jacobi_max_sweeps,
+                     (double*)ctx->cur->scratch.p, eps_lr, o.jacobi_max_sweeps,
                      lr_grid, &p.counters->err, &p.counters->sched[1], jst(ctx), s);
   launch_compress_dense(cv, p.l_dcomp_s, &p.counters->n_dcomp, nullptr, nullptr, 0,
-                        (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p, max_cluster(c),
+                        (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p,
                         eps_lr, 0.0, 0, 0, o.jacobi_max_sweeps, lr_grid, &p.counters->err,
                         &p.counters->sched[2], jst(ctx), s);
   CLR_CHECK_LAUNCH("recompression");
@@ -1114,11 +1108,11 @@ extern "C" int clr_lincomb(clr_ctx_t ctx, double a, clr_mat_t x, double b, clr_m
   MatView xv = x->view(), yv = y->view(), ov = out->view();
   launch_lincomb_plan(a, xv, b, yv, diag, ov, p, (double*)ctx->cur->ws.p, o.recompress_dense, s);
   launch_compress_qr(ov, p.l_qr_s, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p,
-                     (double*)ctx->cur->scratch.p, max_cluster(out), o.eps_lr,
+                     (double*)ctx->cur->scratch.p, o.eps_lr,
                      o.jacobi_max_sweeps, grid, &p.counters->err, &p.counters->sched[1],
                      jst(ctx), s);
   launch_compress_dense(ov, p.l_dcomp_s, &p.counters->n_dcomp, nullptr, nullptr, 0,
-                        (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p, max_cluster(out),
+                        (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p,
                         o.eps_lr, 0.0, 0, 0, o.jacobi_max_sweeps, grid, &p.counters->err,
                         &p.counters->sched[2], jst(ctx), s);
   CLR_CHECK_LAUNCH("lincomb");

@@ -123,11 +123,10 @@ void launch_lr_products(const MatView& A, const MatView& B, const MatView& C, co
 // svd_scratch: grid x kSvdScratchPerCta doubles (FP32 working copies and an FP64 q x q factor
 // of the mixed-precision SVD).
 constexpr int64_t kSvdScratchPerCta = (int64_t)2 * CLR_MAX_CLUSTER * CLR_MAX_CLUSTER;
-// max_cluster: the largest row or column cluster of C (sizes the shared-memory request).
 // sched: a zeroed work counter (dynamic tile distribution).
 void launch_compress_qr(const MatView& C, const int* list, const int* count, const int* rsum,
-                        double* ws, double* svd_scratch, int max_cluster, double eps,
-                        int max_sweeps, int grid, int* err, int* sched,
+                        double* ws, double* svd_scratch, double eps, int max_sweeps, int grid,
+                        int* err, int* sched,
                         unsigned long long* jstats, cudaStream_t st);
 // Dense truncated SVD of blocks listed in `list` (count on device).  The source of block b is
 // either the matrix's own slot (src == nullptr) or a row-major dense matrix src with leading
@@ -137,7 +136,7 @@ void launch_compress_qr(const MatView& C, const int* list, const int* count, con
 // rrqr: truncate by rank-revealing QR instead of the SVD.
 void launch_compress_dense(const MatView& C, const int* list, const int* count,
                            const int* order, const double* src, int64_t lds, double* ws,
-                           double* svd_scratch, int max_cluster, double eps, double drop_norm,
+                           double* svd_scratch, double eps, double drop_norm,
                            int dense_only, int rrqr, int max_sweeps, int grid, int* err,
                            int* sched, unsigned long long* jstats, cudaStream_t st);
 void launch_block_norms(const MatView& M, cudaStream_t st);

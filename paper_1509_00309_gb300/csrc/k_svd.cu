@@ -15,8 +15,7 @@
 //                          (mixed FP32/FP64 stages, svd_mixed);
 //   rank-revealing QR      the paper's construction for building from dense (option).
 // FP64 working arrays live in the tile's workspace slot (2 m n doubles per tile, enough for
-// either route); the FP32 copies of the mixed-precision SVD in shared memory where they fit,
-// else in a per-CTA scratch.
+// either route); the FP32 copies of the mixed-precision SVD in a per-CTA scratch (L1-cached).
 #include <cfloat>
 #include <mutex>
 
@@ -536,8 +535,7 @@ __device__ void right_multiply_fp64(double* m, int rows, int64_t ldm, int q, con
 // Pairs whose inner product is below the noise floor are not rotated: p u ||A||_F in FP32 on A,
 // and max(p u ||A||_F, 1e-3 eps) on G (columns that small cannot move a truncation at eps).
 // On return g = U S in FP64, and v the right factor when sh.v_tracked (else workspace).  sc:
-// kSvdScratchPerCta doubles; sm32:
-// sm_cap floats of shared memory for the FP32 copies (used where they fit).
+// kSvdScratchPerCta doubles.
 //
 // Certified dense exit (dense_h >= 0): the block is stored dense when its eps-rank exceeds
 // dense_h, i.e. when the singular-value tail sqrt(sum_{i >= dense_h} s_i^2) exceeds eps.  After
@@ -548,12 +546,14 @@ __device__ void right_multiply_fp64(double* m, int rows, int64_t ldm, int q, con
 // noise floor).  So tail(A) >= tail(c) - sqrt(q - dense_h) delta, and when that exceeds eps the
 // later stages could only confirm "dense": they are skipped and the function returns 1.
 __device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, double* sc,
-                         float* sm32, int sm_cap, int max_sweeps, double eps, int dense_h,
+                         int max_sweeps, double eps, int dense_h,
                          double fro, SvdShared& sh, unsigned long long* jstats) {
-  // FP32 copies in shared memory where they fit (sm_cap floats), else in the scratch
+  // FP32 copies in the per-CTA scratch: the kernels run with the largest L1 carveout, which
+  // measured as fast as holding the copies in shared memory and gives the 256-column tiles
+  // (copies of 512 KB) the most cache
   const int64_t pq = (int64_t)p * q;
-  float* g32 = pq <= sm_cap ? sm32 : reinterpret_cast<float*>(sc);
-  float* v32 = pq + (int64_t)q * q <= sm_cap ? sm32 + pq : reinterpret_cast<float*>(sc) + pq;
+  float* g32 = reinterpret_cast<float*>(sc);
+  float* v32 = g32 + pq;
   double* v2 = sc + (int64_t)CLR_MAX_CLUSTER * CLR_MAX_CLUSTER;  // after p q + q^2 floats
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
   for (int e = threadIdx.x; e < p * q; e += kThreads) g32[e] = (float)a.at(e % p, e / p);
@@ -652,12 +652,11 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
                                                                const int* count,
                                                                const int* rsum, double* ws,
                                                                double* svd_scratch,
-                                                               int sm_cap, double eps,
-                                                               int max_sweeps, int* sched,
+                                                               double eps, int max_sweeps,
+                                                               int* sched,
                                                                unsigned long long* jstats) {
   __shared__ SvdShared sh;
   __shared__ int sh_next;
-  extern __shared__ float dyn32[];
   double* sc = svd_scratch + (int64_t)blockIdx.x * kSvdScratchPerCta;
   const int n_items = *count;
   for (int it = next_item(sched, &sh_next); it < n_items; it = next_item(sched, &sh_next)) {
@@ -690,7 +689,7 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
       for (int e = threadIdx.x; e < R * R; e += kThreads) part = fma(M[e], M[e], part);
       const double mfro = sqrt(block_sum(part, sh.red));
       SrcView mv{M, 1, R, false};
-      svd_mixed(mv, R, R, G, V, sc, dyn32, sm_cap, max_sweeps, eps, -1, mfro, sh, jstats);
+      svd_mixed(mv, R, R, G, V, sc, max_sweeps, eps, -1, mfro, sh, jstats);
     }
     sort_and_truncate(G, R, R, R, eps, sh);
     const int r = sh.rank;
@@ -734,53 +733,34 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
   }
 }
 
-// Launch shape of a recompression kernel: shared memory for the FP32 copies of the largest
-// SVD it may run (need_floats), capped by the opt-in limit, and as many CTAs per SM as that
-// leaves room for (at most 2), within the caller's grid (the scratch is sized for it).
-struct SvdLaunchCfg {
-  int grid;
-  size_t dyn;
-  int cap;
-};
-
+// Launch shape of a recompression kernel: one CTA per SM (512 threads x 128 registers fill the
+// register file) within the caller's grid (the scratch is sized for it), with the shared memory
+// carveout at its minimum so that L1 caches the FP32 working copies.
 template <typename K>
-SvdLaunchCfg svd_launch_cfg(K kernel, int64_t need_floats, int grid_max, bool* attr_done) {
+int svd_launch_grid(K kernel, int grid_max, bool* attr_done) {
   int dev = 0;
   cudaGetDevice(&dev);
-  int n_sm = 1, optin = 0, per_sm = 0;
+  int n_sm = 1;
   cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
-  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-  cudaFuncAttributes fa;
-  cudaFuncGetAttributes(&fa, kernel);
-  const int64_t avail = (int64_t)optin - (int64_t)fa.sharedSizeBytes;
-  int64_t want = need_floats * (int64_t)sizeof(float);
-  if (want > avail) want = avail;
-  if (want < 0) want = 0;
   // set once per device (outside any stream capture the first time a product runs)
   if (dev >= 0 && dev < 64 && !attr_done[dev]) {
-    cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)avail);
+    cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout, 0);
     attr_done[dev] = true;
   }
-  const int64_t per_cta = want + (int64_t)fa.sharedSizeBytes + 1024;
-  int ctas = per_cta > 0 ? (int)(per_sm / per_cta) : 2;
-  ctas = ctas < 1 ? 1 : (ctas > 2 ? 2 : ctas);
-  int grid = n_sm * ctas;
+  int grid = n_sm;
   if (grid > grid_max) grid = grid_max;
-  if (grid < 1) grid = 1;
-  return {grid, (size_t)want, (int)(want / (int64_t)sizeof(float))};
+  return grid < 1 ? 1 : grid;
 }
 
 void launch_compress_qr(const MatView& C, const int* list, const int* count, const int* rsum,
-                        double* ws, double* svd_scratch, int max_cluster, double eps,
-                        int max_sweeps, int grid, int* err, int* sched,
+                        double* ws, double* svd_scratch, double eps, int max_sweeps, int grid,
+                        int* err, int* sched,
                         unsigned long long* jstats, cudaStream_t st) {
   (void)err;
   static bool attr_done[64] = {false};
-  const int64_t r = max_cluster / 2;  // core size R <= floor(min(m, n) / 2)
-  const SvdLaunchCfg cfg = svd_launch_cfg(compress_qr_kernel, 2 * r * r, grid, attr_done);
-  compress_qr_kernel<<<cfg.grid, kThreads, cfg.dyn, st>>>(C, list, count, rsum, ws, svd_scratch,
-                                                         cfg.cap, eps, max_sweeps, sched, jstats);
+  const int g = svd_launch_grid(compress_qr_kernel, grid, attr_done);
+  compress_qr_kernel<<<g, kThreads, 0, st>>>(C, list, count, rsum, ws, svd_scratch, eps,
+                                             max_sweeps, sched, jstats);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -886,11 +866,10 @@ __device__ int rrqr_block(const double* S, int64_t s_r, int64_t s_c, int m, int 
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
     MatView C, const int* list, const int* count, const int* order, const double* src,
-    int64_t lds, double* ws, double* svd_scratch, int sm_cap, double eps, double drop_norm,
+    int64_t lds, double* ws, double* svd_scratch, double eps, double drop_norm,
     int dense_only, int rrqr, int max_sweeps, int* err, int* sched, unsigned long long* jstats) {
   __shared__ SvdShared sh;
   __shared__ int sh_next;
-  extern __shared__ float dyn32[];
   double* sc = svd_scratch + (int64_t)blockIdx.x * kSvdScratchPerCta;
   const int n_items = list ? *count : C.nr * C.nc;
   for (int it = next_item(sched, &sh_next); it < n_items; it = next_item(sched, &sh_next)) {
@@ -955,8 +934,7 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
     } else if (!dense_only) {
       const SrcView view{S, s_r, s_c, tr};
       const int early_dense =
-          svd_mixed(view, p, q, G, V, sc, dyn32, sm_cap, max_sweeps, eps, q / 2, nrm, sh,
-                    jstats);
+          svd_mixed(view, p, q, G, V, sc, max_sweeps, eps, q / 2, nrm, sh, jstats);
       if (!early_dense) {
         sort_and_truncate(G, p, q, p, eps, sh);
         r = sh.rank;
@@ -1023,17 +1001,14 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
 
 void launch_compress_dense(const MatView& C, const int* list, const int* count,
                            const int* order, const double* src, int64_t lds, double* ws,
-                           double* svd_scratch, int max_cluster, double eps, double drop_norm,
+                           double* svd_scratch, double eps, double drop_norm,
                            int dense_only, int rrqr, int max_sweeps, int grid, int* err,
                            int* sched, unsigned long long* jstats, cudaStream_t st) {
   static bool attr_done[64] = {false};
-  const int64_t c = max_cluster;
-  const SvdLaunchCfg cfg =
-      svd_launch_cfg(compress_dense_kernel, dense_only ? 0 : 2 * c * c, grid, attr_done);
-  compress_dense_kernel<<<cfg.grid, kThreads, cfg.dyn, st>>>(C, list, count, order, src, lds, ws,
-                                                            svd_scratch, cfg.cap, eps, drop_norm,
-                                                            dense_only, rrqr, max_sweeps, err,
-                                                            sched, jstats);
+  const int g = svd_launch_grid(compress_dense_kernel, grid, attr_done);
+  compress_dense_kernel<<<g, kThreads, 0, st>>>(C, list, count, order, src, lds, ws, svd_scratch,
+                                                eps, drop_norm, dense_only, rrqr, max_sweeps, err,
+                                                sched, jstats);
 }
 
 // ---------------------------------------------------------------------------------------------
