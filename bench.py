@@ -347,17 +347,14 @@ def run_ours(args):
         b_h = torch.from_numpy(w.b).pin_memory()
         c_h = torch.empty((n, n), dtype=torch.float64).pin_memory()
         e2e_steps = max(1, min(args.steps, 3))
+        ctx.multiply_host_stream(a_h, b_h, c_h, w.row_sizes, n_chunks=4)   # warm-up: buffers
         torch.cuda.synchronize()
         barrier(ws)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            ha = ctx.from_dense(a_h, w.row_sizes)
-            hb = ctx.from_dense(b_h, w.row_sizes)
-            hc = ctx.multiply(ha, hb)
-            hc.to_dense(c_h)
-            ha.close()
-            hb.close()
-            hc.close()
+            # the streamed host product: A up once, B and C in 4 column chunks whose copies
+            # overlap the chunk products (clr_multiply_host_stream)
+            ctx.multiply_host_stream(a_h, b_h, c_h, w.row_sizes, n_chunks=4)
         torch.cuda.synchronize()
         el = max_over_ranks(time.perf_counter() - t0, ws)
         e2e = {"value": alg_flops * ws * e2e_steps / el / 1e12, "unit": "TFLOP/s",

@@ -116,6 +116,9 @@ _SIGNATURES = {
     "clr_profile_enable": (C.c_int, [_VP, C.c_int]),
     "clr_profile_read": (C.c_int, [_VP, C.POINTER(ClrProfile)]),
     "clr_probe_fp64_rate": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "clr_multiply_host_stream": (C.c_int, [_VP, _VP, C.c_int64, _VP, C.c_int64, _VP, C.c_int64,
+                                           C.c_int, _VP, C.c_int, _VP, C.c_int, _VP, C.c_int,
+                                           _VP]),
 }
 
 _LIB: Optional[C.CDLL] = None
@@ -367,6 +370,19 @@ class Context:
         return {"n_triples": list(s.n_triples), "flops": s.flops, "n_tiles": list(s.n_tiles),
                 "max_rank_sum": s.max_rank_sum, "precision": PREC_NAME[s.precision],
                 "n_tiles_tensor": s.n_tiles_tensor}
+
+    def multiply_host_stream(self, a, b, c, row_sizes, inner_sizes=None, col_sizes=None,
+                             n_chunks: int = 4, stream=None):
+        """C = A B for page-locked host torch tensors (row-major float64), streamed in column
+        chunks so that host-device copies overlap the products (clr_multiply_host_stream)."""
+        inner_sizes = row_sizes if inner_sizes is None else inner_sizes
+        col_sizes = inner_sizes if col_sizes is None else col_sizes
+        rs, ks, cs = _i32(row_sizes), _i32(inner_sizes), _i32(col_sizes)
+        self._check(load().clr_multiply_host_stream(
+            self.handle, _ptr(a), a.stride(0), _ptr(b), b.stride(0), _ptr(c), c.stride(0),
+            len(rs), _ptr(rs), len(ks), _ptr(ks), len(cs), _ptr(cs), int(n_chunks),
+            _stream(stream)))
+        return c
 
     def multiply_batched(self, a: Sequence[Matrix], b: Sequence[Matrix],
                          stream=None) -> List[Matrix]:

@@ -128,9 +128,16 @@ DevicePool& pool() {
 // graph run on several branches, each with its own set.
 struct WorkSet {
   DevBuf plan_ints, triples, counters, ws, scratch, panels_a, panels_b, tile_flags, order;
+  // A's bf16 panels as staged for (matrix, terms, padded sizes): reused only while a caller
+  // that guarantees A does not change (clr_multiply_host_stream) sets ctx->reuse_a
+  DevBuf host_b, host_c, host_err;  // staging of the streamed host product (per pipeline slot)
+  const void* staged_a = nullptr;
+  const void* staged_buf = nullptr;  // panels_a's allocation the staging went to
+  int staged_terms = 0;
+  int64_t staged_m = 0, staged_k = 0;
   void release() {
     for (DevBuf* b : {&plan_ints, &triples, &counters, &ws, &scratch, &panels_a, &panels_b,
-                      &tile_flags, &order})
+                      &tile_flags, &order, &host_b, &host_c, &host_err})
       b->release();
   }
 };
@@ -168,6 +175,7 @@ struct clr_ctx_s {
   // NS runs its two independent products of an iteration concurrently on a side stream
   cudaStream_t side = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool reuse_a = false;  // split products may reuse A's staged panels (see WorkSet::staged_a)
   std::vector<cudaEvent_t> event_pool;
   clr_profile prof;
   // NS snapshot of one iteration: X, T, Y, Z (opts.ns_snapshot_iter)
@@ -877,10 +885,21 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
   const int* idx_m = c->d_row_idx;
   const int* idx_n = c->d_col_idx;
   const int* idx_k = a->d_col_idx;
-  launch_split_stage(av, idx_m, idx_k, ctx->cur->panels_a.p, terms, M_pad, K_pad, 1, s);
-  launch_split_stage(bv, idx_k, idx_n, ctx->cur->panels_b.p, terms, N_pad, K_pad, 0, s);
+  WorkSet* w = ctx->cur;
+  const bool reuse = ctx->reuse_a && w->staged_a == (const void*)a && w->staged_terms == terms &&
+                     w->staged_m == M_pad && w->staged_k == K_pad &&
+                     w->staged_buf == (const void*)w->panels_a.p;
+  if (!reuse) {
+    launch_split_stage(av, idx_m, idx_k, w->panels_a.p, terms, M_pad, K_pad, 1, s);
+    w->staged_a = ctx->reuse_a ? (const void*)a : nullptr;
+    w->staged_buf = w->panels_a.p;
+    w->staged_terms = terms;
+    w->staged_m = M_pad;
+    w->staged_k = K_pad;
+  }
+  launch_split_stage(bv, idx_k, idx_n, w->panels_b.p, terms, N_pad, K_pad, 0, s);
   CLR_CHECK_LAUNCH("split staging");
-  prof_launches(ctx, 4);  // dense and low-rank passes for both operands
+  prof_launches(ctx, reuse ? 2 : 4);  // dense and low-rank passes per staged operand
   prof_mark(ctx, s, PH_STAGE);
   SplitGemmArgs g;
   g.A = &av;
@@ -1785,4 +1804,110 @@ extern "C" int clr_multiply_batched(clr_ctx_t ctx, int n, const clr_mat_t* a,
   bt->c.clear();
   clr_batch_free(ctx, bt);
   return st;
+}
+
+// =============================================================================================
+// Streamed product of page-locked host matrices
+// =============================================================================================
+extern "C" int clr_multiply_host_stream(clr_ctx_t ctx, const double* a, int64_t lda,
+                                        const double* b, int64_t ldb, double* c, int64_t ldc,
+                                        int n_rt, const int32_t* rs, int n_kt, const int32_t* ks,
+                                        int n_ct, const int32_t* cs, int n_chunks,
+                                        void* stream) {
+  if (!ctx || !a || !b || !c || !rs || !ks || !cs || n_rt < 1 || n_kt < 1 || n_ct < 1 ||
+      n_chunks < 1)
+    return CLR_EINVAL;
+  int64_t m = 0, k = 0, n = 0;
+  for (int i = 0; i < n_rt; ++i) m += rs[i];
+  for (int i = 0; i < n_kt; ++i) k += ks[i];
+  for (int i = 0; i < n_ct; ++i) n += cs[i];
+  if (lda < k || ldb < n || ldc < n) return fail(ctx, CLR_EINVAL, "leading dimension too small");
+  if (!host_device_ptr(a) || !host_device_ptr(b) || !host_device_ptr(c))
+    return fail(ctx, CLR_EINVAL, "host buffers must be page-locked");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  MatGuard g;
+  clr_mat_t A = nullptr;
+  int st = clr_mat_from_dense(ctx, a, lda, 1, n_rt, rs, n_kt, ks, 0.0, 0.0, stream, &A);
+  if (st) return st;
+  g.v.push_back(A);
+  // column chunks of whole clusters, balanced by column count
+  if (n_chunks > n_ct) n_chunks = n_ct;
+  std::vector<int> cut(1, 0);
+  int64_t acc = 0;
+  for (int j = 0; j < n_ct; ++j) {
+    acc += cs[j];
+    if ((int)cut.size() < n_chunks && acc * n_chunks >= n * (int64_t)cut.size() && j + 1 < n_ct)
+      cut.push_back(j + 1);
+  }
+  cut.push_back(n_ct);
+  const int nch = (int)cut.size() - 1;
+  int64_t nk_max = 0;
+  std::vector<int64_t> col0(nch + 1, 0);
+  for (int q = 0; q < nch; ++q) {
+    int64_t w = 0;
+    for (int j = cut[q]; j < cut[q + 1]; ++j) w += cs[j];
+    col0[q + 1] = col0[q] + w;
+    nk_max = std::max(nk_max, w);
+  }
+  // every chunk's matrices up front: alloc_mat's synchronous metadata uploads would otherwise
+  // wait for the products already in flight and serialise the pipeline
+  std::vector<clr_mat_t> bq(nch, nullptr), cq(nch, nullptr);
+  for (int q = 0; q < nch; ++q) {
+    const int nj = cut[q + 1] - cut[q];
+    if ((st = alloc_mat(ctx, n_kt, ks, nj, cs + cut[q], &bq[q]))) return st;
+    g.v.push_back(bq[q]);
+    if ((st = alloc_mat(ctx, n_rt, rs, nj, cs + cut[q], &cq[q]))) return st;
+    g.v.push_back(cq[q]);
+  }
+  if ((st = fork_side(ctx, s))) return st;
+  WorkSet* saved = ctx->cur;
+  for (int sl = 0; sl < 2; ++sl) {
+    WorkSet* w = ctx->wsets[sl].get();
+    CLR_CUDA(w->host_b.ensure((size_t)k * nk_max * sizeof(double)));
+    CLR_CUDA(w->host_c.ensure((size_t)m * nk_max * sizeof(double)));
+    CLR_CUDA(w->host_err.ensure(sizeof(int)));
+    CLR_CUDA(cudaMemsetAsync(w->host_err.p, 0, sizeof(int), sl ? ctx->side : s));
+    w->staged_a = nullptr;
+  }
+  ctx->reuse_a = true;  // A does not change during this call
+  Tuning t;
+  t.prec = choose_precision(ctx, A, A);
+  for (int q = 0; q < nch && !st; ++q) {
+    const int sl = q & 1;
+    cudaStream_t ss = sl ? ctx->side : s;
+    WorkSet* w = ctx->wsets[sl].get();
+    ctx->cur = w;
+    const int64_t nk = col0[q + 1] - col0[q];
+    clr_mat_t Bq = bq[q], Cq = cq[q];
+    // B's column chunk: copy engine host -> device, then the block layout
+    cudaError_t e = cudaMemcpy2DAsync(w->host_b.p, nk * sizeof(double), b + col0[q],
+                                      ldb * sizeof(double), nk * sizeof(double), k,
+                                      cudaMemcpyHostToDevice, ss);
+    if (e != cudaSuccess) { st = cuda_fail(ctx, e, "stream upload"); break; }
+    launch_rowmajor_to_pool(Bq->view(), Bq->d_row_idx, (const double*)w->host_b.p, nk, ss);
+    launch_block_norms_dense(Bq->view(), ss);
+    launch_dense_kinds(Bq->view(), 0.0, (int*)w->host_err.p, ss);
+    if ((st = multiply_into(ctx, A, Bq, Cq, 1.0, t, nullptr, ss))) break;
+    // C's column chunk back: layout to row-major, copy engine device -> host
+    launch_pool_to_rowmajor(Cq->view(), Cq->d_row_idx, Cq->d_col_idx, (double*)w->host_c.p, nk,
+                            ss);
+    e = cudaMemcpy2DAsync(c + col0[q], ldc * sizeof(double), w->host_c.p, nk * sizeof(double),
+                          nk * sizeof(double), m, cudaMemcpyDeviceToHost, ss);
+    if (e != cudaSuccess) { st = cuda_fail(ctx, e, "stream download"); break; }
+  }
+  const int sj = join_side(ctx, s);
+  ctx->reuse_a = false;
+  for (int sl = 0; sl < 2; ++sl) ctx->wsets[sl]->staged_a = nullptr;
+  ctx->cur = saved;
+  cudaError_t e = cudaStreamSynchronize(s);
+  if (st) return st;
+  if (sj) return sj;
+  if (e != cudaSuccess) return cuda_fail(ctx, e, "streamed product");
+  for (int sl = 0; sl < 2; ++sl) {
+    int flag = 0;
+    CLR_CUDA(cudaMemcpy(&flag, ctx->wsets[sl]->host_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return fail(ctx, CLR_EINVAL, "non-finite input in B");
+  }
+  return CLR_OK;
 }

@@ -160,3 +160,33 @@ def test_low_rank_sums_on_tensor_cores_follow_error_bound(ctx):
         assert st["n_tiles_tensor"] == (9 if want_gemm else 3)
         _check_product(ctx, a_or, b_or, eps, gc)
     ctx.set_opts(precision="bf16x3", eps_lr=1e-8)
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "fp64"])
+def test_streamed_host_product_equals_regular_product(ctx, mode):
+    # C = A B for page-locked host matrices in 3 column chunks on two streams (A's panels staged
+    # once per stream): every entry equals the regular product's, which runs the same k order
+    import torch
+    from paper_1509_00309_gb300 import clr
+    rng = np.random.default_rng(71)
+    rs, ks, cs = [130, 77, 200], [64, 190, 33, 90], [100, 60, 150, 41, 90]
+    m, k, n = sum(rs), sum(ks), sum(cs)
+    a = torch.from_numpy(rng.standard_normal((m, k))).pin_memory()
+    b = torch.from_numpy(rng.standard_normal((k, n))).pin_memory()
+    c = torch.full((m, n), np.nan, dtype=torch.float64).pin_memory()
+    ctx.set_opts(precision=mode)
+    ctx.multiply_host_stream(a, b, c, rs, ks, cs, n_chunks=3)
+    ga = ctx.from_dense(a.numpy(), rs, ks)
+    gb = ctx.from_dense(b.numpy(), ks, cs)
+    want = ctx.multiply(ga, gb).to_dense()
+    assert np.array_equal(c.numpy(), want)
+    ref = a.numpy() @ b.numpy()
+    an, bn = np.linalg.norm(a.numpy()), np.linalg.norm(b.numpy())
+    # fp64: the product tolerance at eps 1e-8; bf16x3 at K ~ 400: its ~2^-16 / sqrt(K) error
+    bound = co.product_tolerance(a.numpy(), b.numpy(), 1e-8) if mode == "fp64" else \
+        2.0 ** -16 * an * bn
+    assert np.linalg.norm(c.numpy() - ref) <= bound
+    with pytest.raises(clr.ClrError) as e:   # pageable buffers are refused
+        ctx.multiply_host_stream(torch.zeros((m, k)), b, c, rs, ks, cs)
+    assert e.value.status == clr.CLR_EINVAL
+    ctx.set_opts(precision="bf16x3")
