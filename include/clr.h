@@ -301,6 +301,13 @@ int clr_profile_read(clr_ctx_t ctx, clr_profile* out);
  * SM (the roofline of the FP64 arithmetic in recompression): *tflops = 2 x FMAs / second.
  * Synchronises the device. */
 int clr_probe_fp64_rate(int device, double* tflops);
+/* The bf16 term split of the split-precision products (the dense operands of a split product
+ * are staged this way): x = a_0 + ... + a_{terms-1} + residual with a_0 = bf16(x) and
+ * a_t = bf16(x - a_0 - ... - a_{t-1}), each rounding to nearest-even from the exact FP64
+ * difference.  x: n doubles on the device (finite); out: terms x n bf16 bit patterns on the
+ * device, term-major (out[t * n + i]).  terms: 2 (bf16x3) or 3 (bf16x6).  Runs on `stream`
+ * (a cudaStream_t, may be null), asynchronous.  Device pointers are the caller's. */
+int clr_split_bf16(const double* x, int64_t n, int terms, uint16_t* out, void* stream);
 
 /* ---- allocation-free single-block compression ---------------------------------------------
  * clr_block_compress_noalloc: the truncated SVD of one m x n block at Frobenius error eps, the

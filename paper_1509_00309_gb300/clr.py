@@ -116,6 +116,7 @@ _SIGNATURES = {
     "clr_profile_enable": (C.c_int, [_VP, C.c_int]),
     "clr_profile_read": (C.c_int, [_VP, C.POINTER(ClrProfile)]),
     "clr_probe_fp64_rate": (C.c_int, [C.c_int, C.POINTER(C.c_double)]),
+    "clr_split_bf16": (C.c_int, [_VP, C.c_int64, C.c_int, _VP, _VP]),
     "clr_multiply_host_stream": (C.c_int, [_VP, _VP, C.c_int64, _VP, C.c_int64, _VP, C.c_int64,
                                            C.c_int, _VP, C.c_int, _VP, C.c_int, _VP, C.c_int,
                                            _VP]),
@@ -468,6 +469,21 @@ def probe_fp64_rate(device: int = 0) -> float:
     if st != CLR_OK:
         raise ClrError(st, "clr_probe_fp64_rate failed")
     return out.value
+
+
+def split_bf16(x, terms: int, out=None, stream=None):
+    """bf16 term split of a contiguous CUDA float64 tensor x (clr_split_bf16): returns a
+    (terms, x.numel()) int16 tensor of bf16 bit patterns (term t of element i at [t, i])."""
+    import torch
+    if not (x.is_cuda and x.dtype == torch.float64 and x.is_contiguous()):
+        raise ClrError(CLR_EINVAL, "x must be a contiguous CUDA float64 tensor")
+    n = x.numel()
+    if out is None:
+        out = torch.empty((terms, n), dtype=torch.int16, device=x.device)
+    st = load().clr_split_bf16(_ptr(x), n, int(terms), _ptr(out), _stream(stream))
+    if st != CLR_OK:
+        raise ClrError(st, "clr_split_bf16 failed")
+    return out
 
 
 def block_compress_noalloc(block, eps: float, x_out, w_out, status, sigma_out=None,

@@ -190,3 +190,21 @@ def test_streamed_host_product_equals_regular_product(ctx, mode):
         ctx.multiply_host_stream(torch.zeros((m, k)), b, c, rs, ks, cs)
     assert e.value.status == clr.CLR_EINVAL
     ctx.set_opts(precision="bf16x3")
+
+
+@pytest.mark.parametrize("terms", [2, 3])
+def test_device_split_terms_bit_exact(ctx, terms):
+    """The device's bf16 term split (the staging kernels' paired split, with its hardware
+    bf16x2 conversion) bit for bit against the oracle's split from the bf16 format's
+    definition, on values over the whole range and the rounding edge cases."""
+    import torch
+    from paper_1509_00309_gb300 import clr
+    from tests.test_split_rounding_host import bf16_bits, cases
+    rng = np.random.default_rng(1510)
+    x = cases(rng)
+    x = np.concatenate([x, rng.permutation(x), x[:1]])   # odd count: a lone last value
+    got = clr.split_bf16(torch.from_numpy(x).cuda(), terms).cpu().numpy().view(np.uint16)
+    for t, want in enumerate(so.split_terms(x, terms)):
+        w = bf16_bits(want)
+        bad = np.nonzero(got[t] != w)[0]
+        assert bad.size == 0, (t, x[bad[:5]], got[t, bad[:5]], w[bad[:5]])
