@@ -201,12 +201,15 @@ int clr_multiply_batched(clr_ctx_t ctx, int n, const clr_mat_t* a, const clr_mat
 /* Dense product of host matrices through the CLR product, streamed: C = A B with A (m x k),
  * B (k x n) and C (m x n) row-major in page-locked host memory (leading dimensions lda, ldb,
  * ldc >= the column counts), tiled by the cluster sizes rs (rows of A and C), ks (columns of A,
- * rows of B) and cs (columns of B and C).  A is uploaded once; B and C move in n_chunks column
- * chunks of whole clusters, alternating between two streams with their own workspaces, so that
- * the copy engines' host-device transfers of one chunk overlap the products of the others (A's
- * bf16 panels are staged once per stream).  Every block is kept dense (the eps = 0 build); the
- * products use the context's precision.  Synchronises `stream` before returning.  CLR_EINVAL
- * when a buffer is not page-locked or holds non-finite values. */
+ * rows of B) and cs (columns of B and C).  A moves in two row chunks and B in n_chunks column
+ * chunks (whole clusters each), uploaded on a copy stream in the order the products need them
+ * (A_0, B_0, A_1, B_1, B_2, ...); the product of row chunk i and column chunk j starts as soon
+ * as both are on the device, on one of two streams with their own workspaces (one per row
+ * chunk, so that chunk's bf16 panels are staged once), and its tile of C goes back to the
+ * host at once: the copy engines' transfers in both directions overlap the products.  Every
+ * block is kept dense (the eps = 0 build); the products use the context's precision.
+ * Synchronises `stream` before returning.  CLR_EINVAL when a buffer is not page-locked or
+ * holds non-finite values. */
 int clr_multiply_host_stream(clr_ctx_t ctx, const double* a, int64_t lda, const double* b,
                              int64_t ldb, double* c, int64_t ldc, int n_rt, const int32_t* rs,
                              int n_kt, const int32_t* ks, int n_ct, const int32_t* cs,

@@ -174,6 +174,7 @@ struct clr_ctx_s {
   std::vector<ProfEvent> prof_events;
   // NS runs its two independent products of an iteration concurrently on a side stream
   cudaStream_t side = nullptr;
+  cudaStream_t up = nullptr;  // host-to-device uploads of the streamed host product
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool reuse_a = false;  // split products may reuse A's staged panels (see WorkSet::staged_a)
   std::vector<cudaEvent_t> event_pool;
@@ -524,6 +525,7 @@ extern "C" int clr_destroy(clr_ctx_t ctx) {
   cudaSetDevice(ctx->device);
   for (auto& pe : ctx->prof_events) cudaEventDestroy(pe.e);
   if (ctx->side) cudaStreamDestroy(ctx->side);
+  if (ctx->up) cudaStreamDestroy(ctx->up);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
@@ -1809,6 +1811,27 @@ extern "C" int clr_multiply_batched(clr_ctx_t ctx, int n, const clr_mat_t* a,
 // =============================================================================================
 // Streamed product of page-locked host matrices
 // =============================================================================================
+namespace {
+
+// Cuts n_t clusters (sizes sz) into at most `parts` runs of whole clusters with balanced
+// element counts: the returned boundaries are cluster indices, first 0, last n_t.
+std::vector<int> cluster_cuts(int n_t, const int32_t* sz, int parts) {
+  int64_t total = 0;
+  for (int i = 0; i < n_t; ++i) total += sz[i];
+  if (parts > n_t) parts = n_t;
+  std::vector<int> cut(1, 0);
+  int64_t acc = 0;
+  for (int j = 0; j < n_t; ++j) {
+    acc += sz[j];
+    if ((int)cut.size() < parts && acc * parts >= total * (int64_t)cut.size() && j + 1 < n_t)
+      cut.push_back(j + 1);
+  }
+  cut.push_back(n_t);
+  return cut;
+}
+
+}  // namespace
+
 extern "C" int clr_multiply_host_stream(clr_ctx_t ctx, const double* a, int64_t lda,
                                         const double* b, int64_t ldb, double* c, int64_t ldc,
                                         int n_rt, const int32_t* rs, int n_kt, const int32_t* ks,
@@ -1817,8 +1840,7 @@ extern "C" int clr_multiply_host_stream(clr_ctx_t ctx, const double* a, int64_t 
   if (!ctx || !a || !b || !c || !rs || !ks || !cs || n_rt < 1 || n_kt < 1 || n_ct < 1 ||
       n_chunks < 1)
     return CLR_EINVAL;
-  int64_t m = 0, k = 0, n = 0;
-  for (int i = 0; i < n_rt; ++i) m += rs[i];
+  int64_t k = 0, n = 0;
   for (int i = 0; i < n_kt; ++i) k += ks[i];
   for (int i = 0; i < n_ct; ++i) n += cs[i];
   if (lda < k || ldb < n || ldc < n) return fail(ctx, CLR_EINVAL, "leading dimension too small");
@@ -1826,76 +1848,119 @@ extern "C" int clr_multiply_host_stream(clr_ctx_t ctx, const double* a, int64_t 
     return fail(ctx, CLR_EINVAL, "host buffers must be page-locked");
   cudaSetDevice(ctx->device);
   cudaStream_t s = as_stream(stream);
+  // A in two row chunks, B and C in n_chunks column chunks (whole clusters); the product of
+  // row chunk i and column chunk j is C's tile (i, j)
+  const std::vector<int> rcut = cluster_cuts(n_rt, rs, 2), ccut = cluster_cuts(n_ct, cs, n_chunks);
+  const int nra = (int)rcut.size() - 1, ncb = (int)ccut.size() - 1;
+  std::vector<int64_t> row0(nra + 1, 0), col0(ncb + 1, 0);
+  for (int i = 0; i < nra; ++i) {
+    row0[i + 1] = row0[i];
+    for (int r = rcut[i]; r < rcut[i + 1]; ++r) row0[i + 1] += rs[r];
+  }
+  for (int j = 0; j < ncb; ++j) {
+    col0[j + 1] = col0[j];
+    for (int q = ccut[j]; q < ccut[j + 1]; ++q) col0[j + 1] += cs[q];
+  }
+  int64_t up_max = 0, c_max = 0;
+  for (int i = 0; i < nra; ++i) up_max = std::max(up_max, (row0[i + 1] - row0[i]) * k);
+  for (int j = 0; j < ncb; ++j) up_max = std::max(up_max, k * (col0[j + 1] - col0[j]));
+  for (int i = 0; i < nra; ++i)
+    for (int j = 0; j < ncb; ++j)
+      c_max = std::max(c_max, (row0[i + 1] - row0[i]) * (col0[j + 1] - col0[j]));
+  // every matrix and buffer up front: alloc_mat's synchronous metadata uploads would otherwise
+  // wait for the work already in flight and serialise the pipeline
   MatGuard g;
-  clr_mat_t A = nullptr;
-  int st = clr_mat_from_dense(ctx, a, lda, 1, n_rt, rs, n_kt, ks, 0.0, 0.0, stream, &A);
+  int st = CLR_OK;
+  std::vector<clr_mat_t> am(nra, nullptr), bm(ncb, nullptr), cm((size_t)nra * ncb, nullptr);
+  for (int i = 0; i < nra && !st; ++i) {
+    st = alloc_mat(ctx, rcut[i + 1] - rcut[i], rs + rcut[i], n_kt, ks, &am[i]);
+    if (!st) g.v.push_back(am[i]);
+  }
+  for (int j = 0; j < ncb && !st; ++j) {
+    st = alloc_mat(ctx, n_kt, ks, ccut[j + 1] - ccut[j], cs + ccut[j], &bm[j]);
+    if (!st) g.v.push_back(bm[j]);
+  }
+  for (int i = 0; i < nra && !st; ++i)
+    for (int j = 0; j < ncb && !st; ++j) {
+      clr_mat_t& m = cm[(size_t)i * ncb + j];
+      st = alloc_mat(ctx, rcut[i + 1] - rcut[i], rs + rcut[i], ccut[j + 1] - ccut[j],
+                     cs + ccut[j], &m);
+      if (!st) g.v.push_back(m);
+    }
   if (st) return st;
-  g.v.push_back(A);
-  // column chunks of whole clusters, balanced by column count
-  if (n_chunks > n_ct) n_chunks = n_ct;
-  std::vector<int> cut(1, 0);
-  int64_t acc = 0;
-  for (int j = 0; j < n_ct; ++j) {
-    acc += cs[j];
-    if ((int)cut.size() < n_chunks && acc * n_chunks >= n * (int64_t)cut.size() && j + 1 < n_ct)
-      cut.push_back(j + 1);
-  }
-  cut.push_back(n_ct);
-  const int nch = (int)cut.size() - 1;
-  int64_t nk_max = 0;
-  std::vector<int64_t> col0(nch + 1, 0);
-  for (int q = 0; q < nch; ++q) {
-    int64_t w = 0;
-    for (int j = cut[q]; j < cut[q + 1]; ++j) w += cs[j];
-    col0[q + 1] = col0[q] + w;
-    nk_max = std::max(nk_max, w);
-  }
-  // every chunk's matrices up front: alloc_mat's synchronous metadata uploads would otherwise
-  // wait for the products already in flight and serialise the pipeline
-  std::vector<clr_mat_t> bq(nch, nullptr), cq(nch, nullptr);
-  for (int q = 0; q < nch; ++q) {
-    const int nj = cut[q + 1] - cut[q];
-    if ((st = alloc_mat(ctx, n_kt, ks, nj, cs + cut[q], &bq[q]))) return st;
-    g.v.push_back(bq[q]);
-    if ((st = alloc_mat(ctx, n_rt, rs, nj, cs + cut[q], &cq[q]))) return st;
-    g.v.push_back(cq[q]);
-  }
   if ((st = fork_side(ctx, s))) return st;
-  WorkSet* saved = ctx->cur;
+  if (!ctx->up && cudaStreamCreateWithFlags(&ctx->up, cudaStreamNonBlocking) != cudaSuccess)
+    return fail(ctx, CLR_ECUDA, "upload stream");
+  CLR_CUDA(cudaStreamWaitEvent(ctx->up, ctx->ev_fork, 0));
   for (int sl = 0; sl < 2; ++sl) {
     WorkSet* w = ctx->wsets[sl].get();
-    CLR_CUDA(w->host_b.ensure((size_t)k * nk_max * sizeof(double)));
-    CLR_CUDA(w->host_c.ensure((size_t)m * nk_max * sizeof(double)));
-    CLR_CUDA(w->host_err.ensure(sizeof(int)));
-    CLR_CUDA(cudaMemsetAsync(w->host_err.p, 0, sizeof(int), sl ? ctx->side : s));
+    CLR_CUDA(w->host_c.ensure((size_t)c_max * sizeof(double)));
     w->staged_a = nullptr;
   }
-  ctx->reuse_a = true;  // A does not change during this call
-  Tuning t;
-  t.prec = choose_precision(ctx, A, A);
-  for (int q = 0; q < nch && !st; ++q) {
-    const int sl = q & 1;
-    cudaStream_t ss = sl ? ctx->side : s;
-    WorkSet* w = ctx->wsets[sl].get();
-    ctx->cur = w;
-    const int64_t nk = col0[q + 1] - col0[q];
-    clr_mat_t Bq = bq[q], Cq = cq[q];
-    // B's column chunk: copy engine host -> device, then the block layout
-    cudaError_t e = cudaMemcpy2DAsync(w->host_b.p, nk * sizeof(double), b + col0[q],
-                                      ldb * sizeof(double), nk * sizeof(double), k,
-                                      cudaMemcpyHostToDevice, ss);
-    if (e != cudaSuccess) { st = cuda_fail(ctx, e, "stream upload"); break; }
-    launch_rowmajor_to_pool(Bq->view(), Bq->d_row_idx, (const double*)w->host_b.p, nk, ss);
-    launch_block_norms_dense(Bq->view(), ss);
-    launch_dense_kinds(Bq->view(), 0.0, (int*)w->host_err.p, ss);
-    if ((st = multiply_into(ctx, A, Bq, Cq, 1.0, t, nullptr, ss))) break;
-    // C's column chunk back: layout to row-major, copy engine device -> host
-    launch_pool_to_rowmajor(Cq->view(), Cq->d_row_idx, Cq->d_col_idx, (double*)w->host_c.p, nk,
-                            ss);
-    e = cudaMemcpy2DAsync(c + col0[q], ldc * sizeof(double), w->host_c.p, nk * sizeof(double),
-                          nk * sizeof(double), m, cudaMemcpyDeviceToHost, ss);
-    if (e != cudaSuccess) { st = cuda_fail(ctx, e, "stream download"); break; }
+  WorkSet* w0 = ctx->wsets[0].get();
+  CLR_CUDA(w0->host_b.ensure((size_t)up_max * sizeof(double)));  // upload staging (stream up)
+  CLR_CUDA(w0->host_err.ensure(sizeof(int)));
+  CLR_CUDA(cudaMemsetAsync(w0->host_err.p, 0, sizeof(int), ctx->up));
+  // one event per uploaded operand chunk (A row chunks, then B column chunks)
+  std::vector<cudaEvent_t> ev(nra + ncb, nullptr);
+  struct EvGuard {
+    std::vector<cudaEvent_t>* v;
+    ~EvGuard() {
+      for (cudaEvent_t e : *v)
+        if (e) cudaEventDestroy(e);
+    }
+  } eg{&ev};
+  for (auto& e : ev)
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+      return fail(ctx, CLR_ECUDA, "events");
+  // uploads on stream up, in the order the products need them: A_0, B_0, A_1, B_1, B_2, ...
+  auto upload = [&](clr_mat_t M, const double* src, int64_t ld, int64_t rows, int64_t cols,
+                    cudaEvent_t done) -> int {
+    cudaError_t e = cudaMemcpy2DAsync(w0->host_b.p, cols * sizeof(double), src,
+                                      ld * sizeof(double), cols * sizeof(double), rows,
+                                      cudaMemcpyHostToDevice, ctx->up);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "stream upload");
+    launch_rowmajor_to_pool(M->view(), M->d_row_idx, (const double*)w0->host_b.p, cols, ctx->up);
+    launch_block_norms_dense(M->view(), ctx->up);
+    launch_dense_kinds(M->view(), 0.0, (int*)w0->host_err.p, ctx->up);
+    e = cudaEventRecord(done, ctx->up);
+    return e == cudaSuccess ? CLR_OK : cuda_fail(ctx, e, "stream upload");
+  };
+  for (int q = 0; q < std::max(nra, ncb) && !st; ++q) {
+    if (q < nra) st = upload(am[q], a + row0[q] * lda, lda, row0[q + 1] - row0[q], k, ev[q]);
+    if (!st && q < ncb)
+      st = upload(bm[q], b + col0[q], ldb, k, col0[q + 1] - col0[q], ev[nra + q]);
   }
+  WorkSet* saved = ctx->cur;
+  ctx->reuse_a = true;  // each stream keeps its row chunk of A: its bf16 panels are staged once
+  Tuning t;
+  if (!st) t.prec = choose_precision(ctx, am[0], am[0]);
+  for (int j = 0; j < ncb && !st; ++j)
+    for (int i = 0; i < nra && !st; ++i) {
+      const int sl = nra > 1 ? (i & 1) : (j & 1);
+      cudaStream_t ss = sl ? ctx->side : s;
+      WorkSet* w = ctx->wsets[sl].get();
+      ctx->cur = w;
+      cudaError_t e = cudaStreamWaitEvent(ss, ev[i], 0);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(ss, ev[nra + j], 0);
+      if (e != cudaSuccess) {
+        st = cuda_fail(ctx, e, "stream order");
+        break;
+      }
+      clr_mat_t Cq = cm[(size_t)i * ncb + j];
+      if ((st = multiply_into(ctx, am[i], bm[j], Cq, 1.0, t, nullptr, ss))) break;
+      // C's tile back: layout to row-major, copy engine device -> host
+      const int64_t nk = col0[j + 1] - col0[j];
+      launch_pool_to_rowmajor(Cq->view(), Cq->d_row_idx, Cq->d_col_idx, (double*)w->host_c.p,
+                              nk, ss);
+      e = cudaMemcpy2DAsync(c + row0[i] * ldc + col0[j], ldc * sizeof(double), w->host_c.p,
+                            nk * sizeof(double), nk * sizeof(double), row0[i + 1] - row0[i],
+                            cudaMemcpyDeviceToHost, ss);
+      if (e != cudaSuccess) st = cuda_fail(ctx, e, "stream download");
+    }
+  // join the upload and side streams back into s
+  cudaError_t ej = cudaEventRecord(ctx->ev_join, ctx->up);
+  if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s, ctx->ev_join, 0);
   const int sj = join_side(ctx, s);
   ctx->reuse_a = false;
   for (int sl = 0; sl < 2; ++sl) ctx->wsets[sl]->staged_a = nullptr;
@@ -1903,11 +1968,10 @@ extern "C" int clr_multiply_host_stream(clr_ctx_t ctx, const double* a, int64_t 
   cudaError_t e = cudaStreamSynchronize(s);
   if (st) return st;
   if (sj) return sj;
+  if (ej != cudaSuccess) return cuda_fail(ctx, ej, "streamed product");
   if (e != cudaSuccess) return cuda_fail(ctx, e, "streamed product");
-  for (int sl = 0; sl < 2; ++sl) {
-    int flag = 0;
-    CLR_CUDA(cudaMemcpy(&flag, ctx->wsets[sl]->host_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-    if (flag) return fail(ctx, CLR_EINVAL, "non-finite input in B");
-  }
+  int flag = 0;
+  CLR_CUDA(cudaMemcpy(&flag, w0->host_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+  if (flag) return fail(ctx, CLR_EINVAL, "non-finite input in A or B");
   return CLR_OK;
 }

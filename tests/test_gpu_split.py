@@ -164,8 +164,9 @@ def test_low_rank_sums_on_tensor_cores_follow_error_bound(ctx):
 
 @pytest.mark.parametrize("mode", ["bf16x3", "fp64"])
 def test_streamed_host_product_equals_regular_product(ctx, mode):
-    # C = A B for page-locked host matrices in 3 column chunks on two streams (A's panels staged
-    # once per stream): every entry equals the regular product's, which runs the same k order
+    # C = A B for page-locked host matrices, A in 2 row chunks and B in 3 column chunks, the 6
+    # tile products on two streams (each row chunk's panels staged once): every entry equals
+    # the regular product's, which runs the same k order
     import torch
     from paper_1509_00309_gb300 import clr
     rng = np.random.default_rng(71)
@@ -188,6 +189,10 @@ def test_streamed_host_product_equals_regular_product(ctx, mode):
     assert np.linalg.norm(c.numpy() - ref) <= bound
     with pytest.raises(clr.ClrError) as e:   # pageable buffers are refused
         ctx.multiply_host_stream(torch.zeros((m, k)), b, c, rs, ks, cs)
+    assert e.value.status == clr.CLR_EINVAL
+    a[m - 1, 5] = float("nan")                 # a non-finite value in A's second row chunk
+    with pytest.raises(clr.ClrError) as e:
+        ctx.multiply_host_stream(a, b, c, rs, ks, cs, n_chunks=3)
     assert e.value.status == clr.CLR_EINVAL
     ctx.set_opts(precision="bf16x3")
 
