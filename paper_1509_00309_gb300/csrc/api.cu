@@ -874,8 +874,10 @@ extern "C" int clr_matvec(clr_ctx_t ctx, clr_mat_t a, const double* x, double* y
 // =============================================================================================
 namespace {
 
+// *fused_norms: set when the dense kernel's epilogue formed the sums of squares of the
+// route-DENSE tiles (then only their square roots remain to be taken).
 int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Plan& p, int prec,
-                 cudaStream_t s) {
+                 cudaStream_t s, bool* fused_norms) {
   const int terms = prec == CLR_PREC_BF16X3 ? 2 : 3;
   const int64_t M_pad = (c->n_rows + 127) / 128 * 128;
   const int64_t N_pad = (c->n_cols + 255) / 256 * 256;
@@ -920,6 +922,13 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
   g.n_sm = ctx->n_sm;
   g.err = &p.counters->err;
   g.encode_fn = ctx->encode_fn;
+  // norms in the epilogue when the dense tiles are final (not re-tested) and the clusters are
+  // wide enough for its per-warp grouping
+  const bool fuse = !ctx->opts.recompress_dense &&
+                    *std::min_element(c->row_sizes.begin(), c->row_sizes.end()) >= 32 &&
+                    *std::min_element(c->col_sizes.begin(), c->col_sizes.end()) >= 16;
+  g.norm_sq = fuse ? c->d_norm : nullptr;
+  *fused_norms = fuse;
   std::string why;
   int st = split_gemm_dd(g, s, &why);
   if (st) return fail(ctx, st, "split GEMM: " + why);
@@ -963,6 +972,7 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   const double u_split = prec == CLR_PREC_BF16X3 ? std::ldexp(1.0, -15)
                          : prec == CLR_PREC_BF16X6 ? std::ldexp(1.0, -22) : 0.0;
   const double dacc_bound = u_split > 0.0 ? eps_lr / (16.0 * u_split) : 0.0;
+  bool fused_norms = false;
   launch_plan(av, bv, p, o.eps_sp, o.recompress_dense, dacc_bound, s);
   launch_set_route_kinds(cv, p, s);
   CLR_CHECK_LAUNCH("plan");
@@ -975,7 +985,7 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
     if (ctx->prof_on) ctx->prof.dense_launches++;
     prof_mark(ctx, s, PH_DENSE);
   } else {
-    st = run_split_dd(ctx, a, b, c, p, prec, s);
+    st = run_split_dd(ctx, a, b, c, p, prec, s, &fused_norms);
     if (st) return st;
   }
   launch_lr_products(av, bv, cv, p, (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p,
@@ -994,7 +1004,10 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   prof_launches(ctx, 2);
   prof_mark(ctx, s, PH_COMPRESS);
   if (!o.recompress_dense) {
-    launch_dense_tile_norms(cv, p, s);
+    if (fused_norms)
+      launch_sqrt_dense_norms(cv, p, s);
+    else
+      launch_dense_tile_norms(cv, p, s);
     prof_launches(ctx, 1);
   }
   if (alpha != 1.0) {

@@ -107,6 +107,8 @@ void launch_dd_fp64(const MatView& A, const MatView& B, const MatView& C, const 
                     int grid, cudaStream_t st);
 void launch_set_route_kinds(const MatView& C, const Plan& p, cudaStream_t st);
 void launch_dense_tile_norms(const MatView& C, const Plan& p, cudaStream_t st);
+// norm = sqrt(norm) of the route-DENSE tiles (their sums of squares came from the GEMM epilogue)
+void launch_sqrt_dense_norms(const MatView& C, const Plan& p, cudaStream_t st);
 // k_layout.cu
 void launch_rowmajor_to_pool(const MatView& M, const int* row_idx, const double* src,
                              int64_t lds, cudaStream_t st);
@@ -165,6 +167,10 @@ struct SplitGemmArgs {
   int n_sm;
   int* err;
   void* encode_fn;    // cuTensorMapEncodeTiled
+  // fused norms (may be null): the epilogue adds the squares of the values it writes into
+  // route-DENSE C tiles to norm_sq[I * nJ + J] (zeroed before; needs row clusters >= 32 rows
+  // and column clusters >= 16 columns)
+  double* norm_sq = nullptr;
 };
 int split_gemm_dd(const SplitGemmArgs& a, cudaStream_t st, std::string* why);
 void launch_split_stage(const MatView& M, const int* row_idx, const int* col_idx, void* panels,

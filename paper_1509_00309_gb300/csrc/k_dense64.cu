@@ -96,6 +96,7 @@ __global__ void set_route_kinds_kernel(MatView C, Plan p) {
   } else if (route == ROUTE_DENSE) {
     C.kind[t] = CLR_KIND_DENSE;
     C.rank[t] = m < n ? m : n;
+    C.norm[t] = 0.0;  // a sum of squares when the dense kernel's epilogue forms the norms
   }
 }
 
@@ -131,6 +132,18 @@ __global__ void __launch_bounds__(256) dense_tile_norms_kernel(MatView C, Plan p
 
 void launch_dense_tile_norms(const MatView& C, const Plan& p, cudaStream_t st) {
   dense_tile_norms_kernel<<<1024, 256, 0, st>>>(C, p);
+}
+
+__global__ void sqrt_dense_norms_kernel(MatView C, Plan p) {
+  const int n_items = p.counters->n_dense;
+  for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n_items; it += gridDim.x * blockDim.x) {
+    const int t = p.l_dense[it];
+    C.norm[t] = sqrt(C.norm[t]);
+  }
+}
+
+void launch_sqrt_dense_norms(const MatView& C, const Plan& p, cudaStream_t st) {
+  sqrt_dense_norms_kernel<<<64, 256, 0, st>>>(C, p);
 }
 
 }  // namespace clr

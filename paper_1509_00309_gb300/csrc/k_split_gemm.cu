@@ -192,7 +192,31 @@ struct Epi {
   const int* t_route;
   int nJ;
   int64_t n_rows, n_cols;
+  // Fused norms (may be null): sums of squares of the values written into route-DENSE C tiles,
+  // added per tile (I, J) into norm_sq[I * nJ + J].  Set only when every row cluster has >= 32
+  // rows (a warp's rows span at most two) and every column cluster >= 16 columns (a 16-column
+  // group spans at most two).
+  double* norm_sq;
 };
+
+// Adds a warp's partial sums of squares for C column cluster J: lanes whose row cluster is the
+// warp's first (I0) and the others (all in I1, at most two clusters per warp) are summed apart;
+// lane 0 adds each nonzero total to its tile.  Uniform in the warp.
+__device__ __forceinline__ void norm_flush(const Epi& epi, int I, int I0, int I1, int J,
+                                           double acc, int lane) {
+  if (J < 0) return;
+  double a = I == I0 ? acc : 0.0;
+  double b = I == I0 ? 0.0 : acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_xor_sync(0xffffffffu, a, o);
+    b += __shfl_xor_sync(0xffffffffu, b, o);
+  }
+  if (lane == 0) {
+    if (a != 0.0 && I0 >= 0) atomicAdd(&epi.norm_sq[(int64_t)I0 * epi.nJ + J], a);
+    if (b != 0.0 && I1 >= 0 && I1 != I0) atomicAdd(&epi.norm_sq[(int64_t)I1 * epi.nJ + J], b);
+  }
+}
 
 // Linear tile id -> (m block, n block), grouped along m for L2 reuse across concurrent CTAs.
 __device__ __forceinline__ void tile_coords(int id, int n_m, int n_n, int* mb, int* nb) {
@@ -206,7 +230,7 @@ __device__ __forceinline__ void tile_coords(int id, int n_m, int n_n, int* mb, i
   *nb = r / gs;
 }
 
-template <int TERMS>
+template <int TERMS, bool NORMS>
 __global__ void __launch_bounds__(THREADS, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, Epi epi, int n_m, int n_n,
@@ -386,21 +410,93 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       if (!ok) break;
       const int64_t row = (int64_t)mb * BM + rl;
-      if (row < epi.n_rows) {
-        const int I = epi.row_tile_of[row];
-        const int mI = epi.row_off[I + 1] - epi.row_off[I];
-        const int64_t rowbase = (int64_t)epi.row_off[I] * epi.n_cols + (row - epi.row_off[I]);
-        const int* route_row = epi.t_route + (int64_t)I * epi.nJ;
-        const int64_t col0 = (int64_t)nb * BN + half * 128;
+      const int64_t col0 = (int64_t)nb * BN + half * 128;
+      if constexpr (!NORMS) {
+        if (row < epi.n_rows) {
+          const int I = epi.row_tile_of[row];
+          const int mI = epi.row_off[I + 1] - epi.row_off[I];
+          const int64_t rowbase = (int64_t)epi.row_off[I] * epi.n_cols + (row - epi.row_off[I]);
+          const int* route_row = epi.t_route + (int64_t)I * epi.nJ;
 #pragma unroll
-        for (int j = 0; j < 128; ++j) {
-          const int64_t col = col0 + j;
-          if (col < epi.n_cols) {
-            const int J = epi.col_tile_of[col];
-            if (route_row[J] == ROUTE_DENSE || route_row[J] == ROUTE_DACC_G)
-              epi.pool[rowbase + col * mI] = (double)hi[j];
+          for (int j = 0; j < 128; ++j) {
+            const int64_t col = col0 + j;
+            if (col < epi.n_cols) {
+              const int J = epi.col_tile_of[col];
+              if (route_row[J] == ROUTE_DENSE || route_row[J] == ROUTE_DACC_G)
+                epi.pool[rowbase + col * mI] = (double)hi[j];
+            }
           }
         }
+      } else {
+        // the same stores, with the sums of squares of route-DENSE values per C tile: per
+        // 16-column group (its first and last column clusters Jf, Jl are uniform in the warp),
+        // one FP64 partial sum, two where the group crosses a cluster boundary
+        const bool valid = row < epi.n_rows;
+        int I = -1, mI = 1;
+        int64_t rowbase = 0;
+        const int* route_row = epi.t_route;
+        if (valid) {
+          I = epi.row_tile_of[row];
+          mI = epi.row_off[I + 1] - epi.row_off[I];
+          rowbase = (int64_t)epi.row_off[I] * epi.n_cols + (row - epi.row_off[I]);
+          route_row = epi.t_route + (int64_t)I * epi.nJ;
+        }
+        const int I0 = __shfl_sync(0xffffffffu, I, 0);
+        const int I1 = __reduce_max_sync(0xffffffffu, I);
+        double acc = 0.0;
+        int acc_j = -1;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int64_t cb = col0 + 16 * c;
+          if (cb < epi.n_cols) {
+            const int64_t ce = cb + 15 < epi.n_cols ? cb + 15 : epi.n_cols - 1;
+            const int Jf = epi.col_tile_of[cb], Jl = epi.col_tile_of[ce];
+            double sa = 0.0, sb = 0.0;
+            if (Jf == Jl) {
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) {
+                const int64_t col = cb + jj;
+                if (valid && col < epi.n_cols) {
+                  const int r = route_row[Jf];
+                  if (r == ROUTE_DENSE || r == ROUTE_DACC_G) {
+                    const double v = (double)hi[16 * c + jj];
+                    epi.pool[rowbase + col * mI] = v;
+                    if (r == ROUTE_DENSE) sa = fma(v, v, sa);
+                  }
+                }
+              }
+            } else {
+#pragma unroll
+              for (int jj = 0; jj < 16; ++jj) {
+                const int64_t col = cb + jj;
+                if (valid && col < epi.n_cols) {
+                  const int J = epi.col_tile_of[col];
+                  const int r = route_row[J];
+                  if (r == ROUTE_DENSE || r == ROUTE_DACC_G) {
+                    const double v = (double)hi[16 * c + jj];
+                    epi.pool[rowbase + col * mI] = v;
+                    if (r == ROUTE_DENSE) {
+                      if (J == Jf) sa = fma(v, v, sa);
+                      else sb = fma(v, v, sb);
+                    }
+                  }
+                }
+              }
+            }
+            if (Jf != acc_j) {
+              norm_flush(epi, I, I0, I1, acc_j, acc, lane);
+              acc = 0.0;
+              acc_j = Jf;
+            }
+            acc += sa;
+            if (Jl != Jf) {
+              norm_flush(epi, I, I0, I1, acc_j, acc, lane);
+              acc = sb;
+              acc_j = Jl;
+            }
+          }
+        }
+        norm_flush(epi, I, I0, I1, acc_j, acc, lane);
       }
     }
   }
@@ -457,7 +553,7 @@ bool encode_panel(EncodeFn fn, CUtensorMap* tm, void* base, int64_t k_pad, int64
          CUDA_SUCCESS;
 }
 
-template <int TERMS>
+template <int TERMS, bool NORMS>
 int launch_terms(const SplitGemmArgs& a, const CUtensorMap& tmA, const CUtensorMap& tmB,
                  const Epi& epi, int n_m, int n_n, int num_k, cudaStream_t st,
                  std::string* why) {
@@ -467,7 +563,7 @@ int launch_terms(const SplitGemmArgs& a, const CUtensorMap& tmA, const CUtensorM
   int dev = 0;
   cudaGetDevice(&dev);
   if (dev < 0 || dev >= 64 || !attr_done[dev]) {
-    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<TERMS>,
+    cudaError_t e = cudaFuncSetAttribute(split_gemm_kernel<TERMS, NORMS>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) {
       if (why) *why = cudaGetErrorString(e);
@@ -476,9 +572,8 @@ int launch_terms(const SplitGemmArgs& a, const CUtensorMap& tmA, const CUtensorM
     if (dev >= 0 && dev < 64) attr_done[dev] = true;
   }
   const int grid = std::max(1, std::min(a.n_sm, n_m * n_n));
-  split_gemm_kernel<TERMS><<<grid, THREADS, smem, st>>>(tmA, tmB, epi, n_m, n_n, num_k,
-                                                        (int)a.M_pad, (int)a.N_pad,
-                                                        a.tile_active, a.err);
+  split_gemm_kernel<TERMS, NORMS><<<grid, THREADS, smem, st>>>(
+      tmA, tmB, epi, n_m, n_n, num_k, (int)a.M_pad, (int)a.N_pad, a.tile_active, a.err);
   return CLR_OK;
 }
 
@@ -521,8 +616,13 @@ int split_gemm_dd(const SplitGemmArgs& a, cudaStream_t st, std::string* why) {
   epi.nJ = C.nc;
   epi.n_rows = C.n_rows;
   epi.n_cols = C.n_cols;
-  if (a.terms == 2) return launch_terms<2>(a, tmA, tmB, epi, n_m, n_n, num_k, st, why);
-  return launch_terms<3>(a, tmA, tmB, epi, n_m, n_n, num_k, st, why);
+  epi.norm_sq = a.norm_sq;
+  if (epi.norm_sq) {
+    if (a.terms == 2) return launch_terms<2, true>(a, tmA, tmB, epi, n_m, n_n, num_k, st, why);
+    return launch_terms<3, true>(a, tmA, tmB, epi, n_m, n_n, num_k, st, why);
+  }
+  if (a.terms == 2) return launch_terms<2, false>(a, tmA, tmB, epi, n_m, n_n, num_k, st, why);
+  return launch_terms<3, false>(a, tmA, tmB, epi, n_m, n_n, num_k, st, why);
 }
 
 }  // namespace clr

@@ -213,3 +213,33 @@ def test_device_split_terms_bit_exact(ctx, terms):
         w = bf16_bits(want)
         bad = np.nonzero(got[t] != w)[0]
         assert bad.size == 0, (t, x[bad[:5]], got[t, bad[:5]], w[bad[:5]])
+
+
+@pytest.mark.parametrize("mode", ["bf16x3", "bf16x6"])
+@pytest.mark.parametrize("sizes", [None, [40, 17, 200, 64, 33, 250]])
+def test_block_norms_after_split_product(ctx, dense_case, mode, sizes):
+    # The dense tiles' norms of a split product (formed in the dense kernel's epilogue when every
+    # row cluster has >= 32 rows and every column cluster >= 16, else by a separate pass) equal
+    # the norms of the stored blocks: sqrt(sum of squared block norms) = ||C||_F
+    w = dense_case
+    rs = w.row_sizes if sizes is None else sizes
+    a, b = w.a[:sum(rs), :sum(rs)], w.b[:sum(rs), :sum(rs)]
+    ctx.set_opts(precision=mode)
+    gc = ctx.multiply(ctx.from_dense(a, rs), ctx.from_dense(b, rs))
+    c = gc.to_dense()
+    assert abs(gc.info()["frob_norm"] - np.linalg.norm(c)) <= 1e-13 * np.linalg.norm(c)
+    ctx.set_opts(precision="bf16x3")
+
+
+def test_block_norms_mixed_routes_split(ctx):
+    # a product with dense and low-rank C tiles (1D chain overlap, bf16x6): the dense tiles'
+    # epilogue norms and the recompressed tiles' norms together give ||C||_F
+    w = wl.chain_overlap()
+    ctx.set_opts(precision="bf16x6", eps_lr=w.eps_lr)
+    s = ctx.from_dense(w.a, w.row_sizes, eps_lr=w.eps_lr, drop_norm=w.drop_norm)
+    gc = ctx.multiply(s, s)
+    c = gc.to_dense()
+    nb = gc.info()["n_blocks"]     # zero, dense, low rank
+    assert nb[1] > 0 and nb[2] > 0
+    assert abs(gc.info()["frob_norm"] - np.linalg.norm(c)) <= 1e-12 * np.linalg.norm(c)
+    ctx.set_opts(precision="bf16x3", eps_lr=1e-8)
