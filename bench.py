@@ -354,8 +354,8 @@ def run_ours(args):
         barrier(ws)
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
-            # the streamed host product: A up once, B and C in 4 column chunks whose copies
-            # overlap the chunk products (clr_multiply_host_stream)
+            # the streamed host product: A in 2 row chunks, B and C in 4 column chunks; the
+            # copies overlap the 8 tile products (clr_multiply_host_stream)
             ctx.multiply_host_stream(a_h, b_h, c_h, w.row_sizes, n_chunks=4)
         torch.cuda.synchronize()
         el = max_over_ranks(time.perf_counter() - t0, ws)

@@ -374,8 +374,9 @@ class Context:
 
     def multiply_host_stream(self, a, b, c, row_sizes, inner_sizes=None, col_sizes=None,
                              n_chunks: int = 4, stream=None):
-        """C = A B for page-locked host torch tensors (row-major float64), streamed in column
-        chunks so that host-device copies overlap the products (clr_multiply_host_stream)."""
+        """C = A B for page-locked host torch tensors (row-major float64), streamed: A in two
+        row chunks, B and C in n_chunks column chunks, so that host-device copies in both
+        directions overlap the tile products (clr_multiply_host_stream)."""
         inner_sizes = row_sizes if inner_sizes is None else inner_sizes
         col_sizes = inner_sizes if col_sizes is None else col_sizes
         rs, ks, cs = _i32(row_sizes), _i32(inner_sizes), _i32(col_sizes)
