@@ -26,42 +26,54 @@ __device__ __forceinline__ unsigned long long triple_flops(int kind, long long m
   return 2ull * k * ra * rb + (rb <= ra ? 2ull * m * ra * rb : 2ull * n * ra * rb);
 }
 
+// One warp per C tile (I, J), its lanes over the inner clusters K.
 // gemm_dacc_bound > 0 (split precision): a tile that would be accumulated densely in FP64
 // (ROUTE_DACC) is summed by the tensor-core GEMM instead (ROUTE_DACC_G) when its norm estimate
 // sum_K ||A_IK|| ||B_KJ|| is at most gemm_dacc_bound = eps / (16 u_split).
 __global__ void plan_count_kernel(MatView A, MatView B, Plan p, double eps_sp,
                                   double gemm_dacc_bound) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= p.nI * p.nJ) return;
-  int I = t / p.nJ, J = t % p.nJ;
-  int m = A.row_off[I + 1] - A.row_off[I];
-  int n = B.col_off[J + 1] - B.col_off[J];
+  const int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32);
+  const int lane = threadIdx.x % 32;
+  if (t >= p.nI * p.nJ) return;  // the whole warp
+  const int I = t / p.nJ, J = t % p.nJ;
+  const int m = A.row_off[I + 1] - A.row_off[I];
+  const int n = B.col_off[J + 1] - B.col_off[J];
   bool pass = true;
   double est = 0.0;
   if (eps_sp > 0.0 || gemm_dacc_bound > 0.0) {
-    for (int K = 0; K < p.nK; ++K) {
-      int ka = A.kind[I * A.nc + K], kb = B.kind[K * B.nc + J];
+    for (int K = lane; K < p.nK; K += 32) {
+      const int ka = A.kind[I * A.nc + K], kb = B.kind[K * B.nc + J];
       if (ka != CLR_KIND_ZERO && kb != CLR_KIND_ZERO)
         est += A.norm[I * A.nc + K] * B.norm[K * B.nc + J];
     }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) est += __shfl_xor_sync(0xffffffffu, est, o);
     if (eps_sp > 0.0) pass = est > eps_sp * (double)m * (double)n;
   }
   int count = 0, has_dd = 0, rsum = 0;
   unsigned long long fl = 0;
-  unsigned long long byk[4] = {0, 0, 0, 0};
+  int byk[4] = {0, 0, 0, 0};
   if (pass) {
-    for (int K = 0; K < p.nK; ++K) {
-      int ka = A.kind[I * A.nc + K], kb = B.kind[K * B.nc + J];
+    for (int K = lane; K < p.nK; K += 32) {
+      const int ka = A.kind[I * A.nc + K], kb = B.kind[K * B.nc + J];
       if (ka == CLR_KIND_ZERO || kb == CLR_KIND_ZERO) continue;
-      int kind = (ka == CLR_KIND_DENSE ? 0 : 2) + (kb == CLR_KIND_DENSE ? 0 : 1);
-      int ra = A.rank[I * A.nc + K], rb = B.rank[K * B.nc + J];
-      int k = A.col_off[K + 1] - A.col_off[K];
+      const int kind = (ka == CLR_KIND_DENSE ? 0 : 2) + (kb == CLR_KIND_DENSE ? 0 : 1);
+      const int ra = A.rank[I * A.nc + K], rb = B.rank[K * B.nc + J];
+      const int k = A.col_off[K + 1] - A.col_off[K];
       ++count;
       byk[kind]++;
       fl += triple_flops(kind, m, k, n, ra, rb);
       if (kind == T_DD) has_dd = 1; else rsum += out_rank(kind, ra, rb);
     }
   }
+  count = __reduce_add_sync(0xffffffffu, (unsigned)count);
+  rsum = __reduce_add_sync(0xffffffffu, (unsigned)rsum);
+  has_dd = __any_sync(0xffffffffu, has_dd);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) byk[q] = __reduce_add_sync(0xffffffffu, (unsigned)byk[q]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) fl += __shfl_xor_sync(0xffffffffu, fl, o);
+  if (lane != 0) return;
   int route = ROUTE_ZERO;
   if (count > 0) {
     int lim = (m < n ? m : n) / 2;
@@ -77,7 +89,7 @@ __global__ void plan_count_kernel(MatView A, MatView B, Plan p, double eps_sp,
   if (count > 0) {
     atomicAdd(&p.counters->n_triples, (unsigned long long)count);
     for (int q = 0; q < 4; ++q)
-      if (byk[q]) atomicAdd(&p.counters->by_kind[q], byk[q]);
+      if (byk[q]) atomicAdd(&p.counters->by_kind[q], (unsigned long long)byk[q]);
     atomicAdd(&p.counters->flops, fl);
     atomicAdd(&p.counters->by_mode[has_dd ? 1 : 2], 1ull);
     if (!has_dd) atomicMax(&p.counters->max_rsum, (unsigned long long)rsum);
@@ -186,26 +198,45 @@ __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(Plan p, int rec
   }
 }
 
+// One warp per C tile: its lanes take 32 inner clusters at a time; a ballot gives each
+// nonzero triple its place (K order) and a warp scan of the output ranks its first factor
+// column in the tile's concatenation.
 __global__ void plan_fill_kernel(MatView A, MatView B, Plan p) {
-  int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= p.nI * p.nJ) return;
-  int count = p.t_count[t];
-  if (count == 0) return;
-  int I = t / p.nJ, J = t % p.nJ;
+  const int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32);
+  const int lane = threadIdx.x % 32;
+  if (t >= p.nI * p.nJ) return;  // the whole warp
+  if (p.t_count[t] == 0) return;
+  const int I = t / p.nJ, J = t % p.nJ;
   int64_t pos = p.t_start[t];
   int col = 0;
-  for (int K = 0; K < p.nK; ++K) {
-    int ka = A.kind[I * A.nc + K], kb = B.kind[K * B.nc + J];
-    if (ka == CLR_KIND_ZERO || kb == CLR_KIND_ZERO) continue;
-    int kind = (ka == CLR_KIND_DENSE ? 0 : 2) + (kb == CLR_KIND_DENSE ? 0 : 1);
-    Triple tr;
-    tr.tile = t;
-    tr.k = K;
-    tr.kind = kind;
-    tr.col = col;
-    col += out_rank(kind, A.rank[I * A.nc + K], B.rank[K * B.nc + J]);
-    if (pos < p.max_triples) p.triples[pos] = tr; else atomicExch(&p.counters->err, 2);
-    ++pos;
+  for (int K0 = 0; K0 < p.nK; K0 += 32) {
+    const int K = K0 + lane;
+    int ka = CLR_KIND_ZERO, kb = CLR_KIND_ZERO;
+    if (K < p.nK) {
+      ka = A.kind[I * A.nc + K];
+      kb = B.kind[K * B.nc + J];
+    }
+    const bool on = ka != CLR_KIND_ZERO && kb != CLR_KIND_ZERO;
+    const unsigned mask = __ballot_sync(0xffffffffu, on);
+    const int kind = (ka == CLR_KIND_DENSE ? 0 : 2) + (kb == CLR_KIND_DENSE ? 0 : 1);
+    const int r = on ? out_rank(kind, A.rank[I * A.nc + K], B.rank[K * B.nc + J]) : 0;
+    int incl = r;  // inclusive prefix sum of the output ranks over the lanes
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int v = __shfl_up_sync(0xffffffffu, incl, o);
+      if (lane >= o) incl += v;
+    }
+    if (on) {
+      Triple tr;
+      tr.tile = t;
+      tr.k = K;
+      tr.kind = kind;
+      tr.col = col + incl - r;
+      const int64_t at = pos + __popc(mask & ((1u << lane) - 1u));
+      if (at < p.max_triples) p.triples[at] = tr; else atomicExch(&p.counters->err, 2);
+    }
+    pos += __popc(mask);
+    col += __shfl_sync(0xffffffffu, incl, 31);
   }
 }
 
@@ -216,8 +247,8 @@ void launch_plan_scan(const Plan& p, int recompress_dense, cudaStream_t st) {
 void launch_plan(const MatView& A, const MatView& B, const Plan& p, double eps_sp,
                  int recompress_dense, double gemm_dacc_bound, cudaStream_t st) {
   const int n = p.nI * p.nJ;
-  const int threads = 128;
-  const int blocks = (n + threads - 1) / threads;
+  const int threads = 128;  // 4 tiles per block: one warp each
+  const int blocks = (int)(((int64_t)n * 32 + threads - 1) / threads);
   cudaMemsetAsync(p.counters, 0, sizeof(PlanCounters), st);
   plan_count_kernel<<<blocks, threads, 0, st>>>(A, B, p, eps_sp, gemm_dacc_bound);
   plan_scan_kernel<<<1, kScanThreads, 0, st>>>(p, recompress_dense);
