@@ -106,8 +106,11 @@ def test_full_size_sampled_tiles(ctx):
     off = np.concatenate([[0], np.cumsum(w.row_sizes)])
     rng = np.random.default_rng(5)
     num, den, ab = 0.0, 0.0, 0.0
-    for _ in range(6):
-        i, j = rng.integers(0, 96, 2)
+    # first and last tiles, the column cluster across the middle, and random tiles
+    j_mid = int(np.searchsorted(off, (w.n // 256) // 2 * 256, side="right")) - 1
+    pairs = [(0, 0), (95, 95), (40, j_mid), (77, j_mid)] + \
+        [tuple(rng.integers(0, 96, 2)) for _ in range(4)]
+    for i, j in pairs:
         r0, r1, c0, c1 = off[i], off[i + 1], off[j], off[j + 1]
         want = w.a[r0:r1] @ w.b[:, c0:c1]
         got = out[r0:r1, c0:c1].cpu().numpy()
@@ -119,9 +122,12 @@ def test_full_size_sampled_tiles(ctx):
     # sum over sampled entries of dC^2 <= (10 eps)^2 * sum ||a_i||^2 ||b_j||^2
     assert num <= (10 * 1e-8) ** 2 * ab
     assert math.sqrt(num / den) < 3e-5
-    # the whole matrix: every block is dense
+    # the whole matrix: every block is dense, and the block norms (formed in the GEMM's
+    # epilogue) add up to ||C||_F
     k, _, _, _ = gc.get_blocks(pool=False)
     assert (k == co.KIND_DENSE).all()
+    fro = float(torch.linalg.norm(out))
+    assert abs(gc.info()["frob_norm"] - fro) <= 1e-12 * fro
 
 
 def test_low_rank_sums_on_tensor_cores_follow_error_bound(ctx):
