@@ -309,7 +309,9 @@ int clr_probe_fp64_rate(int device, double* tflops);
  * a_t = bf16(x - a_0 - ... - a_{t-1}), each rounding to nearest-even from the exact FP64
  * difference.  x: n doubles on the device (finite); out: terms x n bf16 bit patterns on the
  * device, term-major (out[t * n + i]).  terms: 2 (bf16x3) or 3 (bf16x6).  Runs on `stream`
- * (a cudaStream_t, may be null), asynchronous.  Device pointers are the caller's. */
+ * (a cudaStream_t, may be null), asynchronous.  Device pointers are the caller's.  CLR_EINVAL
+ * for n < 0, other term counts, null pointers with n > 0, or n >= 2^40; CLR_ECUDA when the
+ * launch fails. */
 int clr_split_bf16(const double* x, int64_t n, int terms, uint16_t* out, void* stream);
 
 /* ---- allocation-free single-block compression ---------------------------------------------

@@ -217,6 +217,7 @@ extern "C" int clr_split_bf16(const double* x, int64_t n, int terms, uint16_t* o
   if (n < 0 || (terms != 2 && terms != 3) || (n > 0 && (!x || !out))) return CLR_EINVAL;
   if (n == 0) return CLR_OK;
   const int64_t pairs = (n + 1) / 2;
+  if ((pairs + 255) / 256 > 0x7fffffff) return CLR_EINVAL;  // beyond one launch's grid
   const unsigned blocks = (unsigned)((pairs + 255) / 256);
   cudaStream_t st = (cudaStream_t)stream;
   if (terms == 2)
