@@ -8,8 +8,10 @@ split-precision bf16x3 on the tensor cores with FP32 accumulation in short segme
 FP64 epilogue.  A step is one whole CLR product through the library (triple list, staging of
 the bf16 term panels, the dense tile products, low-rank/recompression passes, norms).
 
-Prints one JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle instead, on a
-bounded sample of the same workload.  Multi-GPU runs (torchrun) are independent replicas:
+Prints one JSON line (rank 0), which also carries Newton-Schulz timings (1D chain, 3D lattice
+overlap and Coulomb-like matrices) and the batched configuration (64 chain products of uneven
+size replayed as one CUDA graph, measured in a child process).  `--impl reference` times the
+FP64 CPU oracle instead, on a bounded sample of the same workload.  Multi-GPU runs (torchrun) are independent replicas:
 each rank multiplies its own matrices, nothing is exchanged between ranks.
 """
 from __future__ import annotations
@@ -51,6 +53,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ns", action="store_true")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-products measurement (64 products, one CUDA graph)")
     ap.add_argument("--ns-prec", default="fp64", choices=["bf16x3", "bf16x6", "fp64"])
     ap.add_argument("--ns-lattice", default="8x8x4",
                     help="lattice sites of the 3D overlap NS measurement (16 points per site), "
@@ -408,6 +412,12 @@ def run_ours(args):
         ns_coul = lattice_ns(clr, wl.lattice_coulomb(shape=shape), args.ns_lattice,
                              "Coulomb-like erf(r)/r", fp64_peak)
 
+    # 64 independent 1D-chain products of uneven size in one CUDA graph (the batched
+    # configuration), measured in a child process with its own context and memory
+    batch = None
+    if rank == 0 and ws == 1 and not args.no_batch:
+        batch = batch_measure(64)
+
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
         fl, el, rows = oracle_sample(w, 15.0)
@@ -424,7 +434,7 @@ def run_ours(args):
                 "config": config(args, {"error": err, "phases_ms_per_step": phases,
                                         "algorithmic_flops_per_step": alg_flops}),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ns": ns,
-                "ns_lattice": ns_lat, "ns_coulomb": ns_coul,
+                "ns_lattice": ns_lat, "ns_coulomb": ns_coul, "batch": batch,
                 "gpu_launches": int(prof["launches"]), "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -433,6 +443,24 @@ def run_ours(args):
 
 
 FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
+
+
+def batch_measure(n: int, timeout: int = 420):
+    """products/s and algorithmic TFLOP/s of n batched chain products replayed as one CUDA graph
+    (`python -m paper_1509_00309_gb300.diagnostics --batch n`), or {"error": ...}."""
+    cmd = [sys.executable, "-m", "paper_1509_00309_gb300.diagnostics", "--batch", str(n)]
+    try:
+        r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=timeout)
+    except subprocess.TimeoutExpired:
+        return {"error": "did not finish within %d s" % timeout}
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    if r.returncode != 0 or not lines:
+        tail = (r.stderr or "").strip().splitlines()[-1:] or [""]
+        return {"error": "exit %d: %s" % (r.returncode, tail[0][:200])}
+    try:
+        return json.loads(lines[-1])
+    except ValueError:
+        return {"error": "unreadable output"}
 
 
 def lattice_ns(clr, w, shape_txt, what, fp64_peak):

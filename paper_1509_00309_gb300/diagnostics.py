@@ -3,6 +3,7 @@ ranks of the 5th-iteration intermediates X, Y, Z, T and of the input S).
 
     python -m paper_1509_00309_gb300.diagnostics --shape 8x8x4 --iter 5 [--matrix coulomb]
     python -m paper_1509_00309_gb300.diagnostics --adjoint --shape 8x8x8 --max-iter 20
+    python -m paper_1509_00309_gb300.diagnostics --batch 64
 
 builds the 3D lattice overlap matrix (16 points per site, clusters of 64..256 points, eps_lr
 1e-6, drop 1e-10, eps_sp 1e-13), or the Coulomb-like erf(r)/r matrix on the same lattice, on
@@ -83,6 +84,49 @@ def adjoint_run(shape, precision: str = "fp64", iters: int = 20, eps: float = 1e
             "grad_frob": gi["frob_norm"], "grad_blocks": gi["n_blocks"]}
 
 
+def batch_run(n_instances: int = 64, steps: int = 10, warmup: int = 3) -> Dict:
+    """The batched configuration: n_instances independent 1D-chain products S S of uneven size
+    (N ~ U[1024, 8192], clusters U[48, 256], eps from {1e-6, 1e-8}) captured into one CUDA graph
+    with the autotuner's per-shape choice (clr_batch_*); products/s and algorithmic TFLOP/s of
+    graph replays timed with CUDA events."""
+    import torch
+    ws = wl.batched_chains(n_instances=n_instances)
+    ctx = clr.Context(0, precision="auto", eps_lr=1e-8)
+    mats = [ctx.from_dense(torch.from_numpy(w.a).cuda(), w.row_sizes, eps_lr=w.eps_lr,
+                           drop_norm=w.drop_norm) for w in ws]
+    torch.cuda.synchronize()
+    # algorithmic flops of every product (the library's triple statistics), untimed
+    flops = 0.0
+    for m, w in zip(mats, ws):
+        ctx.set_opts(eps_lr=w.eps_lr)
+        out = ctx.zeros(w.row_sizes)
+        flops += float(ctx.multiply_into(m, m, out, stats=True)["flops"])
+        out.close()
+    ctx.set_opts(eps_lr=1e-8)
+    batch = ctx.batch(mats, mats, eps=[w.eps_lr for w in ws], tune=True)
+    for _ in range(warmup):
+        batch.run()
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    ev[0].record()
+    for _ in range(steps):
+        batch.run()
+    ev[1].record()
+    torch.cuda.synchronize()
+    ms = ev[0].elapsed_time(ev[1]) / steps
+    prec = {}
+    for i in range(batch.n):
+        t = batch.tuning(i)["precision"]
+        prec[t] = prec.get(t, 0) + 1
+    batch.close()
+    return {"workload": "%d batched 1D-chain products S S, N ~ U[1024,8192], clusters U[48,256], "
+                        "eps in {1e-6, 1e-8}, one CUDA graph" % n_instances,
+            "instances": n_instances, "sum_n": int(sum(w.n for w in ws)),
+            "ms_per_batch": ms, "products_per_s": n_instances / (ms * 1e-3),
+            "tflops": flops / (ms * 1e-3) / 1e12, "algorithmic_flops_per_batch": flops,
+            "precisions": prec, "steps": steps, "warmup": warmup}
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--shape", default="8x8x4", help="lattice sites, e.g. 16x16x8 (N = 16 x sites)")
@@ -95,9 +139,14 @@ def main() -> None:
     ap.add_argument("--adjoint", action="store_true",
                     help="time forward + adjoint of trace(W S^-1/2) instead (eps_lr 1e-8, "
                          "--max-iter iterations)")
+    ap.add_argument("--batch", type=int, default=0, metavar="N",
+                    help="time N batched 1D-chain products in one CUDA graph instead")
     args = ap.parse_args()
     import torch
     shape = tuple(int(v) for v in args.shape.split("x"))
+    if args.batch:
+        print(json.dumps(batch_run(args.batch)))
+        return
     if args.adjoint:
         print(json.dumps(adjoint_run(shape, args.precision, min(args.max_iter, 40))))
         return
