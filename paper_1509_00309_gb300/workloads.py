@@ -48,8 +48,9 @@ def uneven_cluster_sizes(rng: np.random.Generator, n_total: int, n_clusters: int
 
 def chain_clusters(rng: np.random.Generator, n_total: int, lo: int, hi: int) -> List[int]:
     """Contiguous clusters of a 1D chain with sizes drawn from [lo, hi] until ``n_total``
-    points are covered; the last cluster takes the remainder (merged into its neighbour if it
-    would be shorter than ``lo // 2``)."""
+    points are covered; the last cluster takes the remainder.  A remainder shorter than
+    ``lo // 2`` joins its neighbour, and where the two together would exceed ``hi`` they are
+    split into two halves instead, so every cluster stays within [lo // 2, hi]."""
     sizes: List[int] = []
     left = n_total
     while left > 0:
@@ -58,8 +59,13 @@ def chain_clusters(rng: np.random.Generator, n_total: int, lo: int, hi: int) -> 
         sizes.append(s)
         left -= s
     if len(sizes) > 1 and sizes[-1] < max(1, lo // 2):
-        sizes[-2] += sizes[-1]
+        both = sizes[-2] + sizes[-1]
         sizes.pop()
+        if both <= hi:
+            sizes[-1] = both
+        else:
+            sizes[-1] = both // 2
+            sizes.append(both - both // 2)
     return sizes
 
 
