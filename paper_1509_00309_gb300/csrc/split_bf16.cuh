@@ -1,9 +1,10 @@
 // Split of a finite FP64 value into bf16 terms, a = a_0 + a_1 (+ a_2) + residual, with
 // a_0 = bf16(a), a_1 = bf16(a - a_0), a_2 = bf16(a - a_0 - a_1), every bf16 rounding to nearest
-// with ties to even and taken directly from the exact FP64 difference (no intermediate FP32
-// rounding).  Integer operations only: on this part FP64 arithmetic runs at a small fraction of
-// the integer rate.  Host and device compile the same code, so the rounding can be checked on
-// the CPU against the format's definition.
+// with ties to even and taken directly from the exact FP64 difference (no double rounding).
+// No FP64 arithmetic (on this part it runs at a small fraction of the integer rate): integer
+// operations on the bit patterns, and in the paired form one FP32 -> bf16x2 conversion of
+// patterns already rounded to odd.  Host and device compile the same code (the host spells the
+// conversion out), so the rounding can be checked on the CPU against the format's definition.
 #pragma once
 
 #include <stdint.h>
