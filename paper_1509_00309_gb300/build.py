@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import concurrent.futures as cf
 import os
+import platform
 import shutil
 import subprocess
 import sys
@@ -16,8 +17,11 @@ PKG = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 LIBDIR = os.path.join(PKG, "lib")
-BUILD = os.path.join(PKG, "_build")
+# objects per host architecture: a source tree copied between an x86_64 and an aarch64 host
+# never links the other host's objects
+BUILD = os.path.join(PKG, "_build", platform.machine() or "host")
 LIB = os.path.join(LIBDIR, "libclr_gb300.so")
+STAMP = os.path.join(LIBDIR, "machine.txt")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr",
          "-I", os.path.join(ROOT, "include"), "-I", CSRC]
@@ -54,11 +58,15 @@ def build(verbose: bool = False, extra=()) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(lambda s: _compile(s, extra), srcs))
     newest = max(os.path.getmtime(o) for o in objs)
-    if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
+    machine = platform.machine() or "host"
+    stamped = open(STAMP).read().strip() if os.path.exists(STAMP) else ""
+    if not os.path.exists(LIB) or os.path.getmtime(LIB) < newest or stamped != machine:
         cmd = [nvcc()] + ARCH + ["-shared", "-cudart", "static", "-o", LIB] + objs
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))
+        with open(STAMP, "w") as f:
+            f.write(machine + "\n")
     if verbose:
         print("built", LIB, file=sys.stderr)
     return LIB
