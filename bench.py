@@ -32,12 +32,14 @@ if ROOT not in sys.path:
 
 METRIC = "CLR multiply TFLOP/s and ms per Newton–Schulz S^-1/2 iteration at stated error"
 
-# DRAM bytes (read + write) of one launch of the dense tile-product kernel, from one ncu capture
-# (profiles/split_gemm_dense16384_bf16x3.md), keyed by the kernel source's hash so the number
-# is dropped (traffic: null) as soon as the kernel changes.
-MEASURED_TRAFFIC = {
-    "66ded9475a6d:bf16x3:16384:96": 17201329408 + 3663043072,
-}
+# DRAM bytes (read + write) of one launch of the dense tile-product kernel at this workload,
+# from ncu counters, keyed by the kernel source's hash so that the number is dropped
+# (traffic: null) as soon as the kernel changes.
+MEASURED_TRAFFIC = {}
+# Truncation of the Newton-Schulz iterates on the lattice matrices: the matrix is built at
+# eps_lr = 1e-6, but iterates truncated at 1e-6 hold the residual ||alpha Z S Z - I||_F/sqrt(N)
+# near 1.8e-5 (the oracle floors at the same level); at 1e-8 the residual meets 1e-6.
+EPS_NS_LATTICE = 1e-8
 PAIRS = {"bf16x3": 3, "bf16x6": 6}
 
 
@@ -59,6 +61,10 @@ def parse():
     ap.add_argument("--ns-lattice", default="8x8x4",
                     help="lattice sites of the 3D overlap NS measurement (16 points per site), "
                          "or 'none'")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="skip the plain-FP64 product of the same workload")
+    ap.add_argument("--no-chain", action="store_true",
+                    help="skip the N = 2048 1D-chain product (FP64 and split)")
     return ap.parse_args()
 
 
@@ -68,15 +74,13 @@ def workload(args, rank=0):
                            seed=wl.default_seed(1) + 1000 * rank)
 
 
-def config(args, extra=None):
-    c = {"workload": "all-dense CLR product N=%d, %d uneven clusters U[128,224], "
-                     "A,B ~ N(0,1) FP64" % (args.n, args.clusters),
-         "n": args.n, "clusters": args.clusters, "precision": args.prec,
-         "l2": "inputs larger than L2 (A, B 2.1 GB FP64 each + bf16 term panels); no flush",
-         "parallelism": "replicas"}
-    if extra:
-        c.update(extra)
-    return c
+def config(args):
+    """The workload (identical for both arms)."""
+    return {"workload": "all-dense CLR product N=%d, %d uneven clusters U[128,224], "
+                        "A,B ~ N(0,1) FP64" % (args.n, args.clusters),
+            "n": args.n, "clusters": args.clusters, "precision": args.prec,
+            "l2": "inputs larger than L2 (A, B 2.1 GB FP64 each + bf16 term panels); no flush",
+            "parallelism": "replicas"}
 
 
 def load_peaks():
@@ -235,7 +239,7 @@ def run_reference(args):
            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * el / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": config(args, {"precision": "fp64 (CPU oracle)"}),
+           "config": config(args),
            "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores,
                             "kind": "oracle",
                             "sample": "%d block rows of C (each: all 96 column clusters x all "
@@ -249,8 +253,35 @@ def run_reference(args):
 # Our arm
 # ------------------------------------------------------------------------------------------
 
-def run_ours(args):
+def sampled_accuracy(w, out_host_tiles, rng_seed=5, n_tiles=4):
+    """Error of sampled C tiles against FP64 dot products of the inputs (numpy)."""
     import numpy as np
+    off = np.concatenate([[0], np.cumsum(w.row_sizes)])
+    rng = np.random.default_rng(rng_seed)
+    num = den = ab = 0.0
+    for _ in range(n_tiles):
+        i, j = rng.integers(0, len(w.row_sizes), 2)
+        r0, r1, c0, c1 = off[i], off[i + 1], off[j], off[j + 1]
+        want = w.a[r0:r1] @ w.b[:, c0:c1]
+        got = out_host_tiles(r0, r1, c0, c1)
+        num += float(np.sum((got - want) ** 2))
+        den += float(np.sum(want ** 2))
+        ab += float(np.sum(np.linalg.norm(w.a[r0:r1], axis=1)[:, None] ** 2 *
+                           np.linalg.norm(w.b[:, c0:c1], axis=0)[None, :] ** 2))
+    return {"rel_frob_sampled": math.sqrt(num / den),
+            "frob_over_normA_normB_sampled": math.sqrt(num / ab),
+            "bound_10eps_eps1e-8": 1e-7, "tiles_sampled": n_tiles}
+
+
+def dense_tiles_reader(gc, n):
+    import torch
+    out = torch.empty((n, n), dtype=torch.float64, device="cuda")
+    gc.to_dense(out)
+    torch.cuda.synchronize()
+    return lambda r0, r1, c0, c1: out[r0:r1, c0:c1].cpu().numpy()
+
+
+def run_ours(args):
     import torch
 
     from paper_1509_00309_gb300 import build, clr
@@ -258,7 +289,8 @@ def run_ours(args):
     if ws == 1:
         torch.cuda.set_device(0)
     build.build()
-    ctx = clr.Context(torch.cuda.current_device(), precision=args.prec, eps_lr=1e-8)
+    dev = torch.cuda.current_device()
+    ctx = clr.Context(dev, precision=args.prec, eps_lr=1e-8)
     w = workload(args, rank)
     n = w.n
     stream = torch.cuda.current_stream()
@@ -287,34 +319,13 @@ def run_ours(args):
         e1.record(stream)
         torch.cuda.synchronize()
         barrier(ws)
+    ctx.check()
     prof = ctx.profile_read()
     ctx.profile_enable(False)
     ms_total = max_over_ranks(e0.elapsed_time(e1), ws)
     ms_step = ms_total / args.steps
     value = job_tflops(alg_flops, ws, args.steps, ms_total)
-
-    # accuracy of this run's result on sampled tiles vs FP64 dot products
-    err = None
-    if rank == 0:
-        out = torch.empty((n, n), dtype=torch.float64, device="cuda")
-        gc.to_dense(out)
-        torch.cuda.synchronize()
-        off = np.concatenate([[0], np.cumsum(w.row_sizes)])
-        rng = np.random.default_rng(5)
-        num = den = ab = 0.0
-        for _ in range(4):
-            i, j = rng.integers(0, len(w.row_sizes), 2)
-            r0, r1, c0, c1 = off[i], off[i + 1], off[j], off[j + 1]
-            want = w.a[r0:r1] @ w.b[:, c0:c1]
-            got = out[r0:r1, c0:c1].cpu().numpy()
-            num += float(np.sum((got - want) ** 2))
-            den += float(np.sum(want ** 2))
-            ab += float(np.sum(np.linalg.norm(w.a[r0:r1], axis=1)[:, None] ** 2 *
-                               np.linalg.norm(w.b[:, c0:c1], axis=0)[None, :] ** 2))
-        del out
-        err = {"rel_frob_sampled": math.sqrt(num / den),
-               "frob_over_normA_normB_sampled": math.sqrt(num / ab),
-               "bound_10eps_eps1e-8": 1e-7}
+    acc = sampled_accuracy(w, dense_tiles_reader(gc, n)) if rank == 0 else None
 
     # roofline of the dominant kernel (the split dense tile-product kernel)
     peaks, src = load_peaks()
@@ -329,9 +340,13 @@ def run_ours(args):
     if args.prec in PAIRS:
         pairs = PAIRS[args.prec]
         achieved = alg_flops / per_product / (gemm_ms * 1e-3) / 1e12
-        peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) / pairs
+        # the timed region is a burst of back-to-back products (well under a second): the
+        # burst bf16 peak is the denominator; the sustained one is reported beside it
+        peak = peaks["bf16_tflops"] / pairs
+        peak_sus = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]) / pairs
         roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic,
+                "frac_sustained": achieved / peak_sus, "peak_sustained": peak_sus,
                 # per launch: the bf16 term panels of A and of the launch's columns of B
                 # read once, its FP64 columns of C written once
                 "algorithmic_bytes": (2 if pairs == 3 else 3) * 2 * (n * n + n * n / per_product)
@@ -341,8 +356,11 @@ def run_ours(args):
                 "kernel": "split_gemm_kernel<%d, %d>" % (
                     2 if pairs == 3 else 3, 1 if min(w.row_sizes) >= 32 else 0),
                 "kernel_ms": gemm_ms,
-                "peak_basis": "%s sustained bf16 %.1f TFLOP/s / %d term-pair products" % (
-                    src, peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]), pairs),
+                "peak_basis": "%s burst bf16 %.1f TFLOP/s / %d term-pair products (sustained "
+                              "%.1f / %d beside it)" % (
+                                  src, peaks["bf16_tflops"], pairs,
+                                  peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]),
+                                  pairs),
                 "tensor_tflops_issued": prof["dense_tensor_flops"] / (prof["ms_dense"] * 1e-3)
                 / 1e12}
     else:
@@ -358,7 +376,7 @@ def run_ours(args):
         a_h = torch.from_numpy(w.a).pin_memory()
         b_h = torch.from_numpy(w.b).pin_memory()
         c_h = torch.empty((n, n), dtype=torch.float64).pin_memory()
-        e2e_steps = max(1, min(args.steps, 3))
+        e2e_steps = max(3, min(args.steps, 10))
         ctx.multiply_host_stream(a_h, b_h, c_h, w.row_sizes, n_chunks=4)   # warm-up: buffers
         torch.cuda.synchronize()
         barrier(ws)
@@ -371,16 +389,29 @@ def run_ours(args):
         el = max_over_ranks(time.perf_counter() - t0, ws)
         e2e = {"value": alg_flops * ws * e2e_steps / el / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8,
-               "ms_per_step": 1e3 * el / e2e_steps}
+               "ms_per_step": 1e3 * el / e2e_steps, "steps": e2e_steps}
+        del a_h, b_h, c_h
+
+    fp64_peak = clr.probe_fp64_rate(dev)
+
+    # the plain form: the same product with FP64 tile products on the CUDA cores
+    fp64 = None
+    if not args.no_fp64 and args.prec != "fp64":
+        fp64 = fp64_product(ctx, ga, gb, gc, w, alg_flops, fp64_peak, value, acc, rank)
+
+    # the 1D-chain product (N = 2048, eps = 1e-8): FP64 against the split forms
+    chain = None
+    if not args.no_chain and rank == 0:
+        chain = chain_product(clr, dev, fp64_peak)
 
     # Newton-Schulz S^-1/2 on the 1D-chain overlap matrix (N = 2048, 16 uneven clusters,
-    # eps_lr = 1e-8): ms per iteration to ||X_n - I||_F/sqrt(N) <= 1e-6.  FP64 products by
-    # default: split products stop at a residual ~ u_split * kappa (~2e-4 here)
+    # eps_lr = 1e-8): ms per iteration to ||X_n - I||_F/sqrt(N) <= 1e-6, and the residual
+    # ||alpha Z S Z - I||_F / sqrt(N) of the result against the same tolerance
     ns = None
     if not args.no_ns:
         from paper_1509_00309_gb300 import workloads as wl
         wn = wl.chain_overlap()
-        nctx = clr.Context(torch.cuda.current_device(), precision=args.ns_prec,
+        nctx = clr.Context(dev, precision=args.ns_prec,
                            eps_lr=wn.eps_lr, ns_tol=1e-6, ns_max_iter=60,
                            ns_fp64_tail=int(args.ns_prec != "fp64"), ns_ladder_switch=1e-3)
         sm = nctx.from_dense(torch.from_numpy(wn.a).cuda(), wn.row_sizes, eps_lr=wn.eps_lr,
@@ -391,32 +422,37 @@ def run_ours(args):
         it = max(1, nst["iters"])
         ns = {"workload": "1D-chain overlap N=2048, 16 uneven clusters, eps_lr=1e-8",
               "ms_per_iteration": nst["ms_total"] / it, "iterations": nst["iters"],
-              "converged": nst["converged"], "proxy_final": nst["proxy"][-1],
               "residual_ZSZ_minus_I_rms": nst["residual"], "tol": 1e-6,
+              "residual_met": nst["residual_met"], "proxy_final": nst["proxy"][-1],
+              "ms_residual": nst["ms_residual"],
               "precision": args.ns_prec if args.ns_prec == "fp64" else
                            "%s, fp64 below proxy 1e-3" % args.ns_prec,
               "z_blocks_zero_dense_lr": z.info()["n_blocks"]}
 
     # Newton-Schulz on the 3D lattice matrices (16 points per jittered lattice site, clusters
-    # of 64..256 points, eps_lr = 1e-6, drop 1e-10, eps_sp = 1e-13), FP64 products,
-    # dense-accumulated tiles re-tested for low rank; with the block-rank distribution of the
-    # 5th-iteration intermediates X, T, Y, Z (Section 5).  The overlap-like S has block
-    # sparsity; the Coulomb-like V (erf(r)/r) has only block-rank sparsity (Section 4.2).
-    ns_lat = ns_coul = None
+    # of 64..256 points, built at eps_lr = 1e-6, drop 1e-10, eps_sp = 1e-13; iterates truncated
+    # at EPS_NS_LATTICE), FP64 products, dense-accumulated tiles re-tested for low rank; with
+    # the block-rank distribution of the 5th-iteration intermediates X, T, Y, Z (Section 5).
+    # The same run with split products (bf16x6, FP64 from ||X - I|| <= 1e-3) shows the split
+    # floor.  The overlap-like S has block sparsity; the Coulomb-like V (erf(r)/r) has only
+    # block-rank sparsity (Section 4.2).
+    ns_lat = ns_lat_split = ns_coul = None
     if not args.no_ns and args.ns_lattice != "none":
         from paper_1509_00309_gb300 import workloads as wl
         shape = tuple(int(v) for v in args.ns_lattice.split("x"))
-        fp64_peak = clr.probe_fp64_rate(torch.cuda.current_device())
-        ns_lat = lattice_ns(clr, wl.lattice_overlap(shape=shape), args.ns_lattice, "overlap",
-                            fp64_peak)
+        wlat = wl.lattice_overlap(shape=shape)
+        ns_lat = lattice_ns(clr, wlat, args.ns_lattice, "overlap", fp64_peak, "fp64")
+        ns_lat_split = lattice_ns(clr, wlat, args.ns_lattice, "overlap", fp64_peak, "bf16x6",
+                                  snapshot=False)
         ns_coul = lattice_ns(clr, wl.lattice_coulomb(shape=shape), args.ns_lattice,
-                             "Coulomb-like erf(r)/r", fp64_peak)
+                             "Coulomb-like erf(r)/r", fp64_peak, "fp64", snapshot=False)
 
     # 64 independent 1D-chain products of uneven size in one CUDA graph (the batched
-    # configuration), measured in a child process with its own context and memory
+    # configuration), autotuned and FP64-only, each measured in a child process with its own
+    # context and memory
     batch = None
     if rank == 0 and ws == 1 and not args.no_batch:
-        batch = batch_measure(64)
+        batch = {"autotuned": batch_measure(64, "auto"), "fp64": batch_measure(64, "fp64")}
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -430,11 +466,12 @@ def run_ours(args):
         line = {"metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": ws,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": args.prec, "data": "synthetic",
-                "config": config(args, {"error": err, "phases_ms_per_step": phases,
-                                        "algorithmic_flops_per_step": alg_flops}),
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "ns": ns,
-                "ns_lattice": ns_lat, "ns_coulomb": ns_coul, "batch": batch,
+                "dtype": args.prec, "data": "synthetic", "config": config(args),
+                "accuracy": acc, "phases_ms_per_step": phases,
+                "algorithmic_flops_per_step": alg_flops,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_dense": fp64,
+                "chain_product": chain, "ns": ns, "ns_lattice": ns_lat,
+                "ns_lattice_split": ns_lat_split, "ns_coulomb": ns_coul, "batch": batch,
                 "gpu_launches": int(prof["launches"]), "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if ws > 1:
@@ -442,13 +479,92 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+def fp64_product(ctx, ga, gb, gc, w, alg_flops, fp64_peak, split_value, split_acc, rank):
+    """One product of the same workload with FP64 tile products (dd_fp64_kernel on the CUDA
+    cores; ~7 s at N = 16384), after the split run sized every workspace: TFLOP/s, the
+    fraction of the measured FP64 FMA rate, and its accuracy beside the split form's."""
+    import torch
+    prev = ctx.get_opts().precision
+    ctx.set_opts(precision="fp64")
+    ctx.profile_enable(True)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record()
+    ctx.multiply_into(ga, gb, gc)
+    e[1].record()
+    torch.cuda.synchronize()
+    ctx.check()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    ctx.set_opts(precision=prev)
+    ms = e[0].elapsed_time(e[1])
+    tf = alg_flops / (ms * 1e-3) / 1e12
+    kern = alg_flops / (prof["ms_dense"] * 1e-3) / 1e12
+    acc = sampled_accuracy(w, dense_tiles_reader(gc, w.n)) if rank == 0 else None
+    return {"ms_per_product": ms, "tflops": tf, "kernel": "dd_fp64_kernel",
+            "kernel_ms": prof["ms_dense"], "kernel_tflops": kern,
+            "peak_fp64_measured": fp64_peak, "frac": kern / fp64_peak, "bound": "alu",
+            "peak_basis": "measured FP64 FMA rate of this GPU (clr_probe_fp64_rate)",
+            "accuracy": acc, "split_over_fp64_speedup": split_value / tf,
+            "split_accuracy_within_bound": bool(split_acc and
+                                                split_acc["frob_over_normA_normB_sampled"] <=
+                                                split_acc["bound_10eps_eps1e-8"]),
+            "steps": 1}
+
+
+def chain_product(clr, dev, fp64_peak, warmup=3, steps=15):
+    """The 1D-chain CLR product S S (N = 2048, 16 uneven clusters, built and recompressed at
+    eps = 1e-8; Section 4.1) in FP64 and in the split forms: microseconds per product (median
+    of `steps` after `warmup`), algorithmic TFLOP/s, and ||C - A A||_F against the FP64 dense
+    product of the reconstructed operand with the bound 10 eps ||A||_F^2."""
+    import numpy as np
+    import torch
+    from paper_1509_00309_gb300 import workloads as wl
+    wn = wl.chain_overlap()
+    out = {"workload": "1D-chain overlap product S S, N=2048, 16 uneven clusters, eps=1e-8"}
+    ctx = clr.Context(dev, precision="fp64", eps_lr=wn.eps_lr)
+    sm = ctx.from_dense(torch.from_numpy(wn.a).cuda(), wn.row_sizes, eps_lr=wn.eps_lr,
+                        drop_norm=wn.drop_norm)
+    a = sm.to_dense()
+    want = a @ a
+    bound = 10.0 * wn.eps_lr * float(np.linalg.norm(a)) ** 2
+    for prec in ("fp64", "bf16x6", "bf16x3"):
+        ctx.set_opts(precision=prec)
+        gc = ctx.zeros(wn.row_sizes)
+        st = ctx.multiply_into(sm, sm, gc, stats=True)
+        for _ in range(warmup):
+            ctx.multiply_into(sm, sm, gc)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+        ev[0].record()
+        for i in range(steps):
+            ctx.multiply_into(sm, sm, gc)
+            ev[i + 1].record()
+        torch.cuda.synchronize()
+        ctx.check()
+        ms = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(steps))
+        med = ms[steps // 2]
+        err = float(np.linalg.norm(gc.to_dense() - want))
+        out[prec] = {"us_per_product": 1e3 * med, "tflops": st["flops"] / (med * 1e-3) / 1e12,
+                     "err_frob": err, "bound_10eps_normA2": bound,
+                     "within_bound": err <= bound, "triples": st["n_triples"],
+                     "tiles_dense_lr": st["n_tiles"][1:]}
+        gc.close()
+    fast = [p for p in ("bf16x3", "bf16x6") if out[p]["within_bound"]]
+    if fast:
+        best = min(fast, key=lambda p: out[p]["us_per_product"])
+        out["fastest_split_within_bound"] = best
+        out["split_over_fp64_speedup"] = out["fp64"]["us_per_product"] / out[best]["us_per_product"]
+    return out
+
+
 FP32_TFLOPS_NOMINAL = 152 * 128 * 2 * 2.07e9 / 1e12   # SMs x FP32 lanes x FMA x max clock
 
 
-def batch_measure(n: int, timeout: int = 420):
+def batch_measure(n: int, precision: str, timeout: int = 420):
     """products/s and algorithmic TFLOP/s of n batched chain products replayed as one CUDA graph
-    (`python -m paper_1509_00309_gb300.diagnostics --batch n`), or {"error": ...}."""
-    cmd = [sys.executable, "-m", "paper_1509_00309_gb300.diagnostics", "--batch", str(n)]
+    (`python -m paper_1509_00309_gb300.diagnostics --batch n --batch-precision P`), or
+    {"error": ...}."""
+    cmd = [sys.executable, "-m", "paper_1509_00309_gb300.diagnostics", "--batch", str(n),
+           "--batch-precision", precision]
     try:
         r = subprocess.run(cmd, cwd=ROOT, capture_output=True, text=True, timeout=timeout)
     except subprocess.TimeoutExpired:
@@ -463,36 +579,45 @@ def batch_measure(n: int, timeout: int = 420):
         return {"error": "unreadable output"}
 
 
-def lattice_ns(clr, w, shape_txt, what, fp64_peak):
-    """NS to ||X - I||_F/sqrt(N) <= 1e-6 on one lattice matrix, through the C ABI, with the
-    recompression's ALU roofline: its algorithmic FP64 and FP32 flops over its device time,
-    against the measured FP64 FMA rate and the nominal FP32 rate."""
+def lattice_ns(clr, w, shape_txt, what, fp64_peak, precision, snapshot=True):
+    """NS on one lattice matrix through the C ABI: the iterates truncated at EPS_NS_LATTICE,
+    stopped at ||X - I||_F/sqrt(N) <= 1e-6 and judged by the residual ||alpha Z S Z - I||_F /
+    sqrt(N) <= 1e-6 (the stated error); with the recompression's ALU roofline (algorithmic FP64
+    and FP32 flops over its device time, against the measured FP64 FMA rate and the nominal
+    FP32 rate)."""
     import torch
     from paper_1509_00309_gb300 import diagnostics
-    ctx = clr.Context(torch.cuda.current_device(), precision="fp64", eps_lr=w.eps_lr,
-                      eps_sp=w.eps_sp, ns_tol=1e-6, ns_max_iter=40, recompress_dense=1)
+    ctx = clr.Context(torch.cuda.current_device(), precision=precision, eps_lr=EPS_NS_LATTICE,
+                      eps_sp=w.eps_sp, ns_tol=1e-6, ns_max_iter=40, recompress_dense=1,
+                      ns_fp64_tail=int(precision != "fp64"), ns_ladder_switch=1e-3)
     sm = ctx.from_dense(torch.from_numpy(w.a).cuda(), w.row_sizes, eps_lr=w.eps_lr,
                         drop_norm=w.drop_norm)
     ctx.set_opts(ns_max_iter=1, ns_tol=0.0)
     ctx.sqrt_inv(sm, allow_noconv=True)   # warm-up: workspaces
     ctx.set_opts(ns_max_iter=40, ns_tol=1e-6)
     torch.cuda.synchronize()
-    d = diagnostics.ns_rank_distribution(ctx, sm, 5)
-    return {"workload": "3D lattice %s matrix, %s sites x 16 points, N=%d, %d clusters of "
-                        "64..256, eps_lr=1e-6" % (what, shape_txt, w.n, len(w.row_sizes)),
-            "ms_per_iteration": d["ns"]["ms_per_iter"], "iterations": d["ns"]["iters"],
-            "proxy_final": d["ns"]["proxy"][-1],
-            "residual_ZSZ_minus_I_rms": d["ns"]["residual"], "tol": 1e-6,
-            "precision": "fp64", "recompress_dense": True,
-            "phases_ms_total": {k: d["profile"][k] for k in
-                                ("ms_dense", "ms_lowrank", "ms_compress")},
-            "svd": {k: d["profile"][k] for k in ("svd_blocks", "svd_sweeps_fp32",
-                                                  "svd_sweeps_fp64", "svd_early_dense")},
-            "roofline_recompress": recompress_roofline(d["profile"], fp64_peak),
-            "rank_distribution_iter5": {
-                k: {f: d[k][f] for f in ("zero", "dense", "low_rank", "lr_rank_mean",
-                                         "lr_rank_max")}
-                for k in ("S", "X_5", "T_5", "Y_5", "Z_5", "Z_final")}}
+    d = diagnostics.ns_rank_distribution(ctx, sm, 5 if snapshot else 0)
+    out = {"workload": "3D lattice %s matrix, %s sites x 16 points, N=%d, %d clusters of "
+                       "64..256, built at eps_lr=%g, iterates truncated at %g" % (
+                           what, shape_txt, w.n, len(w.row_sizes), w.eps_lr, EPS_NS_LATTICE),
+           "ms_per_iteration": d["ns"]["ms_per_iter"], "iterations": d["ns"]["iters"],
+           "ms_residual": d["ns"]["ms_residual"], "proxy_final": d["ns"]["proxy"][-1],
+           "residual_ZSZ_minus_I_rms": d["ns"]["residual"], "tol": 1e-6,
+           "residual_met": d["ns"]["residual_met"], "proxy_met": d["ns"]["proxy_met"],
+           "precision": precision if precision == "fp64" else
+                        "%s, fp64 below proxy 1e-3" % precision,
+           "recompress_dense": True,
+           "phases_ms_total": {k: d["profile"][k] for k in
+                               ("ms_dense", "ms_lowrank", "ms_compress")},
+           "svd": {k: d["profile"][k] for k in ("svd_blocks", "svd_sweeps_fp32",
+                                                 "svd_sweeps_fp64", "svd_early_dense",
+                                                 "svd_prereduced")},
+           "roofline_recompress": recompress_roofline(d["profile"], fp64_peak)}
+    if snapshot:
+        out["rank_distribution_iter5"] = {
+            k: {f: d[k][f] for f in ("zero", "dense", "low_rank", "lr_rank_mean", "lr_rank_max")}
+            for k in ("S", "X_5", "T_5", "Y_5", "Z_5", "Z_final") if d.get(k)}
+    return out
 
 
 def recompress_roofline(prof, fp64_peak):

@@ -10,6 +10,13 @@
  *  - Every call returns an int status: CLR_OK (0) or a negative CLR_E* code.  No C++
  *    exception crosses this boundary.  clr_strerror() names a code; clr_last_error() gives
  *    the context's last detailed message.
+ *  - Errors found on the device (a bounded device-side wait that gave up, non-finite data met
+ *    by recompression, an overflowing triple list) raise a sticky flag in the context's
+ *    workspaces.  Asynchronous calls cannot report it; the next call that synchronises (NS
+ *    iterations, clr_multiply_into with stats, clr_check, clr_multiply_host_stream,
+ *    clr_multiply_batched, clr_multiply_backward, clr_batch_create, clr_mat_from_dense)
+ *    returns it as CLR_ETIMEOUT
+ *    or CLR_EINVAL and clears it.  The outputs of the failed work are then unspecified.
  *  - A CLR matrix (clr_mat_t) is an opaque, library-owned handle living on the context's
  *    device.  Handles returned through an out-pointer are new and owned by the caller, who
  *    releases them with clr_mat_free().  Input matrices are never modified.
@@ -73,8 +80,10 @@ typedef struct clr_opts {
   int precision;         /* CLR_PREC_* for dense x dense tile products */
   int recompress_dense;  /* 1: dense-accumulated C tiles are re-tested for low rank */
   int ns_max_iter;       /* Newton–Schulz: maximum number of Z updates */
-  double ns_tol;         /* NS stops when ||X_n - I||_F / sqrt(N) <= ns_tol; 0 runs
-                            exactly ns_max_iter updates */
+  double ns_tol;         /* stated error of NS: the loop stops when ||X_n - I||_F / sqrt(N)
+                            <= ns_tol, and succeeds when the returned Z has
+                            ||alpha Z S Z - I||_F / sqrt(N) <= ns_tol; 0 runs exactly
+                            ns_max_iter updates */
   double ns_alpha;       /* NS scale alpha; 0 = 1 / (1.01 * power-iteration estimate) */
   int ns_power_steps;    /* power iterations for the alpha estimate (default 30) */
   int ns_fp64_tail;      /* precision ladder: switch tile products to FP64 once
@@ -88,7 +97,15 @@ typedef struct clr_opts {
                             (greedy column pivoting, truncated at ||R_22||_F <= eps_lr; the
                             paper's construction, Section 4.1) instead of the truncated SVD
                             (the minimal rank for the same error) */
-  int reserved[6];
+  int wait_timeout_us;   /* limit of every bounded device-side wait of the tensor-core
+                            pipeline, in microseconds (0: 2 s).  A wait that runs out stops
+                            the kernel cleanly and raises CLR_ETIMEOUT at the next
+                            synchronising call */
+  int svd_no_prereduce;  /* 1: dense truncated SVDs (recompression of densely accumulated
+                            tiles, clr_mat_from_dense) always run the one-sided Jacobi on the
+                            whole block; 0 (default): a column-pivoted QR stopped at eps/16
+                            first reduces blocks of low numerical rank to a k x q factor */
+  int reserved[4];
 } clr_opts;
 
 /* Summary of a CLR matrix (clr_mat_info). */
@@ -120,12 +137,16 @@ typedef struct clr_product_stats {
 #define CLR_NS_MAX_HISTORY 256
 typedef struct clr_ns_stats {
   int32_t iters;            /* Z updates applied */
-  int32_t converged;
+  int32_t converged;        /* the stated error was met: residual <= ns_tol (ns_tol > 0), or
+                               ns_tol == 0 (a fixed number of iterations) */
   double alpha;
   double residual;          /* ||alpha Z S Z - I||_F / sqrt(N) of the returned Z */
   double proxy[CLR_NS_MAX_HISTORY]; /* ||X_n - I||_F / sqrt(N), n = 0..iters */
   int32_t precision_used[CLR_NS_MAX_HISTORY];
   double ms_total;          /* device time of the iteration loop (CUDA events) */
+  int32_t proxy_met;        /* the loop's stopping test ||X_n - I||_F / sqrt(N) <= ns_tol held */
+  int32_t residual_met;     /* residual <= ns_tol */
+  double ms_residual;       /* device time of the final residual (two CLR products) */
 } clr_ns_stats;
 
 /* ---- errors and options ------------------------------------------------------------------ */
@@ -173,6 +194,9 @@ int clr_mat_info(clr_ctx_t ctx, clr_mat_t m, clr_info* info, void* stream);
 int clr_mat_shape(clr_mat_t m, int64_t* n_rows, int64_t* n_cols, int* n_rt, int* n_ct);
 int clr_mat_copy(clr_ctx_t ctx, clr_mat_t src, clr_mat_t dst, void* stream);
 int clr_mat_transpose(clr_ctx_t ctx, clr_mat_t src, clr_mat_t* out, void* stream);
+/* clr_mat_free returns the storage to the caching allocator below, whose buffers are handed to
+ * later allocations without stream ordering: the device work that reads or writes `m` must have
+ * completed (synchronise its stream first). */
 int clr_mat_free(clr_ctx_t ctx, clr_mat_t m);
 /* Matrix storage comes from a process-wide caching allocator: freed buffers are kept (up to
  * 64 GiB) and reused by later matrices of the same size.  clr_mem_trim returns the context
@@ -197,6 +221,14 @@ int clr_multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, doub
                       clr_product_stats* stats, void* stream);
 int clr_multiply_batched(clr_ctx_t ctx, int n, const clr_mat_t* a, const clr_mat_t* b,
                          clr_mat_t* c, void* stream);
+/* clr_multiply_backward: the adjoint of C = A B (Section 4.1's block product run backwards,
+ * with truncation treated as the identity): given cbar = dL/dC (A's row clusters, B's column
+ * clusters), returns abar = cbar B^T (A's clusters) and bbar = A^T cbar (B's clusters), each a
+ * CLR product of the transposed operand recompressed at eps_lr in the context's precision.
+ * Either output pointer may be NULL (that adjoint is skipped), not both.  The outputs are new
+ * handles.  Synchronises `stream` (the transposed operands are freed after the products). */
+int clr_multiply_backward(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t cbar,
+                          clr_mat_t* abar, clr_mat_t* bbar, void* stream);
 
 /* Dense product of host matrices through the CLR product, streamed: C = A B with A (m x k),
  * B (k x n) and C (m x n) row-major in page-locked host memory (leading dimensions lda, ldb,
@@ -225,6 +257,8 @@ int clr_multiply_host_stream(clr_ctx_t ctx, const double* a, int64_t lda, const 
  *   run on up to 4 parallel branches with their own workspaces (longest-first assignment).
  *   Synchronises `stream`.  The inputs must stay alive and unchanged while the batch exists.
  * clr_batch_run: one graph launch computing every product on `stream` (replayable).
+ * clr_batch_free: waits for the batch's last launch (an event recorded by clr_batch_run), then
+ *   frees its outputs and workspaces.
  * clr_batch_output: the i-th output (owned by the batch until clr_batch_free).
  * clr_batch_tuning: the chosen precision, CTAs per SM and branch of product i.
  * clr_autotune_save / clr_autotune_load: the autotuner's cache as a text file (one line per
@@ -251,13 +285,19 @@ int clr_lincomb(clr_ctx_t ctx, double a, clr_mat_t x, double b, clr_mat_t y, dou
  * X_n = alpha Y_n Z_n, T_n = (15 I - 10 X_n + 3 X_n^2)/8, Z_{n+1} = Z_n T_n,
  * Y_{n+1} = T_n Y_n, Z_0 = I, Y_0 = S; returns Z = sqrt(alpha) Z_n.  Every product is a CLR
  * product at the context's eps_lr / eps_sp; T is formed by clr_lincomb.  Synchronises
- * `stream` once per iteration to read the convergence scalar.  Returns CLR_ENOCONV (with *z
- * still set) when ns_tol > 0 is not reached.  With `tape` non-NULL the iterates (Y_n, Z_n)
+ * `stream` once per iteration to read the loop's stopping scalar ||X_n - I||_F / sqrt(N).
+ * With ns_tol > 0 the loop stops once that proxy is <= ns_tol, and the stated error is then
+ * checked on the returned Z: the residual ||alpha Z S Z - I||_F / sqrt(N) (two more CLR
+ * products).  Returns CLR_ENOCONV (with *z still set) unless that residual is <= ns_tol: the
+ * proxy can meet the tolerance while truncation at eps_lr holds the residual above it.  With `tape` non-NULL the iterates (Y_n, Z_n)
  * are kept for clr_sqrt_inv_backward (checkpointed every iteration); the tape owns copies of
  * everything it needs, so S may be freed before the backward call. */
 int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s, clr_mat_t* z, clr_ns_stats* stats,
                  clr_tape_t* tape, void* stream);
 /* ||alpha Z S Z - I||_F / sqrt(N) for z = sqrt(alpha) Z (two CLR products); synchronises. */
+/* clr_check: synchronises `stream` and returns (and clears) any error a kernel raised since the
+ * last synchronising call. */
+int clr_check(clr_ctx_t ctx, void* stream);
 int clr_ns_residual(clr_ctx_t ctx, clr_mat_t s, clr_mat_t z, double* out, void* stream);
 /* Adjoint of clr_sqrt_inv for L = trace(W^T-weighted) losses: given zbar = dL/dZ (Z the
  * returned sqrt(alpha) Z_n), returns sbar = dL/dS by running the NS recurrences backwards
@@ -297,6 +337,7 @@ typedef struct clr_profile {
                                   products, orthonormalisations 2q^3, projections 2pq^2, Jacobi
                                   4pq^2 per FP64 sweep, factor recovery / re-expansion */
   double svd_flops_fp32;       /* algorithmic FP32 flops: Jacobi 4pq^2 per FP32 sweep */
+  int64_t svd_prereduced;      /* dense blocks truncated through the pivoted-QR pre-reduction */
 } clr_profile;
 int clr_profile_enable(clr_ctx_t ctx, int on);
 int clr_profile_read(clr_ctx_t ctx, clr_profile* out);
@@ -310,14 +351,15 @@ int clr_probe_fp64_rate(int device, double* tflops);
  * difference.  x: n doubles on the device (finite); out: terms x n bf16 bit patterns on the
  * device, term-major (out[t * n + i]).  terms: 2 (bf16x3) or 3 (bf16x6).  Runs on `stream`
  * (a cudaStream_t, may be null), asynchronous.  Device pointers are the caller's.  CLR_EINVAL
- * for n < 0, other term counts, null pointers with n > 0, or n >= 2^40; CLR_ECUDA when the
- * launch fails. */
+ * for n < 0, other term counts, null pointers with n > 0, or n > 2^40 - 512 (one launch covers
+ * at most 2^31 - 1 blocks of 256 value pairs); CLR_ECUDA when the launch fails. */
 int clr_split_bf16(const double* x, int64_t n, int terms, uint16_t* out, void* stream);
 
 /* ---- allocation-free single-block compression ---------------------------------------------
- * clr_block_compress_noalloc: the truncated SVD of one m x n block at Frobenius error eps, the
- * same per-block computation as clr_mat_from_dense (drop threshold 0), for callers that must
- * not allocate device memory: code running while a CUDA stream is being captured into a graph,
+ * clr_block_compress_noalloc: the truncated SVD of one m x n block at Frobenius error eps (an
+ * FP64 one-sided Jacobi SVD; its result matches clr_mat_from_dense with drop threshold 0 to
+ * within eps, and the rank may differ by one where the singular-value tail crosses eps), for
+ * callers that must not allocate device memory: code running while a CUDA stream is being captured into a graph,
  * real-time or embedded hosts whose device memory is planned ahead, and plugins living inside a
  * framework whose allocator owns all device memory.  It calls no cudaMalloc, cudaFree or
  * allocating library routine and needs no context.  The paper has no counterpart: it is a
@@ -327,11 +369,17 @@ int clr_split_bf16(const double* x, int64_t n, int terms, uint16_t* out, void* s
  *   x_out, w_out device buffers for X (m x min(m,n)) and W (n x min(m,n)), column-major with
  *                leading dimensions m and n; written only when the result is low rank
  *   sigma_out    optional device buffer of min(m,n) singular values, descending
- *   status       device int32[3]: kind (CLR_KIND_*), rank, error flag (3: non-finite input)
+ *   status       device int32[3]: kind (CLR_KIND_*), rank, error flag: 0 ok; 3 non-finite
+ *                input (the block is then reported as kind ZERO: read status[2] before
+ *                trusting status[0]); 4 the Jacobi sweeps reached max_sweeps before
+ *                converging (the truncation is then based on column norms that may be
+ *                inexact)
  * Scratch: a fixed 1 MiB device array compiled into the library (2 x 256 x 256 doubles) that
  * every GPU loading the library holds until exit.  The first call on a device looks up the
  * array's device address (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture.  Every call shares the array and overwrites it; calls that overlap
+ * before any stream capture.  That address is cached for the life of the process: after a
+ * cudaDeviceReset of that device the cache is stale and the entry point must not be called
+ * again.  Every call shares the array and overwrites it; calls that overlap
  * on the GPU race, so issue them on one stream (or serialise them).  Asynchronous on `stream`. */
 int clr_block_compress_noalloc(int device, const double* block, int64_t ld, int m, int n,
                                double eps, int max_sweeps, double* x_out, double* w_out,

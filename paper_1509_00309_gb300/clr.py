@@ -31,7 +31,8 @@ class ClrOpts(C.Structure):
                 ("ns_power_steps", C.c_int), ("ns_fp64_tail", C.c_int),
                 ("ns_ladder_switch", C.c_double), ("jacobi_max_sweeps", C.c_int),
                 ("ns_snapshot_iter", C.c_int), ("build_rrqr", C.c_int),
-                ("reserved", C.c_int * 6)]
+                ("wait_timeout_us", C.c_int), ("svd_no_prereduce", C.c_int),
+                ("reserved", C.c_int * 4)]
 
 
 class ClrInfo(C.Structure):
@@ -51,7 +52,9 @@ class ClrProductStats(C.Structure):
 class ClrNsStats(C.Structure):
     _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("alpha", C.c_double),
                 ("residual", C.c_double), ("proxy", C.c_double * NS_MAX_HISTORY),
-                ("precision_used", C.c_int32 * NS_MAX_HISTORY), ("ms_total", C.c_double)]
+                ("precision_used", C.c_int32 * NS_MAX_HISTORY), ("ms_total", C.c_double),
+                ("proxy_met", C.c_int32), ("residual_met", C.c_int32),
+                ("ms_residual", C.c_double)]
 
 
 class ClrProfile(C.Structure):
@@ -62,7 +65,7 @@ class ClrProfile(C.Structure):
                 ("ms_finalize", C.c_double), ("svd_blocks", C.c_int64),
                 ("svd_sweeps_fp32", C.c_int64), ("svd_sweeps_fp64", C.c_int64),
                 ("svd_early_dense", C.c_int64), ("svd_flops_fp64", C.c_double),
-                ("svd_flops_fp32", C.c_double)]
+                ("svd_flops_fp32", C.c_double), ("svd_prereduced", C.c_int64)]
 
 
 _VP = C.c_void_p
@@ -91,10 +94,13 @@ _SIGNATURES = {
     "clr_multiply_into": (C.c_int, [_VP, _VP, _VP, _VP, C.c_double,
                                     C.POINTER(ClrProductStats), _VP]),
     "clr_multiply_batched": (C.c_int, [_VP, C.c_int, _VP, _VP, _VP, _VP]),
+    "clr_multiply_backward": (C.c_int, [_VP, _VP, _VP, _VP, C.POINTER(_VP), C.POINTER(_VP),
+                                        _VP]),
     "clr_lincomb": (C.c_int, [_VP, C.c_double, _VP, C.c_double, _VP, C.c_double, _VP, _VP]),
     "clr_sqrt_inv": (C.c_int, [_VP, _VP, C.POINTER(_VP), C.POINTER(ClrNsStats),
                                C.POINTER(_VP), _VP]),
     "clr_ns_residual": (C.c_int, [_VP, _VP, _VP, C.POINTER(C.c_double), _VP]),
+    "clr_check": (C.c_int, [_VP, _VP]),
     "clr_sqrt_inv_backward": (C.c_int, [_VP, _VP, _VP, C.POINTER(_VP), _VP]),
     "clr_tape_free": (C.c_int, [_VP, _VP]),
     "clr_ns_snapshot": (C.c_int, [_VP, C.c_int, C.POINTER(_VP)]),
@@ -289,6 +295,11 @@ class Context:
             setattr(o, k, v)
         self._check(load().clr_set_opts(self.handle, C.byref(o)))
 
+    def check(self, stream=None):
+        """Synchronise and raise any error a kernel reported since the last synchronising
+        call (clr_check)."""
+        self._check(load().clr_check(self.handle, _stream(stream)))
+
     def mem_trim(self):
         self._check(load().clr_mem_trim(self.handle))
 
@@ -372,6 +383,19 @@ class Context:
                 "max_rank_sum": s.max_rank_sum, "precision": PREC_NAME[s.precision],
                 "n_tiles_tensor": s.n_tiles_tensor}
 
+    def multiply_backward(self, a: Matrix, b: Matrix, cbar: Matrix, need_a: bool = True,
+                          need_b: bool = True, stream=None):
+        """Adjoint of C = A B: (cbar B^T, A^T cbar) as CLR matrices (clr_multiply_backward);
+        an adjoint not asked for is None."""
+        ha, hb = C.c_void_p(), C.c_void_p()
+        self._check(load().clr_multiply_backward(self.handle, a.handle, b.handle, cbar.handle,
+                                                 C.byref(ha) if need_a else None,
+                                                 C.byref(hb) if need_b else None,
+                                                 _stream(stream)))
+        abar = Matrix(self, ha.value, a.row_sizes, a.col_sizes) if need_a else None
+        bbar = Matrix(self, hb.value, b.row_sizes, b.col_sizes) if need_b else None
+        return abar, bbar
+
     def multiply_host_stream(self, a, b, c, row_sizes, inner_sizes=None, col_sizes=None,
                              n_chunks: int = 4, stream=None):
         """C = A B for page-locked host torch tensors (row-major float64), streamed: A in two
@@ -439,7 +463,9 @@ class Context:
         stats = {"iters": st.iters, "converged": bool(st.converged), "alpha": st.alpha,
                  "residual": st.residual, "proxy": list(st.proxy[:n]),
                  "precision_used": [PREC_NAME[p] for p in st.precision_used[:n]],
-                 "ms_total": st.ms_total, "status": status}
+                 "ms_total": st.ms_total, "proxy_met": bool(st.proxy_met),
+                 "residual_met": bool(st.residual_met), "ms_residual": st.ms_residual,
+                 "status": status}
         return Matrix(self, z.value, s.row_sizes, s.col_sizes), stats, \
             (Tape(self, tape.value) if keep_tape else None)
 
@@ -492,10 +518,25 @@ def block_compress_noalloc(block, eps: float, x_out, w_out, status, sigma_out=No
     """Truncated SVD of one dense block (a column-major view: a CUDA float64 tensor whose
     transpose is contiguous, or any tensor with stride(0) == 1) into caller-owned device
     buffers, without any device allocation (see clr_block_compress_noalloc in clr.h)."""
+    import torch
     m, n = block.shape
+    if not block.is_cuda or block.dtype != torch.float64:
+        raise ValueError("block must be a CUDA float64 tensor")
     if block.stride(0) != 1:
         raise ValueError("block must be column-major (stride(0) == 1)")
     ld = block.stride(1) if n > 1 else m
+    k = min(m, n)
+    # the kernel writes m*k, n*k and k doubles and 3 int32: refuse buffers it would overrun
+    for name, t, need, dt in (("x_out", x_out, m * k, torch.float64),
+                              ("w_out", w_out, n * k, torch.float64),
+                              ("sigma_out", sigma_out, k, torch.float64),
+                              ("status", status, 3, torch.int32)):
+        if t is None and name == "sigma_out":
+            continue
+        if t is None or not t.is_cuda or t.device != block.device or t.dtype != dt or \
+                not t.is_contiguous() or t.numel() < need:
+            raise ValueError("%s must be a contiguous %s tensor on %s with at least %d "
+                             "elements" % (name, dt, block.device, need))
     st = load().clr_block_compress_noalloc(block.device.index or 0, _ptr(block), ld, m, n,
                                            float(eps), int(max_sweeps), _ptr(x_out),
                                            _ptr(w_out), _ptr(sigma_out), _ptr(status),

@@ -159,7 +159,7 @@ struct clr_ctx_s {
   // workspaces (grow-only)
   std::vector<std::unique_ptr<WorkSet>> wsets;
   WorkSet* cur = nullptr;  // workspace set used by the next product
-  DevBuf small, upload, jstats;  // jstats: 6 SVD counters accumulated while profiling
+  DevBuf small, upload, jstats;  // jstats: 7 SVD counters accumulated while profiling
   bool capturing = false;
   // autotuner cache: shape key -> tuning and measured ms
   std::map<std::string, std::pair<Tuning, double>> tune_cache;
@@ -334,13 +334,61 @@ int alloc_mat(clr_ctx_t ctx, int nr, const int32_t* rs, int nc, const int32_t* c
 
 bool same_clusters(const std::vector<int>& a, const std::vector<int>& b) { return a == b; }
 
+// Frees the matrices it holds when it goes out of scope, except those handed out by keep().
+struct MatGuard {
+  std::vector<clr_mat_t> v;
+  ~MatGuard() {
+    for (clr_mat_t m : v) free_mat(m);
+  }
+  clr_mat_t keep(clr_mat_t m) {
+    v.erase(std::find(v.begin(), v.end(), m));
+    return m;
+  }
+};
+
+
+// The plan counters of a workspace set, zeroed (the sticky error flag included) when first
+// allocated; plans clear only the fields before the flag.
+int ensure_counters(clr_ctx_t ctx, WorkSet* w) {
+  if (w->counters.p) return CLR_OK;
+  CLR_CUDA(w->counters.ensure(sizeof(PlanCounters)));
+  CLR_CUDA(cudaMemset(w->counters.p, 0, sizeof(PlanCounters)));
+  return CLR_OK;
+}
+
+// Reads and clears the sticky device error flags of the context's workspace sets and of
+// `extra` (kernels raise them on a bounded-wait timeout or on bad data).  The streams that used
+// those sets must have been synchronised.
+int take_device_error(clr_ctx_t ctx, const std::vector<std::unique_ptr<WorkSet>>* extra = nullptr) {
+  int worst = 0;
+  auto visit = [&](WorkSet* w) -> cudaError_t {
+    if (!w->counters.p) return cudaSuccess;
+    int* pe = &((PlanCounters*)w->counters.p)->err;
+    int e = 0;
+    cudaError_t ce = cudaMemcpy(&e, pe, sizeof(int), cudaMemcpyDeviceToHost);
+    if (ce == cudaSuccess && e) {
+      ce = cudaMemset(pe, 0, sizeof(int));
+      if (worst != 1) worst = e;
+    }
+    return ce;
+  };
+  for (auto& w : ctx->wsets) CLR_CUDA(visit(w.get()));
+  if (extra)
+    for (auto& w : *extra) CLR_CUDA(visit(w.get()));
+  if (worst == 1) return fail(ctx, CLR_ETIMEOUT, "a device-side wait timed out");
+  if (worst == 3) return fail(ctx, CLR_EINVAL, "non-finite data met on the device");
+  if (worst) return fail(ctx, CLR_EINVAL, "device reported bad data (flag " + std::to_string(worst) + ")");
+  return CLR_OK;
+}
+
 // Grow the context workspaces needed by a plan over nI x nJ tiles and nK inner clusters.
 int make_plan(clr_ctx_t ctx, int nI, int nJ, int nK, Plan* p) {
   const size_t nt = (size_t)nI * nJ;
   CLR_CUDA(ctx->cur->plan_ints.ensure(10 * nt * sizeof(int)));
   const int64_t max_tr = (int64_t)nt * nK;
   CLR_CUDA(ctx->cur->triples.ensure((size_t)max_tr * sizeof(Triple)));
-  CLR_CUDA(ctx->cur->counters.ensure(sizeof(PlanCounters)));
+  int st = ensure_counters(ctx, ctx->cur);
+  if (st) return st;
   int* base = (int*)ctx->cur->plan_ints.p;
   p->nI = nI;
   p->nJ = nJ;
@@ -638,13 +686,17 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
   cudaError_t e = ctx->cur->ws.ensure(2 * (size_t)m->n_rows * m->n_cols * sizeof(double));
   if (e == cudaSuccess)
     e = ctx->cur->scratch.ensure((size_t)grid_of(ctx, 2) * scratch_per_cta() * sizeof(double));
-  if (e == cudaSuccess) e = ctx->cur->counters.ensure(sizeof(PlanCounters));
   if (e != cudaSuccess) {
     free_mat(m);
     return cuda_fail(ctx, e, "from_dense workspace");
   }
+  st = ensure_counters(ctx, ctx->cur);
+  if (st) {
+    free_mat(m);
+    return st;
+  }
   PlanCounters* pc = (PlanCounters*)ctx->cur->counters.p;
-  cudaMemsetAsync(pc, 0, sizeof(PlanCounters), s);
+  cudaMemsetAsync(pc, 0, kPlanCountersClear, s);
   if (eps_lr == 0.0) {
     // every kept block is dense: a coalesced layout copy, then norms decide what is dropped
     launch_rowmajor_to_pool(m->view(), m->d_row_idx, src, lda, s);
@@ -672,20 +724,21 @@ extern "C" int clr_mat_from_dense(clr_ctx_t ctx, const double* a, int64_t lda, i
     launch_compress_dense(m->view(), nullptr, nullptr, (const int*)ctx->cur->order.p, src, lda,
                           (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p,
                           eps_lr, drop_norm, 0, ctx->opts.build_rrqr ? 1 : 0,
+                          ctx->opts.svd_no_prereduce ? 0 : 1,
                           ctx->opts.jacobi_max_sweeps, grid_of(ctx, 2), &pc->err, &pc->sched[2],
                           jst(ctx), s);
   }
   e = cudaGetLastError();
-  int errflag = 0;
-  if (e == cudaSuccess) e = cudaMemcpyAsync(&errflag, &pc->err, sizeof(int), cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
     free_mat(m);
     return cuda_fail(ctx, e, "from_dense");
   }
-  if (errflag) {
+  st = take_device_error(ctx);  // 3: a block with non-finite values
+  if (st) {
     free_mat(m);
-    return fail(ctx, CLR_EINVAL, "non-finite input");
+    if (st == CLR_EINVAL) ctx->err = "non-finite input (or an earlier device error)";
+    return st;
   }
   *out = m;
   return CLR_OK;
@@ -922,6 +975,8 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
   g.n_sm = ctx->n_sm;
   g.err = &p.counters->err;
   g.encode_fn = ctx->encode_fn;
+  g.wait_ns = ctx->opts.wait_timeout_us > 0 ? 1000ull * (unsigned long long)ctx->opts.wait_timeout_us
+                                            : 2000000000ull;
   // norms in the epilogue when the dense tiles are final (not re-tested) and the clusters are
   // wide enough for its per-warp grouping
   const bool fuse = !ctx->opts.recompress_dense &&
@@ -998,7 +1053,8 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
                      lr_grid, &p.counters->err, &p.counters->sched[1], jst(ctx), s);
   launch_compress_dense(cv, p.l_dcomp_s, &p.counters->n_dcomp, nullptr, nullptr, 0,
                         (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p,
-                        eps_lr, 0.0, 0, 0, o.jacobi_max_sweeps, lr_grid, &p.counters->err,
+                        eps_lr, 0.0, 0, 0, o.svd_no_prereduce ? 0 : 1, o.jacobi_max_sweeps,
+                        lr_grid, &p.counters->err,
                         &p.counters->sched[2], jst(ctx), s);
   CLR_CHECK_LAUNCH("recompression");
   prof_launches(ctx, 2);
@@ -1029,8 +1085,8 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
     stats->precision = prec;
     stats->n_tiles_tensor =
         prec == CLR_PREC_FP64 ? 0 : (int32_t)(pc.by_mode[1] + pc.n_gemm_dacc);
-    if (pc.err == 1) return fail(ctx, CLR_ETIMEOUT, "a device-side wait timed out");
-    if (pc.err) return fail(ctx, CLR_EINVAL, "device reported bad data (flag " + std::to_string(pc.err) + ")");
+    st = take_device_error(ctx);
+    if (st) return st;
   }
   return CLR_OK;
 }
@@ -1045,8 +1101,8 @@ extern "C" int clr_profile_enable(clr_ctx_t ctx, int on) {
   std::memset(&ctx->prof, 0, sizeof(ctx->prof));
   ctx->prof_on = on != 0;
   if (ctx->prof_on) {
-    CLR_CUDA(ctx->jstats.ensure(6 * sizeof(unsigned long long)));
-    CLR_CUDA(cudaMemset(ctx->jstats.p, 0, 6 * sizeof(unsigned long long)));
+    CLR_CUDA(ctx->jstats.ensure(7 * sizeof(unsigned long long)));
+    CLR_CUDA(cudaMemset(ctx->jstats.p, 0, 7 * sizeof(unsigned long long)));
   }
   return CLR_OK;
 }
@@ -1076,7 +1132,7 @@ extern "C" int clr_profile_read(clr_ctx_t ctx, clr_profile* out) {
     ctx->prof_events.clear();
   }
   if (ctx->jstats.p) {
-    unsigned long long j[6];
+    unsigned long long j[7];
     CLR_CUDA(cudaMemcpy(j, ctx->jstats.p, sizeof(j), cudaMemcpyDeviceToHost));
     ctx->prof.svd_blocks = (int64_t)j[0];
     ctx->prof.svd_sweeps_fp32 = (int64_t)j[1];
@@ -1084,6 +1140,7 @@ extern "C" int clr_profile_read(clr_ctx_t ctx, clr_profile* out) {
     ctx->prof.svd_early_dense = (int64_t)j[3];
     ctx->prof.svd_flops_fp64 = (double)j[4];
     ctx->prof.svd_flops_fp32 = (double)j[5];
+    ctx->prof.svd_prereduced = (int64_t)j[6];
   }
   *out = ctx->prof;
   return CLR_OK;
@@ -1117,6 +1174,58 @@ extern "C" int clr_multiply(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t* 
   return CLR_OK;
 }
 
+extern "C" int clr_multiply_backward(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t cbar,
+                                     clr_mat_t* abar, clr_mat_t* bbar, void* stream) {
+  // Adjoint of C = A B (Section 4.1's block product, truncation treated as the identity):
+  // Abar = Cbar B^T and Bbar = A^T Cbar, each a CLR product recompressed at eps_lr.
+  if (!ctx || !a || !b || !cbar || (!abar && !bbar)) return CLR_EINVAL;
+  if (abar) *abar = nullptr;
+  if (bbar) *bbar = nullptr;
+  if (!same_clusters(a->col_sizes, b->row_sizes))
+    return fail(ctx, CLR_EINVAL, "inner clusters of A and B differ");
+  if (!same_clusters(cbar->row_sizes, a->row_sizes) ||
+      !same_clusters(cbar->col_sizes, b->col_sizes))
+    return fail(ctx, CLR_EINVAL, "Cbar clusters do not match A rows / B columns");
+  cudaSetDevice(ctx->device);
+  cudaStream_t s = as_stream(stream);
+  MatGuard g;
+  Tuning t;
+  int st = CLR_OK;
+  clr_mat_t ab = nullptr, bb = nullptr;
+  if (abar) {
+    clr_mat_t bt = nullptr;
+    if ((st = alloc_mat(ctx, b->nc, b->col_sizes.data(), b->nr, b->row_sizes.data(), &bt)))
+      return st;
+    g.v.push_back(bt);
+    launch_transpose(b->view(), bt->view(), s);
+    CLR_CHECK_LAUNCH("transpose");
+    if ((st = alloc_mat(ctx, a->nr, a->row_sizes.data(), a->nc, a->col_sizes.data(), &ab)))
+      return st;
+    g.v.push_back(ab);
+    t.prec = choose_precision(ctx, cbar, bt);
+    if ((st = multiply_into(ctx, cbar, bt, ab, 1.0, t, nullptr, s))) return st;
+  }
+  if (bbar) {
+    clr_mat_t at = nullptr;
+    if ((st = alloc_mat(ctx, a->nc, a->col_sizes.data(), a->nr, a->row_sizes.data(), &at)))
+      return st;
+    g.v.push_back(at);
+    launch_transpose(a->view(), at->view(), s);
+    CLR_CHECK_LAUNCH("transpose");
+    if ((st = alloc_mat(ctx, b->nr, b->row_sizes.data(), b->nc, b->col_sizes.data(), &bb)))
+      return st;
+    g.v.push_back(bb);
+    t.prec = choose_precision(ctx, at, cbar);
+    if ((st = multiply_into(ctx, at, cbar, bb, 1.0, t, nullptr, s))) return st;
+  }
+  // the transposes go back to the allocator only once the products that read them are done
+  CLR_CUDA(cudaStreamSynchronize(s));
+  if ((st = take_device_error(ctx))) return st;
+  if (abar) *abar = g.keep(ab);
+  if (bbar) *bbar = g.keep(bb);
+  return CLR_OK;
+}
+
 extern "C" int clr_lincomb(clr_ctx_t ctx, double a, clr_mat_t x, double b, clr_mat_t y,
                            double diag, clr_mat_t out, void* stream) {
   if (!ctx || !x || !y || !out) return CLR_EINVAL;
@@ -1147,7 +1256,8 @@ extern "C" int clr_lincomb(clr_ctx_t ctx, double a, clr_mat_t x, double b, clr_m
                      jst(ctx), s);
   launch_compress_dense(ov, p.l_dcomp_s, &p.counters->n_dcomp, nullptr, nullptr, 0,
                         (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p,
-                        o.eps_lr, 0.0, 0, 0, o.jacobi_max_sweeps, grid, &p.counters->err,
+                        o.eps_lr, 0.0, 0, 0, o.svd_no_prereduce ? 0 : 1, o.jacobi_max_sweeps,
+                        grid, &p.counters->err,
                         &p.counters->sched[2], jst(ctx), s);
   CLR_CHECK_LAUNCH("lincomb");
   return CLR_OK;
@@ -1237,20 +1347,22 @@ int identity_distance(clr_ctx_t ctx, clr_mat_t x, cudaStream_t s, double* out) {
   double sq = 0.0;
   CLR_CUDA(cudaMemcpyAsync(&sq, part, sizeof(double), cudaMemcpyDeviceToHost, s));
   CLR_CUDA(cudaStreamSynchronize(s));
+  const int st = take_device_error(ctx);
+  if (st) return st;
   *out = std::sqrt(std::max(sq, 0.0) / (double)x->n_rows);
   return CLR_OK;
 }
 
-struct MatGuard {
-  std::vector<clr_mat_t> v;
-  ~MatGuard() {
-    for (clr_mat_t m : v) free_mat(m);
-  }
-  clr_mat_t keep(clr_mat_t m) {
-    v.erase(std::find(v.begin(), v.end(), m));
-    return m;
-  }
-};
+}  // namespace
+
+namespace {
+
+// Truncation of the residual's two products: at most 1/100 of the tolerance, so that their
+// truncation error (at most about 11 eps sqrt(#tiles / N) for ||Z||_2 <= 10, far less in
+// practice) cannot decide whether the residual meets ns_tol.
+double residual_eps(const clr_opts& o) {
+  return o.ns_tol > 0.0 ? std::min(o.eps_lr, 1e-2 * o.ns_tol) : o.eps_lr;
+}
 
 }  // namespace
 
@@ -1267,13 +1379,23 @@ extern "C" int clr_ns_residual(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t z, doub
   st = alloc_mat(ctx, z->nr, z->row_sizes.data(), z->nc, z->col_sizes.data(), &zsz);
   if (st) return st;
   g.v.push_back(zsz);
+  // FP64 products (the residual is the stated error, so it is not taken in split precision)
   Tuning t;
-  t.prec = choose_precision(ctx, z, s_mat);
+  t.prec = CLR_PREC_FP64;
+  t.eps = residual_eps(ctx->opts);
   st = multiply_into(ctx, z, s_mat, zs, 1.0, t, nullptr, s);
   if (st) return st;
   st = multiply_into(ctx, zs, z, zsz, 1.0, t, nullptr, s);
   if (st) return st;
   return identity_distance(ctx, zsz, s, out);
+}
+
+extern "C" int clr_check(clr_ctx_t ctx, void* stream) {
+  if (!ctx) return CLR_EINVAL;
+  cudaSetDevice(ctx->device);
+  CLR_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  if (ctx->side) CLR_CUDA(cudaStreamSynchronize(ctx->side));
+  return take_device_error(ctx);
 }
 
 extern "C" int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t* z_out,
@@ -1329,7 +1451,7 @@ extern "C" int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t* z_out,
   tn.prec = choose_precision(ctx, s_mat, s_mat);
   int& prec = tn.prec;
   int it = 0;
-  bool converged = false;
+  bool proxy_met = false;
   std::vector<double> proxies;
   std::vector<int> precs;
   while (true) {
@@ -1345,7 +1467,7 @@ extern "C" int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t* z_out,
       break;
     }
     if (o.ns_tol > 0.0 && px <= o.ns_tol) {
-      converged = true;
+      proxy_met = true;
       break;
     }
     if (it >= o.ns_max_iter) break;
@@ -1408,30 +1530,62 @@ extern "C" int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t* z_out,
   }
   // Z_out = sqrt(alpha) Z
   clr_mat_t zo = g.keep(Z);
+  auto drop = [&](int code) {
+    free_mat(zo);
+    if (tape)
+      for (size_t i = 0; i < tape->y.size(); ++i) {
+        free_mat(tape->y[i]);
+        free_mat(tape->z[i]);
+      }
+    return code;
+  };
   launch_scale_blocks(zo->view(), std::sqrt(alpha), s);
   cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    free_mat(zo);
-    return cuda_fail(ctx, e, "scale");
+  if (e != cudaSuccess) return drop(cuda_fail(ctx, e, "scale"));
+  // The stated error: the residual of the returned Z (FP64 products, Section 4.2's
+  // convergence target), whenever a tolerance is set or statistics are wanted.
+  double res = NAN;
+  float ms_res = 0.f;
+  if (o.ns_tol > 0.0 || stats) {
+    cudaEvent_t r0, r1;
+    cudaEventCreate(&r0);
+    cudaEventCreate(&r1);
+    cudaEventRecord(r0, s);
+    const int rs = clr_ns_residual(ctx, s_mat, zo, &res, stream);
+    cudaEventRecord(r1, s);
+    cudaEventSynchronize(r1);
+    cudaEventElapsedTime(&ms_res, r0, r1);
+    cudaEventDestroy(r0);
+    cudaEventDestroy(r1);
+    if (rs) return drop(rs);
   }
+  const bool residual_met = o.ns_tol > 0.0 && res <= o.ns_tol;
+  const bool converged = o.ns_tol == 0.0 || residual_met;
   if (stats) {
     std::memset(stats, 0, sizeof(*stats));
     stats->iters = it;
-    stats->converged = converged || o.ns_tol == 0.0;
+    stats->converged = converged ? 1 : 0;
     stats->alpha = alpha;
     for (size_t i = 0; i < proxies.size() && i < CLR_NS_MAX_HISTORY; ++i) {
       stats->proxy[i] = proxies[i];
       stats->precision_used[i] = precs[i];
     }
     stats->ms_total = ms;
-    double res = 0.0;
-    int rs = clr_ns_residual(ctx, s_mat, zo, &res, stream);
-    stats->residual = rs ? NAN : res;
+    stats->residual = res;
+    stats->proxy_met = proxy_met ? 1 : 0;
+    stats->residual_met = residual_met ? 1 : 0;
+    stats->ms_residual = ms_res;
   }
   *z_out = zo;
   if (tape_out) *tape_out = tape.release();
-  if (o.ns_tol > 0.0 && !converged) {
-    ctx->err = "Newton-Schulz did not reach ns_tol";
+  if (!converged) {
+    char msg[160];
+    snprintf(msg, sizeof(msg),
+             proxy_met ? "Newton-Schulz: ||X - I|| met ns_tol but the residual %.3e exceeds it "
+                         "(truncation at eps_lr holds it above the tolerance)"
+                       : "Newton-Schulz did not reach ns_tol within ns_max_iter (residual %.3e)",
+             res);
+    ctx->err = msg;
     return CLR_ENOCONV;
   }
   return CLR_OK;
@@ -1663,7 +1817,9 @@ struct clr_batch_s {
   std::vector<cudaEvent_t> events;              // fork + joins
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
+  cudaEvent_t last_run = nullptr;  // recorded after each launch on the caller's stream
   ~clr_batch_s() {
+    if (last_run) cudaEventDestroy(last_run);
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
     for (cudaEvent_t e : events) cudaEventDestroy(e);
@@ -1734,6 +1890,10 @@ extern "C" int clr_batch_create(clr_ctx_t ctx, int n, const clr_mat_t* a, const 
   }
   ctx->cur = saved;
   CLR_CUDA(cudaStreamSynchronize(s));
+  {
+    const int st = take_device_error(ctx, &bt->wsets);
+    if (st) return st;
+  }
   // capture every product into one graph: fork to nb branches, join on the origin stream
   bt->streams.resize(nb + 1, nullptr);
   for (auto& st : bt->streams) CLR_CUDA(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
@@ -1761,6 +1921,7 @@ extern "C" int clr_batch_create(clr_ctx_t ctx, int n, const clr_mat_t* a, const 
   if (e != cudaSuccess) return cuda_fail(ctx, e, "batch capture");
   e = cudaGraphInstantiate(&bt->exec, bt->graph, 0);
   if (e != cudaSuccess) return cuda_fail(ctx, e, "batch graph instantiate");
+  CLR_CUDA(cudaEventCreateWithFlags(&bt->last_run, cudaEventDisableTiming));
   *out = bt.release();
   return CLR_OK;
 }
@@ -1769,6 +1930,7 @@ extern "C" int clr_batch_run(clr_ctx_t ctx, clr_batch_t batch, void* stream) {
   if (!ctx || !batch || !batch->exec) return CLR_EINVAL;
   cudaSetDevice(ctx->device);
   CLR_CUDA(cudaGraphLaunch(batch->exec, as_stream(stream)));
+  CLR_CUDA(cudaEventRecord(batch->last_run, as_stream(stream)));
   return CLR_OK;
 }
 
@@ -1790,6 +1952,9 @@ extern "C" int clr_batch_tuning(clr_batch_t batch, int i, int* precision, int* l
 extern "C" int clr_batch_free(clr_ctx_t ctx, clr_batch_t batch) {
   if (!batch) return CLR_EINVAL;
   if (ctx) cudaSetDevice(ctx->device);
+  // the graph runs on the caller's stream: wait for its last launch before the outputs and
+  // workspaces go back to the allocator
+  if (batch->last_run) cudaEventSynchronize(batch->last_run);
   for (cudaStream_t s : batch->streams) cudaStreamSynchronize(s);
   delete batch;
   return CLR_OK;
@@ -1811,6 +1976,7 @@ extern "C" int clr_multiply_batched(clr_ctx_t ctx, int n, const clr_mat_t* a,
     cudaError_t e = cudaStreamSynchronize(as_stream(stream));
     if (e != cudaSuccess) st = cuda_fail(ctx, e, "batched products");
   }
+  if (st == CLR_OK) st = take_device_error(ctx, &bt->wsets);
   if (st == CLR_OK)
     for (int i = 0; i < n; ++i) {
       c[i] = bt->c[i];
@@ -1986,5 +2152,5 @@ extern "C" int clr_multiply_host_stream(clr_ctx_t ctx, const double* a, int64_t 
   int flag = 0;
   CLR_CUDA(cudaMemcpy(&flag, w0->host_err.p, sizeof(int), cudaMemcpyDeviceToHost));
   if (flag) return fail(ctx, CLR_EINVAL, "non-finite input in A or B");
-  return CLR_OK;
+  return take_device_error(ctx);
 }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <string>
@@ -72,8 +73,13 @@ struct PlanCounters {
   unsigned long long n_gemm_dacc;  // tiles routed ROUTE_DACC_G
   int n_dense, n_lr, n_qr, n_dacc, n_dcomp;
   int sched[4];   // work counters of the tile-list kernels (next_item), zeroed with the plan
-  int err;  // error flag raised by kernels (bounded waits, bad metadata)
+  // error flag raised by kernels (1: a bounded wait gave up, 2: triple list overflow, 3:
+  // non-finite data).  Sticky: a plan clears only the fields before it, and the host reads and
+  // clears it at its next synchronisation.
+  int err;
 };
+// Bytes of PlanCounters a new plan clears (everything but the sticky error flag).
+constexpr size_t kPlanCountersClear = offsetof(PlanCounters, err);
 
 struct Plan {
   int nI, nJ, nK;
@@ -136,11 +142,15 @@ void launch_compress_qr(const MatView& C, const int* list, const int* count, con
 // SVD (eps = 0 rule) and store every non-dropped block dense.
 // order (list == nullptr only, may be null): the order in which all blocks are visited.
 // rrqr: truncate by rank-revealing QR instead of the SVD.
+// prereduce: reduce blocks of low numerical rank by a column-pivoted QR (stopped at eps/16)
+// before the SVD of the small factor; blocks whose QR passes floor(q/2) steps take the full SVD.
+// jstats (7 counters): SVD blocks, FP32 sweeps, FP64 sweeps, early dense exits, FP64 flops,
+// FP32 flops, pre-reduced blocks.
 void launch_compress_dense(const MatView& C, const int* list, const int* count,
                            const int* order, const double* src, int64_t lds, double* ws,
                            double* svd_scratch, double eps, double drop_norm,
-                           int dense_only, int rrqr, int max_sweeps, int grid, int* err,
-                           int* sched, unsigned long long* jstats, cudaStream_t st);
+                           int dense_only, int rrqr, int prereduce, int max_sweeps, int grid,
+                           int* err, int* sched, unsigned long long* jstats, cudaStream_t st);
 void launch_block_norms(const MatView& M, cudaStream_t st);
 void launch_block_norms_dense(const MatView& M, cudaStream_t st);
 void launch_scale_blocks(const MatView& M, double alpha, cudaStream_t st);
@@ -166,6 +176,7 @@ struct SplitGemmArgs {
   unsigned char* tile_active;  // (M_pad/128) * (N_pad/256) flags
   int n_sm;
   int* err;
+  unsigned long long wait_ns = 2000000000ull;  // give-up limit of the pipeline's waits
   void* encode_fn;    // cuTensorMapEncodeTiled
   // fused norms (may be null): the epilogue adds the squares of the values it writes into
   // route-DENSE C tiles to norm_sq[I * nJ + J] (zeroed before; needs row clusters >= 32 rows

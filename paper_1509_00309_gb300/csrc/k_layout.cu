@@ -49,7 +49,7 @@ __global__ void dense_kinds_kernel(MatView M, double drop_norm, int* err) {
   const int m = M.row_off[I + 1] - M.row_off[I];
   const int n = M.col_off[J + 1] - M.col_off[J];
   const double nrm = M.norm[t];
-  if (!isfinite(nrm)) atomicExch(err, 3);
+  if (!isfinite(nrm)) atomicCAS(err, 0, 3);  // an earlier error keeps precedence
   if (!(nrm >= drop_norm) || nrm == 0.0) {
     M.kind[t] = CLR_KIND_ZERO;
     M.rank[t] = 0;

@@ -140,7 +140,7 @@ void launch_lincomb_plan(double a, const MatView& X, double b, const MatView& Y,
                          const MatView& O, const Plan& p, double* ws, int recompress_dense,
                          cudaStream_t st) {
   const int n = p.nI * p.nJ;
-  cudaMemsetAsync(p.counters, 0, sizeof(PlanCounters), st);
+  cudaMemsetAsync(p.counters, 0, kPlanCountersClear, st);
   lincomb_route_kernel<<<(n + 127) / 128, 128, 0, st>>>(a, X, b, Y, diag, p);
   launch_plan_scan(p, recompress_dense, st);
   lincomb_apply_kernel<<<n, kT, 0, st>>>(a, X, b, Y, diag, O, p, ws);

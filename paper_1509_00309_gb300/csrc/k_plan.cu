@@ -233,7 +233,7 @@ __global__ void plan_fill_kernel(MatView A, MatView B, Plan p) {
       tr.kind = kind;
       tr.col = col + incl - r;
       const int64_t at = pos + __popc(mask & ((1u << lane) - 1u));
-      if (at < p.max_triples) p.triples[at] = tr; else atomicExch(&p.counters->err, 2);
+      if (at < p.max_triples) p.triples[at] = tr; else atomicCAS(&p.counters->err, 0, 2);
     }
     pos += __popc(mask);
     col += __shfl_sync(0xffffffffu, incl, 31);
@@ -249,7 +249,7 @@ void launch_plan(const MatView& A, const MatView& B, const Plan& p, double eps_s
   const int n = p.nI * p.nJ;
   const int threads = 128;  // 4 tiles per block: one warp each
   const int blocks = (int)(((int64_t)n * 32 + threads - 1) / threads);
-  cudaMemsetAsync(p.counters, 0, sizeof(PlanCounters), st);
+  cudaMemsetAsync(p.counters, 0, kPlanCountersClear, st);
   plan_count_kernel<<<blocks, threads, 0, st>>>(A, B, p, eps_sp, gemm_dacc_bound);
   plan_scan_kernel<<<1, kScanThreads, 0, st>>>(p, recompress_dense);
   plan_fill_kernel<<<blocks, threads, 0, st>>>(A, B, p);

@@ -22,9 +22,10 @@
 // per thread) while the next segment runs.  After the last segment the registers are
 // converted to FP64 and stored into the C block pool (column-major blocks: consecutive lanes
 // -> consecutive rows).
-// Every mbarrier wait is bounded (about 2 s of %globaltimer); on a timeout the kernel raises
-// the error flag, stops issuing work, waits (bounded) for its copies and MMAs in flight,
-// frees its TMEM and returns.
+// Every mbarrier wait is bounded (wait_ns of %globaltimer, 2 s unless the context sets another
+// limit); on a timeout the kernel raises the error flag, stops issuing work, waits (bounded by
+// a fixed 2 s, whatever wait_ns is) for its copies and MMAs in flight, frees its TMEM and
+// returns.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -98,8 +99,9 @@ __device__ __forceinline__ bool mbar_try(uint64_t* b, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
-// Bounded wait on the phase of parity `parity`; false on timeout or abort.
-__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag) {
+// Bounded wait on the phase of parity `parity`; false on timeout (after limit_ns) or abort.
+__device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag,
+                          unsigned long long limit_ns) {
   if (mbar_try(b, parity)) return true;
   const unsigned long long t0 = gtimer();
   while (true) {
@@ -107,7 +109,7 @@ __device__ bool mbar_wait(uint64_t* b, uint32_t parity, volatile int* abort_flag
     for (int i = 0; i < 32; ++i)
       if (mbar_try(b, parity)) return true;
     if (*abort_flag) return false;
-    if (gtimer() - t0 > kTimeoutNs) {
+    if (gtimer() - t0 > limit_ns) {
       *abort_flag = 1;
       return false;
     }
@@ -235,7 +237,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     split_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, Epi epi, int n_m, int n_n,
                       int num_k, int M_pad, int N_pad, const unsigned char* tile_active,
-                      int* err) {
+                      int* err, unsigned long long wait_ns) {
   using C = Cfg<TERMS>;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         int mb, nb;
         tile_coords(tile, n_m, n_n, &mb, &nb);
         for (int kc = 0; kc < num_k; ++kc) {
-          if (!mbar_wait(&empty[s], phase ^ 1, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&empty[s], phase ^ 1, abort_flag, wait_ns)) { ok = false; break; }
           unsigned char* st = smem + (size_t)s * C::STAGE;
           mbar_expect_tx(&full[s], C::STAGE);
           issued[s] = true;
@@ -333,11 +335,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int k1 = min(num_k, k0 + C::SEG);
           const int b = seg_count & 1;
           const uint32_t tp = (seg_count >> 1) & 1;
-          if (!mbar_wait(&tempty[b], tp ^ 1, abort_flag)) { ok = false; break; }
+          if (!mbar_wait(&tempty[b], tp ^ 1, abort_flag, wait_ns)) { ok = false; break; }
           fence_after();
           const uint32_t d_tmem = tmem_base + (uint32_t)(b * BN);
           for (int kc = k0; kc < k1; ++kc) {
-            if (!mbar_wait(&full[s], phase, abort_flag)) { ok = false; break; }
+            if (!mbar_wait(&full[s], phase, abort_flag, wait_ns)) { ok = false; break; }
             fence_after();
             const uint32_t st = saddr(smem + (size_t)s * C::STAGE);
 #pragma unroll
@@ -389,7 +391,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int b = seg_count & 1;
         const uint32_t tp = (seg_count >> 1) & 1;
         int got = 0;
-        if (lane == 0) got = mbar_wait(&tfull[b], tp, abort_flag) ? 1 : 0;
+        if (lane == 0) got = mbar_wait(&tfull[b], tp, abort_flag, wait_ns) ? 1 : 0;
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) { ok = false; break; }
         fence_after();
@@ -573,7 +575,8 @@ int launch_terms(const SplitGemmArgs& a, const CUtensorMap& tmA, const CUtensorM
   }
   const int grid = std::max(1, std::min(a.n_sm, n_m * n_n));
   split_gemm_kernel<TERMS, NORMS><<<grid, THREADS, smem, st>>>(
-      tmA, tmB, epi, n_m, n_n, num_k, (int)a.M_pad, (int)a.N_pad, a.tile_active, a.err);
+      tmA, tmB, epi, n_m, n_n, num_k, (int)a.M_pad, (int)a.N_pad, a.tile_active, a.err,
+      a.wait_ns > 0 ? a.wait_ns : kTimeoutNs);
   return CLR_OK;
 }
 

@@ -319,6 +319,10 @@ struct SvdShared {
                   // reached): the right factor needs the least-squares form (ls_solve)
   int rank;
   double kept_sq;
+  // pivoted QR pre-reduction (compress_by_pivoted_qr): reflector coefficients and column order
+  double qr_tau[CLR_MAX_CLUSTER];
+  int qr_perm[CLR_MAX_CLUSTER];
+  int qr_pivot;
 };
 
 // Column norms of g, their descending order, and the truncation rank at eps.
@@ -432,7 +436,10 @@ __device__ void recover_right(const SrcView& a, int p, int q, const double* g, c
 // order perm, with norms d: the least-squares right factor when G_r is not orthogonal to FP64
 // precision.  The Gram matrix of the normalised columns (unit diagonal, off-diagonal at the
 // FP32 stages' tolerance, so well conditioned) is factored by Cholesky in mw (r x r).
-__device__ void ls_solve(double* y, int q, int r, const double* g, int p, const int* perm,
+// Returns false, with y unchanged, when that factorisation meets a pivot that is not positive
+// (kept columns at the rounding level of a block whose norm is near eps); the caller then uses
+// the orthogonal-columns formula y S^-2.
+__device__ bool ls_solve(double* y, int q, int r, const double* g, int p, const int* perm,
                          const double* d, double* mw, SvdShared& sh) {
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
   for (int e = w; e < r * r; e += kWarps) {
@@ -446,10 +453,15 @@ __device__ void ls_solve(double* y, int q, int r, const double* g, int p, const 
     if (l == 0) mw[i + (int64_t)j * r] = s2 / (d[i] * d[j]);
   }
   __syncthreads();
+  if (threadIdx.x == 0) sh.flag = 1;
   for (int j = 0; j < r; ++j) {  // lower Cholesky, column by column
     if (threadIdx.x == 0) {
       double a = mw[j + (int64_t)j * r];
       for (int k = 0; k < j; ++k) a -= mw[j + (int64_t)k * r] * mw[j + (int64_t)k * r];
+      if (!(a > 0.0) || !isfinite(a)) {
+        sh.flag = 0;
+        a = 1.0;
+      }
       mw[j + (int64_t)j * r] = sqrt(a);
     }
     __syncthreads();
@@ -460,6 +472,10 @@ __device__ void ls_solve(double* y, int q, int r, const double* g, int p, const 
       mw[i + (int64_t)j * r] = a / ljj;
     }
     __syncthreads();
+  }
+  if (!sh.flag) {
+    __syncthreads();
+    return false;
   }
   // each row t: x = (y_t D^-1) (L L^T)^-1 D^-1
   for (int t = threadIdx.x; t < q; t += kThreads) {
@@ -477,6 +493,7 @@ __device__ void ls_solve(double* y, int q, int r, const double* g, int p, const 
     for (int i = 0; i < r; ++i) yt[(int64_t)i * q] /= d[i];
   }
   __syncthreads();
+  return true;
 }
 
 // m (rows x q, ld ldm) <- m w in FP64 with the q x q factor w given row-major (wt[k q + c] =
@@ -694,12 +711,12 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
     sort_and_truncate(G, R, R, R, eps, sh);
     const int r = sh.rank;
     const bool tracked = sh.v_tracked;
-    const bool ls = !tracked && sh.ls_recover;
+    bool ls = !tracked && sh.ls_recover;
     if (!tracked) {
       // V_r S_r^2 = M^T G_r into V (M is still intact), or the least-squares V_r
       SrcView mv{M, 1, R, false};
       recover_right(mv, R, R, G, sh.perm, r, V);
-      if (ls) ls_solve(V, R, r, G, R, sh.perm, sh.sorted, sc, sh);
+      if (ls) ls = ls_solve(V, R, r, G, R, sh.perm, sh.sorted, sc, sh);
     }
     double* Xo = C.pool + sC;
     double* Wo = Xo + (int64_t)m * r;
@@ -861,13 +878,258 @@ __device__ int rrqr_block(const double* S, int64_t s_r, int64_t s_c, int m, int 
 }
 
 // ---------------------------------------------------------------------------------------------
+// Truncated SVD of a block of low numerical rank through a column-pivoted QR (pre-reduction).
+//
+// A (p x q, the block or its transpose, p >= q) is reduced by Householder QR with column
+// pivoting (at step j the remaining column of largest norm over rows j..p-1, first maximum on
+// ties; the norms are recomputed exactly in the same pass that applies the reflector), stopped
+// at the first step k whose trailing block has ||R_22||_F <= tau = eps/16:
+//   A P = Q [R_11 R_12; 0 R_22].
+// R_22 is dropped and the k x q factor R = [R_11 R_12] gets the mixed-precision SVD, truncated
+// at the remaining budget sqrt(eps^2 - ||R_22||_F^2).  The two errors are orthogonal (rows
+// 0..k-1 and k..p-1 of Q^T A P), so ||A - X W^T||_F <= eps, with X = Q_k X_R and W = P W_R.
+// Cost: about 3 p q k FP64 FMAs for the QR and O(q k^2) for the SVD of R, instead of the
+// O(p q^2)-per-sweep Jacobi on all q columns.  Ranks can exceed the minimal eps-rank where the
+// singular-value tail crosses eps within the budget split (the rank reading allows one).
+// Blocks of numerical rank above q/2 (stored dense): the QR stops after J = floor(q/2) + 1
+// steps, and the block is certified dense when sigma_min(R_11) > eps for the leading J x J
+// triangle: R_11 is a submatrix of Q^T A P, so sigma_J(A) >= sigma_min(R_11), and the eps-rank
+// exceeds q/2 as soon as sigma_{q/2+1}(A) > eps.  sigma_min(R_11) is bounded below by
+// 1 / ||R_11^-1||_F (a triangular inverse, J^3/6 FMAs).
+// Returns 1 when the block is done (low rank or zero, written to slot and the outputs), 2 when
+// it is certified dense (the source untouched: the caller stores it), 0 when neither holds
+// (a QR rank above q/2 at eps/16, or an inconclusive bound); the caller then takes the full
+// SVD, the source still untouched.
+// g: p x q copy (ld p); wv: the tile's second workspace half (p q doubles); slot: the block's
+// m n output slot (also the source of product tiles, read only before R is written there).
+// ---------------------------------------------------------------------------------------------
+// sigma_min(R) >= 1 / ||R^-1||_F for the J x J upper triangle R of g (ld p), by back
+// substitution of the unit vectors, one warp per column of the inverse (x: J x J scratch).
+__device__ double sigma_min_lower_bound(const double* g, int p, int J, double* x,
+                                        SvdShared& sh) {
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  double part = 0.0;
+  for (int c = w; c < J; c += kWarps) {
+    double* xc = x + (int64_t)c * J;
+    for (int i = c; i >= 0; --i) {
+      double d = 0.0;
+      for (int t = i + 1 + l; t <= c; t += 32) d = fma(g[i + (int64_t)t * p], xc[t], d);
+      d = warp_sum(d);
+      const double rhs = (i == c ? 1.0 : 0.0) - d;
+      const double xi = rhs / g[i + (int64_t)i * p];
+      __syncwarp();
+      if (l == 0) xc[i] = xi;
+      __syncwarp();
+      if (l == 0) part = fma(xi, xi, part);
+    }
+  }
+  const double f2 = block_sum(part, sh.red);
+  return (f2 > 0.0 && isfinite(f2)) ? 1.0 / sqrt(f2) : 0.0;
+}
+
+__device__ int compress_by_pivoted_qr(const SrcView& a, int p, int q, bool tr, int m, int n,
+                                      double eps, int max_sweeps, double* g, double* wv,
+                                      double* sc, double* slot, int* kind_out, int* rank_out,
+                                      double* norm_out, SvdShared& sh,
+                                      unsigned long long* jstats) {
+  const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  // ranks up to q/2 are stored low rank: R (k x q) then goes to the slot (the source is no
+  // longer needed once the QR has met the threshold) and the SVD factors of R^T (q x k and
+  // k x k, at most 3 q^2 / 4 <= p q doubles) to wv
+  const int kmax = q / 2;
+  // steps after which a block still above the threshold is tested for the dense certificate
+  const int jmax = q / 2 + 1 <= q ? q / 2 + 1 : q;
+  const double tau2 = (eps / 16.0) * (eps / 16.0);
+  // copy with the column norms
+  for (int c = w; c < q; c += kWarps) {
+    double* gc = g + (int64_t)c * p;
+    double s2 = 0.0;
+    for (int i = l; i < p; i += 32) {
+      const double x = a.at(i, c);
+      gc[i] = x;
+      s2 = fma(x, x, s2);
+    }
+    s2 = warp_sum(s2);
+    if (l == 0) {
+      sh.sigma[c] = s2;
+      sh.qr_perm[c] = c;
+    }
+  }
+  __syncthreads();
+  unsigned long long fma_count = 0;
+  int k = -1;
+  for (int j = 0; j <= jmax; ++j) {
+    // trailing norm and pivot (warp 0)
+    if (w == 0) {
+      double tot = 0.0, best = -1.0;
+      int arg = j;
+      for (int c = j + l; c < q; c += 32) {
+        const double v = sh.sigma[c];
+        tot += v;
+        if (v > best) { best = v; arg = c; }
+      }
+      tot = warp_sum(tot);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int oa = __shfl_xor_sync(0xffffffffu, arg, o);
+        if (ob > best || (ob == best && oa < arg)) { best = ob; arg = oa; }
+      }
+      if (l == 0) {
+        sh.kept_sq = tot;
+        sh.qr_pivot = arg;
+      }
+    }
+    __syncthreads();
+    if (sh.kept_sq <= tau2) { k = j; break; }
+    if (j == jmax) break;  // not reached within floor(q/2) + 1 steps
+    const int piv = sh.qr_pivot;
+    if (piv != j) {
+      double* x = g + (int64_t)j * p;
+      double* y = g + (int64_t)piv * p;
+      for (int i = threadIdx.x; i < p; i += kThreads) {
+        const double t = x[i];
+        x[i] = y[i];
+        y[i] = t;
+      }
+    }
+    __syncthreads();
+    if (piv != j && threadIdx.x == 0) {
+      const double t = sh.sigma[j];
+      sh.sigma[j] = sh.sigma[piv];
+      sh.sigma[piv] = t;
+      const int ti = sh.qr_perm[j];
+      sh.qr_perm[j] = sh.qr_perm[piv];
+      sh.qr_perm[piv] = ti;
+    }
+    // Householder reflector of column j below the diagonal (as householder_qr)
+    double* col = g + (int64_t)j * p;
+    double part = 0.0;
+    for (int i = j + 1 + threadIdx.x; i < p; i += kThreads) part = fma(col[i], col[i], part);
+    const double sv = block_sum(part, sh.red);
+    const double x0 = col[j];
+    double t = 0.0, beta = x0, v0 = 1.0;
+    if (sv > 0.0) {
+      beta = -copysign(sqrt(x0 * x0 + sv), x0);
+      v0 = x0 - beta;
+      t = (beta - x0) / beta;
+    }
+    if (sv > 0.0) {
+      const double inv = 1.0 / v0;
+      for (int i = j + 1 + threadIdx.x; i < p; i += kThreads) col[i] *= inv;
+    }
+    if (threadIdx.x == 0) {
+      col[j] = beta;
+      sh.qr_tau[j] = t;
+    }
+    __syncthreads();
+    // apply to the remaining columns, recomputing their norms over rows j+1..p-1
+    for (int c = j + 1 + w; c < q; c += kWarps) {
+      double* y = g + (int64_t)c * p;
+      double d = 0.0;
+      for (int i = j + 1 + l; i < p; i += 32) d = fma(col[i], y[i], d);
+      d = warp_sum(d) + y[j];
+      const double f = t * d;
+      double s2 = 0.0;
+      for (int i = j + 1 + l; i < p; i += 32) {
+        const double yi = fma(-f, col[i], y[i]);
+        y[i] = yi;
+        s2 = fma(yi, yi, s2);
+      }
+      s2 = warp_sum(s2);
+      if (l == 0) {
+        y[j] -= f;
+        sh.sigma[c] = s2;
+      }
+    }
+    fma_count += 3ull * (unsigned long long)(p - j) * (unsigned long long)(q - j - 1) + (p - j);
+    __syncthreads();
+  }
+  if (jstats && threadIdx.x == 0) atomicAdd(&jstats[4], 2ull * fma_count);
+  if (k < 0) {
+    // still above the threshold after jmax steps: dense if sigma_min(R_11) > eps
+    const double smin = sigma_min_lower_bound(g, p, jmax, wv, sh);
+    if (jstats && threadIdx.x == 0)
+      atomicAdd(&jstats[4], (unsigned long long)jmax * jmax * jmax / 3);
+    return smin > eps ? 2 : 0;
+  }
+  if (k > kmax) return 0;   // rank above q/2 at eps/16: the full SVD decides
+  const double trail2 = sh.kept_sq;
+  __syncthreads();
+  if (k == 0) {
+    if (threadIdx.x == 0) { *kind_out = CLR_KIND_ZERO; *rank_out = 0; *norm_out = 0.0; }
+    __syncthreads();
+    return 1;
+  }
+  // R (k x q, ld k, zero below the diagonal) and the SVD of M = R^T (q x k)
+  double* rb = slot;
+  double* gs = wv;                    // q x k
+  double* vs = gs + (int64_t)q * k;   // k x k
+  double part = 0.0;
+  for (int e = threadIdx.x; e < k * q; e += kThreads) {
+    const int i = e % k, c = e / k;
+    const double x = i <= c ? g[i + (int64_t)c * p] : 0.0;
+    rb[e] = x;
+    part = fma(x, x, part);
+  }
+  const double rfro = sqrt(block_sum(part, sh.red));
+  const double budget = sqrt(fmax(eps * eps - trail2, 0.0));
+  const SrcView mv{rb, k, 1, false};   // M(i, j) = R(j, i)
+  svd_mixed(mv, q, k, gs, vs, sc, max_sweeps, budget, -1, rfro, sh, jstats);
+  sort_and_truncate(gs, q, k, q, budget, sh);
+  const int r = sh.rank;
+  if (r == 0) {
+    if (threadIdx.x == 0) { *kind_out = CLR_KIND_ZERO; *rank_out = 0; *norm_out = 0.0; }
+    __syncthreads();
+    return 1;
+  }
+  const bool tracked = sh.v_tracked;
+  bool ls = !tracked && sh.ls_recover;
+  if (!tracked) recover_right(mv, q, k, gs, sh.perm, r, vs);   // Y = R G_r (k x r)
+  if (ls) ls = ls_solve(vs, k, r, gs, q, sh.perm, sh.sorted, sc, sh);
+  // R = V_M S U_M^T:  X_R = (V_M S)_r (k x r), W_R = (U_M)_r (q x r); A ~ (Q_k X_R) (P W_R)^T
+  // (R in the slot is no longer read: the factors overwrite it)
+  __syncthreads();
+  double* xa = tr ? slot + (int64_t)m * r : slot;   // Q_k X_R: p x r, ld p
+  double* wa = tr ? slot : slot + (int64_t)m * r;   // P W_R: q x r, ld q
+  for (int e = threadIdx.x; e < p * r; e += kThreads) {
+    const int i = e % p, c = e / p;
+    double v = 0.0;
+    if (i < k)
+      v = tracked ? vs[i + (int64_t)sh.perm[c] * k] * sh.sorted[c]
+          : ls    ? vs[i + (int64_t)c * k]
+                  : vs[i + (int64_t)c * k] / sh.sorted[c];
+    xa[e] = v;
+  }
+  for (int e = threadIdx.x; e < q * r; e += kThreads) {
+    const int j = e % q, c = e / q;
+    const double v = gs[j + (int64_t)sh.perm[c] * q];
+    wa[sh.qr_perm[j] + (int64_t)c * q] = ls ? v : v / sh.sorted[c];
+  }
+  __syncthreads();
+  apply_q(g, p, k, p, sh.qr_tau, xa, r, p);
+  if (threadIdx.x == 0) {
+    *kind_out = CLR_KIND_LR;
+    *rank_out = r;
+    *norm_out = sqrt(sh.kept_sq);
+    if (jstats) {
+      atomicAdd(&jstats[4], 4ull * (unsigned long long)p * k * r);
+      atomicAdd(&jstats[6], 1ull);
+    }
+  }
+  __syncthreads();
+  return 1;
+}
+
+// ---------------------------------------------------------------------------------------------
 // Dense truncated SVD of whole blocks (ROUTE_DACC tiles, recompressed dense tiles, building a
 // CLR matrix from a dense one).
 // ---------------------------------------------------------------------------------------------
 __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
     MatView C, const int* list, const int* count, const int* order, const double* src,
     int64_t lds, double* ws, double* svd_scratch, double eps, double drop_norm,
-    int dense_only, int rrqr, int max_sweeps, int* err, int* sched, unsigned long long* jstats) {
+    int dense_only, int rrqr, int prereduce, int max_sweeps, int* err, int* sched,
+    unsigned long long* jstats) {
   __shared__ SvdShared sh;
   __shared__ int sh_next;
   double* sc = svd_scratch + (int64_t)blockIdx.x * kSvdScratchPerCta;
@@ -895,7 +1157,7 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
     }
     const double nsq = block_sum(part, sh.red);
     if (!isfinite(nsq)) {
-      if (threadIdx.x == 0) atomicExch(err, 3);
+      if (threadIdx.x == 0) atomicCAS(err, 0, 3);  // a timeout (1) keeps precedence
     }
     const double nrm = sqrt(nsq);
     int kind;
@@ -933,11 +1195,22 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
       }
     } else if (!dense_only) {
       const SrcView view{S, s_r, s_c, tr};
-      const int early_dense =
-          svd_mixed(view, p, q, G, V, sc, max_sweeps, eps, q / 2, nrm, sh, jstats);
-      if (!early_dense) {
-        sort_and_truncate(G, p, q, p, eps, sh);
-        r = sh.rank;
+      // pivoted QR first: blocks of low numerical rank are truncated through the SVD of
+      // the k x q factor, blocks of rank above q/2 certified dense
+      const int pre = prereduce ? compress_by_pivoted_qr(view, p, q, tr, m, n, eps, max_sweeps,
+                                                         G, V, sc, slot, &C.kind[t], &C.rank[t],
+                                                         &C.norm[t], sh, jstats)
+                                : 0;
+      if (pre == 1) continue;
+      if (pre == 0) {
+        const int early_dense =
+            svd_mixed(view, p, q, G, V, sc, max_sweeps, eps, q / 2, nrm, sh, jstats);
+        if (!early_dense) {
+          sort_and_truncate(G, p, q, p, eps, sh);
+          r = sh.rank;
+        }
+      } else if (jstats && threadIdx.x == 0) {
+        atomicAdd(&jstats[3], 1ull);   // certified dense without an SVD
       }
     }
     const int lim = q / 2;
@@ -956,9 +1229,9 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
       // Y = V_r S_r^2 from the accumulated V
       const SrcView view{S, s_r, s_c, tr};
       const bool tracked = sh.v_tracked;
-      const bool ls = !tracked && sh.ls_recover;
+      bool ls = !tracked && sh.ls_recover;
       if (!tracked) recover_right(view, p, q, G, sh.perm, r, V);
-      if (ls) ls_solve(V, q, r, G, p, sh.perm, sh.sorted, sc, sh);
+      if (ls) ls = ls_solve(V, q, r, G, p, sh.perm, sh.sorted, sc, sh);
       if (jstats && threadIdx.x == 0 && !tracked)
         atomicAdd(&jstats[4], 2ull * p * q * r);
       double* Xo = slot;
@@ -1002,13 +1275,13 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
 void launch_compress_dense(const MatView& C, const int* list, const int* count,
                            const int* order, const double* src, int64_t lds, double* ws,
                            double* svd_scratch, double eps, double drop_norm,
-                           int dense_only, int rrqr, int max_sweeps, int grid, int* err,
-                           int* sched, unsigned long long* jstats, cudaStream_t st) {
+                           int dense_only, int rrqr, int prereduce, int max_sweeps, int grid,
+                           int* err, int* sched, unsigned long long* jstats, cudaStream_t st) {
   static bool attr_done[64] = {false};
   const int g = svd_launch_grid(compress_dense_kernel, grid, attr_done);
   compress_dense_kernel<<<g, kThreads, 0, st>>>(C, list, count, order, src, lds, ws, svd_scratch,
-                                                eps, drop_norm, dense_only, rrqr, max_sweeps, err,
-                                                sched, jstats);
+                                                eps, drop_norm, dense_only, rrqr, prereduce,
+                                                max_sweeps, err, sched, jstats);
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -1104,7 +1377,8 @@ constexpr int kNoAllocMaxDevices = 64;
 double* g_noalloc_ptr[kNoAllocMaxDevices] = {nullptr};
 std::mutex g_noalloc_mutex;
 
-// status[0] = kind, status[1] = rank, status[2] = error flag (3: non-finite input)
+// status[0] = kind, status[1] = rank, status[2] = error flag (3: non-finite input, 4: sweep
+// limit reached before convergence)
 __global__ void __launch_bounds__(kThreads) compress_block_noalloc_kernel(
     const double* src, int64_t lds, int m, int n, double eps, int max_sweeps, double* scratch,
     double* x_out, double* w_out, double* sigma_out, int* status) {
@@ -1126,7 +1400,14 @@ __global__ void __launch_bounds__(kThreads) compress_block_noalloc_kernel(
     if (threadIdx.x == 0) { status[0] = CLR_KIND_ZERO; status[1] = 0; }
     return;
   }
-  jacobi_svd(G, p, q, p, V, q, max_sweeps, &sh.flag);
+  // pairs of columns at the FP64 rounding level of the block (p u ||A||_F) are left alone:
+  // rotating them changes nothing that a truncation can see, and they would keep the sweeps
+  // from ever converging
+  const double floor64 = (double)p * DBL_EPSILON * sqrt(nsq);
+  const int sweeps = jacobi_svd(G, p, q, p, V, q, max_sweeps, &sh.flag, true, 1.0,
+                                floor64 * floor64);
+  // every sweep still rotated a pair: the column norms the truncation uses may be inexact
+  if (sweeps >= max_sweeps && threadIdx.x == 0) status[2] = 4;
   sort_and_truncate(G, p, q, p, eps, sh);
   const int r = sh.rank;
   if (sigma_out)

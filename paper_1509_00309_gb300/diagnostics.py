@@ -50,11 +50,14 @@ def ns_rank_distribution(ctx: "clr.Context", s: "clr.Matrix", k: int = 5) -> Dic
     out["Z_final"] = histogram_summary(z)
     out["ns"] = {"iters": st["iters"], "residual": st["residual"], "wall_s": wall,
                  "ms_per_iter": st["ms_total"] / max(1, st["iters"]),
-                 "proxy": st["proxy"], "status": st["status"]}
+                 "ms_residual": st["ms_residual"], "proxy": st["proxy"],
+                 "proxy_met": st["proxy_met"], "residual_met": st["residual_met"],
+                 "converged": st["converged"], "status": st["status"]}
     out["profile"] = {key: prof[key] for key in ("products", "ms_dense", "ms_lowrank",
                                                   "ms_compress", "svd_blocks", "svd_sweeps_fp32",
                                                   "svd_sweeps_fp64", "svd_early_dense",
-                                                  "svd_flops_fp64", "svd_flops_fp32")}
+                                                  "svd_prereduced", "svd_flops_fp64",
+                                                  "svd_flops_fp32")}
     ctx.set_opts(ns_snapshot_iter=0)
     return out
 
@@ -84,26 +87,39 @@ def adjoint_run(shape, precision: str = "fp64", iters: int = 20, eps: float = 1e
             "grad_frob": gi["frob_norm"], "grad_blocks": gi["n_blocks"]}
 
 
-def batch_run(n_instances: int = 64, steps: int = 10, warmup: int = 3) -> Dict:
+def batch_run(n_instances: int = 64, steps: int = 10, warmup: int = 3,
+              precision: str = "auto", n_check: int = 8) -> Dict:
     """The batched configuration: n_instances independent 1D-chain products S S of uneven size
     (N ~ U[1024, 8192], clusters U[48, 256], eps from {1e-6, 1e-8}) captured into one CUDA graph
-    with the autotuner's per-shape choice (clr_batch_*); products/s and algorithmic TFLOP/s of
-    graph replays timed with CUDA events."""
+    (clr_batch_*), with the autotuner's per-shape choice of precision and CTAs per SM
+    (precision "auto") or FP64 products throughout (precision "fp64", tuned CTAs per SM only);
+    products/s and algorithmic TFLOP/s of graph replays timed with CUDA events.  Also: the
+    device-time split of one uncaptured pass over all products (the dominant kernel and its
+    share), and for n_check instances spread over the batch the error of the replayed output
+    against the FP64 dense product of the reconstructed operand (10 eps ||A||_F^2 bound)."""
     import torch
     ws = wl.batched_chains(n_instances=n_instances)
-    ctx = clr.Context(0, precision="auto", eps_lr=1e-8)
+    ctx = clr.Context(0, precision=precision, eps_lr=1e-8)
     mats = [ctx.from_dense(torch.from_numpy(w.a).cuda(), w.row_sizes, eps_lr=w.eps_lr,
                            drop_norm=w.drop_norm) for w in ws]
     torch.cuda.synchronize()
-    # algorithmic flops of every product (the library's triple statistics), untimed
+    batch = ctx.batch(mats, mats, eps=[w.eps_lr for w in ws], tune=True)
+    tuned = [batch.tuning(i) for i in range(batch.n)]
+    # algorithmic flops of every product (the library's triple statistics) and the device-time
+    # split of one uncaptured pass with the tuned precisions, untimed
     flops = 0.0
-    for m, w in zip(mats, ws):
-        ctx.set_opts(eps_lr=w.eps_lr)
+    outs = []
+    ctx.profile_enable(True)
+    for m, w, t in zip(mats, ws, tuned):
+        ctx.set_opts(eps_lr=w.eps_lr, precision=t["precision"])
         out = ctx.zeros(w.row_sizes)
         flops += float(ctx.multiply_into(m, m, out, stats=True)["flops"])
-        out.close()
-    ctx.set_opts(eps_lr=1e-8)
-    batch = ctx.batch(mats, mats, eps=[w.eps_lr for w in ws], tune=True)
+        outs.append(out)
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    for o in outs:
+        o.close()
+    ctx.set_opts(eps_lr=1e-8, precision=precision)
     for _ in range(warmup):
         batch.run()
     torch.cuda.synchronize()
@@ -115,16 +131,41 @@ def batch_run(n_instances: int = 64, steps: int = 10, warmup: int = 3) -> Dict:
     torch.cuda.synchronize()
     ms = ev[0].elapsed_time(ev[1]) / steps
     prec = {}
-    for i in range(batch.n):
-        t = batch.tuning(i)["precision"]
-        prec[t] = prec.get(t, 0) + 1
+    for t in tuned:
+        prec[t["precision"]] = prec.get(t["precision"], 0) + 1
+    # per-instance error of the replayed outputs
+    errs = []
+    for i in np.linspace(0, n_instances - 1, min(n_check, n_instances)).astype(int):
+        a = mats[i].to_dense()
+        c = batch.output(int(i)).to_dense()
+        nrm = float(np.linalg.norm(a))
+        err = float(np.linalg.norm(c - a @ a))
+        errs.append({"instance": int(i), "n": ws[i].n, "eps": ws[i].eps_lr,
+                     "precision": tuned[i]["precision"], "err_frob": err,
+                     "bound_10eps_normA2": 10.0 * ws[i].eps_lr * nrm * nrm,
+                     "within_bound": err <= 10.0 * ws[i].eps_lr * nrm * nrm})
     batch.close()
+    phases = {k: prof[k] for k in ("ms_plan", "ms_stage", "ms_dense", "ms_lowrank",
+                                   "ms_compress", "ms_finalize")}
+    tot = sum(phases.values())
+    top = max(phases, key=phases.get)
+    names = {"ms_plan": "plan kernels", "ms_stage": "split_stage kernels",
+             "ms_dense": "dense tile products (split_gemm_kernel / dd_fp64_kernel)",
+             "ms_lowrank": "lr_products_kernel",
+             "ms_compress": "compress_qr_kernel + compress_dense_kernel",
+             "ms_finalize": "norms / scaling"}
     return {"workload": "%d batched 1D-chain products S S, N ~ U[1024,8192], clusters U[48,256], "
                         "eps in {1e-6, 1e-8}, one CUDA graph" % n_instances,
+            "precision_mode": precision,
             "instances": n_instances, "sum_n": int(sum(w.n for w in ws)),
             "ms_per_batch": ms, "products_per_s": n_instances / (ms * 1e-3),
             "tflops": flops / (ms * 1e-3) / 1e12, "algorithmic_flops_per_batch": flops,
-            "precisions": prec, "steps": steps, "warmup": warmup}
+            "precisions": prec, "steps": steps, "warmup": warmup,
+            "uncaptured_pass_ms": phases, "dominant": {"phase": names[top],
+                                                       "share": phases[top] / tot if tot else None},
+            "svd": {k: prof[k] for k in ("svd_blocks", "svd_sweeps_fp32", "svd_sweeps_fp64",
+                                         "svd_flops_fp64", "svd_flops_fp32")},
+            "errors": errs, "all_within_bound": all(e["within_bound"] for e in errs)}
 
 
 def main() -> None:
@@ -134,6 +175,9 @@ def main() -> None:
     ap.add_argument("--precision", default="fp64")
     ap.add_argument("--max-iter", type=int, default=40)
     ap.add_argument("--tol", type=float, default=1e-6)
+    ap.add_argument("--eps-ns", type=float, default=0.0,
+                    help="truncation of the NS iterates (default: the matrix's build eps_lr, "
+                         "1e-6)")
     ap.add_argument("--no-recompress-dense", action="store_true")
     ap.add_argument("--matrix", default="overlap", choices=["overlap", "coulomb"])
     ap.add_argument("--adjoint", action="store_true",
@@ -141,24 +185,28 @@ def main() -> None:
                          "--max-iter iterations)")
     ap.add_argument("--batch", type=int, default=0, metavar="N",
                     help="time N batched 1D-chain products in one CUDA graph instead")
+    ap.add_argument("--batch-precision", default="auto", choices=["auto", "fp64"])
     args = ap.parse_args()
     import torch
     shape = tuple(int(v) for v in args.shape.split("x"))
     if args.batch:
-        print(json.dumps(batch_run(args.batch)))
+        print(json.dumps(batch_run(args.batch, precision=args.batch_precision)))
         return
     if args.adjoint:
         print(json.dumps(adjoint_run(shape, args.precision, min(args.max_iter, 40))))
         return
     w = wl.lattice_overlap(shape=shape) if args.matrix == "overlap" else \
         wl.lattice_coulomb(shape=shape)
-    ctx = clr.Context(0, precision=args.precision, eps_lr=w.eps_lr, eps_sp=w.eps_sp,
+    eps_ns = args.eps_ns if args.eps_ns > 0 else w.eps_lr
+    ctx = clr.Context(0, precision=args.precision, eps_lr=eps_ns, eps_sp=w.eps_sp,
                       ns_tol=args.tol, ns_max_iter=args.max_iter,
-                      recompress_dense=0 if args.no_recompress_dense else 1)
+                      recompress_dense=0 if args.no_recompress_dense else 1,
+                      ns_fp64_tail=int(args.precision != "fp64"), ns_ladder_switch=1e-3)
     s = ctx.from_dense(torch.from_numpy(w.a).cuda(), w.row_sizes, eps_lr=w.eps_lr,
                        drop_norm=w.drop_norm)
     out = {"workload": w.name, "n": w.n, "clusters": len(w.row_sizes),
-           "precision": args.precision, "recompress_dense": not args.no_recompress_dense}
+           "precision": args.precision, "eps_build": w.eps_lr, "eps_ns": eps_ns,
+           "recompress_dense": not args.no_recompress_dense}
     out.update(ns_rank_distribution(ctx, s, args.iter))
     print(json.dumps(out))
 

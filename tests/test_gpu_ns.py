@@ -22,22 +22,27 @@ def test_ns_chain_matches_oracle_and_eigh(ctx):
     w = wl.chain_overlap(n=768, n_clusters=6, lo=96, hi=160)
     s_or = co.build(w.a, w.row_sizes, w.col_sizes, w.eps_lr, w.drop_norm)
     gs = clr_pack.to_library(ctx, s_or)
-    # with eps = 1e-8 the proxy floors near 2e-9; 1e-8 is reached one iteration after 2e-4
+    # with eps = 1e-8 the proxy floors near 2e-9; 1e-8 is reached one iteration after 2e-4.
+    # The residual of the returned Z is held near the truncation level, which may lie above
+    # this tolerance: then the proxy is met and the stated error is not
+    from paper_1509_00309_gb300 import clr
     ctx.set_opts(ns_tol=1e-8, ns_max_iter=60, ns_alpha=0.0, eps_lr=1e-8)
-    z, st, _ = ctx.sqrt_inv(gs)
+    z, st, _ = ctx.sqrt_inv(gs, allow_noconv=True)
     alpha_or = co.alpha_estimate(s_or.to_dense())
     assert abs(st["alpha"] - alpha_or) <= 1e-12 * alpha_or
     ref = co.ns_clr(s_or, alpha_or, 1e-8, max_iter=60, tol=1e-8)
-    assert st["converged"] and st["iters"] == ref.iters
+    assert st["proxy_met"] and ref.converged and st["iters"] == ref.iters
+    assert st["converged"] == st["residual_met"] == (st["residual"] <= 1e-8)
+    assert st["status"] == (clr.CLR_OK if st["converged"] else clr.CLR_ENOCONV)
     assert np.allclose(st["proxy"], ref.proxy, rtol=1e-6, atol=2e-8)
     zd = z.to_dense()
     exact = co.inv_sqrt_eigh(s_or.to_dense())
     assert np.linalg.norm(zd - exact) / np.linalg.norm(exact) < 1e-6
     assert np.linalg.norm(zd - ref.z.to_dense()) / np.linalg.norm(exact) < 1e-7
     assert st["residual"] < 1e-7
-    # the library's residual runs through two CLR products truncated at eps_lr, the oracle's
-    # is exact: they agree to the truncation level
-    assert abs(st["residual"] - co.residual(s_or.to_dense(), zd)) < 0.1 * st["residual"] + 1e-9
+    # the library's residual runs through two FP64 CLR products truncated at
+    # min(eps_lr, ns_tol / 100) = 1e-10, the oracle's is exact: they agree to that level
+    assert abs(st["residual"] - co.residual(s_or.to_dense(), zd)) < 0.01 * st["residual"] + 1e-10
 
 
 def test_ns_fixed_iterations_and_noconv(ctx):
@@ -57,6 +62,7 @@ def test_ns_fixed_iterations_and_noconv(ctx):
 
 
 def test_ns_fp64_meets_residual_and_split_floor(ctx):
+    from paper_1509_00309_gb300 import clr
     # FP64 products reach the residual tolerance 1e-6 on the 1D chain (kappa ~ 8400).  Split
     # products (bf16x6, FP64 from ||X - I|| <= 1e-3 on) stop at the floor ~ u_split * kappa:
     # early absolute rounding errors are large relative to the small-eigenvalue components of
@@ -66,15 +72,18 @@ def test_ns_fp64_meets_residual_and_split_floor(ctx):
     ctx.set_opts(precision="fp64", ns_tol=1e-6, ns_max_iter=60, ns_alpha=0.0, eps_lr=1e-8,
                  ns_fp64_tail=0)
     z_64, st_64, _ = ctx.sqrt_inv(gs)
-    assert st_64["converged"] and st_64["residual"] < 1e-6
+    assert st_64["converged"] and st_64["residual_met"] and st_64["residual"] < 1e-6
     exact = co.inv_sqrt_eigh(w.a)
     assert np.linalg.norm(z_64.to_dense() - exact) / np.linalg.norm(exact) < 1e-6
     ctx.set_opts(precision="bf16x6", ns_fp64_tail=1, ns_ladder_switch=1e-3)
-    z_lad, st_lad, _ = ctx.sqrt_inv(gs)
-    assert st_lad["converged"]
+    z_lad, st_lad, _ = ctx.sqrt_inv(gs, allow_noconv=True)
+    assert st_lad["proxy_met"]
     lam = np.linalg.eigvalsh(w.a)
     floor = 2.0 ** -24 * lam[-1] / lam[0]
     assert st_lad["residual"] < 30 * floor
+    # the split floor is far above the tolerance: not reported as converged
+    assert not st_lad["converged"] and not st_lad["residual_met"]
+    assert st_lad["status"] == clr.CLR_ENOCONV
     ctx.set_opts(precision="fp64", ns_fp64_tail=0)
 
 

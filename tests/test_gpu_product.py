@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from oracle import clr_oracle as co
+from oracle import split_oracle as so
 from paper_1509_00309_gb300 import workloads as wl
 from tests import clr_pack
 
@@ -18,13 +19,21 @@ def ctx():
     return clr.Context(0, precision="fp64", eps_lr=1e-8)
 
 
-def _check_product(ctx, a_or, b_or, eps, got, stats=None):
+def _check_product(ctx, a_or, b_or, eps, got, stats=None, split_mode=None):
     """Compare a GPU product with the oracle's: reconstruction within the truncation bound,
-    kinds equal (ranks within one of the oracle's at the threshold)."""
+    kinds equal (ranks within one of the oracle's at the threshold), and every dense tile
+    against its exact value.  FP64 tile products (split_mode None): the oracle's FP64 tile sum
+    up to rounding -- the two sum the same exact products in different orders (dense x dense
+    blocks whole, low-rank ones in factored form), so they differ by a few units of
+    u |A_I*| |B_*J| (bound 1e-13 |A||B|, about 450 u, far below any dropped or misplaced
+    contribution).  Split precision: a dense tile is summed entirely by the tensor cores (the
+    low-rank operand blocks staged as their reconstructions), so it equals the exact split
+    product of the reconstructed block row and column up to the FP32 accumulation (2^-18)."""
     want = co.multiply(a_or, b_or, eps)
     g = clr_pack.from_library(got)
     da, db = a_or.to_dense(), b_or.to_dense()
     ref = da @ db
+    absab = so.abs_product(da, db)
     err = np.linalg.norm(g.to_dense() - want.to_dense())
     tol = co.product_tolerance(da, db, max(eps, 1e-12))
     assert err <= tol, (err, tol)
@@ -33,6 +42,16 @@ def _check_product(ctx, a_or, b_or, eps, got, stats=None):
     gr, wr = g.ranks(), want.ranks()
     for i in range(len(a_or.row_sizes)):
         for j in range(len(b_or.col_sizes)):
+            if gk[i, j] == wk[i, j] == co.KIND_DENSE:
+                rows = slice(a_or.row_off[i], a_or.row_off[i + 1])
+                cols = slice(b_or.col_off[j], b_or.col_off[j + 1])
+                if split_mode is None:
+                    d = np.linalg.norm(g.block_dense(i, j) - want.block_dense(i, j))
+                    assert d <= 1e-13 * np.linalg.norm(absab[rows, cols]) + 1e-300, (i, j, d)
+                else:
+                    exact = so.split_product(da[rows], db[:, cols], split_mode)
+                    d = np.linalg.norm(g.block_dense(i, j) - exact)
+                    assert d <= 2.0 ** -18 * np.linalg.norm(exact) + 1e-300, (i, j, d)
             if gk[i, j] != wk[i, j]:
                 # a kind may only differ at the dense/low-rank threshold
                 lim = co.dense_rank_limit(a_or.row_sizes[i], b_or.col_sizes[j])

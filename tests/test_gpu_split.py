@@ -88,6 +88,19 @@ def test_split_inside_mixed_clr_product(ctx):
     assert np.array_equal(g.kinds(), want.kinds())
     err = np.linalg.norm(g.to_dense() - want.to_dense())
     assert err <= co.product_tolerance(w.a, w.a, w.eps_lr)
+    # every dense tile is summed entirely by the tensor cores (low-rank operand blocks staged as
+    # their reconstructions): it equals the exact split product of the reconstructed block row
+    # and column up to the FP32 accumulation
+    sd = s_or.to_dense()
+    for i in range(len(w.row_sizes)):
+        for j in range(len(w.row_sizes)):
+            if g.kinds()[i, j] != co.KIND_DENSE:
+                continue
+            rows = slice(s_or.row_off[i], s_or.row_off[i + 1])
+            cols = slice(s_or.col_off[j], s_or.col_off[j + 1])
+            exact = so.split_product(sd[rows], sd[:, cols], "bf16x6")
+            d = np.linalg.norm(g.block_dense(i, j) - exact)
+            assert d <= 2.0 ** -18 * np.linalg.norm(exact), (i, j, d)
 
 
 def test_full_size_sampled_tiles(ctx):
@@ -104,19 +117,27 @@ def test_full_size_sampled_tiles(ctx):
     gc.to_dense(out)
     torch.cuda.synchronize()
     off = np.concatenate([[0], np.cumsum(w.row_sizes)])
-    rng = np.random.default_rng(5)
     num, den, ab = 0.0, 0.0, 0.0
-    # first and last tiles, the column cluster across the middle, and random tiles
+    # whole block rows (every column cluster) and whole block columns (every row cluster):
+    # the first and last, the ones across the middle of the 128 x 256 GEMM grid, and two more
     j_mid = int(np.searchsorted(off, (w.n // 256) // 2 * 256, side="right")) - 1
-    pairs = [(0, 0), (95, 95), (40, j_mid), (77, j_mid)] + \
-        [tuple(rng.integers(0, 96, 2)) for _ in range(4)]
-    for i, j in pairs:
-        r0, r1, c0, c1 = off[i], off[i + 1], off[j], off[j + 1]
-        want = w.a[r0:r1] @ w.b[:, c0:c1]
-        got = out[r0:r1, c0:c1].cpu().numpy()
+    i_mid = int(np.searchsorted(off, (w.n // 128) // 2 * 128, side="right")) - 1
+    host = out.cpu().numpy()
+    for i in (0, 95, i_mid, 33):
+        r0, r1 = off[i], off[i + 1]
+        want = w.a[r0:r1] @ w.b
+        got = host[r0:r1]
         num += float(np.sum((got - want) ** 2))
         den += float(np.sum(want ** 2))
         ab += float(np.sum(np.linalg.norm(w.a[r0:r1], axis=1)[:, None] ** 2 *
+                           np.linalg.norm(w.b, axis=0)[None, :] ** 2))
+    for j in (0, 95, j_mid, 61):
+        c0, c1 = off[j], off[j + 1]
+        want = w.a @ w.b[:, c0:c1]
+        got = host[:, c0:c1]
+        num += float(np.sum((got - want) ** 2))
+        den += float(np.sum(want ** 2))
+        ab += float(np.sum(np.linalg.norm(w.a, axis=1)[:, None] ** 2 *
                            np.linalg.norm(w.b[:, c0:c1], axis=0)[None, :] ** 2))
     # per-sample form of ||dC||_F <= 10 eps ||A||_F ||B||_F with eps = 1e-8:
     # sum over sampled entries of dC^2 <= (10 eps)^2 * sum ||a_i||^2 ||b_j||^2
@@ -126,6 +147,7 @@ def test_full_size_sampled_tiles(ctx):
     # epilogue) add up to ||C||_F
     k, _, _, _ = gc.get_blocks(pool=False)
     assert (k == co.KIND_DENSE).all()
+    del host
     fro = float(torch.linalg.norm(out))
     assert abs(gc.info()["frob_norm"] - fro) <= 1e-12 * fro
 
@@ -164,7 +186,7 @@ def test_low_rank_sums_on_tensor_cores_follow_error_bound(ctx):
         # diagonal tiles hold a dense x dense product (tensor cores in both cases); the six
         # off-diagonal tiles are densely accumulated low-rank sums
         assert st["n_tiles_tensor"] == (9 if want_gemm else 3)
-        _check_product(ctx, a_or, b_or, eps, gc)
+        _check_product(ctx, a_or, b_or, eps, gc, split_mode="bf16x6")
     ctx.set_opts(precision="bf16x3", eps_lr=1e-8)
 
 

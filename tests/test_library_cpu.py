@@ -38,6 +38,8 @@ def test_struct_layouts_match_header(repo_root, tmp_path):
                    'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(clr_opts),'
                    ' sizeof(clr_info), sizeof(clr_product_stats), sizeof(clr_ns_stats),'
                    ' offsetof(clr_opts, jacobi_max_sweeps), offsetof(clr_ns_stats, ms_total));'
+                   'printf("%zu %zu\\n", offsetof(clr_opts, wait_timeout_us),'
+                   ' offsetof(clr_ns_stats, ms_residual));'
                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(repo_root, "include"), str(src), "-o",
@@ -45,7 +47,8 @@ def test_struct_layouts_match_header(repo_root, tmp_path):
     got = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     want = [ctypes.sizeof(clr.ClrOpts), ctypes.sizeof(clr.ClrInfo),
             ctypes.sizeof(clr.ClrProductStats), ctypes.sizeof(clr.ClrNsStats),
-            clr.ClrOpts.jacobi_max_sweeps.offset, clr.ClrNsStats.ms_total.offset]
+            clr.ClrOpts.jacobi_max_sweeps.offset, clr.ClrNsStats.ms_total.offset,
+            clr.ClrOpts.wait_timeout_us.offset, clr.ClrNsStats.ms_residual.offset]
     assert got == want
 
 
