@@ -34,8 +34,13 @@ METRIC = "CLR multiply TFLOP/s and ms per Newton–Schulz S^-1/2 iteration at st
 
 # DRAM bytes (read + write) of one launch of the dense tile-product kernel at this workload,
 # from ncu counters, keyed by the kernel source's hash so that the number is dropped
-# (traffic: null) as soon as the kernel changes.
-MEASURED_TRAFFIC = {}
+# (traffic: null) as soon as the kernel changes.  Counters are taken on the N = 8192 case of the
+# same construction (48 clusters; 2.281 GB read, 0.896 GB written per launch) and scaled to
+# N = 16384 by the units each part grows with: panel reads by the tile-k steps (N^3, x8), C
+# writes by the output (N^2, x4).
+MEASURED_TRAFFIC = {
+    "a7f5dda373a2:bf16x3:16384:96": 8 * 2280723456 + 4 * 896034816,
+}
 # Truncation of the Newton-Schulz iterates on the lattice matrices: the matrix is built at
 # eps_lr = 1e-6, but iterates truncated at 1e-6 hold the residual ||alpha Z S Z - I||_F/sqrt(N)
 # near 1.8e-5 (the oracle floors at the same level); at 1e-8 the residual meets 1e-6.
@@ -582,9 +587,11 @@ def batch_measure(n: int, precision: str, timeout: int = 420):
 def lattice_ns(clr, w, shape_txt, what, fp64_peak, precision, snapshot=True):
     """NS on one lattice matrix through the C ABI: the iterates truncated at EPS_NS_LATTICE,
     stopped at ||X - I||_F/sqrt(N) <= 1e-6 and judged by the residual ||alpha Z S Z - I||_F /
-    sqrt(N) <= 1e-6 (the stated error); with the recompression's ALU roofline (algorithmic FP64
-    and FP32 flops over its device time, against the measured FP64 FMA rate and the nominal
-    FP32 rate)."""
+    sqrt(N) <= 1e-6 (the stated error).  One profiled run (the iteration's two products one
+    after the other, so that the phase intervals time their own kernels) gives the phase split,
+    the SVD counters, the recompression kernels' ALU rooflines and the rank distribution; a
+    second, unprofiled run (the two products on two streams, as in production) gives the time
+    per iteration."""
     import torch
     from paper_1509_00309_gb300 import diagnostics
     ctx = clr.Context(torch.cuda.current_device(), precision=precision, eps_lr=EPS_NS_LATTICE,
@@ -597,22 +604,29 @@ def lattice_ns(clr, w, shape_txt, what, fp64_peak, precision, snapshot=True):
     ctx.set_opts(ns_max_iter=40, ns_tol=1e-6)
     torch.cuda.synchronize()
     d = diagnostics.ns_rank_distribution(ctx, sm, 5 if snapshot else 0)
+    torch.cuda.synchronize()
+    _, st, _ = ctx.sqrt_inv(sm, allow_noconv=True)
+    prof = d["profile"]
     out = {"workload": "3D lattice %s matrix, %s sites x 16 points, N=%d, %d clusters of "
                        "64..256, built at eps_lr=%g, iterates truncated at %g" % (
                            what, shape_txt, w.n, len(w.row_sizes), w.eps_lr, EPS_NS_LATTICE),
-           "ms_per_iteration": d["ns"]["ms_per_iter"], "iterations": d["ns"]["iters"],
-           "ms_residual": d["ns"]["ms_residual"], "proxy_final": d["ns"]["proxy"][-1],
-           "residual_ZSZ_minus_I_rms": d["ns"]["residual"], "tol": 1e-6,
-           "residual_met": d["ns"]["residual_met"], "proxy_met": d["ns"]["proxy_met"],
+           "ms_per_iteration": st["ms_total"] / max(1, st["iters"]),
+           "iterations": st["iters"], "ms_residual": st["ms_residual"],
+           "proxy_final": st["proxy"][-1],
+           "residual_ZSZ_minus_I_rms": st["residual"], "tol": 1e-6,
+           "residual_met": st["residual_met"], "proxy_met": st["proxy_met"],
            "precision": precision if precision == "fp64" else
                         "%s, fp64 below proxy 1e-3" % precision,
            "recompress_dense": True,
-           "phases_ms_total": {k: d["profile"][k] for k in
-                               ("ms_dense", "ms_lowrank", "ms_compress")},
-           "svd": {k: d["profile"][k] for k in ("svd_blocks", "svd_sweeps_fp32",
-                                                 "svd_sweeps_fp64", "svd_early_dense",
-                                                 "svd_prereduced")},
-           "roofline_recompress": recompress_roofline(d["profile"], fp64_peak)}
+           "profiled_run": {
+               "ms_per_iteration_serial": d["ns"]["ms_per_iter"],
+               "phases_ms_total": {k: prof[k] for k in
+                                   ("ms_dense", "ms_lowrank", "ms_compress_qr",
+                                    "ms_compress_dense")},
+               "svd": {k: prof[k] for k in ("svd_blocks", "svd_sweeps_fp32",
+                                            "svd_sweeps_fp64", "svd_early_dense",
+                                            "svd_prereduced")},
+               "roofline_recompress": recompress_roofline(prof, fp64_peak)}}
     if snapshot:
         out["rank_distribution_iter5"] = {
             k: {f: d[k][f] for f in ("zero", "dense", "low_rank", "lr_rank_mean", "lr_rank_max")}
@@ -620,17 +634,28 @@ def lattice_ns(clr, w, shape_txt, what, fp64_peak, precision, snapshot=True):
     return out
 
 
-def recompress_roofline(prof, fp64_peak):
-    t = prof["ms_compress"] * 1e-3
+def _alu_roofline(f64, f32, ms, fp64_peak):
+    t = ms * 1e-3
     if not t > 0:
         return None
-    a64 = prof["svd_flops_fp64"] / t / 1e12
-    a32 = prof["svd_flops_fp32"] / t / 1e12
+    a64, a32 = f64 / t / 1e12, f32 / t / 1e12
     # time the two pipes would need at their peaks, as a fraction of the measured time
-    frac = a64 / fp64_peak + a32 / FP32_TFLOPS_NOMINAL
     return {"bound": "alu", "achieved_fp64": a64, "peak_fp64": fp64_peak,
             "achieved_fp32": a32, "peak_fp32": FP32_TFLOPS_NOMINAL, "unit": "TFLOP/s",
-            "frac": frac, "traffic": None,
+            "frac": a64 / fp64_peak + a32 / FP32_TFLOPS_NOMINAL, "kernel_ms": ms,
+            "traffic": None}
+
+
+def recompress_roofline(prof, fp64_peak):
+    """ALU rooflines of the two recompression kernels from the library's algorithmic flop
+    counters and their device times: FP64 flops against the measured FMA rate, FP32 flops
+    against the nominal rate."""
+    qr = _alu_roofline(prof["svd_flops_fp64_qr"], prof["svd_flops_fp32_qr"],
+                       prof["ms_compress_qr"], fp64_peak)
+    dn = _alu_roofline(prof["svd_flops_fp64"] - prof["svd_flops_fp64_qr"],
+                       prof["svd_flops_fp32"] - prof["svd_flops_fp32_qr"],
+                       prof["ms_compress_dense"], fp64_peak)
+    return {"compress_qr_kernel": qr, "compress_dense_kernel": dn,
             "peak_basis": "FP64: measured FMA rate (clr_probe_fp64_rate); FP32: 152 SMs x 128 "
                           "lanes x 2 x 2.07 GHz (nominal)"}
 

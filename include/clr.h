@@ -315,7 +315,8 @@ int clr_ns_snapshot(clr_ctx_t ctx, int which, clr_mat_t* out);
 
 /* ---- observability ------------------------------------------------------------------------
  * With profiling on, every product records CUDA events on its stream at its phase boundaries
- * and counts the kernels it launches.  clr_profile_read synchronises the device, converts the
+ * and counts the kernels it launches; clr_sqrt_inv then runs its two independent products one
+ * after the other (not on two streams), so that each interval times its own kernels.  clr_profile_read synchronises the device, converts the
  * events to per-phase device times (ms, summed over products) and returns the totals;
  * clr_profile_enable(ctx, 1) resets them. */
 typedef struct clr_profile {
@@ -327,7 +328,7 @@ typedef struct clr_profile {
   double ms_stage;             /* split-precision staging of operand panels */
   double ms_dense;             /* dense x dense tile products */
   double ms_lowrank;           /* low-rank tile products and accumulation */
-  double ms_compress;          /* recompression (QR + SVD) */
+  double ms_compress;          /* recompression (QR + SVD): the two kernels below */
   double ms_finalize;          /* norms and scaling */
   int64_t svd_blocks;          /* truncated SVDs (one-sided Jacobi) run by recompression */
   int64_t svd_sweeps_fp32;     /* FP32 sweeps, summed over those SVDs */
@@ -338,6 +339,10 @@ typedef struct clr_profile {
                                   4pq^2 per FP64 sweep, factor recovery / re-expansion */
   double svd_flops_fp32;       /* algorithmic FP32 flops: Jacobi 4pq^2 per FP32 sweep */
   int64_t svd_prereduced;      /* dense blocks truncated through the pivoted-QR pre-reduction */
+  double ms_compress_qr;       /* the QR route's recompression (compress_qr_kernel) */
+  double ms_compress_dense;    /* dense truncated SVDs (compress_dense_kernel) */
+  double svd_flops_fp64_qr;    /* the part of svd_flops_fp64 done by the QR route */
+  double svd_flops_fp32_qr;    /* the part of svd_flops_fp32 done by the QR route */
 } clr_profile;
 int clr_profile_enable(clr_ctx_t ctx, int on);
 int clr_profile_read(clr_ctx_t ctx, clr_profile* out);

@@ -65,7 +65,9 @@ class ClrProfile(C.Structure):
                 ("ms_finalize", C.c_double), ("svd_blocks", C.c_int64),
                 ("svd_sweeps_fp32", C.c_int64), ("svd_sweeps_fp64", C.c_int64),
                 ("svd_early_dense", C.c_int64), ("svd_flops_fp64", C.c_double),
-                ("svd_flops_fp32", C.c_double), ("svd_prereduced", C.c_int64)]
+                ("svd_flops_fp32", C.c_double), ("svd_prereduced", C.c_int64),
+                ("ms_compress_qr", C.c_double), ("ms_compress_dense", C.c_double),
+                ("svd_flops_fp64_qr", C.c_double), ("svd_flops_fp32_qr", C.c_double)]
 
 
 _VP = C.c_void_p

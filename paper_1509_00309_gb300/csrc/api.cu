@@ -384,7 +384,7 @@ int take_device_error(clr_ctx_t ctx, const std::vector<std::unique_ptr<WorkSet>>
 // Grow the context workspaces needed by a plan over nI x nJ tiles and nK inner clusters.
 int make_plan(clr_ctx_t ctx, int nI, int nJ, int nK, Plan* p) {
   const size_t nt = (size_t)nI * nJ;
-  CLR_CUDA(ctx->cur->plan_ints.ensure(10 * nt * sizeof(int)));
+  CLR_CUDA(ctx->cur->plan_ints.ensure(11 * nt * sizeof(int)));
   const int64_t max_tr = (int64_t)nt * nK;
   CLR_CUDA(ctx->cur->triples.ensure((size_t)max_tr * sizeof(Triple)));
   int st = ensure_counters(ctx, ctx->cur);
@@ -403,6 +403,7 @@ int make_plan(clr_ctx_t ctx, int nI, int nJ, int nK, Plan* p) {
   p->l_dcomp = base + 7 * nt;
   p->l_qr_s = base + 8 * nt;
   p->l_dcomp_s = base + 9 * nt;
+  p->l_dense_s = base + 10 * nt;
   p->row_off = nullptr;
   p->col_off = nullptr;
   p->triples = (Triple*)ctx->cur->triples.p;
@@ -449,13 +450,17 @@ const double* host_device_ptr(const void* p) {
 }
 
 
-// SVD counters while profiling (not inside a graph capture), else null
-unsigned long long* jst(clr_ctx_t ctx) {
+// SVD counters while profiling (not inside a graph capture), else null.  Two blocks of 8:
+// [0, 8) for dense truncated SVDs (compress_dense_kernel), [8, 16) for the QR route
+// (compress_qr_kernel).
+constexpr int kJstatsBlock = 8;
+unsigned long long* jst(clr_ctx_t ctx, int block = 0) {
   return (ctx->prof_on && !ctx->capturing && ctx->jstats.p)
-             ? (unsigned long long*)ctx->jstats.p : nullptr;
+             ? (unsigned long long*)ctx->jstats.p + block * kJstatsBlock : nullptr;
 }
 
-enum { PH_START = -1, PH_PLAN = 0, PH_STAGE, PH_DENSE, PH_LOWRANK, PH_COMPRESS, PH_FINALIZE };
+enum { PH_START = -1, PH_PLAN = 0, PH_STAGE, PH_DENSE, PH_LOWRANK, PH_COMPRESS_QR, PH_COMPRESS,
+       PH_FINALIZE };
 
 void prof_mark(clr_ctx_t ctx, cudaStream_t s, int phase) {
   if (!ctx->prof_on || ctx->capturing) return;
@@ -1050,7 +1055,8 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   prof_mark(ctx, s, PH_LOWRANK);
   launch_compress_qr(cv, p.l_qr_s, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p,
                      (double*)ctx->cur->scratch.p, eps_lr, o.jacobi_max_sweeps,
-                     lr_grid, &p.counters->err, &p.counters->sched[1], jst(ctx), s);
+                     lr_grid, &p.counters->err, &p.counters->sched[1], jst(ctx, 1), s);
+  prof_mark(ctx, s, PH_COMPRESS_QR);
   launch_compress_dense(cv, p.l_dcomp_s, &p.counters->n_dcomp, nullptr, nullptr, 0,
                         (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p,
                         eps_lr, 0.0, 0, 0, o.svd_no_prereduce ? 0 : 1, o.jacobi_max_sweeps,
@@ -1101,8 +1107,8 @@ extern "C" int clr_profile_enable(clr_ctx_t ctx, int on) {
   std::memset(&ctx->prof, 0, sizeof(ctx->prof));
   ctx->prof_on = on != 0;
   if (ctx->prof_on) {
-    CLR_CUDA(ctx->jstats.ensure(7 * sizeof(unsigned long long)));
-    CLR_CUDA(cudaMemset(ctx->jstats.p, 0, 7 * sizeof(unsigned long long)));
+    CLR_CUDA(ctx->jstats.ensure(2 * kJstatsBlock * sizeof(unsigned long long)));
+    CLR_CUDA(cudaMemset(ctx->jstats.p, 0, 2 * kJstatsBlock * sizeof(unsigned long long)));
   }
   return CLR_OK;
 }
@@ -1122,9 +1128,11 @@ extern "C" int clr_profile_read(clr_ctx_t ctx, clr_profile* out) {
                      : pe.phase == PH_STAGE ? &ctx->prof.ms_stage
                      : pe.phase == PH_DENSE ? &ctx->prof.ms_dense
                      : pe.phase == PH_LOWRANK ? &ctx->prof.ms_lowrank
-                     : pe.phase == PH_COMPRESS ? &ctx->prof.ms_compress
+                     : pe.phase == PH_COMPRESS_QR ? &ctx->prof.ms_compress_qr
+                     : pe.phase == PH_COMPRESS ? &ctx->prof.ms_compress_dense
                      : &ctx->prof.ms_finalize;
         *slot += ms;
+        if (pe.phase == PH_COMPRESS_QR || pe.phase == PH_COMPRESS) ctx->prof.ms_compress += ms;
       }
       prev[pe.s] = pe.e;
     }
@@ -1132,15 +1140,18 @@ extern "C" int clr_profile_read(clr_ctx_t ctx, clr_profile* out) {
     ctx->prof_events.clear();
   }
   if (ctx->jstats.p) {
-    unsigned long long j[7];
+    unsigned long long j[2 * kJstatsBlock];
     CLR_CUDA(cudaMemcpy(j, ctx->jstats.p, sizeof(j), cudaMemcpyDeviceToHost));
-    ctx->prof.svd_blocks = (int64_t)j[0];
-    ctx->prof.svd_sweeps_fp32 = (int64_t)j[1];
-    ctx->prof.svd_sweeps_fp64 = (int64_t)j[2];
+    const unsigned long long* q = j + kJstatsBlock;   // the QR route's block
+    ctx->prof.svd_blocks = (int64_t)(j[0] + q[0]);
+    ctx->prof.svd_sweeps_fp32 = (int64_t)(j[1] + q[1]);
+    ctx->prof.svd_sweeps_fp64 = (int64_t)(j[2] + q[2]);
     ctx->prof.svd_early_dense = (int64_t)j[3];
-    ctx->prof.svd_flops_fp64 = (double)j[4];
-    ctx->prof.svd_flops_fp32 = (double)j[5];
+    ctx->prof.svd_flops_fp64 = (double)(j[4] + q[4]);
+    ctx->prof.svd_flops_fp32 = (double)(j[5] + q[5]);
     ctx->prof.svd_prereduced = (int64_t)j[6];
+    ctx->prof.svd_flops_fp64_qr = (double)q[4];
+    ctx->prof.svd_flops_fp32_qr = (double)q[5];
   }
   *out = ctx->prof;
   return CLR_OK;
@@ -1253,7 +1264,7 @@ extern "C" int clr_lincomb(clr_ctx_t ctx, double a, clr_mat_t x, double b, clr_m
   launch_compress_qr(ov, p.l_qr_s, &p.counters->n_qr, p.t_rsum, (double*)ctx->cur->ws.p,
                      (double*)ctx->cur->scratch.p, o.eps_lr,
                      o.jacobi_max_sweeps, grid, &p.counters->err, &p.counters->sched[1],
-                     jst(ctx), s);
+                     jst(ctx, 1), s);
   launch_compress_dense(ov, p.l_dcomp_s, &p.counters->n_dcomp, nullptr, nullptr, 0,
                         (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p,
                         o.eps_lr, 0.0, 0, 0, o.svd_no_prereduce ? 0 : 1, o.jacobi_max_sweeps,
@@ -1487,18 +1498,26 @@ extern "C" int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t* z_out,
     st = clr_lincomb(ctx, -10.0 / 8.0, X, 3.0 / 8.0, X2, 15.0 / 8.0, T, s);
     if (st) break;
     // Z T and T Y are independent: T Y runs on the side stream with the second workspace set,
-    // so that the SMs one product's longest tiles leave idle take the other's work
-    st = fork_side(ctx, s);
-    if (st) break;
-    {
-      WorkSet* saved = ctx->cur;
-      ctx->cur = ctx->wsets[1].get();
-      st = multiply_into(ctx, T, Y, Yn, 1.0, tn, nullptr, ctx->side);
-      ctx->cur = saved;
+    // so that the SMs one product's longest tiles leave idle take the other's work.  While
+    // profiling they run one after the other, so that the per-phase event intervals time one
+    // kernel each.
+    if (ctx->prof_on) {
+      st = multiply_into(ctx, T, Y, Yn, 1.0, tn, nullptr, s);
+      if (!st) st = multiply_into(ctx, Z, T, Zn, 1.0, tn, nullptr, s);
+      if (st) break;
+    } else {
+      st = fork_side(ctx, s);
+      if (st) break;
+      {
+        WorkSet* saved = ctx->cur;
+        ctx->cur = ctx->wsets[1].get();
+        st = multiply_into(ctx, T, Y, Yn, 1.0, tn, nullptr, ctx->side);
+        ctx->cur = saved;
+      }
+      if (!st) st = multiply_into(ctx, Z, T, Zn, 1.0, tn, nullptr, s);
+      const int sj = join_side(ctx, s);
+      if (st || (st = sj)) break;
     }
-    if (!st) st = multiply_into(ctx, Z, T, Zn, 1.0, tn, nullptr, s);
-    const int sj = join_side(ctx, s);
-    if (st || (st = sj)) break;
     std::swap(Z, Zn);
     std::swap(Y, Yn);
     ++it;

@@ -56,6 +56,58 @@ __device__ __forceinline__ int next_item(int* counter, int* sh_slot) {
   return *sh_slot;
 }
 
+// out(i,j) (= or +=) sum_l a(i,l) b(l,j) for a P x Q output with arbitrary element strides, by a
+// CTA of NT threads.  FP64 runs at ~2 FMAs per clock per SM on this part, and a single
+// accumulator per thread leaves the pipe waiting on each FMA's latency and its two loads: the
+// output is cut into 4 x 2 micro-tiles (4 consecutive rows, 2 consecutive columns; the ragged
+// last ones clamped), taken by the threads in turn, so a thread runs 8 independent chains whose 6
+// loads per step feed 8 FMAs, and skinny outputs (a few dozen columns: the rank of a low-rank
+// factor) waste no lanes.  No synchronisation inside: the caller orders dependent calls.
+template <int NT>
+__device__ __forceinline__ void cta_gemm_tiled(int P, int Q, int L, const double* a,
+                                               int64_t a_r, int64_t a_c, const double* b,
+                                               int64_t b_r, int64_t b_c, double* out,
+                                               int64_t ldo, bool accumulate) {
+  const int mp = (P + 3) / 4, mq = (Q + 1) / 2;
+  for (int t = threadIdx.x; t < mp * mq; t += NT) {
+    const int i0 = (t % mp) * 4, j0 = (t / mp) * 2;
+    const double* ap[4];
+    const double* bp[2];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) ap[x] = a + (int64_t)(i0 + x < P ? i0 + x : i0) * a_r;
+#pragma unroll
+    for (int y = 0; y < 2; ++y) bp[y] = b + (int64_t)(j0 + y < Q ? j0 + y : j0) * b_c;
+    double acc[4][2];
+#pragma unroll
+    for (int x = 0; x < 4; ++x) acc[x][0] = acc[x][1] = 0.0;
+    for (int l = 0; l < L; ++l) {
+      double av[4], bv[2];
+#pragma unroll
+      for (int x = 0; x < 4; ++x) {
+        av[x] = *ap[x];
+        ap[x] += a_c;
+      }
+#pragma unroll
+      for (int y = 0; y < 2; ++y) {
+        bv[y] = *bp[y];
+        bp[y] += b_r;
+      }
+#pragma unroll
+      for (int x = 0; x < 4; ++x)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) acc[x][y] = fma(av[x], bv[y], acc[x][y]);
+    }
+#pragma unroll
+    for (int x = 0; x < 4; ++x)
+#pragma unroll
+      for (int y = 0; y < 2; ++y)
+        if (i0 + x < P && j0 + y < Q) {
+          double* o = out + (i0 + x) + (int64_t)(j0 + y) * ldo;
+          *o = accumulate ? *o + acc[x][y] : acc[x][y];
+        }
+  }
+}
+
 struct Triple {
   int tile;   // C block index I * nJ + J
   int k;      // inner cluster K
@@ -94,6 +146,7 @@ struct Plan {
                   // dense tiles are recompressed)
   int* l_qr_s;    // l_qr and l_dcomp reordered by decreasing recompression cost (plan_scan)
   int* l_dcomp_s;
+  int* l_dense_s;  // l_dense reordered by decreasing cost m n (number of products)
   const int* row_off;  // C's cluster offsets (device), for those costs
   const int* col_off;
   Triple* triples;
@@ -109,6 +162,7 @@ void launch_plan(const MatView& A, const MatView& B, const Plan& p, double eps_s
                  int recompress_dense, double gemm_dacc_bound, cudaStream_t st);
 void launch_plan_scan(const Plan& p, int recompress_dense, cudaStream_t st);
 // k_dense64.cu
+// uses p.counters->sched[3]
 void launch_dd_fp64(const MatView& A, const MatView& B, const MatView& C, const Plan& p,
                     int grid, cudaStream_t st);
 void launch_set_route_kinds(const MatView& C, const Plan& p, cudaStream_t st);

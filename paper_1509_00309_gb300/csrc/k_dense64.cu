@@ -2,10 +2,14 @@
 // block GEMM task of Section 3.2, C_ij += A_ik B_kj), reconstruction, and per-tile kind
 // bookkeeping.
 //
-// On GB300 FP64 runs on the CUDA cores at a small fraction of the tensor rate, so these
-// kernels are ALU-bound and kept simple: one CTA computes a 64x64 sub-tile of one C tile in
-// registers (4x4 per thread), walking that tile's dense x dense products in k order
-// (deterministic, no atomics).
+// On GB300 FP64 runs on the CUDA cores at a small fraction of the tensor rate (~2 FMAs per clock
+// per SM), so these kernels are FP64-pipe-bound and the work is cut to waste no lanes: a C tile
+// (m x n, up to 256 x 256) is split into ceil(m/64) x ceil(n/64) sub-tiles of equal size (at
+// most 64 x 64, so a 170-row tile gives three 57-row sub-tiles rather than two full ones and a
+// 42-row one); one CTA computes a sub-tile in registers (4 x 4 per thread), walking that tile's
+// dense x dense products in k order (deterministic, no atomics).  Sub-tiles are taken from a
+// launch-wide counter over the tiles in decreasing cost order (longest-processing-time
+// scheduling: tiles differ in size and in their number of products).
 #include "clr_internal.h"
 
 namespace clr {
@@ -17,18 +21,26 @@ constexpr int kSubPerTile = (CLR_MAX_CLUSTER / kSub) * (CLR_MAX_CLUSTER / kSub);
 __global__ void __launch_bounds__(256) dd_fp64_kernel(MatView A, MatView B, MatView C, Plan p) {
   __shared__ double As[kKc][kSub + 1];
   __shared__ double Bs[kKc][kSub + 1];
+  __shared__ int sh_next;
   const int tid = threadIdx.x;
   const int tx = tid % 16, ty = tid / 16;
   const int n_items = p.counters->n_dense * kSubPerTile;
-  for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
-    const int t = p.l_dense[item / kSubPerTile];
+  int* sched = &p.counters->sched[3];
+  for (int item = next_item(sched, &sh_next); item < n_items;
+       item = next_item(sched, &sh_next)) {
+    const int t = p.l_dense_s[item / kSubPerTile];
     const int s = item % kSubPerTile;
     const int I = t / p.nJ, J = t % p.nJ;
-    const int m = C.row_off[I + 1] - C.row_off[I];
-    const int n = C.col_off[J + 1] - C.col_off[J];
-    const int i0 = (s / (CLR_MAX_CLUSTER / kSub)) * kSub;
-    const int j0 = (s % (CLR_MAX_CLUSTER / kSub)) * kSub;
-    if (i0 >= m || j0 >= n) continue;
+    const int mt = C.row_off[I + 1] - C.row_off[I];
+    const int nt = C.col_off[J + 1] - C.col_off[J];
+    // equal sub-tiles of at most kSub x kSub
+    const int nsi = (mt + kSub - 1) / kSub, nsj = (nt + kSub - 1) / kSub;
+    const int si = s / (CLR_MAX_CLUSTER / kSub), sj = s % (CLR_MAX_CLUSTER / kSub);
+    if (si >= nsi || sj >= nsj) continue;
+    const int hi = (mt + nsi - 1) / nsi, hj = (nt + nsj - 1) / nsj;
+    const int i0 = si * hi, j0 = sj * hj;
+    const int m = mt, n = nt;
+    const int ie = min(mt, i0 + hi), je = min(nt, j0 + hj);
     double acc[4][4];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -45,9 +57,9 @@ __global__ void __launch_bounds__(256) dd_fp64_kernel(MatView A, MatView B, MatV
       for (int k0 = 0; k0 < k; k0 += kKc) {
         for (int e = tid; e < kKc * kSub; e += 256) {
           const int r = e % kSub, kk = e / kSub;
-          As[kk][r] = (i0 + r < m && k0 + kk < k) ? Ab[(i0 + r) + (int64_t)(k0 + kk) * m] : 0.0;
+          As[kk][r] = (i0 + r < ie && k0 + kk < k) ? Ab[(i0 + r) + (int64_t)(k0 + kk) * m] : 0.0;
           const int kk2 = e % kKc, c = e / kKc;
-          Bs[kk2][c] = (j0 + c < n && k0 + kk2 < k) ? Bb[(k0 + kk2) + (int64_t)(j0 + c) * k] : 0.0;
+          Bs[kk2][c] = (j0 + c < je && k0 + kk2 < k) ? Bb[(k0 + kk2) + (int64_t)(j0 + c) * k] : 0.0;
         }
         __syncthreads();
 #pragma unroll
@@ -71,7 +83,7 @@ __global__ void __launch_bounds__(256) dd_fp64_kernel(MatView A, MatView B, MatV
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         const int r = i0 + ty + 16 * a, c = j0 + tx + 16 * b;
-        if (r < m && c < n) D[r + (int64_t)c * m] = acc[a][b];
+        if (r < ie && c < je) D[r + (int64_t)c * m] = acc[a][b];
       }
   }
 }

@@ -19,19 +19,12 @@
 
 namespace clr {
 
-// out(i,j) (= or +=) sum_l a(i,l) b(l,j) for a P x Q output with arbitrary element strides.
-__device__ void cta_gemm(int P, int Q, int L, const double* a, int64_t a_r, int64_t a_c,
-                         const double* b, int64_t b_r, int64_t b_c, double* out, int64_t ldo,
-                         bool accumulate) {
-  for (int e = threadIdx.x; e < P * Q; e += blockDim.x) {
-    const int i = e % P, j = e / P;
-    const double* ap = a + i * a_r;
-    const double* bp = b + j * b_c;
-    double s = 0.0;
-    for (int l = 0; l < L; ++l) s = fma(ap[l * a_c], bp[l * b_r], s);
-    double* o = out + i + (int64_t)j * ldo;
-    *o = accumulate ? *o + s : s;
-  }
+// out(i,j) (= or +=) sum_l a(i,l) b(l,j) for a P x Q output with arbitrary element strides
+// (register-tiled, clr_internal.h).
+__device__ __forceinline__ void cta_gemm(int P, int Q, int L, const double* a, int64_t a_r,
+                                         int64_t a_c, const double* b, int64_t b_r, int64_t b_c,
+                                         double* out, int64_t ldo, bool accumulate) {
+  cta_gemm_tiled<256>(P, Q, L, a, a_r, a_c, b, b_r, b_c, out, ldo, accumulate);
 }
 
 __device__ void cta_copy_cols(int rows, int cols, const double* src, int64_t lds, double* dst,

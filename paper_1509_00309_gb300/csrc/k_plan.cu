@@ -105,7 +105,8 @@ constexpr int kScanThreads = 1024;
 constexpr int kScanQ = 5;
 constexpr int kCostBuckets = 32;
 
-// log2 bucket of a tile's recompression cost (which = 0: QR route, 1: dense SVD)
+// log2 bucket of a tile's cost (which = 0: QR route recompression, 1: dense SVD, 2: dense x
+// dense products, m n times the tile's number of products)
 __device__ __forceinline__ int cost_bucket(const Plan& p, int t, int which) {
   const int I = t / p.nJ, J = t % p.nJ;
   const long long m = p.row_off[I + 1] - p.row_off[I];
@@ -114,8 +115,10 @@ __device__ __forceinline__ int cost_bucket(const Plan& p, int t, int which) {
   if (which == 0) {
     const long long R = p.t_rsum[t];
     c = (m + n) * R * R + R * R * R;
-  } else {
+  } else if (which == 1) {
     c = m * n * (m < n ? m : n);
+  } else {
+    c = m * n * (long long)p.t_count[t];
   }
   const int b = c > 0 ? 63 - __clzll(c) : 0;
   return b < kCostBuckets ? b : kCostBuckets - 1;
@@ -167,22 +170,29 @@ __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(Plan p, int rec
     p.counters->n_dcomp = sh[4][tid];
     p.counters->n_dacc = 0;
   }
-  // The recompression lists again, largest cost first (longest-processing-time order for the
-  // dynamically distributed SVD kernels): a counting sort on log2 of the cost, m n min(m, n)
-  // for a dense SVD, (m + n) R^2 for a QR route.  The order within a bucket is immaterial:
-  // every tile is recompressed independently.
+  // The recompression lists and the dense-product list again, largest cost first
+  // (longest-processing-time order for the dynamically distributed kernels): a counting sort on
+  // log2 of the cost, m n min(m, n) for a dense SVD, (m + n) R^2 for a QR route, m n times the
+  // number of products for dense x dense products.  The order within a bucket is immaterial:
+  // every tile is processed independently.
   __syncthreads();
   const int n_qr = sh[3][kScanThreads - 1], n_dc = sh[4][kScanThreads - 1];
-  __shared__ int bcount[2][kCostBuckets], boff[2][kCostBuckets];
-  if (tid < 2 * kCostBuckets) (&bcount[0][0])[tid] = 0;
+  const int n_de = sh[1][kScanThreads - 1];
+  __shared__ int bcount[3][kCostBuckets], boff[3][kCostBuckets];
+  if (tid < 3 * kCostBuckets) (&bcount[0][0])[tid] = 0;
   __syncthreads();
-  for (int i = tid; i < n_qr + n_dc; i += kScanThreads) {
-    const int which = i < n_qr ? 0 : 1;
-    const int t = which == 0 ? p.l_qr[i] : p.l_dcomp[i - n_qr];
+  auto item = [&](int i, int* which) {
+    *which = i < n_qr ? 0 : (i < n_qr + n_dc ? 1 : 2);
+    return *which == 0 ? p.l_qr[i] : *which == 1 ? p.l_dcomp[i - n_qr]
+                                                  : p.l_dense[i - n_qr - n_dc];
+  };
+  for (int i = tid; i < n_qr + n_dc + n_de; i += kScanThreads) {
+    int which;
+    const int t = item(i, &which);
     atomicAdd(&bcount[which][cost_bucket(p, t, which)], 1);
   }
   __syncthreads();
-  if (tid < 2) {
+  if (tid < 3) {
     int acc = 0;
     for (int b = kCostBuckets - 1; b >= 0; --b) {
       boff[tid][b] = acc;
@@ -190,11 +200,11 @@ __global__ void __launch_bounds__(kScanThreads) plan_scan_kernel(Plan p, int rec
     }
   }
   __syncthreads();
-  for (int i = tid; i < n_qr + n_dc; i += kScanThreads) {
-    const int which = i < n_qr ? 0 : 1;
-    const int t = which == 0 ? p.l_qr[i] : p.l_dcomp[i - n_qr];
+  for (int i = tid; i < n_qr + n_dc + n_de; i += kScanThreads) {
+    int which;
+    const int t = item(i, &which);
     const int pos = atomicAdd(&boff[which][cost_bucket(p, t, which)], 1);
-    (which == 0 ? p.l_qr_s : p.l_dcomp_s)[pos] = t;
+    (which == 0 ? p.l_qr_s : which == 1 ? p.l_dcomp_s : p.l_dense_s)[pos] = t;
   }
 }
 

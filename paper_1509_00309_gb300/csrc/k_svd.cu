@@ -406,29 +406,26 @@ __device__ void orthonormalise_fp64(const float* v32, double* v, int q, SvdShare
   }
 }
 
-// g (p x q, ld p) = A v in FP64.
+// g (p x q, ld p) = A v in FP64 (register-tiled, cta_gemm_tiled).
 __device__ void project_fp64(const SrcView& a, int p, int q, const double* v, double* g) {
-  for (int e = threadIdx.x; e < p * q; e += kThreads) {
-    const int i = e % p, j = e / p;
-    const double* vj = v + (int64_t)j * q;
-    double s2 = 0.0;
-    for (int k = 0; k < q; ++k) s2 = fma(a.at(i, k), vj[k], s2);
-    g[e] = s2;
-  }
+  const int64_t a_i = a.tr ? a.s_c : a.s_r, a_k = a.tr ? a.s_r : a.s_c;
+  cta_gemm_tiled<kThreads>(p, q, q, a.src, a_i, a_k, v, 1, q, g, p, false);
   __syncthreads();
 }
 
 // y (q x r, ld q) = A^T G_r in FP64, G_r the r kept columns of g (p x q, ld p) in the order
-// perm; with G_r = U_r S_r this is V_r S_r^2.
+// perm; with G_r = U_r S_r this is V_r S_r^2.  G_r is first gathered into `gather` (p r
+// doubles, not overlapping g or y) so that the product runs register-tiled.
 __device__ void recover_right(const SrcView& a, int p, int q, const double* g, const int* perm,
-                              int r, double* y) {
-  for (int e = threadIdx.x; e < q * r; e += kThreads) {
-    const int j = e % q, c = e / q;
-    const double* gc = g + (int64_t)perm[c] * p;
-    double s2 = 0.0;
-    for (int k = 0; k < p; ++k) s2 = fma(a.at(k, j), gc[k], s2);
-    y[e] = s2;
+                              int r, double* y, double* gather) {
+  for (int e = threadIdx.x; e < p * r; e += kThreads) {
+    const int k = e % p, c = e / p;
+    gather[e] = g[k + (int64_t)perm[c] * p];
   }
+  __syncthreads();
+  // y(j, c) = sum_k A(k, j) G_r(k, c)
+  const int64_t a_j = a.tr ? a.s_r : a.s_c, a_k = a.tr ? a.s_c : a.s_r;
+  cta_gemm_tiled<kThreads>(q, r, p, a.src, a_j, a_k, gather, 1, p, y, q, false);
   __syncthreads();
 }
 
@@ -562,9 +559,9 @@ __device__ void right_multiply_fp64(double* m, int rows, int64_t ldm, int q, con
 // non-orthogonality of G32's columns: pairs within 4 u32 sqrt(p) of orthogonal or below the FP32
 // noise floor).  So tail(A) >= tail(c) - sqrt(q - dense_h) delta, and when that exceeds eps the
 // later stages could only confirm "dense": they are skipped and the function returns 1.
-__device__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v, double* sc,
-                         int max_sweeps, double eps, int dense_h,
-                         double fro, SvdShared& sh, unsigned long long* jstats) {
+__device__ __noinline__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v,
+                                      double* sc, int max_sweeps, double eps, int dense_h,
+                                      double fro, SvdShared& sh, unsigned long long* jstats) {
   // FP32 copies in the per-CTA scratch: the kernels run with the largest L1 carveout, which
   // measured as fast as holding the copies in shared memory and gives the 256-column tiles
   // (copies of 512 KB) the most cache
@@ -715,7 +712,7 @@ __global__ void __launch_bounds__(kThreads) compress_qr_kernel(MatView C, const 
     if (!tracked) {
       // V_r S_r^2 = M^T G_r into V (M is still intact), or the least-squares V_r
       SrcView mv{M, 1, R, false};
-      recover_right(mv, R, R, G, sh.perm, r, V);
+      recover_right(mv, R, R, G, sh.perm, r, V, sc);
       if (ls) ls = ls_solve(V, R, r, G, R, sh.perm, sh.sorted, sc, sh);
     }
     double* Xo = C.pool + sC;
@@ -927,11 +924,13 @@ __device__ double sigma_min_lower_bound(const double* g, int p, int J, double* x
   return (f2 > 0.0 && isfinite(f2)) ? 1.0 / sqrt(f2) : 0.0;
 }
 
-__device__ int compress_by_pivoted_qr(const SrcView& a, int p, int q, bool tr, int m, int n,
-                                      double eps, int max_sweeps, double* g, double* wv,
-                                      double* sc, double* slot, int* kind_out, int* rank_out,
-                                      double* norm_out, SvdShared& sh,
-                                      unsigned long long* jstats) {
+// (not inlined: the kernel's register allocation stays with its own paths)
+__device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int q, bool tr,
+                                                   int m, int n, double eps, int max_sweeps,
+                                                   double* g, double* wv, double* sc,
+                                                   double* slot, int* kind_out, int* rank_out,
+                                                   double* norm_out, SvdShared& sh,
+                                                   unsigned long long* jstats) {
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
   // ranks up to q/2 are stored low rank: R (k x q) then goes to the slot (the source is no
   // longer needed once the QR has met the threshold) and the SVD factors of R^T (q x k and
@@ -1085,7 +1084,7 @@ __device__ int compress_by_pivoted_qr(const SrcView& a, int p, int q, bool tr, i
   }
   const bool tracked = sh.v_tracked;
   bool ls = !tracked && sh.ls_recover;
-  if (!tracked) recover_right(mv, q, k, gs, sh.perm, r, vs);   // Y = R G_r (k x r)
+  if (!tracked) recover_right(mv, q, k, gs, sh.perm, r, vs, sc);   // Y = R G_r (k x r)
   if (ls) ls = ls_solve(vs, k, r, gs, q, sh.perm, sh.sorted, sc, sh);
   // R = V_M S U_M^T:  X_R = (V_M S)_r (k x r), W_R = (U_M)_r (q x r); A ~ (Q_k X_R) (P W_R)^T
   // (R in the slot is no longer read: the factors overwrite it)
@@ -1125,7 +1124,7 @@ __device__ int compress_by_pivoted_qr(const SrcView& a, int p, int q, bool tr, i
 // Dense truncated SVD of whole blocks (ROUTE_DACC tiles, recompressed dense tiles, building a
 // CLR matrix from a dense one).
 // ---------------------------------------------------------------------------------------------
-__global__ void __launch_bounds__(kThreads) compress_dense_kernel(
+__global__ void __launch_bounds__(kThreads, 1) compress_dense_kernel(
     MatView C, const int* list, const int* count, const int* order, const double* src,
     int64_t lds, double* ws, double* svd_scratch, double eps, double drop_norm,
     int dense_only, int rrqr, int prereduce, int max_sweeps, int* err, int* sched,
@@ -1230,7 +1229,7 @@ __global__ void __launch_bounds__(kThreads) compress_dense_kernel(
       const SrcView view{S, s_r, s_c, tr};
       const bool tracked = sh.v_tracked;
       bool ls = !tracked && sh.ls_recover;
-      if (!tracked) recover_right(view, p, q, G, sh.perm, r, V);
+      if (!tracked) recover_right(view, p, q, G, sh.perm, r, V, sc);
       if (ls) ls = ls_solve(V, q, r, G, p, sh.perm, sh.sorted, sc, sh);
       if (jstats && threadIdx.x == 0 && !tracked)
         atomicAdd(&jstats[4], 2ull * p * q * r);

@@ -54,10 +54,12 @@ def ns_rank_distribution(ctx: "clr.Context", s: "clr.Matrix", k: int = 5) -> Dic
                  "proxy_met": st["proxy_met"], "residual_met": st["residual_met"],
                  "converged": st["converged"], "status": st["status"]}
     out["profile"] = {key: prof[key] for key in ("products", "ms_dense", "ms_lowrank",
-                                                  "ms_compress", "svd_blocks", "svd_sweeps_fp32",
-                                                  "svd_sweeps_fp64", "svd_early_dense",
-                                                  "svd_prereduced", "svd_flops_fp64",
-                                                  "svd_flops_fp32")}
+                                                  "ms_compress", "ms_compress_qr",
+                                                  "ms_compress_dense", "svd_blocks",
+                                                  "svd_sweeps_fp32", "svd_sweeps_fp64",
+                                                  "svd_early_dense", "svd_prereduced",
+                                                  "svd_flops_fp64", "svd_flops_fp32",
+                                                  "svd_flops_fp64_qr", "svd_flops_fp32_qr")}
     ctx.set_opts(ns_snapshot_iter=0)
     return out
 
