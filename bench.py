@@ -70,6 +70,9 @@ def parse():
                     help="skip the plain-FP64 product of the same workload")
     ap.add_argument("--no-chain", action="store_true",
                     help="skip the N = 2048 1D-chain product (FP64 and split)")
+    ap.add_argument("--ns-lattice-large", default="8x8x8",
+                    help="lattice sites of a second, larger overlap NS measurement (timed run "
+                         "only), or 'none'")
     return ap.parse_args()
 
 
@@ -400,9 +403,10 @@ def run_ours(args):
     fp64_peak = clr.probe_fp64_rate(dev)
 
     # the plain form: the same product with FP64 tile products on the CUDA cores
-    fp64 = None
+    fp64 = ozaki = None
     if not args.no_fp64 and args.prec != "fp64":
         fp64 = fp64_product(ctx, ga, gb, gc, w, alg_flops, fp64_peak, value, acc, rank)
+        ozaki = ozaki_product(ctx, ga, gb, gc, w, alg_flops, fp64["tflops"], rank)
 
     # the 1D-chain product (N = 2048, eps = 1e-8): FP64 against the split forms
     chain = None
@@ -441,7 +445,7 @@ def run_ours(args):
     # The same run with split products (bf16x6, FP64 from ||X - I|| <= 1e-3) shows the split
     # floor.  The overlap-like S has block sparsity; the Coulomb-like V (erf(r)/r) has only
     # block-rank sparsity (Section 4.2).
-    ns_lat = ns_lat_split = ns_coul = None
+    ns_lat = ns_lat_split = ns_lat_ozaki = ns_coul = None
     if not args.no_ns and args.ns_lattice != "none":
         from paper_1509_00309_gb300 import workloads as wl
         shape = tuple(int(v) for v in args.ns_lattice.split("x"))
@@ -449,8 +453,17 @@ def run_ours(args):
         ns_lat = lattice_ns(clr, wlat, args.ns_lattice, "overlap", fp64_peak, "fp64")
         ns_lat_split = lattice_ns(clr, wlat, args.ns_lattice, "overlap", fp64_peak, "bf16x6",
                                   snapshot=False)
+        ns_lat_ozaki = lattice_ns(clr, wlat, args.ns_lattice, "overlap", fp64_peak, "ozaki",
+                                  snapshot=False)
         ns_coul = lattice_ns(clr, wl.lattice_coulomb(shape=shape), args.ns_lattice,
                              "Coulomb-like erf(r)/r", fp64_peak, "fp64", snapshot=False)
+    ns_large = None
+    if not args.no_ns and args.ns_lattice_large != "none":
+        from paper_1509_00309_gb300 import workloads as wl
+        shape = tuple(int(v) for v in args.ns_lattice_large.split("x"))
+        wlarge = wl.lattice_overlap(shape=shape)
+        ns_large = {p: lattice_ns_timed(clr, wlarge, args.ns_lattice_large, p)
+                    for p in ("ozaki", "fp64")}
 
     # 64 independent 1D-chain products of uneven size in one CUDA graph (the batched
     # configuration), autotuned and FP64-only, each measured in a child process with its own
@@ -475,13 +488,49 @@ def run_ours(args):
                 "accuracy": acc, "phases_ms_per_step": phases,
                 "algorithmic_flops_per_step": alg_flops,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "fp64_dense": fp64,
+                "fp64_accurate_tensor": ozaki,
                 "chain_product": chain, "ns": ns, "ns_lattice": ns_lat,
-                "ns_lattice_split": ns_lat_split, "ns_coulomb": ns_coul, "batch": batch,
+                "ns_lattice_split": ns_lat_split, "ns_lattice_ozaki": ns_lat_ozaki,
+                "ns_coulomb": ns_coul,
+                "ns_lattice_large": ns_large, "batch": batch,
                 "gpu_launches": int(prof["launches"]), "clocks": clk.summary()}
         print(json.dumps(line), flush=True)
     if ws > 1:
         import torch.distributed as dist
         dist.destroy_process_group()
+
+
+def ozaki_product(ctx, ga, gb, gc, w, alg_flops, fp64_value, rank, warmup=2, steps=5):
+    """The same workload with FP64-accurate dense products on the tensor cores (exact slices,
+    precision "ozaki"): TFLOP/s over `steps` products after `warmup`, the exact-slice kernel's
+    time, and the accuracy beside the FP64 form's."""
+    import torch
+    prev = ctx.get_opts().precision
+    ctx.set_opts(precision="ozaki")
+    for _ in range(warmup):
+        ctx.multiply_into(ga, gb, gc)
+    torch.cuda.synchronize()
+    ctx.profile_enable(True)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    e[0].record()
+    for _ in range(steps):
+        ctx.multiply_into(ga, gb, gc)
+    e[1].record()
+    torch.cuda.synchronize()
+    ctx.check()
+    prof = ctx.profile_read()
+    ctx.profile_enable(False)
+    ctx.set_opts(precision=prev)
+    ms = e[0].elapsed_time(e[1]) / steps
+    tf = alg_flops / (ms * 1e-3) / 1e12
+    kern_ms = prof["ms_dense"] / steps
+    acc = sampled_accuracy(w, dense_tiles_reader(gc, w.n)) if rank == 0 else None
+    return {"ms_per_product": ms, "tflops": tf, "kernel": "ozaki_gemm_kernel",
+            "kernel_ms": kern_ms, "kernel_tflops": alg_flops / (kern_ms * 1e-3) / 1e12,
+            "staging_ms": prof["ms_stage"] / steps,
+            "tensor_products_per_flop": 28,
+            "accuracy": acc, "over_fp64_speedup": tf / fp64_value if fp64_value else None,
+            "steps": steps, "warmup": warmup}
 
 
 def fp64_product(ctx, ga, gb, gc, w, alg_flops, fp64_peak, split_value, split_acc, rank):
@@ -594,9 +643,10 @@ def lattice_ns(clr, w, shape_txt, what, fp64_peak, precision, snapshot=True):
     per iteration."""
     import torch
     from paper_1509_00309_gb300 import diagnostics
+    split = precision in ("bf16x3", "bf16x6")
     ctx = clr.Context(torch.cuda.current_device(), precision=precision, eps_lr=EPS_NS_LATTICE,
                       eps_sp=w.eps_sp, ns_tol=1e-6, ns_max_iter=40, recompress_dense=1,
-                      ns_fp64_tail=int(precision != "fp64"), ns_ladder_switch=1e-3)
+                      ns_fp64_tail=int(split), ns_ladder_switch=1e-3)
     sm = ctx.from_dense(torch.from_numpy(w.a).cuda(), w.row_sizes, eps_lr=w.eps_lr,
                         drop_norm=w.drop_norm)
     ctx.set_opts(ns_max_iter=1, ns_tol=0.0)
@@ -615,7 +665,7 @@ def lattice_ns(clr, w, shape_txt, what, fp64_peak, precision, snapshot=True):
            "proxy_final": st["proxy"][-1],
            "residual_ZSZ_minus_I_rms": st["residual"], "tol": 1e-6,
            "residual_met": st["residual_met"], "proxy_met": st["proxy_met"],
-           "precision": precision if precision == "fp64" else
+           "precision": precision if precision in ("fp64", "ozaki") else
                         "%s, fp64 below proxy 1e-3" % precision,
            "recompress_dense": True,
            "profiled_run": {
@@ -632,6 +682,33 @@ def lattice_ns(clr, w, shape_txt, what, fp64_peak, precision, snapshot=True):
             k: {f: d[k][f] for f in ("zero", "dense", "low_rank", "lr_rank_mean", "lr_rank_max")}
             for k in ("S", "X_5", "T_5", "Y_5", "Z_5", "Z_final") if d.get(k)}
     return out
+
+
+def lattice_ns_timed(clr, w, shape_txt, precision="fp64"):
+    """NS on a larger lattice overlap matrix at the stated error: one unprofiled run (after a
+    one-iteration warm-up that sizes the workspaces), FP64 products, iterates truncated at
+    EPS_NS_LATTICE, dense-accumulated tiles re-tested."""
+    import torch
+    ctx = clr.Context(torch.cuda.current_device(), precision=precision,
+                      eps_lr=EPS_NS_LATTICE, eps_sp=w.eps_sp, ns_tol=1e-6, ns_max_iter=40,
+                      recompress_dense=1)
+    sm = ctx.from_dense(torch.from_numpy(w.a).cuda(), w.row_sizes, eps_lr=w.eps_lr,
+                        drop_norm=w.drop_norm)
+    ctx.set_opts(ns_max_iter=1, ns_tol=0.0)
+    ctx.sqrt_inv(sm, allow_noconv=True)
+    ctx.set_opts(ns_max_iter=40, ns_tol=1e-6)
+    torch.cuda.synchronize()
+    z, st, _ = ctx.sqrt_inv(sm, allow_noconv=True)
+    info = z.info()
+    return {"workload": "3D lattice overlap matrix, %s sites x 16 points, N=%d, %d clusters of "
+                        "64..256, built at eps_lr=%g, iterates truncated at %g" % (
+                            shape_txt, w.n, len(w.row_sizes), w.eps_lr, EPS_NS_LATTICE),
+            "ms_per_iteration": st["ms_total"] / max(1, st["iters"]),
+            "iterations": st["iters"], "ms_residual": st["ms_residual"],
+            "proxy_final": st["proxy"][-1], "residual_ZSZ_minus_I_rms": st["residual"],
+            "tol": 1e-6, "residual_met": st["residual_met"], "proxy_met": st["proxy_met"],
+            "precision": precision, "recompress_dense": True,
+            "z_blocks_zero_dense_lr": info["n_blocks"]}
 
 
 def _alu_roofline(f64, f32, ms, fp64_peak):

@@ -64,6 +64,13 @@ extern "C" {
 #define CLR_PREC_BF16X3 1  /* 2-term bf16 split, 3 tensor-core products, FP32 accumulation */
 #define CLR_PREC_BF16X6 2  /* 3-term bf16 split, 6 tensor-core products, FP32 accumulation */
 #define CLR_PREC_AUTO   3  /* cheapest of the above whose a-priori error bound meets eps_lr */
+#define CLR_PREC_OZAKI  4  /* FP64-accurate dense x dense products on the tensor cores: rows
+                              of A and columns of B scaled by powers of two and cut into 7
+                              fixed-point slices of 6 bits (bf16 digits), the 28 slice pairs of
+                              weight >= 2^-42 summed exactly in FP32 over segments of 2048 and
+                              in FP64 across segments (Ozaki, Ogita, Oishi, Rump 2012); error
+                              <~ K 2^-39 max|a_i.| max|b_.j| per entry.  Low-rank contributions
+                              stay FP64, as with CLR_PREC_FP64 */
 
 #define CLR_MAX_CLUSTER 256
 

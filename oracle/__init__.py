@@ -14,4 +14,6 @@ Modules:
                    the Daleckii–Krein gradient of trace(W S^-1/2) and the NS adjoint.
   split_oracle  -- bit-level bfloat16 rounding and the exact value of a split-precision
                    (multi-term bf16) product, used to check split tensor-core products.
+  ozaki_oracle  -- exact-slice (Ozaki-scheme) digits, exponents and the exact value of the
+                   sliced product, used to check the FP64-accurate tensor-core products.
 """

@@ -18,7 +18,7 @@ from . import build as _build
 CLR_OK, CLR_EINVAL, CLR_ENOMEM, CLR_ENOCONV, CLR_ETIMEOUT, CLR_ECUDA, CLR_ENOTSUP = \
     0, -1, -2, -3, -4, -5, -6
 KIND_ZERO, KIND_DENSE, KIND_LR = 0, 1, 2
-PREC = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "auto": 3}
+PREC = {"fp64": 0, "bf16x3": 1, "bf16x6": 2, "auto": 3, "ozaki": 4}
 PREC_NAME = {v: k for k, v in PREC.items()}
 MAX_CLUSTER = 256
 NS_MAX_HISTORY = 256

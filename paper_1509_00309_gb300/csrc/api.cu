@@ -128,6 +128,7 @@ DevicePool& pool() {
 // graph run on several branches, each with its own set.
 struct WorkSet {
   DevBuf plan_ints, triples, counters, ws, scratch, panels_a, panels_b, tile_flags, order;
+  DevBuf oz_exps;  // row exponents of the exact-slice products (A rows, then B panel rows)
   // A's bf16 panels as staged for (matrix, terms, padded sizes): reused only while a caller
   // that guarantees A does not change (clr_multiply_host_stream) sets ctx->reuse_a
   DevBuf host_b, host_c, host_err;  // staging of the streamed host product (per pipeline slot)
@@ -137,7 +138,7 @@ struct WorkSet {
   int64_t staged_m = 0, staged_k = 0;
   void release() {
     for (DevBuf* b : {&plan_ints, &triples, &counters, &ws, &scratch, &panels_a, &panels_b,
-                      &tile_flags, &order, &host_b, &host_c, &host_err})
+                      &tile_flags, &order, &oz_exps, &host_b, &host_c, &host_err})
       b->release();
   }
 };
@@ -596,7 +597,7 @@ extern "C" int clr_destroy(clr_ctx_t ctx) {
 
 extern "C" int clr_set_opts(clr_ctx_t ctx, const clr_opts* o) {
   if (!ctx || !o) return CLR_EINVAL;
-  if (!(o->eps_lr >= 0.0) || !(o->eps_sp >= 0.0) || o->precision < 0 || o->precision > 3)
+  if (!(o->eps_lr >= 0.0) || !(o->eps_sp >= 0.0) || o->precision < 0 || o->precision > 4)
     return fail(ctx, CLR_EINVAL, "bad options");
   ctx->opts = *o;
   return CLR_OK;
@@ -1006,6 +1007,56 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
   return CLR_OK;
 }
 
+// Dense x dense products by exact slices on the tensor cores (CLR_PREC_OZAKI): the dense blocks
+// of A and B are staged as 7 bf16 digit planes with per-row exponents, and the exact-slice GEMM
+// writes the route-DENSE tiles; low-rank contributions follow in FP64 (low-rank kernel).
+int run_ozaki_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Plan& p,
+                 cudaStream_t s) {
+  const int64_t M_pad = (c->n_rows + 127) / 128 * 128;
+  const int64_t N_pad = (c->n_cols + 63) / 64 * 64;
+  const int64_t K_pad = (a->n_cols + 127) / 128 * 128;
+  WorkSet* w = ctx->cur;
+  CLR_CUDA(w->panels_a.ensure((size_t)kOzakiSlices * M_pad * K_pad * 2));
+  CLR_CUDA(w->panels_b.ensure((size_t)kOzakiSlices * N_pad * K_pad * 2));
+  CLR_CUDA(w->oz_exps.ensure((size_t)(M_pad + N_pad) * sizeof(int)));
+  CLR_CUDA(w->tile_flags.ensure((size_t)(M_pad / 128) * (N_pad / 64)));
+  w->staged_a = nullptr;   // the panels no longer hold a split staging
+  MatView av = a->view(), bv = b->view(), cv = c->view();
+  int* ea = (int*)w->oz_exps.p;
+  int* eb = ea + M_pad;
+  launch_ozaki_stage(av, c->d_row_idx, a->d_col_idx, w->panels_a.p, ea, M_pad, K_pad, 1, s);
+  launch_ozaki_stage(bv, a->d_col_idx, c->d_col_idx, w->panels_b.p, eb, N_pad, K_pad, 0, s);
+  CLR_CHECK_LAUNCH("exact-slice staging");
+  prof_launches(ctx, 4);   // 2 exponent + 2 digit kernels (the exponent memsets are not kernels)
+  prof_mark(ctx, s, PH_STAGE);
+  OzakiGemmArgs g;
+  g.C = &cv;
+  g.p = &p;
+  g.a_panels = w->panels_a.p;
+  g.b_panels = w->panels_b.p;
+  g.ea = ea;
+  g.eb = eb;
+  g.M_pad = M_pad;
+  g.N_pad = N_pad;
+  g.K_pad = K_pad;
+  g.row_tile_of = c->d_row_idx;
+  g.col_tile_of = c->d_col_idx;
+  g.tile_active = (unsigned char*)w->tile_flags.p;
+  g.n_sm = ctx->n_sm;
+  g.err = &p.counters->err;
+  g.wait_ns = ctx->opts.wait_timeout_us > 0
+                  ? 1000ull * (unsigned long long)ctx->opts.wait_timeout_us : 2000000000ull;
+  g.encode_fn = ctx->encode_fn;
+  std::string why;
+  const int st = ozaki_gemm_dd(g, s, &why);
+  if (st) return fail(ctx, st, "exact-slice GEMM: " + why);
+  CLR_CHECK_LAUNCH("exact-slice GEMM");
+  prof_launches(ctx, 2);   // tile flags + GEMM
+  if (ctx->prof_on) ctx->prof.dense_launches++;
+  prof_mark(ctx, s, PH_DENSE);
+  return CLR_OK;
+}
+
 int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double alpha,
                   const Tuning& tune, clr_product_stats* stats, cudaStream_t s) {
   const int prec = tune.prec;
@@ -1044,12 +1095,16 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
     prof_launches(ctx, 1);
     if (ctx->prof_on) ctx->prof.dense_launches++;
     prof_mark(ctx, s, PH_DENSE);
+  } else if (prec == CLR_PREC_OZAKI) {
+    st = run_ozaki_dd(ctx, a, b, c, p, s);
+    if (st) return st;
   } else {
     st = run_split_dd(ctx, a, b, c, p, prec, s, &fused_norms);
     if (st) return st;
   }
+  const bool split = prec == CLR_PREC_BF16X3 || prec == CLR_PREC_BF16X6;
   launch_lr_products(av, bv, cv, p, (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p,
-                     kScratchPerCta, prec != CLR_PREC_FP64, lr_grid, s);
+                     kScratchPerCta, split, lr_grid, s);
   CLR_CHECK_LAUNCH("low-rank products");
   prof_launches(ctx, 1);
   prof_mark(ctx, s, PH_LOWRANK);
@@ -1089,8 +1144,9 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
     for (int q = 0; q < 3; ++q) stats->n_tiles[q] = (int64_t)pc.by_mode[q];
     stats->max_rank_sum = (int64_t)pc.max_rsum;
     stats->precision = prec;
-    stats->n_tiles_tensor =
-        prec == CLR_PREC_FP64 ? 0 : (int32_t)(pc.by_mode[1] + pc.n_gemm_dacc);
+    stats->n_tiles_tensor = prec == CLR_PREC_FP64 ? 0
+                            : prec == CLR_PREC_OZAKI ? (int32_t)pc.by_mode[1]
+                                                     : (int32_t)(pc.by_mode[1] + pc.n_gemm_dacc);
     st = take_device_error(ctx);
     if (st) return st;
   }

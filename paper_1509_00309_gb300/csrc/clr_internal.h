@@ -238,6 +238,29 @@ struct SplitGemmArgs {
   double* norm_sq = nullptr;
 };
 int split_gemm_dd(const SplitGemmArgs& a, cudaStream_t st, std::string* why);
+// k_ozaki.cu: FP64-accurate dense x dense products on the tensor cores (exact slices)
+constexpr int kOzakiSlices = 7;
+struct OzakiGemmArgs {
+  const MatView* C;
+  const Plan* p;
+  void* a_panels;     // kOzakiSlices x M_pad x K_pad bf16 digits
+  void* b_panels;     // kOzakiSlices x N_pad x K_pad
+  const int* ea;      // M_pad row exponents of A
+  const int* eb;      // N_pad column exponents (rows of the B panel)
+  int64_t M_pad, N_pad, K_pad;   // multiples of 128, 64, 128
+  const int* row_tile_of;
+  const int* col_tile_of;
+  unsigned char* tile_active;  // (M_pad/128) * (N_pad/64) flags
+  int n_sm;
+  int* err;
+  unsigned long long wait_ns = 2000000000ull;
+  void* encode_fn;
+};
+int ozaki_gemm_dd(const OzakiGemmArgs& a, cudaStream_t st, std::string* why);
+// exps: rows_pad ints, written (the row exponents); panels: kOzakiSlices planes
+void launch_ozaki_stage(const MatView& M, const int* row_idx, const int* col_idx, void* panels,
+                        int* exps, int64_t rows_pad, int64_t cols_pad, int a_mode,
+                        cudaStream_t st);
 void launch_split_stage(const MatView& M, const int* row_idx, const int* col_idx, void* panels,
                         int terms, int64_t rows_pad, int64_t cols_pad, int a_mode,
                         cudaStream_t st);

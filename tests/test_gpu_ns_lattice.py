@@ -36,14 +36,16 @@ def case():
     return clr, golden, w, s_or
 
 
-@pytest.mark.parametrize("idx", [0, 1])
-def test_lattice_ns_n4096_matches_oracle(case, idx):
+@pytest.mark.parametrize("idx,prec", [(0, "fp64"), (1, "fp64"), (1, "ozaki")])
+def test_lattice_ns_n4096_matches_oracle(case, idx, prec):
+    # FP64 products, and dense x dense products by exact slices on the tensor cores (their
+    # ~1e-12 relative error is far below the truncation at eps, so the iteration is the same)
     import torch
     clr, golden, w, s_or = case
     g = golden["runs"][idx]
     eps = g["eps_ns"]
     assert [int(x) for x in w.row_sizes] == g["row_sizes"] and w.n == g["n"] == 4096
-    ctx = clr.Context(0, precision="fp64", eps_lr=eps, eps_sp=w.eps_sp, ns_tol=g["tol"],
+    ctx = clr.Context(0, precision=prec, eps_lr=eps, eps_sp=w.eps_sp, ns_tol=g["tol"],
                       ns_max_iter=40, recompress_dense=1, ns_alpha=g["alpha"])
     gs = clr_pack.to_library(ctx, s_or)
     z, st, _ = ctx.sqrt_inv(gs, allow_noconv=True)
