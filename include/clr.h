@@ -63,7 +63,9 @@ extern "C" {
 #define CLR_PREC_FP64   0  /* FP64 on CUDA cores */
 #define CLR_PREC_BF16X3 1  /* 2-term bf16 split, 3 tensor-core products, FP32 accumulation */
 #define CLR_PREC_BF16X6 2  /* 3-term bf16 split, 6 tensor-core products, FP32 accumulation */
-#define CLR_PREC_AUTO   3  /* cheapest of the above whose a-priori error bound meets eps_lr */
+#define CLR_PREC_AUTO   3  /* cheapest of bf16x3, bf16x6, the exact slices below and FP64 whose
+                              a-priori error model meets eps_lr (the batch autotuner times each
+                              candidate and keeps the fastest) */
 #define CLR_PREC_OZAKI  4  /* FP64-accurate dense x dense products on the tensor cores: rows
                               of A and columns of B scaled by powers of two and cut into 7
                               fixed-point slices of 6 bits (bf16 digits), the 28 slice pairs of

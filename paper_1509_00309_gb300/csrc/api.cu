@@ -496,11 +496,14 @@ int choose_precision(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, double eps_in = -1
   // product term, including FP32 accumulation): bf16x3 ~ 2^-16.5, bf16x6 ~ 2^-23.  The
   // expected ||dC||_F is about u ||A||_F ||B||_F / sqrt(K); the product tolerance is
   // 10 eps ||A||_F ||B||_F.  Take the cheapest mode with a factor-4 margin.
+  // The exact-slice products err by ~2^-42 relative to the rows' and columns' largest entries
+  // per term; 2^-38 allows for the spread between those and the RMS entry.
   const double e0 = eps_in >= 0.0 ? eps_in : ctx->opts.eps_lr;
   const double eps = e0 > 0 ? e0 : 1e-8;
   const double sk = std::sqrt((double)a->n_cols);
   if (std::ldexp(1.0, -16) * 0.6 / sk * 4.0 <= 10.0 * eps) return CLR_PREC_BF16X3;
   if (std::ldexp(1.0, -23) / sk * 4.0 <= 10.0 * eps) return CLR_PREC_BF16X6;
+  if (std::ldexp(1.0, -38) / sk * 4.0 <= 10.0 * eps) return CLR_PREC_OZAKI;
   (void)b;
   return CLR_PREC_FP64;
 }
@@ -1786,7 +1789,8 @@ std::vector<int> precision_candidates(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, d
   const int cheapest = choose_precision(ctx, a, b, eps);
   std::vector<int> out;
   if (cheapest == CLR_PREC_BF16X3) out.push_back(CLR_PREC_BF16X3);
-  if (cheapest != CLR_PREC_FP64) out.push_back(CLR_PREC_BF16X6);
+  if (cheapest == CLR_PREC_BF16X3 || cheapest == CLR_PREC_BF16X6) out.push_back(CLR_PREC_BF16X6);
+  if (cheapest != CLR_PREC_FP64) out.push_back(CLR_PREC_OZAKI);
   out.push_back(CLR_PREC_FP64);
   return out;
 }
@@ -1867,7 +1871,7 @@ extern "C" int clr_autotune_load(clr_ctx_t ctx, const char* path) {
   double ms = 0.0;
   int n = 0;
   while (fscanf(f, "%255s %d %d %lf", key, &prec, &mult, &ms) == 4) {
-    if (prec < 0 || prec > 2 || mult < 1 || mult > 8) continue;
+    if (prec < 0 || prec > 4 || prec == CLR_PREC_AUTO || mult < 1 || mult > 8) continue;
     Tuning t;
     t.prec = prec;
     t.lr_mult = mult;

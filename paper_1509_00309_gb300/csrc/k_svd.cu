@@ -893,10 +893,14 @@ __device__ int rrqr_block(const double* S, int64_t s_r, int64_t s_c, int m, int 
 // triangle: R_11 is a submatrix of Q^T A P, so sigma_J(A) >= sigma_min(R_11), and the eps-rank
 // exceeds q/2 as soon as sigma_{q/2+1}(A) > eps.  sigma_min(R_11) is bounded below by
 // 1 / ||R_11^-1||_F (a triangular inverse, J^3/6 FMAs).
+// A block that meets neither (its QR rank at eps/16 lies between q/2 + 1 and 3q/5) goes on to
+// that threshold; the SVD of its R then decides: rank <= q/2 is stored low rank, otherwise the
+// block is stored dense as Q_k [R; 0] P^T (within eps/16 of the block).
 // Returns 1 when the block is done (low rank or zero, written to slot and the outputs), 2 when
-// it is certified dense (the source untouched: the caller stores it), 0 when neither holds
-// (a QR rank above q/2 at eps/16, or an inconclusive bound); the caller then takes the full
-// SVD, the source still untouched.
+// it is stored dense (certified with the source untouched, or reconstructed into the slot: the
+// caller stores the kind and copies an external source over it), 0 when the QR passed 3q/5
+// steps without meeting the threshold; the caller then takes the full SVD on the untouched
+// source.
 // g: p x q copy (ld p); wv: the tile's second workspace half (p q doubles); slot: the block's
 // m n output slot (also the source of product tiles, read only before R is written there).
 // ---------------------------------------------------------------------------------------------
@@ -932,12 +936,14 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
                                                    double* norm_out, SvdShared& sh,
                                                    unsigned long long* jstats) {
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
-  // ranks up to q/2 are stored low rank: R (k x q) then goes to the slot (the source is no
-  // longer needed once the QR has met the threshold) and the SVD factors of R^T (q x k and
-  // k x k, at most 3 q^2 / 4 <= p q doubles) to wv
+  // Once the QR has met the threshold the source is no longer needed: R (k x q) goes to the
+  // slot and the SVD factors of R^T (q x k and k x k, at most 0.96 q^2 <= p q doubles for
+  // k <= 3q/5) to wv.  Ranks up to q/2 are stored low rank.
   const int kmax = q / 2;
-  // steps after which a block still above the threshold is tested for the dense certificate
-  const int jmax = q / 2 + 1 <= q ? q / 2 + 1 : q;
+  // steps after which a block still above the threshold is tested for the dense certificate,
+  // and the most steps taken (the SVD of R must fit wv)
+  const int jcert = q / 2 + 1 <= q ? q / 2 + 1 : q;
+  const int jmax = (3 * q) / 5 > jcert ? (3 * q) / 5 : jcert;
   const double tau2 = (eps / 16.0) * (eps / 16.0);
   // copy with the column norms
   for (int c = w; c < q; c += kWarps) {
@@ -981,7 +987,15 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
     }
     __syncthreads();
     if (sh.kept_sq <= tau2) { k = j; break; }
-    if (j == jmax) break;  // not reached within floor(q/2) + 1 steps
+    if (j == jcert) {
+      // still above the threshold after floor(q/2) + 1 steps: dense if sigma_min(R_11) > eps
+      const double smin = sigma_min_lower_bound(g, p, jcert, wv, sh);
+      if (jstats && threadIdx.x == 0)
+        atomicAdd(&jstats[4], 2ull * fma_count + (unsigned long long)jcert * jcert * jcert / 3);
+      fma_count = 0;
+      if (smin > eps) return 2;
+    }
+    if (j == jmax) break;  // not reached within jmax steps
     const int piv = sh.qr_pivot;
     if (piv != j) {
       double* x = g + (int64_t)j * p;
@@ -1044,15 +1058,9 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
     fma_count += 3ull * (unsigned long long)(p - j) * (unsigned long long)(q - j - 1) + (p - j);
     __syncthreads();
   }
-  if (jstats && threadIdx.x == 0) atomicAdd(&jstats[4], 2ull * fma_count);
-  if (k < 0) {
-    // still above the threshold after jmax steps: dense if sigma_min(R_11) > eps
-    const double smin = sigma_min_lower_bound(g, p, jmax, wv, sh);
-    if (jstats && threadIdx.x == 0)
-      atomicAdd(&jstats[4], (unsigned long long)jmax * jmax * jmax / 3);
-    return smin > eps ? 2 : 0;
-  }
-  if (k > kmax) return 0;   // rank above q/2 at eps/16: the full SVD decides
+  if (jstats && threadIdx.x == 0)
+    atomicAdd(&jstats[4], 2ull * fma_count);   // (the QR's flops after the certificate test)
+  if (k < 0) return 0;   // no threshold within jmax steps: the full SVD decides
   const double trail2 = sh.kept_sq;
   __syncthreads();
   if (k == 0) {
@@ -1081,6 +1089,28 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
     if (threadIdx.x == 0) { *kind_out = CLR_KIND_ZERO; *rank_out = 0; *norm_out = 0.0; }
     __syncthreads();
     return 1;
+  }
+  if (r > kmax) {
+    // stored dense: the slot (overwritten by R) gets Q_k [R; 0] P^T, within ||R_22||_F <=
+    // eps/16 of the block (the caller copies an external source over it)
+    __syncthreads();
+    double* tmp = wv;   // p x q, pivoted column order
+    for (int e = threadIdx.x; e < p * q; e += kThreads) {
+      const int i = e % p, c = e / p;
+      tmp[e] = i < k ? rb[i + (int64_t)c * k] : 0.0;
+    }
+    __syncthreads();
+    apply_q(g, p, k, p, sh.qr_tau, tmp, q, p);
+    for (int e = threadIdx.x; e < p * q; e += kThreads) {
+      const int i = e % p, c = e / p;
+      const int oc = sh.qr_perm[c];
+      // A = block (p = m) or block^T (p = n); the slot is the block, column-major, ld m
+      slot[tr ? oc + (int64_t)i * m : i + (int64_t)oc * m] = tmp[e];
+    }
+    if (jstats && threadIdx.x == 0)
+      atomicAdd(&jstats[4], 4ull * (unsigned long long)p * q * k);
+    __syncthreads();
+    return 2;
   }
   const bool tracked = sh.v_tracked;
   bool ls = !tracked && sh.ls_recover;
