@@ -389,15 +389,19 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier(ws)
         t0 = time.perf_counter()
+        marks = [t0]
         for _ in range(e2e_steps):
             # the streamed host product: A in 2 row chunks, B and C in 4 column chunks; the
-            # copies overlap the 8 tile products (clr_multiply_host_stream)
+            # copies overlap the 8 tile products (clr_multiply_host_stream, which returns
+            # after synchronising)
             ctx.multiply_host_stream(a_h, b_h, c_h, w.row_sizes, n_chunks=4)
+            marks.append(time.perf_counter())
         torch.cuda.synchronize()
         el = max_over_ranks(time.perf_counter() - t0, ws)
         e2e = {"value": alg_flops * ws * e2e_steps / el / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8,
-               "ms_per_step": 1e3 * el / e2e_steps, "steps": e2e_steps}
+               "ms_per_step": 1e3 * el / e2e_steps, "steps": e2e_steps,
+               "ms_each": [round(1e3 * (b - a), 2) for a, b in zip(marks, marks[1:])]}
         del a_h, b_h, c_h
 
     fp64_peak = clr.probe_fp64_rate(dev)
@@ -676,6 +680,12 @@ def lattice_ns(clr, w, shape_txt, what, fp64_peak, precision, snapshot=True):
                "svd": {k: prof[k] for k in ("svd_blocks", "svd_sweeps_fp32",
                                             "svd_sweeps_fp64", "svd_early_dense",
                                             "svd_prereduced")},
+               "compress_dense_paths": {
+                   name: {"blocks": prof["svd_path_blocks"][i],
+                          "mcycles_per_block": prof["svd_path_cycles"][i] / 1e6 /
+                          max(1, prof["svd_path_blocks"][i])}
+                   for i, name in enumerate(("pivoted_qr_low_rank", "dense_without_svd",
+                                             "full_svd"))},
                "roofline_recompress": recompress_roofline(prof, fp64_peak)}}
     if snapshot:
         out["rank_distribution_iter5"] = {

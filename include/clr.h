@@ -352,6 +352,9 @@ typedef struct clr_profile {
   double ms_compress_dense;    /* dense truncated SVDs (compress_dense_kernel) */
   double svd_flops_fp64_qr;    /* the part of svd_flops_fp64 done by the QR route */
   double svd_flops_fp32_qr;    /* the part of svd_flops_fp32 done by the QR route */
+  double svd_path_cycles[3];   /* SM cycles in compress_dense_kernel per block, by path: pivoted
+                                  QR with the small SVD, dense without a full SVD, full SVD */
+  int64_t svd_path_blocks[3];  /* blocks by path */
 } clr_profile;
 int clr_profile_enable(clr_ctx_t ctx, int on);
 int clr_profile_read(clr_ctx_t ctx, clr_profile* out);

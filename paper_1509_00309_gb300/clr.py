@@ -67,7 +67,8 @@ class ClrProfile(C.Structure):
                 ("svd_early_dense", C.c_int64), ("svd_flops_fp64", C.c_double),
                 ("svd_flops_fp32", C.c_double), ("svd_prereduced", C.c_int64),
                 ("ms_compress_qr", C.c_double), ("ms_compress_dense", C.c_double),
-                ("svd_flops_fp64_qr", C.c_double), ("svd_flops_fp32_qr", C.c_double)]
+                ("svd_flops_fp64_qr", C.c_double), ("svd_flops_fp32_qr", C.c_double),
+                ("svd_path_cycles", C.c_double * 3), ("svd_path_blocks", C.c_int64 * 3)]
 
 
 _VP = C.c_void_p
@@ -312,7 +313,10 @@ class Context:
     def profile_read(self) -> Dict:
         p = ClrProfile()
         self._check(load().clr_profile_read(self.handle, C.byref(p)))
-        return {f: getattr(p, f) for f, _ in ClrProfile._fields_}
+        out = {f: getattr(p, f) for f, _ in ClrProfile._fields_}
+        for f in ("svd_path_cycles", "svd_path_blocks"):
+            out[f] = list(out[f])
+        return out
 
     # matrices ------------------------------------------------------------------------------
     def zeros(self, row_sizes, col_sizes=None) -> Matrix:

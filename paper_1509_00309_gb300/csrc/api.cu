@@ -451,9 +451,9 @@ const double* host_device_ptr(const void* p) {
 }
 
 
-// SVD counters while profiling (not inside a graph capture), else null.  Two blocks of 8:
+// SVD counters while profiling (not inside a graph capture), else null.  Three blocks of 8:
 // [0, 8) for dense truncated SVDs (compress_dense_kernel), [8, 16) for the QR route
-// (compress_qr_kernel).
+// (compress_qr_kernel), [16, 24) SM cycles and counts of compress_dense_kernel's paths.
 constexpr int kJstatsBlock = 8;
 unsigned long long* jst(clr_ctx_t ctx, int block = 0) {
   return (ctx->prof_on && !ctx->capturing && ctx->jstats.p)
@@ -1166,8 +1166,8 @@ extern "C" int clr_profile_enable(clr_ctx_t ctx, int on) {
   std::memset(&ctx->prof, 0, sizeof(ctx->prof));
   ctx->prof_on = on != 0;
   if (ctx->prof_on) {
-    CLR_CUDA(ctx->jstats.ensure(2 * kJstatsBlock * sizeof(unsigned long long)));
-    CLR_CUDA(cudaMemset(ctx->jstats.p, 0, 2 * kJstatsBlock * sizeof(unsigned long long)));
+    CLR_CUDA(ctx->jstats.ensure(3 * kJstatsBlock * sizeof(unsigned long long)));
+    CLR_CUDA(cudaMemset(ctx->jstats.p, 0, 3 * kJstatsBlock * sizeof(unsigned long long)));
   }
   return CLR_OK;
 }
@@ -1199,7 +1199,7 @@ extern "C" int clr_profile_read(clr_ctx_t ctx, clr_profile* out) {
     ctx->prof_events.clear();
   }
   if (ctx->jstats.p) {
-    unsigned long long j[2 * kJstatsBlock];
+    unsigned long long j[3 * kJstatsBlock];
     CLR_CUDA(cudaMemcpy(j, ctx->jstats.p, sizeof(j), cudaMemcpyDeviceToHost));
     const unsigned long long* q = j + kJstatsBlock;   // the QR route's block
     ctx->prof.svd_blocks = (int64_t)(j[0] + q[0]);
@@ -1211,6 +1211,11 @@ extern "C" int clr_profile_read(clr_ctx_t ctx, clr_profile* out) {
     ctx->prof.svd_prereduced = (int64_t)j[6];
     ctx->prof.svd_flops_fp64_qr = (double)q[4];
     ctx->prof.svd_flops_fp32_qr = (double)q[5];
+    const unsigned long long* pc = j + 2 * kJstatsBlock;   // per-path SM cycles and counts
+    for (int path = 0; path < 3; ++path) {
+      ctx->prof.svd_path_cycles[path] = (double)pc[2 * path];
+      ctx->prof.svd_path_blocks[path] = (int64_t)pc[2 * path + 1];
+    }
   }
   *out = ctx->prof;
   return CLR_OK;

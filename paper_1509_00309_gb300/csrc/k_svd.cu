@@ -24,6 +24,8 @@
 namespace clr {
 
 constexpr int kThreads = 512;
+// index of the per-path cycle counters in the profiling counters (third block of 8)
+constexpr int kPathCounters = 16;
 constexpr int kWarps = kThreads / 32;
 constexpr int kFp64SweepCap = 1;  // FP64 sweeps of svd_mixed when the right factor is recovered
 
@@ -1224,13 +1226,13 @@ __global__ void __launch_bounds__(kThreads, 1) compress_dense_kernel(
       }
     } else if (!dense_only) {
       const SrcView view{S, s_r, s_c, tr};
+      const long long c0 = clock64();
       // pivoted QR first: blocks of low numerical rank are truncated through the SVD of
       // the k x q factor, blocks of rank above q/2 certified dense
       const int pre = prereduce ? compress_by_pivoted_qr(view, p, q, tr, m, n, eps, max_sweeps,
                                                          G, V, sc, slot, &C.kind[t], &C.rank[t],
                                                          &C.norm[t], sh, jstats)
                                 : 0;
-      if (pre == 1) continue;
       if (pre == 0) {
         const int early_dense =
             svd_mixed(view, p, q, G, V, sc, max_sweeps, eps, q / 2, nrm, sh, jstats);
@@ -1238,9 +1240,17 @@ __global__ void __launch_bounds__(kThreads, 1) compress_dense_kernel(
           sort_and_truncate(G, p, q, p, eps, sh);
           r = sh.rank;
         }
-      } else if (jstats && threadIdx.x == 0) {
-        atomicAdd(&jstats[3], 1ull);   // certified dense without an SVD
+      } else if (pre == 2 && jstats && threadIdx.x == 0) {
+        atomicAdd(&jstats[3], 1ull);   // stored dense without a full SVD
       }
+      // SM cycles per path while profiling (block 2 of the counters): QR and small SVD,
+      // dense without a full SVD, full SVD (after the QR attempt)
+      if (jstats && threadIdx.x == 0) {
+        const int path = pre == 1 ? 0 : pre == 2 ? 1 : 2;
+        atomicAdd(&jstats[kPathCounters + 2 * path], (unsigned long long)(clock64() - c0));
+        atomicAdd(&jstats[kPathCounters + 2 * path + 1], 1ull);
+      }
+      if (pre == 1) continue;
     }
     const int lim = q / 2;
     if (r == 0) {
