@@ -686,6 +686,13 @@ def lattice_ns(clr, w, shape_txt, what, fp64_peak, precision, snapshot=True):
                           max(1, prof["svd_path_blocks"][i])}
                    for i, name in enumerate(("pivoted_qr_low_rank", "dense_without_svd",
                                              "full_svd"))},
+               "full_svd_stages_mcycles": dict(
+                   zip(("pivoted_qr_attempt", "fp32_sweeps_on_a", "fp64_orthonormalise_project",
+                        "fp32_sweeps_on_g", "fp64_orthonormalise_multiply", "fp64_sweeps",
+                        "truncate_store"),
+                       (round(c / 1e6, 1) for c in prof["svd_full_cycles"])),
+                   blocks_all_stages=prof["svd_full_blocks"],
+                   blocks_stored_dense=prof["svd_full_dense"]),
                "roofline_recompress": recompress_roofline(prof, fp64_peak)}}
     if snapshot:
         out["rank_distribution_iter5"] = {

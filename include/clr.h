@@ -298,15 +298,19 @@ int clr_lincomb(clr_ctx_t ctx, double a, clr_mat_t x, double b, clr_mat_t y, dou
  * With ns_tol > 0 the loop stops once that proxy is <= ns_tol, and the stated error is then
  * checked on the returned Z: the residual ||alpha Z S Z - I||_F / sqrt(N) (two more CLR
  * products).  Returns CLR_ENOCONV (with *z still set) unless that residual is <= ns_tol: the
- * proxy can meet the tolerance while truncation at eps_lr holds the residual above it.  With `tape` non-NULL the iterates (Y_n, Z_n)
- * are kept for clr_sqrt_inv_backward (checkpointed every iteration); the tape owns copies of
- * everything it needs, so S may be freed before the backward call. */
+ * proxy can meet the tolerance while truncation at eps_lr holds the residual above it.  With
+ * `tape` non-NULL the iterates (Y_n, Z_n) are kept for clr_sqrt_inv_backward (checkpointed
+ * every iteration); the tape owns copies of everything it needs, so S may be freed before the
+ * backward call. */
 int clr_sqrt_inv(clr_ctx_t ctx, clr_mat_t s, clr_mat_t* z, clr_ns_stats* stats,
                  clr_tape_t* tape, void* stream);
-/* ||alpha Z S Z - I||_F / sqrt(N) for z = sqrt(alpha) Z (two CLR products); synchronises. */
 /* clr_check: synchronises `stream` and returns (and clears) any error a kernel raised since the
  * last synchronising call. */
 int clr_check(clr_ctx_t ctx, void* stream);
+/* ||alpha Z S Z - I||_F / sqrt(N) for z = sqrt(alpha) Z: two CLR products in FP64, or by exact
+ * slices when the context's precision is CLR_PREC_OZAKI (FP64-accurate: at most
+ * K 2^-39 2^(e_i + f_j) per entry), whose densely accumulated tiles are summed without the
+ * low-rank re-test; synchronises. */
 int clr_ns_residual(clr_ctx_t ctx, clr_mat_t s, clr_mat_t z, double* out, void* stream);
 /* Adjoint of clr_sqrt_inv for L = trace(W^T-weighted) losses: given zbar = dL/dZ (Z the
  * returned sqrt(alpha) Z_n), returns sbar = dL/dS by running the NS recurrences backwards
@@ -355,6 +359,15 @@ typedef struct clr_profile {
   double svd_path_cycles[3];   /* SM cycles in compress_dense_kernel per block, by path: pivoted
                                   QR with the small SVD, dense without a full SVD, full SVD */
   int64_t svd_path_blocks[3];  /* blocks by path */
+  double svd_full_cycles[7];   /* SM cycles summed over the full-SVD blocks of
+                                  compress_dense_kernel, by stage: the pivoted QR attempt, FP32
+                                  sweeps on A, FP64 orthonormalisation and A V, FP32 sweeps on G,
+                                  FP64 orthonormalisation and G V2, FP64 sweeps, truncation and
+                                  the stores of the result */
+  int64_t svd_full_blocks;     /* full-SVD blocks that ran every stage (not certified dense
+                                  after the first FP32 stage) */
+  int64_t svd_full_dense;      /* of those, blocks whose truncation rank exceeded half the
+                                  smaller side (stored dense) */
 } clr_profile;
 int clr_profile_enable(clr_ctx_t ctx, int on);
 int clr_profile_read(clr_ctx_t ctx, clr_profile* out);

@@ -148,6 +148,8 @@ struct Tuning {
   int prec = CLR_PREC_FP64;
   int lr_mult = 2;     // CTAs per SM of the low-rank product and recompression kernels
   double eps = -1.0;   // truncation threshold of this product (< 0: the context's eps_lr)
+  int recompress = -1; // dense-accumulated C tiles re-tested for low rank (< 0: the context's
+                       // recompress_dense)
 };
 
 struct clr_ctx_s {
@@ -160,7 +162,7 @@ struct clr_ctx_s {
   // workspaces (grow-only)
   std::vector<std::unique_ptr<WorkSet>> wsets;
   WorkSet* cur = nullptr;  // workspace set used by the next product
-  DevBuf small, upload, jstats;  // jstats: 7 SVD counters accumulated while profiling
+  DevBuf small, upload, jstats;  // jstats: SVD counters accumulated while profiling
   bool capturing = false;
   // autotuner cache: shape key -> tuning and measured ms
   std::map<std::string, std::pair<Tuning, double>> tune_cache;
@@ -455,6 +457,9 @@ const double* host_device_ptr(const void* p) {
 // [0, 8) for dense truncated SVDs (compress_dense_kernel), [8, 16) for the QR route
 // (compress_qr_kernel), [16, 24) SM cycles and counts of compress_dense_kernel's paths.
 constexpr int kJstatsBlock = 8;
+// counter blocks: 0 compress_dense_kernel, 1 compress_qr_kernel, 2 per-path cycles of
+// compress_dense_kernel, 3 its full-SVD stages
+constexpr int kJstatsBlocks = 4;
 unsigned long long* jst(clr_ctx_t ctx, int block = 0) {
   return (ctx->prof_on && !ctx->capturing && ctx->jstats.p)
              ? (unsigned long long*)ctx->jstats.p + block * kJstatsBlock : nullptr;
@@ -939,7 +944,7 @@ namespace {
 // *fused_norms: set when the dense kernel's epilogue formed the sums of squares of the
 // route-DENSE tiles (then only their square roots remain to be taken).
 int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Plan& p, int prec,
-                 cudaStream_t s, bool* fused_norms) {
+                 bool recompress_dense, cudaStream_t s, bool* fused_norms) {
   const int terms = prec == CLR_PREC_BF16X3 ? 2 : 3;
   const int64_t M_pad = (c->n_rows + 127) / 128 * 128;
   const int64_t N_pad = (c->n_cols + 255) / 256 * 256;
@@ -988,7 +993,7 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
                                             : 2000000000ull;
   // norms in the epilogue when the dense tiles are final (not re-tested) and the clusters are
   // wide enough for its per-warp grouping
-  const bool fuse = !ctx->opts.recompress_dense &&
+  const bool fuse = !recompress_dense &&
                     *std::min_element(c->row_sizes.begin(), c->row_sizes.end()) >= 32 &&
                     *std::min_element(c->col_sizes.begin(), c->col_sizes.end()) >= 16;
   g.norm_sq = fuse ? c->d_norm : nullptr;
@@ -1080,6 +1085,8 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   CLR_CUDA(ctx->cur->scratch.ensure((size_t)lr_grid * scratch_per_cta() * sizeof(double)));
   MatView av = a->view(), bv = b->view(), cv = c->view();
   const clr_opts& o = ctx->opts;
+  const bool recompress_dense =
+      tune.recompress >= 0 ? tune.recompress != 0 : o.recompress_dense != 0;
   prof_mark(ctx, s, PH_START);
   // split precision: densely accumulated low-rank sums go to the tensor-core GEMM where its
   // error bound u sum_K ||A_IK|| ||B_KJ|| stays below eps / 16 (u: 2^-15 bf16x3, 2^-22 bf16x6)
@@ -1087,7 +1094,7 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
                          : prec == CLR_PREC_BF16X6 ? std::ldexp(1.0, -22) : 0.0;
   const double dacc_bound = u_split > 0.0 ? eps_lr / (16.0 * u_split) : 0.0;
   bool fused_norms = false;
-  launch_plan(av, bv, p, o.eps_sp, o.recompress_dense, dacc_bound, s);
+  launch_plan(av, bv, p, o.eps_sp, recompress_dense, dacc_bound, s);
   launch_set_route_kinds(cv, p, s);
   CLR_CHECK_LAUNCH("plan");
   prof_launches(ctx, 4);
@@ -1102,7 +1109,7 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
     st = run_ozaki_dd(ctx, a, b, c, p, s);
     if (st) return st;
   } else {
-    st = run_split_dd(ctx, a, b, c, p, prec, s, &fused_norms);
+    st = run_split_dd(ctx, a, b, c, p, prec, recompress_dense, s, &fused_norms);
     if (st) return st;
   }
   const bool split = prec == CLR_PREC_BF16X3 || prec == CLR_PREC_BF16X6;
@@ -1123,7 +1130,7 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   CLR_CHECK_LAUNCH("recompression");
   prof_launches(ctx, 2);
   prof_mark(ctx, s, PH_COMPRESS);
-  if (!o.recompress_dense) {
+  if (!recompress_dense) {
     if (fused_norms)
       launch_sqrt_dense_norms(cv, p, s);
     else
@@ -1166,8 +1173,9 @@ extern "C" int clr_profile_enable(clr_ctx_t ctx, int on) {
   std::memset(&ctx->prof, 0, sizeof(ctx->prof));
   ctx->prof_on = on != 0;
   if (ctx->prof_on) {
-    CLR_CUDA(ctx->jstats.ensure(3 * kJstatsBlock * sizeof(unsigned long long)));
-    CLR_CUDA(cudaMemset(ctx->jstats.p, 0, 3 * kJstatsBlock * sizeof(unsigned long long)));
+    const size_t bytes = kJstatsBlocks * kJstatsBlock * sizeof(unsigned long long);
+    CLR_CUDA(ctx->jstats.ensure(bytes));
+    CLR_CUDA(cudaMemset(ctx->jstats.p, 0, bytes));
   }
   return CLR_OK;
 }
@@ -1199,7 +1207,7 @@ extern "C" int clr_profile_read(clr_ctx_t ctx, clr_profile* out) {
     ctx->prof_events.clear();
   }
   if (ctx->jstats.p) {
-    unsigned long long j[3 * kJstatsBlock];
+    unsigned long long j[kJstatsBlocks * kJstatsBlock];
     CLR_CUDA(cudaMemcpy(j, ctx->jstats.p, sizeof(j), cudaMemcpyDeviceToHost));
     const unsigned long long* q = j + kJstatsBlock;   // the QR route's block
     ctx->prof.svd_blocks = (int64_t)(j[0] + q[0]);
@@ -1216,6 +1224,10 @@ extern "C" int clr_profile_read(clr_ctx_t ctx, clr_profile* out) {
       ctx->prof.svd_path_cycles[path] = (double)pc[2 * path];
       ctx->prof.svd_path_blocks[path] = (int64_t)pc[2 * path + 1];
     }
+    const unsigned long long* fc = j + 3 * kJstatsBlock;  // full-SVD stages (kFullStage*)
+    for (int st = 0; st < 7; ++st) ctx->prof.svd_full_cycles[st] = (double)fc[st];
+    ctx->prof.svd_full_blocks = (int64_t)fc[7];
+    ctx->prof.svd_full_dense = (int64_t)j[7];
   }
   *out = ctx->prof;
   return CLR_OK;
@@ -1454,10 +1466,15 @@ extern "C" int clr_ns_residual(clr_ctx_t ctx, clr_mat_t s_mat, clr_mat_t z, doub
   st = alloc_mat(ctx, z->nr, z->row_sizes.data(), z->nc, z->col_sizes.data(), &zsz);
   if (st) return st;
   g.v.push_back(zsz);
-  // FP64 products (the residual is the stated error, so it is not taken in split precision)
+  // FP64-accurate products (the residual is the stated error, so it is not taken in split
+  // precision): FP64, or exact slices when the context runs them, whose error per entry is at
+  // most K 2^-39 2^(e_i + f_j) (|a_ik| < 2^e_i, |b_kj| < 2^f_j), far below any stated error
+  // these iterates reach.  Densely accumulated tiles are not re-tested for low rank: Z S and
+  // Z S Z are only summed, and their tiles stay as accurate as the products make them.
   Tuning t;
-  t.prec = CLR_PREC_FP64;
+  t.prec = ctx->opts.precision == CLR_PREC_OZAKI ? CLR_PREC_OZAKI : CLR_PREC_FP64;
   t.eps = residual_eps(ctx->opts);
+  t.recompress = 0;
   st = multiply_into(ctx, z, s_mat, zs, 1.0, t, nullptr, s);
   if (st) return st;
   st = multiply_into(ctx, zs, z, zsz, 1.0, t, nullptr, s);

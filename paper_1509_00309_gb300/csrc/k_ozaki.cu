@@ -25,8 +25,13 @@
 //   warp 0     TMA producer: per 32-wide k chunk the 7 slices of the A tile (128 x 32) and of
 //              the B tile (64 x 32), 64-byte swizzle, into one of two pipeline stages;
 //   warp 1     allocates 512 TMEM columns (seven 128 x 64 FP32 accumulators, one per weight
-//              group g) and issues tcgen05.mma (M=128, N=64, K=16, kind::f16, bf16 in, FP32
-//              accumulate) for the 28 slice pairs;
+//              group g, side by side) and issues tcgen05.mma (M=128, K=16, kind::f16, bf16 in,
+//              FP32 accumulate) for the 28 slice pairs as 10 MMAs per K16 step: slice s of A
+//              against the B slices t = 0 .. 6 - s at once (N = 64 (7 - s), split at 256),
+//              which writes groups s .. 6 together.  Each A slice is then read from shared
+//              memory once per step instead of once per pair: 96 KB of operand reads per step
+//              instead of 168 KB, and the tensor core's operand fetch, not its math, is what
+//              bounds N = 64 MMAs;
 //   warps 2-9  epilogue: after every K segment of 2048 the seven exact group sums are read from
 //              TMEM and added, scaled by 2^(-6 g), into FP64 registers (32 per thread); after
 //              the tile's last segment the FP64 values are scaled by 2^(e_i + f_j - 10) and
@@ -147,9 +152,13 @@ __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   d |= (uint64_t)4 << 61;
   return d;
 }
-// Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, N = 64, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+// Instruction descriptor of kind::f16: D f32, A and B bf16, both K-major, M = 128, N = n
+// (a multiple of 16 up to 256).
+__device__ __forceinline__ uint32_t idesc_n(int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) |
+         ((uint32_t)(BM >> 4) << 24);
+}
+constexpr int kMaxSlicesPerMma = 256 / BN;   // B slices one MMA covers (N <= 256)
 
 __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
   asm volatile(
@@ -294,17 +303,21 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!mbar_wait(&full[s], phase, abort_flag, wait_ns)) { ok = false; break; }
             fence_after();
             const uint32_t st = saddr(smem + (size_t)s * STAGE);
-#pragma unroll 1
-            for (int g = 0; g < GROUPS; ++g) {
-              const uint32_t d_tmem = tmem_base + (uint32_t)(g * BN);
-              for (int sa = 0; sa <= g; ++sa) {
-                const uint32_t a_addr = st + sa * A_TILE;
-                const uint32_t b_addr = st + S * A_TILE + (g - sa) * B_TILE;
+            // A slice s times the consecutive B slices t = 0 .. 6 - s in one MMA of
+            // N = 64 (7 - s) (two where that exceeds 256): its output columns land in the
+            // accumulators of groups s .. 6, which are consecutive in TMEM.  The two MMAs of
+            // s = 0 cover every group, so they alone start a segment (accumulate off).
 #pragma unroll
-                for (int k16 = 0; k16 < BK / 16; ++k16) {
+            for (int k16 = 0; k16 < BK / 16; ++k16) {
+#pragma unroll 1
+              for (int sa = 0; sa < S; ++sa) {
+                const uint32_t a_addr = st + sa * A_TILE + k16 * 32;
+                for (int t0 = 0; t0 < S - sa; t0 += kMaxSlicesPerMma) {
+                  const int cnt = min(kMaxSlicesPerMma, S - sa - t0);
+                  const uint32_t d_tmem = tmem_base + (uint32_t)((sa + t0) * BN);
+                  const uint32_t b_addr = st + S * A_TILE + t0 * B_TILE + k16 * 32;
                   const uint32_t acc = (kc != k0 || sa != 0 || k16 != 0) ? 1u : 0u;
-                  umma_bf16(d_tmem, sdesc(a_addr + k16 * 32), sdesc(b_addr + k16 * 32), kIdesc,
-                            acc);
+                  umma_bf16(d_tmem, sdesc(a_addr), sdesc(b_addr), idesc_n(cnt * BN), acc);
                 }
               }
             }

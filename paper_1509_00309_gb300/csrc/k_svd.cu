@@ -26,6 +26,9 @@ namespace clr {
 constexpr int kThreads = 512;
 // index of the per-path cycle counters in the profiling counters (third block of 8)
 constexpr int kPathCounters = 16;
+// compress_dense_kernel's full-SVD stages while profiling (block 3 of the counters): cycles of
+// the pivoted QR attempt, the five stages of svd_mixed, truncation and stores; then the count
+constexpr int kFullStageCounters = 24;
 constexpr int kWarps = kThreads / 32;
 constexpr int kFp64SweepCap = 1;  // FP64 sweeps of svd_mixed when the right factor is recovered
 
@@ -189,6 +192,12 @@ __device__ __forceinline__ void rotation(double al, double be, double g, double&
 // equals g v^T (times the initial v^T when v is not reset).  T is float or double; the
 // convergence threshold is the type's epsilon times sqrt(p) (times tol_scale); pairs whose inner
 // product is below floor2 are left alone.
+// A pair found converged (or below the floor) is checked again only once one of its columns has
+// been rotated: each pair meets at the same round of every sweep (cyclic round-robin order), so
+// when neither column has been rotated since the pair's check one sweep earlier, its inner
+// product is the one that check computed and the pair is skipped.  Late sweeps, and the
+// refinement of columns that are already orthogonal to each other, then touch only the pairs
+// of recently rotated columns.
 template <typename T>
 __device__ int jacobi_svd(T* g, int p, int q, int64_t ldg, T* v, int64_t ldv,
                           int max_sweeps, int* sh_flag, bool reset_v = true,
@@ -197,6 +206,8 @@ __device__ int jacobi_svd(T* g, int p, int q, int64_t ldg, T* v, int64_t ldv,
   // refreshed (fused into the rotation pass) for the two columns of every rotated pair, so a
   // pair costs one inner product unless it is rotated.
   __shared__ T nrm2[CLR_MAX_CLUSTER];
+  // per column: the step (sweep * (qq - 1) + round) of its last rotation, -1 if none
+  __shared__ int last_rot[CLR_MAX_CLUSTER];
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
   if (reset_v && v) {
     for (int e = threadIdx.x; e < q * q; e += kThreads)
@@ -206,6 +217,7 @@ __device__ int jacobi_svd(T* g, int p, int q, int64_t ldg, T* v, int64_t ldv,
   const int qq = q + (q & 1);  // even number of slots; slot q is a dummy when q is odd
   const T eps_t = sizeof(T) == 4 ? T(FLT_EPSILON) : T(DBL_EPSILON);
   const T tol = eps_t * sqrt(T(p)) * tol_scale;
+  for (int c = threadIdx.x; c < q; c += kThreads) last_rot[c] = -1;
   int sweep = 0;
   for (; sweep < max_sweeps; ++sweep) {
     for (int c = w; c < q; c += kWarps) {
@@ -230,47 +242,53 @@ __device__ int jacobi_svd(T* g, int p, int q, int64_t ldg, T* v, int64_t ldv,
           if (b < 0) b += qq - 1;
         }
         if (a >= q || b >= q) continue;
+        const int step = sweep * (qq - 1) + round;
+        // neither column rotated since this pair's check one sweep ago (step - (qq - 1))
+        if (sweep > 0 && last_rot[a] < step - (qq - 1) && last_rot[b] < step - (qq - 1))
+          continue;
         const T al = nrm2[a], be = nrm2[b];
         // both columns at the noise floor: |g_a . g_b| <= |g_a| |g_b| <= floor2, nothing to do
         if (pair_below_floor(al, be, floor2)) continue;
         T* ga = g + (int64_t)a * ldg;
         T* gb = g + (int64_t)b * ldg;
-        // FP64 (global memory): the two columns stay in registers between the inner product
-        // and the rotation; FP32 (shared memory): re-read
-        constexpr int kPer = sizeof(T) == 8 ? CLR_MAX_CLUSTER / 32 : 1;
+        // The working copies live in global scratch (L2 for the largest blocks): the two
+        // columns stay in registers between the inner product and the rotation, and in FP32
+        // the two columns of v are fetched before the rotation is formed, so that their latency
+        // overlaps it (in FP64 the registers that takes would spill)
+        constexpr int kPer = CLR_MAX_CLUSTER / 32;
+        constexpr bool kPrefetchV = sizeof(T) == 4;
         T xa[kPer], xb[kPer];
         T ga_gb = 0;
-        if constexpr (sizeof(T) == 8) {
 #pragma unroll
-          for (int j = 0; j < kPer; ++j) {
-            if (32 * j >= p) break;
-            const int i = l + 32 * j;
-            xa[j] = i < p ? ga[i] : T(0);
-            xb[j] = i < p ? gb[i] : T(0);
-            ga_gb = fma(xa[j], xb[j], ga_gb);
-          }
-        } else {
-          for (int i = l; i < p; i += 32) ga_gb = fma(ga[i], gb[i], ga_gb);
+        for (int j = 0; j < kPer; ++j) {
+          const int i = l + 32 * j;
+          xa[j] = i < p ? ga[i] : T(0);
+          xb[j] = i < p ? gb[i] : T(0);
+          ga_gb = fma(xa[j], xb[j], ga_gb);
         }
         ga_gb = warp_sum(ga_gb);
         if (pair_converged(al, be, ga_gb, tol, floor2)) continue;
-        T c, sn, t;
-        rotation(al, be, ga_gb, c, sn, t);
-        if constexpr (sizeof(T) == 8) {
+        T* va = v ? v + (int64_t)a * ldv : nullptr;
+        T* vb = v ? v + (int64_t)b * ldv : nullptr;
+        T ya[kPrefetchV ? kPer : 1], yb[kPrefetchV ? kPer : 1];
+        if constexpr (kPrefetchV) {
+          if (v) {
 #pragma unroll
-          for (int j = 0; j < kPer; ++j) {
-            if (32 * j >= p) break;
-            const int i = l + 32 * j;
-            if (i < p) {
-              ga[i] = c * xa[j] - sn * xb[j];
-              gb[i] = sn * xa[j] + c * xb[j];
+            for (int j = 0; j < kPer; ++j) {
+              const int i = l + 32 * j;
+              ya[j] = i < q ? va[i] : T(0);
+              yb[j] = i < q ? vb[i] : T(0);
             }
           }
-        } else {
-          for (int i = l; i < p; i += 32) {
-            const T x = ga[i], y = gb[i];
-            ga[i] = c * x - sn * y;
-            gb[i] = sn * x + c * y;
+        }
+        T c, sn, t;
+        rotation(al, be, ga_gb, c, sn, t);
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+          const int i = l + 32 * j;
+          if (i < p) {
+            ga[i] = c * xa[j] - sn * xb[j];
+            gb[i] = sn * xa[j] + c * xb[j];
           }
         }
         // new squared norms: a - t g and b + t g exactly; recomputed from the rotated columns
@@ -287,17 +305,28 @@ __device__ int jacobi_svd(T* g, int p, int q, int64_t ldg, T* v, int64_t ldv,
           nb = warp_sum(sb);
         }
         if (v) {
-          T* va = v + (int64_t)a * ldv;
-          T* vb = v + (int64_t)b * ldv;
-          for (int i = l; i < q; i += 32) {
-            const T x = va[i], y = vb[i];
-            va[i] = c * x - sn * y;
-            vb[i] = sn * x + c * y;
+          if constexpr (kPrefetchV) {
+#pragma unroll
+            for (int j = 0; j < kPer; ++j) {
+              const int i = l + 32 * j;
+              if (i < q) {
+                va[i] = c * ya[j] - sn * yb[j];
+                vb[i] = sn * ya[j] + c * yb[j];
+              }
+            }
+          } else {
+            for (int i = l; i < q; i += 32) {
+              const T x = va[i], y = vb[i];
+              va[i] = c * x - sn * y;
+              vb[i] = sn * x + c * y;
+            }
           }
         }
         if (l == 0) {
           nrm2[a] = na;
           nrm2[b] = nb;
+          last_rot[a] = step;
+          last_rot[b] = step;
           *sh_flag = 1;
         }
       }
@@ -325,6 +354,7 @@ struct SvdShared {
   double qr_tau[CLR_MAX_CLUSTER];
   int qr_perm[CLR_MAX_CLUSTER];
   int qr_pivot;
+  double cert;    // tail_lower_bound_sq's result
 };
 
 // Column norms of g, their descending order, and the truncation rank at eps.
@@ -563,7 +593,17 @@ __device__ void right_multiply_fp64(double* m, int rows, int64_t ldm, int q, con
 // later stages could only confirm "dense": they are skipped and the function returns 1.
 __device__ __noinline__ int svd_mixed(const SrcView& a, int p, int q, double* g, double* v,
                                       double* sc, int max_sweeps, double eps, int dense_h,
-                                      double fro, SvdShared& sh, unsigned long long* jstats) {
+                                      double fro, SvdShared& sh, unsigned long long* jstats,
+                                      unsigned long long* stage_clk = nullptr) {
+  // while profiling the full-SVD path: SM cycles per stage (1..5 of kFullStageCounters)
+  long long ck = stage_clk ? clock64() : 0;
+  auto mark = [&](int stage) {
+    if (stage_clk && threadIdx.x == 0) {
+      const long long now = clock64();
+      atomicAdd(&stage_clk[stage], (unsigned long long)(now - ck));
+      ck = now;
+    }
+  };
   // FP32 copies in the per-CTA scratch: the kernels run with the largest L1 carveout, which
   // measured as fast as holding the copies in shared memory and gives the 256-column tiles
   // (copies of 512 KB) the most cache
@@ -577,6 +617,7 @@ __device__ __noinline__ int svd_mixed(const SrcView& a, int p, int q, double* g,
   const float floor32 = (float)((double)p * FLT_EPSILON * fro);
   const int sw32 = jacobi_svd<float>(g32, p, q, p, v32, q, max_sweeps, &sh.flag, true, 4.0f,
                                      floor32 * floor32);
+  mark(1);
   if (dense_h >= 0 && dense_h < q) {
     for (int c = w; c < q; c += kWarps) {
       const float* gc = g32 + (int64_t)c * p;
@@ -611,6 +652,7 @@ __device__ __noinline__ int svd_mixed(const SrcView& a, int p, int q, double* g,
   }
   orthonormalise_fp64(v32, v, q, sh);
   project_fp64(a, p, q, v, g);
+  mark(2);
   // FP64 noise floor, raised to 1e-3 eps: columns below it hold less than 1e-6 eps^2 each, so
   // their mutual (non-)orthogonality cannot move a truncation decision at eps except within a
   // hair of the threshold, while orthogonalising them costs most of the sweeps
@@ -620,6 +662,7 @@ __device__ __noinline__ int svd_mixed(const SrcView& a, int p, int q, double* g,
   const float floor_g = (float)floor64;
   const int sw32b = jacobi_svd<float>(g32, p, q, p, v32, q, max_sweeps, &sh.flag, true, 4.0f,
                                       floor_g * floor_g);
+  mark(3);
   // The FP64 sweeps rotate G alone when eps is well above the noise floor: the right factor
   // of the kept columns is then recovered from A and G afterwards (recover_right), a p q r
   // product instead of 4 q flops per rotation.  Near the floor (eps < 1e3 p u ||A||_F) kept
@@ -636,6 +679,7 @@ __device__ __noinline__ int svd_mixed(const SrcView& a, int p, int q, double* g,
     if (track_v) right_multiply_fp64(v, q, q, q, v2t);
   }
   if (threadIdx.x == 0) sh.v_tracked = track_v ? 1 : 0;
+  mark(4);
   // Without V accumulation the FP64 sweeps stop after kFp64SweepCap: one sweep takes the pairs'
   // cosines from the FP32 stages' ~1e-5 to ~1e-10 (quadratic step), which fixes the column
   // norms (the truncation) to ~1e-20 relative; a block whose spectrum has a tight cluster would
@@ -647,6 +691,7 @@ __device__ __noinline__ int svd_mixed(const SrcView& a, int p, int q, double* g,
   const int sw64 = jacobi_svd<double>(g, p, q, p, track_v ? v : nullptr, q, cap64, &sh.flag,
                                       false, 1.0, floor64 * floor64);
   if (threadIdx.x == 0) sh.ls_recover = (!track_v && sw64 >= cap64) ? 1 : 0;
+  mark(5);
   if (jstats && threadIdx.x == 0) {
     // algorithmic flops: Jacobi 4 p q^2 per sweep, orthonormalisation 2 q^3, products 2 p q^2
     const unsigned long long pq2 = (unsigned long long)p * q * q, q3 = (unsigned long long)q * q * q;
@@ -895,25 +940,37 @@ __device__ int rrqr_block(const double* S, int64_t s_r, int64_t s_c, int m, int 
 // triangle: R_11 is a submatrix of Q^T A P, so sigma_J(A) >= sigma_min(R_11), and the eps-rank
 // exceeds q/2 as soon as sigma_{q/2+1}(A) > eps.  sigma_min(R_11) is bounded below by
 // 1 / ||R_11^-1||_F (a triangular inverse, J^3/6 FMAs).
-// A block that meets neither (its QR rank at eps/16 lies between q/2 + 1 and 3q/5) goes on to
-// that threshold; the SVD of its R then decides: rank <= q/2 is stored low rank, otherwise the
-// block is stored dense as Q_k [R; 0] P^T (within eps/16 of the block).
+// A block that meets neither goes on; when its QR rank at eps/16 is at most 3q/5 the SVD of its
+// R decides: rank <= q/2 is stored low rank, otherwise the block is stored dense as
+// Q_k [R; 0] P^T (within eps/16 of the block).  Past 3q/5 steps the QR runs on over all q
+// columns and the block is certified dense when a leading triangle R_K' bounds the tail
+// sum_{i > q/2} sigma_i(A)^2 above eps^2: sigma_min alone certifies only blocks whose
+// (q/2 + 1)-th singular value exceeds eps, while the tail of a block with many singular
+// values just below eps also exceeds it (tail_lower_bound_sq).
 // Returns 1 when the block is done (low rank or zero, written to slot and the outputs), 2 when
 // it is stored dense (certified with the source untouched, or reconstructed into the slot: the
 // caller stores the kind and copies an external source over it), 0 when the QR passed 3q/5
-// steps without meeting the threshold; the caller then takes the full SVD on the untouched
-// source.
+// steps without meeting the threshold and without the certificate; the caller then takes the
+// full SVD on the untouched source.
 // g: p x q copy (ld p); wv: the tile's second workspace half (p q doubles); slot: the block's
 // m n output slot (also the source of product tiles, read only before R is written there).
 // ---------------------------------------------------------------------------------------------
-// sigma_min(R) >= 1 / ||R^-1||_F for the J x J upper triangle R of g (ld p), by back
-// substitution of the unit vectors, one warp per column of the inverse (x: J x J scratch).
-__device__ double sigma_min_lower_bound(const double* g, int p, int J, double* x,
-                                        SvdShared& sh) {
+// A lower bound on sum_{i > h} sigma_i(A)^2 from the leading K x K upper triangle R_K of the
+// pivoted QR in g (ld p).  For every K' in (h, K], R_K' is the upper part of the first K'
+// columns of Q^T A P, so sigma_i(A) >= sigma_i(R_K') (removing columns does not raise singular
+// values), and the Cauchy-Schwarz inequality over the K' - h smallest singular values of R_K'
+// gives  sum_{i > h} sigma_i(R_K')^2 >= (K' - h)^2 / sum_{i > h} sigma_i(R_K')^-2
+// >= (K' - h)^2 / ||R_K'^-1||_F^2.  The columns of R_K^-1 come by back substitution of the unit
+// vectors, one warp per column (x: K x K scratch); column c depends only on the leading
+// (c + 1) x (c + 1) triangle, so R_K'^-1 is the leading block of R_K^-1 and its squared
+// Frobenius norm a prefix sum of column norms.  Returns the largest of the K - h bounds
+// (h = K - 1: 1 / ||R_K^-1||_F^2 <= sigma_min(R_K)^2).
+__device__ double tail_lower_bound_sq(const double* g, int p, int h, int K, double* x,
+                                      SvdShared& sh) {
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
-  double part = 0.0;
-  for (int c = w; c < J; c += kWarps) {
-    double* xc = x + (int64_t)c * J;
+  for (int c = w; c < K; c += kWarps) {
+    double* xc = x + (int64_t)c * K;
+    double s2 = 0.0;
     for (int i = c; i >= 0; --i) {
       double d = 0.0;
       for (int t = i + 1 + l; t <= c; t += 32) d = fma(g[i + (int64_t)t * p], xc[t], d);
@@ -923,11 +980,23 @@ __device__ double sigma_min_lower_bound(const double* g, int p, int J, double* x
       __syncwarp();
       if (l == 0) xc[i] = xi;
       __syncwarp();
-      if (l == 0) part = fma(xi, xi, part);
+      s2 = fma(xi, xi, s2);
     }
+    if (l == 0) sh.sorted[c] = s2;
   }
-  const double f2 = block_sum(part, sh.red);
-  return (f2 > 0.0 && isfinite(f2)) ? 1.0 / sqrt(f2) : 0.0;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double f = 0.0, best = 0.0;
+    for (int c = 0; c < K; ++c) {
+      f += sh.sorted[c];
+      if (!(f > 0.0) || !isfinite(f)) break;   // a zero pivot: no larger K' bounds anything
+      const int kk = c + 1;
+      if (kk > h) best = fmax(best, (double)(kk - h) * (double)(kk - h) / f);
+    }
+    sh.cert = best;
+  }
+  __syncthreads();
+  return sh.cert;
 }
 
 // (not inlined: the kernel's register allocation stays with its own paths)
@@ -946,6 +1015,10 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
   // and the most steps taken (the SVD of R must fit wv)
   const int jcert = q / 2 + 1 <= q ? q / 2 + 1 : q;
   const int jmax = (3 * q) / 5 > jcert ? (3 * q) / 5 : jcert;
+  // a block still above the threshold after jmax steps: the QR goes on to all q columns for
+  // the dense certificate over every leading triangle (tail_lower_bound_sq); the steps after
+  // jmax cost a few percent of the first ones (their trailing blocks are small)
+  const int jext = q;
   const double tau2 = (eps / 16.0) * (eps / 16.0);
   // copy with the column norms
   for (int c = w; c < q; c += kWarps) {
@@ -965,7 +1038,8 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
   __syncthreads();
   unsigned long long fma_count = 0;
   int k = -1;
-  for (int j = 0; j <= jmax; ++j) {
+  int kc = 0;   // steps completed when the threshold was not met within jmax
+  for (int j = 0; j <= jext; ++j) {
     // trailing norm and pivot (warp 0)
     if (w == 0) {
       double tot = 0.0, best = -1.0;
@@ -988,16 +1062,20 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
       }
     }
     __syncthreads();
-    if (sh.kept_sq <= tau2) { k = j; break; }
+    if (sh.kept_sq <= tau2) {
+      if (j <= jmax) k = j;
+      else kc = j;   // met only past jmax: R_j is complete up to a negligible trailing block
+      break;
+    }
     if (j == jcert) {
       // still above the threshold after floor(q/2) + 1 steps: dense if sigma_min(R_11) > eps
-      const double smin = sigma_min_lower_bound(g, p, jcert, wv, sh);
+      const double b2 = tail_lower_bound_sq(g, p, jcert - 1, jcert, wv, sh);
       if (jstats && threadIdx.x == 0)
         atomicAdd(&jstats[4], 2ull * fma_count + (unsigned long long)jcert * jcert * jcert / 3);
       fma_count = 0;
-      if (smin > eps) return 2;
+      if (b2 > eps * eps) return 2;
     }
-    if (j == jmax) break;  // not reached within jmax steps
+    if (j == jext) { kc = j; break; }
     const int piv = sh.qr_pivot;
     if (piv != j) {
       double* x = g + (int64_t)j * p;
@@ -1062,7 +1140,14 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
   }
   if (jstats && threadIdx.x == 0)
     atomicAdd(&jstats[4], 2ull * fma_count);   // (the QR's flops after the certificate test)
-  if (k < 0) return 0;   // no threshold within jmax steps: the full SVD decides
+  if (k < 0) {
+    // no threshold within jmax steps: dense when sum_{i > q/2} sigma_i^2 > eps^2 is certified
+    // by some leading triangle of the kc completed steps, else the full SVD decides
+    const double b2 = tail_lower_bound_sq(g, p, kmax, kc, wv, sh);
+    if (jstats && threadIdx.x == 0)
+      atomicAdd(&jstats[4], (unsigned long long)kc * kc * kc / 3);
+    return b2 > eps * eps ? 2 : 0;
+  }
   const double trail2 = sh.kept_sq;
   __syncthreads();
   if (k == 0) {
@@ -1199,6 +1284,7 @@ __global__ void __launch_bounds__(kThreads, 1) compress_dense_kernel(
       continue;
     }
     int r = q;
+    long long c_full = -1;   // while profiling: start of a full-SVD block's truncation
     if (rrqr && !dense_only) {
       r = rrqr_block(S, s_r, s_c, m, n, eps, G, sh);
       if (r > 0 && r <= q / 2) {
@@ -1234,9 +1320,13 @@ __global__ void __launch_bounds__(kThreads, 1) compress_dense_kernel(
                                                          &C.norm[t], sh, jstats)
                                 : 0;
       if (pre == 0) {
-        const int early_dense =
-            svd_mixed(view, p, q, G, V, sc, max_sweeps, eps, q / 2, nrm, sh, jstats);
+        unsigned long long* stage_clk = jstats ? jstats + kFullStageCounters : nullptr;
+        if (stage_clk && threadIdx.x == 0)
+          atomicAdd(&stage_clk[0], (unsigned long long)(clock64() - c0));
+        const int early_dense = svd_mixed(view, p, q, G, V, sc, max_sweeps, eps, q / 2, nrm,
+                                          sh, jstats, stage_clk);
         if (!early_dense) {
+          c_full = clock64();
           sort_and_truncate(G, p, q, p, eps, sh);
           r = sh.rank;
         }
@@ -1308,6 +1398,11 @@ __global__ void __launch_bounds__(kThreads, 1) compress_dense_kernel(
       }
     }
     __syncthreads();
+    if (jstats && c_full >= 0 && threadIdx.x == 0) {
+      atomicAdd(&jstats[kFullStageCounters + 6], (unsigned long long)(clock64() - c_full));
+      atomicAdd(&jstats[kFullStageCounters + 7], 1ull);
+      if (r > q / 2) atomicAdd(&jstats[7], 1ull);   // full SVD, stored dense
+    }
   }
 }
 

@@ -60,7 +60,9 @@ def ns_rank_distribution(ctx: "clr.Context", s: "clr.Matrix", k: int = 5) -> Dic
                                                   "svd_early_dense", "svd_prereduced",
                                                   "svd_flops_fp64", "svd_flops_fp32",
                                                   "svd_flops_fp64_qr", "svd_flops_fp32_qr",
-                                                  "svd_path_cycles", "svd_path_blocks")}
+                                                  "svd_path_cycles", "svd_path_blocks",
+                                                  "svd_full_cycles", "svd_full_blocks",
+                                                  "svd_full_dense")}
     ctx.set_opts(ns_snapshot_iter=0)
     return out
 
