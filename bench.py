@@ -532,7 +532,7 @@ def ozaki_product(ctx, ga, gb, gc, w, alg_flops, fp64_value, rank, warmup=2, ste
     return {"ms_per_product": ms, "tflops": tf, "kernel": "ozaki_gemm_kernel",
             "kernel_ms": kern_ms, "kernel_tflops": alg_flops / (kern_ms * 1e-3) / 1e12,
             "staging_ms": prof["ms_stage"] / steps,
-            "tensor_products_per_flop": 28,
+            "tensor_products_per_flop": 36,
             "accuracy": acc, "over_fp64_speedup": tf / fp64_value if fp64_value else None,
             "steps": steps, "warmup": warmup}
 

@@ -66,13 +66,16 @@ extern "C" {
 #define CLR_PREC_AUTO   3  /* cheapest of bf16x3, bf16x6, the exact slices below and FP64 whose
                               a-priori error model meets eps_lr (the batch autotuner times each
                               candidate and keeps the fastest) */
-#define CLR_PREC_OZAKI  4  /* FP64-accurate dense x dense products on the tensor cores: rows
-                              of A and columns of B scaled by powers of two and cut into 7
-                              fixed-point slices of 6 bits (bf16 digits), the 28 slice pairs of
-                              weight >= 2^-42 summed exactly in FP32 over segments of 2048 and
-                              in FP64 across segments (Ozaki, Ogita, Oishi, Rump 2012); error
-                              <~ K 2^-39 max|a_i.| max|b_.j| per entry.  Low-rank contributions
-                              stay FP64, as with CLR_PREC_FP64 */
+#define CLR_PREC_OZAKI  4  /* FP64-accurate tile products on the tensor cores: in each K
+                              segment of 1024, rows of A and columns of B scaled by powers of
+                              two and cut into 8 fixed-point slices of 6 bits (bf16 digits), the
+                              36 slice pairs of weight >= 2^-48 summed exactly in FP32, segments
+                              summed in FP64 (Ozaki, Ogita, Oishi, Rump 2012); error at most
+                              sum over segments of K_seg 2^-44 max|a_i.| max|b_.j| (maxima over
+                              the segment) per entry.  Low-rank operand blocks enter as their
+                              reconstructions, so the GEMM forms the whole sum of the dense C
+                              tiles and of densely accumulated low-rank sums whose expected
+                              sliced error is within eps_lr / 64; other low-rank sums stay FP64 */
 
 #define CLR_MAX_CLUSTER 256
 

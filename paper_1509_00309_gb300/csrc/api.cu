@@ -501,14 +501,14 @@ int choose_precision(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, double eps_in = -1
   // product term, including FP32 accumulation): bf16x3 ~ 2^-16.5, bf16x6 ~ 2^-23.  The
   // expected ||dC||_F is about u ||A||_F ||B||_F / sqrt(K); the product tolerance is
   // 10 eps ||A||_F ||B||_F.  Take the cheapest mode with a factor-4 margin.
-  // The exact-slice products err by ~2^-42 relative to the rows' and columns' largest entries
-  // per term; 2^-38 allows for the spread between those and the RMS entry.
+  // The exact-slice products err by ~2^-48 relative to the rows' and columns' largest entries
+  // (per K segment) per term; 2^-44 allows for the spread between those and the RMS entry.
   const double e0 = eps_in >= 0.0 ? eps_in : ctx->opts.eps_lr;
   const double eps = e0 > 0 ? e0 : 1e-8;
   const double sk = std::sqrt((double)a->n_cols);
   if (std::ldexp(1.0, -16) * 0.6 / sk * 4.0 <= 10.0 * eps) return CLR_PREC_BF16X3;
   if (std::ldexp(1.0, -23) / sk * 4.0 <= 10.0 * eps) return CLR_PREC_BF16X6;
-  if (std::ldexp(1.0, -38) / sk * 4.0 <= 10.0 * eps) return CLR_PREC_OZAKI;
+  if (std::ldexp(1.0, -44) / sk * 4.0 <= 10.0 * eps) return CLR_PREC_OZAKI;
   (void)b;
   return CLR_PREC_FP64;
 }
@@ -1018,32 +1018,62 @@ int run_split_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Pla
 // Dense x dense products by exact slices on the tensor cores (CLR_PREC_OZAKI): the dense blocks
 // of A and B are staged as 7 bf16 digit planes with per-row exponents, and the exact-slice GEMM
 // writes the route-DENSE tiles; low-rank contributions follow in FP64 (low-rank kernel).
-int run_ozaki_dd(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, const Plan& p,
-                 cudaStream_t s) {
+// Exact slices, before the plan: digit panels of A and B (dense blocks and reconstructed
+// low-rank blocks) with their exponents per K segment, and the routing rule of densely
+// accumulated low-rank sums.  Such a sum goes to the tensor-core GEMM when the expected error of
+// its sliced evaluation -- about 1.2 2^-48 per term of a segment relative to 2^(e_i + f_j)
+// (truncation of both operands and the dropped slice pairs, rounding independently), i.e.
+// 1.2 2^-48 sqrt(K_seg sum_s sa[I][s] sb[J][s]) over the tile -- is, times 4, within eps/16.
+int stage_ozaki(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double eps_lr,
+                cudaStream_t s, OzDaccRule* rule) {
   const int64_t M_pad = (c->n_rows + 127) / 128 * 128;
   const int64_t N_pad = (c->n_cols + 63) / 64 * 64;
   const int64_t K_pad = (a->n_cols + 127) / 128 * 128;
+  const int n_seg = (int)((K_pad + kOzakiSegK - 1) / kOzakiSegK);
   WorkSet* w = ctx->cur;
   CLR_CUDA(w->panels_a.ensure((size_t)kOzakiSlices * M_pad * K_pad * 2));
   CLR_CUDA(w->panels_b.ensure((size_t)kOzakiSlices * N_pad * K_pad * 2));
-  CLR_CUDA(w->oz_exps.ensure((size_t)(M_pad + N_pad) * sizeof(int)));
-  CLR_CUDA(w->tile_flags.ensure((size_t)(M_pad / 128) * (N_pad / 64)));
+  const size_t exp_bytes = ((size_t)n_seg * (M_pad + N_pad) * sizeof(int) + 255) / 256 * 256;
+  CLR_CUDA(w->oz_exps.ensure(exp_bytes + (size_t)n_seg * (c->nr + c->nc) * sizeof(double)));
   w->staged_a = nullptr;   // the panels no longer hold a split staging
-  MatView av = a->view(), bv = b->view(), cv = c->view();
+  MatView av = a->view(), bv = b->view();
   int* ea = (int*)w->oz_exps.p;
-  int* eb = ea + M_pad;
+  int* eb = ea + (size_t)n_seg * M_pad;
+  double* sa = (double*)((char*)w->oz_exps.p + exp_bytes);
+  double* sb = sa + (size_t)n_seg * c->nr;
   launch_ozaki_stage(av, c->d_row_idx, a->d_col_idx, w->panels_a.p, ea, M_pad, K_pad, 1, s);
   launch_ozaki_stage(bv, a->d_col_idx, c->d_col_idx, w->panels_b.p, eb, N_pad, K_pad, 0, s);
+  launch_ozaki_scale_sums(ea, M_pad, c->d_row_off, c->nr, n_seg, sa, s);
+  launch_ozaki_scale_sums(eb, N_pad, c->d_col_off, c->nc, n_seg, sb, s);
   CLR_CHECK_LAUNCH("exact-slice staging");
-  prof_launches(ctx, 4);   // 2 exponent + 2 digit kernels (the exponent memsets are not kernels)
+  prof_launches(ctx, 10);  // per operand: 2 exponent + 2 digit kernels; 2 scale sums
   prof_mark(ctx, s, PH_STAGE);
+  const double u = 4.0 * 1.2 * std::ldexp(1.0, -48);
+  const double budget = eps_lr / 16.0;
+  rule->sa = sa;
+  rule->sb = sb;
+  rule->n_seg = n_seg;
+  rule->bound2 = budget * budget / (u * u * (double)kOzakiSegK);
+  return CLR_OK;
+}
+
+// Exact slices, after the plan: the GEMM over the tiles of route-DENSE and DACC_G C tiles.
+int run_ozaki_gemm(clr_ctx_t ctx, clr_mat_t a, clr_mat_t c, const Plan& p, cudaStream_t s) {
+  const int64_t M_pad = (c->n_rows + 127) / 128 * 128;
+  const int64_t N_pad = (c->n_cols + 63) / 64 * 64;
+  const int64_t K_pad = (a->n_cols + 127) / 128 * 128;
+  const int n_seg = (int)((K_pad + kOzakiSegK - 1) / kOzakiSegK);
+  WorkSet* w = ctx->cur;
+  CLR_CUDA(w->tile_flags.ensure((size_t)(M_pad / 128) * (N_pad / 64)));
+  MatView cv = c->view();
+  int* ea = (int*)w->oz_exps.p;
   OzakiGemmArgs g;
   g.C = &cv;
   g.p = &p;
   g.a_panels = w->panels_a.p;
   g.b_panels = w->panels_b.p;
   g.ea = ea;
-  g.eb = eb;
+  g.eb = ea + (size_t)n_seg * M_pad;
   g.M_pad = M_pad;
   g.N_pad = N_pad;
   g.K_pad = K_pad;
@@ -1094,7 +1124,12 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
                          : prec == CLR_PREC_BF16X6 ? std::ldexp(1.0, -22) : 0.0;
   const double dacc_bound = u_split > 0.0 ? eps_lr / (16.0 * u_split) : 0.0;
   bool fused_norms = false;
-  launch_plan(av, bv, p, o.eps_sp, recompress_dense, dacc_bound, s);
+  OzDaccRule oz_rule;
+  if (prec == CLR_PREC_OZAKI) {
+    st = stage_ozaki(ctx, a, b, c, eps_lr, s, &oz_rule);
+    if (st) return st;
+  }
+  launch_plan(av, bv, p, o.eps_sp, recompress_dense, dacc_bound, oz_rule, s);
   launch_set_route_kinds(cv, p, s);
   CLR_CHECK_LAUNCH("plan");
   prof_launches(ctx, 4);
@@ -1106,15 +1141,17 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
     if (ctx->prof_on) ctx->prof.dense_launches++;
     prof_mark(ctx, s, PH_DENSE);
   } else if (prec == CLR_PREC_OZAKI) {
-    st = run_ozaki_dd(ctx, a, b, c, p, s);
+    st = run_ozaki_gemm(ctx, a, c, p, s);
     if (st) return st;
   } else {
     st = run_split_dd(ctx, a, b, c, p, prec, recompress_dense, s, &fused_norms);
     if (st) return st;
   }
-  const bool split = prec == CLR_PREC_BF16X3 || prec == CLR_PREC_BF16X6;
+  // the tensor-core GEMMs form the whole sum of the tiles they serve (route DENSE and DACC_G:
+  // the low-rank blocks are staged as reconstructions): the low-rank kernel skips those
+  const bool dense_by_gemm = prec != CLR_PREC_FP64;
   launch_lr_products(av, bv, cv, p, (double*)ctx->cur->ws.p, (double*)ctx->cur->scratch.p,
-                     kScratchPerCta, split, lr_grid, s);
+                     kScratchPerCta, dense_by_gemm, lr_grid, s);
   CLR_CHECK_LAUNCH("low-rank products");
   prof_launches(ctx, 1);
   prof_mark(ctx, s, PH_LOWRANK);
@@ -1154,9 +1191,8 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
     for (int q = 0; q < 3; ++q) stats->n_tiles[q] = (int64_t)pc.by_mode[q];
     stats->max_rank_sum = (int64_t)pc.max_rsum;
     stats->precision = prec;
-    stats->n_tiles_tensor = prec == CLR_PREC_FP64 ? 0
-                            : prec == CLR_PREC_OZAKI ? (int32_t)pc.by_mode[1]
-                                                     : (int32_t)(pc.by_mode[1] + pc.n_gemm_dacc);
+    stats->n_tiles_tensor =
+        prec == CLR_PREC_FP64 ? 0 : (int32_t)(pc.by_mode[1] + pc.n_gemm_dacc);
     st = take_device_error(ctx);
     if (st) return st;
   }

@@ -158,8 +158,17 @@ struct Plan {
 // Kernel launchers (defined in the .cu files).  All are asynchronous on `st`.
 // ---------------------------------------------------------------------------------------------
 // k_plan.cu
+// Exact slices: the routing of densely accumulated low-rank sums to the tensor-core GEMM
+// (plan_count_kernel); sa/sb: per cluster and K segment, sum over its rows (columns) of 4^e.
+struct OzDaccRule {
+  const double* sa = nullptr;   // nI x n_seg
+  const double* sb = nullptr;   // nJ x n_seg
+  int n_seg = 0;
+  double bound2 = 0.0;
+};
 void launch_plan(const MatView& A, const MatView& B, const Plan& p, double eps_sp,
-                 int recompress_dense, double gemm_dacc_bound, cudaStream_t st);
+                 int recompress_dense, double gemm_dacc_bound, const OzDaccRule& oz,
+                 cudaStream_t st);
 void launch_plan_scan(const Plan& p, int recompress_dense, cudaStream_t st);
 // k_dense64.cu
 // uses p.counters->sched[3]
@@ -239,14 +248,15 @@ struct SplitGemmArgs {
 };
 int split_gemm_dd(const SplitGemmArgs& a, cudaStream_t st, std::string* why);
 // k_ozaki.cu: FP64-accurate dense x dense products on the tensor cores (exact slices)
-constexpr int kOzakiSlices = 7;
+constexpr int kOzakiSlices = 8;
+constexpr int kOzakiSegK = 1024;   // K segment: exact FP32 group sums, exponents per segment
 struct OzakiGemmArgs {
   const MatView* C;
   const Plan* p;
   void* a_panels;     // kOzakiSlices x M_pad x K_pad bf16 digits
   void* b_panels;     // kOzakiSlices x N_pad x K_pad
-  const int* ea;      // M_pad row exponents of A
-  const int* eb;      // N_pad column exponents (rows of the B panel)
+  const int* ea;      // n_seg x M_pad row exponents of A per K segment
+  const int* eb;      // n_seg x N_pad column exponents (rows of the B panel) per K segment
   int64_t M_pad, N_pad, K_pad;   // multiples of 128, 64, 128
   const int* row_tile_of;
   const int* col_tile_of;
@@ -257,10 +267,14 @@ struct OzakiGemmArgs {
   void* encode_fn;
 };
 int ozaki_gemm_dd(const OzakiGemmArgs& a, cudaStream_t st, std::string* why);
-// exps: rows_pad ints, written (the row exponents); panels: kOzakiSlices planes
+// exps: n_seg x rows_pad ints (n_seg = K segments of kOzakiSegK), written (the row exponents
+// per segment); panels: kOzakiSlices planes
 void launch_ozaki_stage(const MatView& M, const int* row_idx, const int* col_idx, void* panels,
                         int* exps, int64_t rows_pad, int64_t cols_pad, int a_mode,
                         cudaStream_t st);
+// out[c * n_seg + s] = sum over rows i in [off[c], off[c + 1]) of 4^exps[s * rows_pad + i]
+void launch_ozaki_scale_sums(const int* exps, int64_t rows_pad, const int* off, int n_cl,
+                             int n_seg, double* out, cudaStream_t st);
 void launch_split_stage(const MatView& M, const int* row_idx, const int* col_idx, void* panels,
                         int terms, int64_t rows_pad, int64_t cols_pad, int a_mode,
                         cudaStream_t st);

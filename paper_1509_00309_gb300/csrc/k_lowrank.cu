@@ -13,8 +13,9 @@
 //                added as X_t W_t^T;
 //   ROUTE_DACC   the concatenated rank exceeds floor(min(m,n)/2), so the sum is accumulated
 //                densely (from zero) and K5 takes a dense truncated SVD.
-// With split precision (dense_by_gemm) the tensor-core GEMM sums all contributions of DENSE and
-// DACC_G tiles; this kernel builds the ROUTE_QR concatenations and the FP64 DACC sums.
+// With a tensor-core GEMM (split precision or exact slices: dense_by_gemm) the GEMM sums all
+// contributions of DENSE and DACC_G tiles; this kernel builds the ROUTE_QR concatenations and the
+// FP64 DACC sums.
 #include "clr_internal.h"
 
 namespace clr {
@@ -52,8 +53,8 @@ __global__ void __launch_bounds__(256) lr_products_kernel(MatView A, MatView B, 
     const int m = C.row_off[I + 1] - C.row_off[I];
     const int n = C.col_off[J + 1] - C.col_off[J];
     const int route = p.t_route[t];
-    // with split precision the tensor-core GEMM has already summed every contribution of the
-    // densely accumulated tiles (low-rank operand blocks staged as X W^T)
+    // with a tensor-core GEMM the dense tiles and the DACC_G tiles already hold every
+    // contribution (low-rank operand blocks staged as X W^T)
     if ((dense_by_gemm && route == ROUTE_DENSE) || route == ROUTE_DACC_G) continue;
     const int R = p.t_rsum[t];
     const int64_t sC = slot_of(C, I, J, m);

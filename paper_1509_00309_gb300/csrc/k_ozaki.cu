@@ -7,32 +7,33 @@
 // slices whose products, and the sums of those products over a bounded number of terms, are
 // exact in the tensor cores' FP32 accumulator.
 //
-// Slices.  Row i of the A panel has exponent e_i (|a_ik| < 2^e_i for every k of the row's dense
-// blocks).  v = round(a 2^(41 - e_i)) is an integer of magnitude <= 2^41; its balanced base-64
-// digits d_0 .. d_6 (d_1..d_6 in [-32, 31], d_0 in [-32, 32]) satisfy
-//   a / 2^e_i = sum_s d_s 2^(-5 - 6 s) + r,   |r| <= 2^-42,
+// Slices.  Row i of the A panel has exponent e_i (|a_ik| < 2^e_i for every k of the row's
+// staged blocks).  v = round(a 2^(47 - e_i)) is an integer of magnitude <= 2^47; its balanced
+// base-64 digits d_0 .. d_7 (d_1..d_7 in [-32, 31], d_0 in [-32, 32]) satisfy
+//   a / 2^e_i = sum_s d_s 2^(-5 - 6 s) + r,   |r| <= 2^-48,
 // and each digit is an integer of magnitude <= 32, exact in bf16.  The same for B with
 // exponents f_j.
 // Products.  C_ij = 2^(e_i + f_j - 10) sum_g 2^(-6 g) G_g with G_g = sum_{s + t = g} sum_k
-// d_s(a_ik) d_t(b_jk): pairs with s + t <= 6 are kept (28 products of bf16 slices), the rest is
+// d_s(a_ik) d_t(b_jk): pairs with s + t <= 7 are kept (36 products of bf16 slices), the rest is
 // below the truncation.  Every product of two digits is an integer of magnitude <= 2^10, so a
-// sum over K_seg = 2048 values of k and the g + 1 <= 7 pairs of a group stays below
-// 7 * 2048 * 2^10 < 2^24: the FP32 accumulator holds it exactly.  The error against the exact
-// product is at most about K 2^-39 2^(e_i + f_j) (truncation of both operands and the dropped
-// pairs), FP64-like relative to the rows' and columns' largest entries.
+// sum over K_seg = 1024 values of k and the g + 1 <= 8 pairs of a group stays within
+// 8 * 1024 * 2^10 = 2^23: the FP32 accumulator holds it exactly.  The error against the exact
+// product is at most K 2^-44 2^(e_i + f_j) (truncation of both operands and the dropped pairs),
+// about 2^-48 sqrt(K) 2^(e_i + f_j) for independent rounding: FP64-like relative to the rows'
+// and columns' largest entries.
 //
 // Kernel (one CTA per SM, persistent over 128 x 64 output tiles):
-//   warp 0     TMA producer: per 32-wide k chunk the 7 slices of the A tile (128 x 32) and of
+//   warp 0     TMA producer: per 32-wide k chunk the 8 slices of the A tile (128 x 32) and of
 //              the B tile (64 x 32), 64-byte swizzle, into one of two pipeline stages;
-//   warp 1     allocates 512 TMEM columns (seven 128 x 64 FP32 accumulators, one per weight
+//   warp 1     allocates all 512 TMEM columns (eight 128 x 64 FP32 accumulators, one per weight
 //              group g, side by side) and issues tcgen05.mma (M=128, K=16, kind::f16, bf16 in,
-//              FP32 accumulate) for the 28 slice pairs as 10 MMAs per K16 step: slice s of A
-//              against the B slices t = 0 .. 6 - s at once (N = 64 (7 - s), split at 256),
-//              which writes groups s .. 6 together.  Each A slice is then read from shared
-//              memory once per step instead of once per pair: 96 KB of operand reads per step
-//              instead of 168 KB, and the tensor core's operand fetch, not its math, is what
-//              bounds N = 64 MMAs;
-//   warps 2-9  epilogue: after every K segment of 2048 the seven exact group sums are read from
+//              FP32 accumulate) for the 36 slice pairs as 12 MMAs per K16 step: slice s of A
+//              against the B slices t = 0 .. 7 - s at once (N = 64 (8 - s), split at 256),
+//              which writes groups s .. 7 together.  Each A slice is then read from shared
+//              memory once per MMA instead of once per pair: 120 KB of operand reads per step
+//              instead of 216 KB (with one MMA per pair the tensor unit was bound by operand
+//              fetch: busy 68% of the time with its math pipe at 28%);
+//   warps 2-9  epilogue: after every K segment of 1024 the eight exact group sums are read from
 //              TMEM and added, scaled by 2^(-6 g), into FP64 registers (32 per thread); after
 //              the tile's last segment the FP64 values are scaled by 2^(e_i + f_j - 10) and
 //              stored into the C tiles whose route is dense.
@@ -50,7 +51,7 @@ namespace clr {
 
 namespace oz {
 
-constexpr int S = kOzakiSlices;  // 7
+constexpr int S = kOzakiSlices;  // 8
 constexpr int BM = 128;
 constexpr int BN = 64;
 constexpr int BK = 32;               // 32 bf16 = 64 bytes: one 64B-swizzle row
@@ -63,7 +64,10 @@ constexpr int STAGES = 2;
 constexpr uint32_t SMEM_DATA = STAGE * STAGES;
 constexpr uint32_t SMEM_TOTAL = SMEM_DATA + 1024 /*barriers*/ + 1024 /*align*/;
 constexpr int GROUPS = S;            // weight groups g = s + t <= S - 1
-constexpr int SEG_CHUNKS = 64;       // K segment of 2048: exact FP32 group sums
+constexpr int SEG_CHUNKS = 32;       // K segment of 1024: exact FP32 group sums
+constexpr int SEG_K = SEG_CHUNKS * BK;
+// the staging kernels' k tiles (256, 128 and 4 x 256 wide) never straddle a segment
+static_assert(SEG_K == 1024 && SEG_K == kOzakiSegK, "staging tiles assume K segments of 1024");
 constexpr int TMEM_COLS = 512;
 constexpr unsigned long long kDrainNs = 2000000000ull;
 
@@ -199,7 +203,14 @@ __device__ __forceinline__ void tile_coords(int id, int n_m, int n_n, int* mb, i
   *nb = r / gs;
 }
 
+// Exponents of rows without entries (the staging's sentinel) scale only zero digits: 0.
 __device__ __forceinline__ int clamp_exp(int e) { return e < -1100 ? 0 : e; }
+
+// 2^x: built from its bits in the normal range, by ldexp outside it.
+__device__ __forceinline__ double pow2(int x) {
+  if (x >= -1022 && x <= 1023) return __longlong_as_double((long long)(x + 1023) << 52);
+  return ldexp(1.0, x);
+}
 
 __global__ void __launch_bounds__(THREADS, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
@@ -303,9 +314,9 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!mbar_wait(&full[s], phase, abort_flag, wait_ns)) { ok = false; break; }
             fence_after();
             const uint32_t st = saddr(smem + (size_t)s * STAGE);
-            // A slice s times the consecutive B slices t = 0 .. 6 - s in one MMA of
-            // N = 64 (7 - s) (two where that exceeds 256): its output columns land in the
-            // accumulators of groups s .. 6, which are consecutive in TMEM.  The two MMAs of
+            // A slice s times the consecutive B slices t = 0 .. 7 - s in one MMA of
+            // N = 64 (8 - s) (two where that exceeds 256): its output columns land in the
+            // accumulators of groups s .. 7, which are consecutive in TMEM.  The two MMAs of
             // s = 0 cover every group, so they alone start a segment (accumulate off).
 #pragma unroll
             for (int k16 = 0; k16 < BK / 16; ++k16) {
@@ -356,7 +367,16 @@ __global__ void __launch_bounds__(THREADS, 1)
       double acc[32];
 #pragma unroll
       for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+      const int64_t row = (int64_t)mb * BM + rl;
+      const int64_t col0 = (int64_t)nb * BN + half * 32;
       for (int k0 = 0; k0 < num_k; k0 += SEG_CHUNKS) {
+        // this segment's scale of every entry: 2^(e_i + f_j - 10) with the exponents of its
+        // own K range (row i of A, column j of B over the segment's columns / rows)
+        const int sg = k0 / SEG_CHUNKS;
+        const int er = clamp_exp(epi.ea[(int64_t)sg * M_pad + row]) - 10;
+        int ex[32];
+#pragma unroll
+        for (int j = 0; j < 32; ++j) ex[j] = er + clamp_exp(epi.eb[(int64_t)sg * N_pad + col0 + j]);
         int got = 0;
         if (lane == 0) got = mbar_wait(tfull, seg_count & 1, abort_flag, wait_ns) ? 1 : 0;
         got = __shfl_sync(0xffffffffu, got, 0);
@@ -368,9 +388,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int g = 0; g < GROUPS; ++g) {
           uint32_t r[32];
           tmem_ld32(tbase + (uint32_t)(g * BN), r);
-          const double w = ldexp(1.0, -6 * g);
 #pragma unroll
-          for (int j = 0; j < 32; ++j) acc[j] = fma((double)__uint_as_float(r[j]), w, acc[j]);
+          for (int j = 0; j < 32; ++j)
+            acc[j] = fma((double)__uint_as_float(r[j]), pow2(ex[j] - 6 * g), acc[j]);
         }
         fence_before();
         __syncwarp();
@@ -378,21 +398,18 @@ __global__ void __launch_bounds__(THREADS, 1)
         ++seg_count;
       }
       if (!ok) break;
-      const int64_t row = (int64_t)mb * BM + rl;
-      const int64_t col0 = (int64_t)nb * BN + half * 32;
       if (row < epi.n_rows) {
         const int I = epi.row_tile_of[row];
         const int mI = epi.row_off[I + 1] - epi.row_off[I];
         const int64_t rowbase = (int64_t)epi.row_off[I] * epi.n_cols + (row - epi.row_off[I]);
         const int* route_row = epi.t_route + (int64_t)I * epi.nJ;
-        const int er = clamp_exp(epi.ea[row]) - 10;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
           const int64_t col = col0 + j;
           if (col < epi.n_cols) {
             const int J = epi.col_tile_of[col];
-            if (route_row[J] == ROUTE_DENSE)
-              epi.pool[rowbase + col * mI] = scalbn(acc[j], er + clamp_exp(epi.eb[col]));
+            const int route = route_row[J];
+            if (route == ROUTE_DENSE || route == ROUTE_DACC_G) epi.pool[rowbase + col * mI] = acc[j];
           }
         }
       }
@@ -408,7 +425,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
 }
 
-// GEMM tile t is active when it overlaps at least one C tile with a dense x dense product.
+// GEMM tile t is active when it overlaps at least one C tile the GEMM forms: one with a
+// dense x dense product, or a densely accumulated low-rank sum routed to the tensor cores.
 __global__ void oz_tile_active_kernel(const int* row_tile_of, const int* col_tile_of, int nc,
                                       const int* t_route, int n_m, int n_n, int64_t n_rows,
                                       int64_t n_cols, unsigned char* active) {
@@ -424,7 +442,8 @@ __global__ void oz_tile_active_kernel(const int* row_tile_of, const int* col_til
     const int j0 = col_tile_of[c0], j1 = col_tile_of[c1 - 1];
     for (int I = i0; I <= i1 && !on; ++I)
       for (int J = j0; J <= j1; ++J)
-        if (t_route[(int64_t)I * nc + J] == ROUTE_DENSE) {
+        if (t_route[(int64_t)I * nc + J] == ROUTE_DENSE ||
+            t_route[(int64_t)I * nc + J] == ROUTE_DACC_G) {
           on = 1;
           break;
         }
@@ -433,8 +452,10 @@ __global__ void oz_tile_active_kernel(const int* row_tile_of, const int* col_til
 }
 
 // ---------------------------------------------------------------------------------------------
-// Staging: exponents, then digits.  Only dense blocks are staged (other entries are zero): the
-// low-rank contributions to dense tiles are added in FP64 by the low-rank product kernel.
+// Staging: exponents, then digits.  Dense blocks and the reconstructions X W^T of low-rank
+// blocks are staged (zero blocks stay zero), so that the GEMM forms the whole sum
+// sum_K A_IK B_KJ of every C tile it serves.  Exponents are per row (of A) or column (of B)
+// and K segment of SEG_K: exps[segment * rows_pad + row].
 // ---------------------------------------------------------------------------------------------
 // x with |a| < 2^x for a finite nonzero a (from the FP64 exponent field; subnormals count as
 // 2^-1022), or INT_MIN for zero.
@@ -445,7 +466,7 @@ __device__ __forceinline__ int exp_bound(double a) {
   return (E ? E : 1) - 1022;
 }
 
-// The 7 balanced digits of a relative to 2^e (see the file header), as bf16 bit patterns,
+// The 8 balanced digits of a relative to 2^e (see the file header), as bf16 bit patterns,
 // most significant first.
 __device__ __forceinline__ void oz_digits(double a, int e, unsigned short (&out)[S]) {
   long long v = 0;
@@ -454,7 +475,7 @@ __device__ __forceinline__ void oz_digits(double a, int e, unsigned short (&out)
     const int E = (int)((bits >> 52) & 0x7FF);
     const unsigned long long mant = (bits & ((1ull << 52) - 1)) | (E ? (1ull << 52) : 0ull);
     const int x = (E ? E : 1) - 1075;          // |a| = mant 2^x
-    const int sh = x - e + 41;                 // v = mant 2^sh, < 2^41 since |a| < 2^e
+    const int sh = x - e + 47;                 // v = mant 2^sh, < 2^47 since |a| < 2^e
     unsigned long long m;
     if (sh >= 0) m = mant << sh;
     else if (sh > -63) m = (mant + (1ull << (-sh - 1))) >> (-sh);   // nearest, ties up
@@ -470,8 +491,8 @@ __device__ __forceinline__ void oz_digits(double a, int e, unsigned short (&out)
   out[0] = (unsigned short)(__float_as_uint((float)v) >> 16);
 }
 
-// A: exponent of every row over its dense blocks.  32 rows x 256 k per CTA (threads along rows:
-// the block-row panels are column-major).
+// A: exponent of every row over its dense blocks, per K segment.  32 rows x 256 k per CTA
+// (threads along rows: the block-row panels are column-major).
 __global__ void __launch_bounds__(256) oz_exp_a_kernel(MatView M, const int* row_idx,
                                                        const int* col_idx, int* ea,
                                                        int64_t rows_pad, int64_t cols_pad) {
@@ -496,14 +517,14 @@ __global__ void __launch_bounds__(256) oz_exp_a_kernel(MatView M, const int* row
   __syncthreads();
   if (ty == 0) {
     for (int i = 1; i < 8; ++i) e = max(e, red[i][threadIdx.x % 32]);
-    if (r < rows_pad && e != INT_MIN) atomicMax(&ea[r], e);
+    if (r < rows_pad && e != INT_MIN) atomicMax(&ea[(k0 / SEG_K) * rows_pad + r], e);
   }
 }
 
-// B: exponent of every panel row j (column j of B) over k: one CTA per (j, 1024 values of k).
+// B: exponent of every panel row j (column j of B) over k: one CTA per (j, K segment).
 __global__ void __launch_bounds__(256) oz_exp_b_kernel(MatView M, const int* row_idx,
                                                        const int* col_idx, int* eb,
-                                                       int64_t cols_pad) {
+                                                       int64_t rows_pad, int64_t cols_pad) {
   __shared__ int red[8];
   const int64_t j = blockIdx.x;
   int e = INT_MIN;
@@ -527,7 +548,7 @@ __global__ void __launch_bounds__(256) oz_exp_b_kernel(MatView M, const int* row
   __syncthreads();
   if (threadIdx.x == 0) {
     for (int i = 1; i < 8; ++i) e = max(e, red[i]);
-    if (e != INT_MIN) atomicMax(&eb[j], e);
+    if (e != INT_MIN) atomicMax(&eb[(int64_t)blockIdx.y * rows_pad + j], e);
   }
 }
 
@@ -567,7 +588,7 @@ __global__ void __launch_bounds__(256) oz_digits_a_kernel(MatView M, const int* 
   const int64_t plane = rows_pad * cols_pad;
   for (int rr = ty; rr < 32; rr += 8) {
     const int64_t i = r0 + rr;
-    const int e = ea[i];
+    const int e = ea[(k0 / SEG_K) * rows_pad + i];
     const int64_t k = k0 + 4 * tx;
     unsigned long long packed[S];
 #pragma unroll
@@ -608,7 +629,7 @@ __global__ void __launch_bounds__(256) oz_digits_b_kernel(MatView M, const int* 
       }
     }
   }
-  const int e = eb[j];
+  const int e = eb[(int64_t)blockIdx.y * rows_pad + j];   // blockIdx.y: the K segment
   unsigned long long packed[S];
 #pragma unroll
   for (int t = 0; t < S; ++t) packed[t] = 0;
@@ -623,6 +644,96 @@ __global__ void __launch_bounds__(256) oz_digits_b_kernel(MatView M, const int* 
 #pragma unroll
   for (int t = 0; t < S; ++t)
     *reinterpret_cast<unsigned long long*>(panels + t * plane + j * cols_pad + k) = packed[t];
+}
+
+// Low-rank blocks: one CTA per block of M (blocks of another kind return at once), entry (i, j)
+// = sum_t X(i, t) W(j, t) in FP64, computed here for the exponents and again for the digits.
+// a_mode: panel row = M's row, panel k = M's column (threads along j); else panel row = M's
+// column, panel k = M's row (threads along i).
+struct LrBlock {
+  const double* x;
+  const double* w;
+  int m, n, r;
+  int64_t row0, col0;
+};
+__device__ __forceinline__ bool lr_block(const MatView& M, int b, LrBlock* o) {
+  if (M.kind[b] != CLR_KIND_LR) return false;
+  const int R = b / M.nc, Cc = b % M.nc;
+  o->m = M.row_off[R + 1] - M.row_off[R];
+  o->n = M.col_off[Cc + 1] - M.col_off[Cc];
+  o->r = M.rank[b];
+  o->x = M.pool + (int64_t)M.row_off[R] * M.n_cols + (int64_t)o->m * M.col_off[Cc];
+  o->w = o->x + (int64_t)o->m * o->r;
+  o->row0 = M.row_off[R];
+  o->col0 = M.col_off[Cc];
+  return true;
+}
+__device__ __forceinline__ double lr_entry(const LrBlock& L, int i, int j) {
+  double v = 0.0;
+  for (int q = 0; q < L.r; ++q) v = fma(L.x[i + (int64_t)q * L.m], L.w[j + (int64_t)q * L.n], v);
+  return v;
+}
+
+__global__ void __launch_bounds__(256) oz_exp_lr_kernel(MatView M, int* exps, int64_t rows_pad,
+                                                        int a_mode) {
+  __shared__ int red[CLR_MAX_CLUSTER][2];   // per panel row: the block's (at most) 2 segments
+  LrBlock L;
+  if (!lr_block(M, blockIdx.x, &L)) return;
+  const int np = a_mode ? L.m : L.n;
+  const int64_t k0 = a_mode ? L.col0 : L.row0;    // the block's first panel k
+  const int s0 = (int)(k0 / SEG_K);
+  for (int i = threadIdx.x; i < np; i += blockDim.x) red[i][0] = red[i][1] = INT_MIN;
+  __syncthreads();
+  for (int e = threadIdx.x; e < L.m * L.n; e += blockDim.x) {
+    const int i = a_mode ? e / L.n : e % L.m;
+    const int j = a_mode ? e % L.n : e / L.m;
+    const int x = exp_bound(lr_entry(L, i, j));
+    const int64_t k = k0 + (a_mode ? j : i);
+    if (x != INT_MIN) atomicMax(&red[a_mode ? i : j][(int)(k / SEG_K) - s0], x);
+  }
+  __syncthreads();
+  const int64_t p0 = a_mode ? L.row0 : L.col0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x)
+    for (int h = 0; h < 2; ++h)
+      if (red[i][h] != INT_MIN) atomicMax(&exps[(int64_t)(s0 + h) * rows_pad + p0 + i], red[i][h]);
+}
+
+__global__ void __launch_bounds__(256) oz_digits_lr_kernel(MatView M, const int* exps,
+                                                           unsigned short* panels,
+                                                           int64_t rows_pad, int64_t cols_pad,
+                                                           int a_mode) {
+  LrBlock L;
+  if (!lr_block(M, blockIdx.x, &L)) return;
+  const int64_t plane = rows_pad * cols_pad;
+  for (int e = threadIdx.x; e < L.m * L.n; e += blockDim.x) {
+    const int i = a_mode ? e / L.n : e % L.m;
+    const int j = a_mode ? e % L.n : e / L.m;
+    const int64_t prow = a_mode ? L.row0 + i : L.col0 + j;
+    const int64_t k = a_mode ? L.col0 + j : L.row0 + i;
+    unsigned short d[S];
+    oz_digits(lr_entry(L, i, j), exps[(k / SEG_K) * rows_pad + prow], d);
+#pragma unroll
+    for (int t = 0; t < S; ++t) panels[t * plane + prow * cols_pad + k] = d[t];
+  }
+}
+
+// Per cluster and K segment: the sum over the cluster's rows (columns) of 4^e, e their
+// exponents in that segment (rows without entries there count 0; past 2^1023 the sum is
+// infinite, which routes nothing to the GEMM).  One warp per (cluster, segment).
+__global__ void oz_scale_sums_kernel(const int* exps, int64_t rows_pad, const int* off, int n_cl,
+                                     int n_seg, double* out) {
+  const int64_t t = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32;
+  const int lane = threadIdx.x % 32;
+  if (t >= (int64_t)n_cl * n_seg) return;
+  const int c = (int)(t / n_seg), sg = (int)(t % n_seg);
+  double sum = 0.0;
+  for (int i = off[c] + lane; i < off[c + 1]; i += 32) {
+    const int e = exps[(int64_t)sg * rows_pad + i];
+    if (e > -1100) sum += ldexp(1.0, 2 * e);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) out[t] = sum;
 }
 
 typedef CUresult (*EncodeFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -649,19 +760,34 @@ void launch_ozaki_stage(const MatView& M, const int* row_idx, const int* col_idx
                         cudaStream_t st) {
   using namespace oz;
   unsigned short* pn = (unsigned short*)panels;
-  // sentinel exponent (bytes 0x80: a large negative int) for rows without dense entries
-  cudaMemsetAsync(exps, 0x80, (size_t)rows_pad * sizeof(int), st);
+  // sentinel exponent (bytes 0x80: a large negative int) for rows without entries in a segment
+  const int64_t n_seg = (cols_pad + SEG_K - 1) / SEG_K;
+  cudaMemsetAsync(exps, 0x80, (size_t)(n_seg * rows_pad) * sizeof(int), st);
+  const unsigned nb = (unsigned)(M.nr * M.nc);
   if (a_mode) {
     const unsigned ne = (unsigned)((rows_pad / 32) * ((cols_pad + 255) / 256));
     oz_exp_a_kernel<<<ne, 256, 0, st>>>(M, row_idx, col_idx, exps, rows_pad, cols_pad);
+  } else {
+    const dim3 ne((unsigned)rows_pad, (unsigned)n_seg);
+    oz_exp_b_kernel<<<ne, 256, 0, st>>>(M, row_idx, col_idx, exps, rows_pad, cols_pad);
+  }
+  oz_exp_lr_kernel<<<nb, 256, 0, st>>>(M, exps, rows_pad, a_mode);
+  if (a_mode) {
     const unsigned nd = (unsigned)((rows_pad / 32) * (cols_pad / 128));
     oz_digits_a_kernel<<<nd, 256, 0, st>>>(M, row_idx, col_idx, exps, pn, rows_pad, cols_pad);
   } else {
-    const dim3 ne((unsigned)rows_pad, (unsigned)((cols_pad + 1023) / 1024));
-    oz_exp_b_kernel<<<ne, 256, 0, st>>>(M, row_idx, col_idx, exps, cols_pad);
     const dim3 nd((unsigned)rows_pad, (unsigned)((cols_pad / 4 + 255) / 256));
     oz_digits_b_kernel<<<nd, 256, 0, st>>>(M, row_idx, col_idx, exps, pn, rows_pad, cols_pad);
   }
+  // (after the dense pass, which writes zeros at the low-rank blocks' entries)
+  oz_digits_lr_kernel<<<nb, 256, 0, st>>>(M, exps, pn, rows_pad, cols_pad, a_mode);
+}
+
+void launch_ozaki_scale_sums(const int* exps, int64_t rows_pad, const int* off, int n_cl,
+                             int n_seg, double* out, cudaStream_t st) {
+  const int64_t warps = (int64_t)n_cl * n_seg;
+  oz::oz_scale_sums_kernel<<<(unsigned)((warps * 32 + 255) / 256), 256, 0, st>>>(
+      exps, rows_pad, off, n_cl, n_seg, out);
 }
 
 int ozaki_gemm_dd(const OzakiGemmArgs& a, cudaStream_t st, std::string* why) {

@@ -30,8 +30,11 @@ __device__ __forceinline__ unsigned long long triple_flops(int kind, long long m
 // gemm_dacc_bound > 0 (split precision): a tile that would be accumulated densely in FP64
 // (ROUTE_DACC) is summed by the tensor-core GEMM instead (ROUTE_DACC_G) when its norm estimate
 // sum_K ||A_IK|| ||B_KJ|| is at most gemm_dacc_bound = eps / (16 u_split).
+// oz.sa non-null (exact slices): the same when the estimate of the sliced sum's error,
+// from the exponents of the tile's rows and columns per K segment, sum over segments
+// s of sa[I][s] sb[J][s] (sa[I][s] = sum over rows i of I of 4^e_is), is at most oz.bound2.
 __global__ void plan_count_kernel(MatView A, MatView B, Plan p, double eps_sp,
-                                  double gemm_dacc_bound) {
+                                  double gemm_dacc_bound, OzDaccRule oz) {
   const int t = (int)(((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32);
   const int lane = threadIdx.x % 32;
   if (t >= p.nI * p.nJ) return;  // the whole warp
@@ -81,6 +84,15 @@ __global__ void plan_count_kernel(MatView A, MatView B, Plan p, double eps_sp,
     if (route == ROUTE_DACC && gemm_dacc_bound > 0.0 && est <= gemm_dacc_bound) {
       route = ROUTE_DACC_G;
       atomicAdd(&p.counters->n_gemm_dacc, 1ull);
+    }
+    if (route == ROUTE_DACC && oz.sa) {
+      double e2 = 0.0;
+      for (int sg = 0; sg < oz.n_seg; ++sg)
+        e2 += oz.sa[(int64_t)I * oz.n_seg + sg] * oz.sb[(int64_t)J * oz.n_seg + sg];
+      if (e2 <= oz.bound2) {
+        route = ROUTE_DACC_G;
+        atomicAdd(&p.counters->n_gemm_dacc, 1ull);
+      }
     }
   }
   p.t_count[t] = count;
@@ -255,12 +267,13 @@ void launch_plan_scan(const Plan& p, int recompress_dense, cudaStream_t st) {
 }
 
 void launch_plan(const MatView& A, const MatView& B, const Plan& p, double eps_sp,
-                 int recompress_dense, double gemm_dacc_bound, cudaStream_t st) {
+                 int recompress_dense, double gemm_dacc_bound, const OzDaccRule& oz,
+                 cudaStream_t st) {
   const int n = p.nI * p.nJ;
   const int threads = 128;  // 4 tiles per block: one warp each
   const int blocks = (int)(((int64_t)n * 32 + threads - 1) / threads);
   cudaMemsetAsync(p.counters, 0, kPlanCountersClear, st);
-  plan_count_kernel<<<blocks, threads, 0, st>>>(A, B, p, eps_sp, gemm_dacc_bound);
+  plan_count_kernel<<<blocks, threads, 0, st>>>(A, B, p, eps_sp, gemm_dacc_bound, oz);
   plan_scan_kernel<<<1, kScanThreads, 0, st>>>(p, recompress_dense);
   plan_fill_kernel<<<blocks, threads, 0, st>>>(A, B, p);
 }

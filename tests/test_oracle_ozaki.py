@@ -1,5 +1,5 @@
 """Pins of the exact-slice (Ozaki-scheme) oracle against the scheme's definition and exact
-arithmetic: digit ranges, reconstruction within 2^-42 of the row scale, the sliced product
+arithmetic: digit ranges, reconstruction within 2^-48 of the row scale, the sliced product
 against a brute-force evaluation in exact rational arithmetic, its error bound against the
 exact product, exact results where the inputs need one digit, and the FP32 exactness
 precondition of the GPU's segments."""
@@ -24,11 +24,11 @@ def test_digit_ranges_and_reconstruction():
     assert np.abs(d[0]).max() <= 32
     for ds in d[1:]:
         assert ds.min() >= -32 and ds.max() <= 31
-    # |a| < 2^e per row, and the digits reconstruct a within 2^-42 2^e
+    # |a| < 2^e per row, and the digits reconstruct a within 2^-48 2^e
     nz = a != 0
     assert np.all(np.abs(a[nz]) < np.ldexp(1.0, np.broadcast_to(e[:, None], a.shape)[nz]))
     err = np.abs(oz.reconstruct(d, e) - a)
-    assert np.all(err <= np.ldexp(1.0, e[:, None] - 42))
+    assert np.all(err <= np.ldexp(1.0, e[:, None] - 48))
     assert not oz.reconstruct(d, e)[3].any()
 
 
@@ -77,10 +77,33 @@ def test_one_digit_inputs_multiply_exactly():
 
 
 def test_segment_sums_fit_fp32():
-    # the GPU sums a weight group over K segments of 2048 in FP32: with |digits| <= 32 the
-    # worst case (all digits at the bound, all signs equal, the 7-pair group) stays below 2^24,
+    # the GPU sums a weight group over K segments of 1024 in FP32: with |digits| <= 32 the
+    # worst case (all digits at the bound, all signs equal, the 8-pair group) stays below 2^24,
     # so every partial sum is an integer that FP32 represents exactly
-    worst = 7 * 2048 * 32 * 32
+    worst = oz.SLICES * 1024 * 32 * 32
     assert worst < 2 ** 24
-    d = np.full((2, 2048), 32.0)
-    assert float(np.max(7 * (d @ d.T))) == worst
+    d = np.full((2, 1024), 32.0)
+    assert float(np.max(oz.SLICES * (d @ d.T))) == worst
+    assert np.float32(worst) == worst and np.float32(worst - 1) == worst - 1
+
+
+def test_segmented_product_within_its_bound_and_sharper():
+    # per-segment exponents: a row whose large entries sit in one K segment keeps its full
+    # relative precision in the others.  A is large in segment 0 and B in segment 1, so no
+    # term pairs two large entries: the segmented bound is far below the whole-row one, and
+    # the segmented product meets it against the exact product (exact rationals)
+    rng = np.random.default_rng(5)
+    m, k, n, seg = 5, 12, 4, 4
+    a = rng.standard_normal((m, k))
+    b = rng.standard_normal((k, n))
+    a[:, :seg] *= 1e6
+    b[seg:2 * seg, :] *= 1e6
+    got = oz.sliced_product(a, b, seg=seg)
+    bound = oz.error_bound(a, b, seg=seg)
+    assert np.all(bound * 1e4 < oz.error_bound(a, b))
+    for i in range(m):
+        for j in range(n):
+            exact = sum(Fraction(a[i, q]) * Fraction(b[q, j]) for q in range(k))
+            assert abs(Fraction(got[i, j]) - exact) <= Fraction(bound[i, j])
+    # one segment covering K is the unsegmented scheme
+    assert np.array_equal(oz.sliced_product(a, b, seg=k), oz.sliced_product(a, b))
