@@ -206,7 +206,8 @@ def main() -> None:
     ctx = clr.Context(0, precision=args.precision, eps_lr=eps_ns, eps_sp=w.eps_sp,
                       ns_tol=args.tol, ns_max_iter=args.max_iter,
                       recompress_dense=0 if args.no_recompress_dense else 1,
-                      ns_fp64_tail=int(args.precision != "fp64"), ns_ladder_switch=1e-3)
+                      ns_fp64_tail=int(args.precision in ("bf16x3", "bf16x6")),
+                      ns_ladder_switch=1e-3)
     s = ctx.from_dense(torch.from_numpy(w.a).cuda(), w.row_sizes, eps_lr=w.eps_lr,
                        drop_norm=w.drop_norm)
     out = {"workload": w.name, "n": w.n, "clusters": len(w.row_sizes),
