@@ -129,6 +129,7 @@ DevicePool& pool() {
 struct WorkSet {
   DevBuf plan_ints, triples, counters, ws, scratch, panels_a, panels_b, tile_flags, order;
   DevBuf oz_exps;  // row exponents of the exact-slice products (A rows, then B panel rows)
+  DevBuf oz_recon; // the exact-slice staging's reconstructions of low-rank operand blocks
   // A's bf16 panels as staged for (matrix, terms, padded sizes): reused only while a caller
   // that guarantees A does not change (clr_multiply_host_stream) sets ctx->reuse_a
   DevBuf host_b, host_c, host_err;  // staging of the streamed host product (per pipeline slot)
@@ -138,7 +139,7 @@ struct WorkSet {
   int64_t staged_m = 0, staged_k = 0;
   void release() {
     for (DevBuf* b : {&plan_ints, &triples, &counters, &ws, &scratch, &panels_a, &panels_b,
-                      &tile_flags, &order, &oz_exps, &host_b, &host_c, &host_err})
+                      &tile_flags, &order, &oz_exps, &oz_recon, &host_b, &host_c, &host_err})
       b->release();
   }
 };
@@ -199,6 +200,7 @@ struct clr_mat_s {
   int* d_rank = nullptr;
   double* d_norm = nullptr;
   double* d_pool = nullptr;
+  unsigned int* d_cost = nullptr;
   MatView view() const {
     MatView v;
     v.nr = nr;
@@ -211,6 +213,7 @@ struct clr_mat_s {
     v.rank = d_rank;
     v.norm = d_norm;
     v.pool = d_pool;
+    v.cost = d_cost;
     return v;
   }
 };
@@ -272,6 +275,7 @@ void free_mat(clr_mat_t m) {
   pl.release(m->device, m->d_kind, nb * sizeof(int));
   pl.release(m->device, m->d_rank, nb * sizeof(int));
   pl.release(m->device, m->d_norm, nb * sizeof(double));
+  pl.release(m->device, m->d_cost, nb * sizeof(unsigned int));
   pl.release(m->device, m->d_pool, (size_t)m->n_rows * m->n_cols * sizeof(double));
   delete m;
 }
@@ -307,6 +311,7 @@ int alloc_mat(clr_ctx_t ctx, int nr, const int32_t* rs, int nc, const int32_t* c
   A((void**)&m->d_kind, nb * sizeof(int));
   A((void**)&m->d_rank, nb * sizeof(int));
   A((void**)&m->d_norm, nb * sizeof(double));
+  A((void**)&m->d_cost, nb * sizeof(unsigned int));
   A((void**)&m->d_pool, (size_t)m->n_rows * m->n_cols * sizeof(double));
   if (e == cudaSuccess)
     e = cudaMemcpy(m->d_row_off, m->row_off.data(), (nr + 1) * sizeof(int),
@@ -327,6 +332,7 @@ int alloc_mat(clr_ctx_t ctx, int nr, const int32_t* rs, int nc, const int32_t* c
   if (e == cudaSuccess) e = cudaMemset(m->d_kind, 0, nb * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(m->d_rank, 0, nb * sizeof(int));
   if (e == cudaSuccess) e = cudaMemset(m->d_norm, 0, nb * sizeof(double));
+  if (e == cudaSuccess) e = cudaMemset(m->d_cost, 0, nb * sizeof(unsigned int));
   if (e != cudaSuccess) {
     free_mat(m);
     return cuda_fail(ctx, e, "matrix allocation");
@@ -409,6 +415,7 @@ int make_plan(clr_ctx_t ctx, int nI, int nJ, int nK, Plan* p) {
   p->l_dense_s = base + 10 * nt;
   p->row_off = nullptr;
   p->col_off = nullptr;
+  p->c_cost = nullptr;
   p->triples = (Triple*)ctx->cur->triples.p;
   p->max_triples = max_tr;
   p->counters = (PlanCounters*)ctx->cur->counters.p;
@@ -1041,12 +1048,18 @@ int stage_ozaki(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double eps
   int* eb = ea + (size_t)n_seg * M_pad;
   double* sa = (double*)((char*)w->oz_exps.p + exp_bytes);
   double* sb = sa + (size_t)n_seg * c->nr;
-  launch_ozaki_stage(av, c->d_row_idx, a->d_col_idx, w->panels_a.p, ea, M_pad, K_pad, 1, s);
-  launch_ozaki_stage(bv, a->d_col_idx, c->d_col_idx, w->panels_b.p, eb, N_pad, K_pad, 0, s);
+  // one reconstruction image, used by A's staging and then (stream-ordered) by B's
+  CLR_CUDA(w->oz_recon.ensure((size_t)std::max(a->n_rows * a->n_cols, b->n_rows * b->n_cols) *
+                              sizeof(double)));
+  double* recon = (double*)w->oz_recon.p;
+  launch_ozaki_stage(av, c->d_row_idx, a->d_col_idx, w->panels_a.p, ea, recon, M_pad, K_pad, 1,
+                     s);
+  launch_ozaki_stage(bv, a->d_col_idx, c->d_col_idx, w->panels_b.p, eb, recon, N_pad, K_pad, 0,
+                     s);
   launch_ozaki_scale_sums(ea, M_pad, c->d_row_off, c->nr, n_seg, sa, s);
   launch_ozaki_scale_sums(eb, N_pad, c->d_col_off, c->nc, n_seg, sb, s);
   CLR_CHECK_LAUNCH("exact-slice staging");
-  prof_launches(ctx, 10);  // per operand: 2 exponent + 2 digit kernels; 2 scale sums
+  prof_launches(ctx, 12);  // per operand: reconstruction, 2 exponent, 2 digit kernels; 2 sums
   prof_mark(ctx, s, PH_STAGE);
   const double u = 4.0 * 1.2 * std::ldexp(1.0, -48);
   const double budget = eps_lr / 16.0;
@@ -1064,7 +1077,7 @@ int run_ozaki_gemm(clr_ctx_t ctx, clr_mat_t a, clr_mat_t c, const Plan& p, cudaS
   const int64_t K_pad = (a->n_cols + 127) / 128 * 128;
   const int n_seg = (int)((K_pad + kOzakiSegK - 1) / kOzakiSegK);
   WorkSet* w = ctx->cur;
-  CLR_CUDA(w->tile_flags.ensure((size_t)(M_pad / 128) * (N_pad / 64)));
+  CLR_CUDA(w->tile_flags.ensure((size_t)(M_pad / 128) * (N_pad / kOzakiTileN)));
   MatView cv = c->view();
   int* ea = (int*)w->oz_exps.p;
   OzakiGemmArgs g;
@@ -1110,6 +1123,7 @@ int multiply_into(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t c, double a
   if (st) return st;
   p.row_off = c->d_row_off;
   p.col_off = c->d_col_off;
+  p.c_cost = c->d_cost;
   CLR_CUDA(ctx->cur->ws.ensure(2 * (size_t)c->n_rows * c->n_cols * sizeof(double)));
   const int lr_grid = grid_of(ctx, tune.lr_mult);
   CLR_CUDA(ctx->cur->scratch.ensure((size_t)lr_grid * scratch_per_cta() * sizeof(double)));

@@ -28,6 +28,9 @@ struct MatView {
   int* rank;             // nr * nc
   double* norm;          // nr * nc, Frobenius norm of each block
   double* pool;          // n_rows * n_cols
+  // nr * nc: SM kilocycles of the block's last dense recompression into this matrix (0: none
+  // yet), the scheduling cost of the next one (recompression lists in decreasing cost)
+  unsigned int* cost = nullptr;
 };
 
 __host__ __device__ inline int64_t slot_of(const MatView& m, int I, int J, int mI) {
@@ -149,6 +152,7 @@ struct Plan {
   int* l_dense_s;  // l_dense reordered by decreasing cost m n (number of products)
   const int* row_off;  // C's cluster offsets (device), for those costs
   const int* col_off;
+  const unsigned int* c_cost;  // C's measured recompression costs (MatView::cost), or null
   Triple* triples;
   int64_t max_triples;
   PlanCounters* counters;
@@ -250,6 +254,7 @@ int split_gemm_dd(const SplitGemmArgs& a, cudaStream_t st, std::string* why);
 // k_ozaki.cu: FP64-accurate dense x dense products on the tensor cores (exact slices)
 constexpr int kOzakiSlices = 8;
 constexpr int kOzakiSegK = 1024;   // K segment: exact FP32 group sums, exponents per segment
+constexpr int kOzakiTileN = 32;    // the GEMM's output tiles are 128 x kOzakiTileN
 struct OzakiGemmArgs {
   const MatView* C;
   const Plan* p;
@@ -257,10 +262,10 @@ struct OzakiGemmArgs {
   void* b_panels;     // kOzakiSlices x N_pad x K_pad
   const int* ea;      // n_seg x M_pad row exponents of A per K segment
   const int* eb;      // n_seg x N_pad column exponents (rows of the B panel) per K segment
-  int64_t M_pad, N_pad, K_pad;   // multiples of 128, 64, 128
+  int64_t M_pad, N_pad, K_pad;   // multiples of 128, kOzakiTileN, 128
   const int* row_tile_of;
   const int* col_tile_of;
-  unsigned char* tile_active;  // (M_pad/128) * (N_pad/64) flags
+  unsigned char* tile_active;  // (M_pad/128) * (N_pad/kOzakiTileN) flags
   int n_sm;
   int* err;
   unsigned long long wait_ns = 2000000000ull;
@@ -269,9 +274,10 @@ struct OzakiGemmArgs {
 int ozaki_gemm_dd(const OzakiGemmArgs& a, cudaStream_t st, std::string* why);
 // exps: n_seg x rows_pad ints (n_seg = K segments of kOzakiSegK), written (the row exponents
 // per segment); panels: kOzakiSlices planes
+// recon: scratch of M.n_rows x M.n_cols doubles (the low-rank blocks' reconstructions)
 void launch_ozaki_stage(const MatView& M, const int* row_idx, const int* col_idx, void* panels,
-                        int* exps, int64_t rows_pad, int64_t cols_pad, int a_mode,
-                        cudaStream_t st);
+                        int* exps, double* recon, int64_t rows_pad, int64_t cols_pad,
+                        int a_mode, cudaStream_t st);
 // out[c * n_seg + s] = sum over rows i in [off[c], off[c + 1]) of 4^exps[s * rows_pad + i]
 void launch_ozaki_scale_sums(const int* exps, int64_t rows_pad, const int* off, int n_cl,
                              int n_seg, double* out, cudaStream_t st);

@@ -22,21 +22,23 @@
 // about 2^-48 sqrt(K) 2^(e_i + f_j) for independent rounding: FP64-like relative to the rows'
 // and columns' largest entries.
 //
-// Kernel (one CTA per SM, persistent over 128 x 64 output tiles):
+// Kernel (one CTA per SM, persistent over 128 x 32 output tiles):
 //   warp 0     TMA producer: per 32-wide k chunk the 8 slices of the A tile (128 x 32) and of
-//              the B tile (64 x 32), 64-byte swizzle, into one of two pipeline stages;
-//   warp 1     allocates all 512 TMEM columns (eight 128 x 64 FP32 accumulators, one per weight
-//              group g, side by side) and issues tcgen05.mma (M=128, K=16, kind::f16, bf16 in,
-//              FP32 accumulate) for the 36 slice pairs as 12 MMAs per K16 step: slice s of A
-//              against the B slices t = 0 .. 7 - s at once (N = 64 (8 - s), split at 256),
+//              the B tile (32 x 32), 64-byte swizzle, into one of two pipeline stages;
+//   warp 1     allocates all 512 TMEM columns: two sets of eight 128 x 32 FP32 accumulators
+//              (one per weight group g, side by side), and issues tcgen05.mma (M=128, K=16,
+//              kind::f16, bf16 in, FP32 accumulate) for the 36 slice pairs as 8 MMAs per K16
+//              step: slice s of A against the B slices t = 0 .. 7 - s at once (N = 32 (8 - s)),
 //              which writes groups s .. 7 together.  Each A slice is then read from shared
-//              memory once per MMA instead of once per pair: 120 KB of operand reads per step
-//              instead of 216 KB (with one MMA per pair the tensor unit was bound by operand
-//              fetch: busy 68% of the time with its math pipe at 28%);
-//   warps 2-9  epilogue: after every K segment of 1024 the eight exact group sums are read from
-//              TMEM and added, scaled by 2^(-6 g), into FP64 registers (32 per thread); after
-//              the tile's last segment the FP64 values are scaled by 2^(e_i + f_j - 10) and
-//              stored into the C tiles whose route is dense.
+//              memory once per MMA instead of once per pair (with one MMA per pair the tensor
+//              unit was bound by operand fetch: busy 68% of the time with its math pipe at
+//              28%).  Consecutive K segments alternate between the two sets;
+//   warps 2-9  epilogue: after every K segment of 1024 the eight exact group sums of its set
+//              are read from TMEM and added, scaled by 2^(e_i + f_j - 10 - 6 g) with the
+//              segment's exponents, into FP64 registers (16 per thread), while the MMAs of the
+//              next segment fill the other set (with one set, 128 x 64 tiles, this FP64 fold
+//              took a third of the kernel's time); after the tile's last segment the values are
+//              stored into the C tiles the GEMM serves (route DENSE or DACC_G).
 // Every mbarrier wait is bounded as in the split-precision kernel; on a timeout the kernel
 // raises the error flag, drains its copies and MMAs (bounded) and returns.
 #include <cuda.h>
@@ -53,17 +55,20 @@ namespace oz {
 
 constexpr int S = kOzakiSlices;  // 8
 constexpr int BM = 128;
-constexpr int BN = 64;
+constexpr int BN = kOzakiTileN;      // 32
 constexpr int BK = 32;               // 32 bf16 = 64 bytes: one 64B-swizzle row
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 64 + 32 * EPI_WARPS;
 constexpr uint32_t A_TILE = BM * BK * 2;   // 8192 B
-constexpr uint32_t B_TILE = BN * BK * 2;   // 4096 B
+constexpr uint32_t B_TILE = BN * BK * 2;   // 2048 B
 constexpr uint32_t STAGE = S * (A_TILE + B_TILE);
 constexpr int STAGES = 2;
 constexpr uint32_t SMEM_DATA = STAGE * STAGES;
 constexpr uint32_t SMEM_TOTAL = SMEM_DATA + 1024 /*barriers*/ + 1024 /*align*/;
 constexpr int GROUPS = S;            // weight groups g = s + t <= S - 1
+constexpr int ACC_COLS = GROUPS * BN;   // one accumulator set: the eight groups side by side
+constexpr int NBUF = 2;                 // two sets: a segment's MMAs overlap the last one's fold
+constexpr int EPC = BN / 2;             // output columns per epilogue thread
 constexpr int SEG_CHUNKS = 32;       // K segment of 1024: exact FP32 group sums
 constexpr int SEG_K = SEG_CHUNKS * BK;
 // the staging kernels' k tiles (256, 128 and 4 x 256 wide) never straddle a segment
@@ -163,18 +168,15 @@ __device__ __forceinline__ uint32_t idesc_n(int n) {
          ((uint32_t)(BM >> 4) << 24);
 }
 constexpr int kMaxSlicesPerMma = 256 / BN;   // B slices one MMA covers (N <= 256)
+static_assert(NBUF * GROUPS * BN == 512, "the accumulator sets fill the 512 TMEM columns");
 
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
         "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-        "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-        "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-        "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-        "=r"(r[31])
+        "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
@@ -193,7 +195,7 @@ struct Epi {
 
 // Linear tile id -> (m block, n block), grouped along m for L2 reuse across concurrent CTAs.
 __device__ __forceinline__ void tile_coords(int id, int n_m, int n_n, int* mb, int* nb) {
-  constexpr int G = 16;
+  constexpr int G = 8;   // 8 x 19 tiles of 128 x 32 per wave: the least panel bytes
   const int per_group = G * n_n;
   const int g = id / per_group;
   const int first = g * G;
@@ -221,9 +223,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + SMEM_DATA);
   uint64_t* empty = full + STAGES;
-  uint64_t* tfull = empty + STAGES;
-  uint64_t* tempty = tfull + 1;
-  uint64_t* drain = tempty + 1;
+  uint64_t* tfull = empty + STAGES;     // per accumulator set
+  uint64_t* tempty = tfull + NBUF;
+  uint64_t* drain = tempty + NBUF;
   uint32_t* tmem_holder = (uint32_t*)(drain + 1);
   volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
 
@@ -235,8 +237,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(tfull, 1);
-    mbar_init(tempty, EPI_WARPS);
+    for (int b = 0; b < NBUF; ++b) {
+      mbar_init(&tfull[b], 1);
+      mbar_init(&tempty[b], EPI_WARPS);
+    }
     mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -307,17 +311,20 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!tile_active[tile]) continue;
         for (int k0 = 0; ok && k0 < num_k; k0 += SEG_CHUNKS) {
           const int k1 = min(num_k, k0 + SEG_CHUNKS);
-          // the epilogue has read the previous segment's group sums
-          if (!mbar_wait(tempty, (seg_count & 1) ^ 1, abort_flag, wait_ns)) { ok = false; break; }
+          // the epilogue has read the group sums of the segment before last from this set
+          const int bset = seg_count & 1;
+          const uint32_t tp = (seg_count >> 1) & 1;
+          if (!mbar_wait(&tempty[bset], tp ^ 1, abort_flag, wait_ns)) { ok = false; break; }
           fence_after();
+          const uint32_t acc_base = tmem_base + (uint32_t)(bset * ACC_COLS);
           for (int kc = k0; kc < k1; ++kc) {
             if (!mbar_wait(&full[s], phase, abort_flag, wait_ns)) { ok = false; break; }
             fence_after();
             const uint32_t st = saddr(smem + (size_t)s * STAGE);
             // A slice s times the consecutive B slices t = 0 .. 7 - s in one MMA of
-            // N = 64 (8 - s) (two where that exceeds 256): its output columns land in the
-            // accumulators of groups s .. 7, which are consecutive in TMEM.  The two MMAs of
-            // s = 0 cover every group, so they alone start a segment (accumulate off).
+            // N = 32 (8 - s): its output columns land in the accumulators of groups s .. 7,
+            // which are consecutive in TMEM.  The MMA of s = 0 covers every group, so it alone
+            // starts a segment (accumulate off).
 #pragma unroll
             for (int k16 = 0; k16 < BK / 16; ++k16) {
 #pragma unroll 1
@@ -325,7 +332,7 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const uint32_t a_addr = st + sa * A_TILE + k16 * 32;
                 for (int t0 = 0; t0 < S - sa; t0 += kMaxSlicesPerMma) {
                   const int cnt = min(kMaxSlicesPerMma, S - sa - t0);
-                  const uint32_t d_tmem = tmem_base + (uint32_t)((sa + t0) * BN);
+                  const uint32_t d_tmem = acc_base + (uint32_t)((sa + t0) * BN);
                   const uint32_t b_addr = st + S * A_TILE + t0 * B_TILE + k16 * 32;
                   const uint32_t acc = (kc != k0 || sa != 0 || k16 != 0) ? 1u : 0u;
                   umma_bf16(d_tmem, sdesc(a_addr), sdesc(b_addr), idesc_n(cnt * BN), acc);
@@ -337,7 +344,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (++s == STAGES) { s = 0; phase ^= 1; }
           }
           if (!ok) break;
-          umma_commit(tfull);
+          umma_commit(&tfull[bset]);
           ++seg_count;
         }
       }
@@ -356,7 +363,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else {
     // ------------------------------------------------------------------ epilogue
     const int quarter = warp % 4;          // TMEM lanes 32*quarter .. 32*quarter+31
-    const int half = (warp - 2) / 4;       // columns 32*half .. 32*half+31
+    const int half = (warp - 2) / 4;       // columns EPC*half .. EPC*half+EPC-1
     const int rl = quarter * 32 + lane;    // row within the tile
     int seg_count = 0;
     bool ok = true;
@@ -364,37 +371,41 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (!tile_active[tile]) continue;
       int mb, nb;
       tile_coords(tile, n_m, n_n, &mb, &nb);
-      double acc[32];
+      double acc[EPC];
 #pragma unroll
-      for (int j = 0; j < 32; ++j) acc[j] = 0.0;
+      for (int j = 0; j < EPC; ++j) acc[j] = 0.0;
       const int64_t row = (int64_t)mb * BM + rl;
-      const int64_t col0 = (int64_t)nb * BN + half * 32;
+      const int64_t col0 = (int64_t)nb * BN + half * EPC;
       for (int k0 = 0; k0 < num_k; k0 += SEG_CHUNKS) {
         // this segment's scale of every entry: 2^(e_i + f_j - 10) with the exponents of its
         // own K range (row i of A, column j of B over the segment's columns / rows)
         const int sg = k0 / SEG_CHUNKS;
         const int er = clamp_exp(epi.ea[(int64_t)sg * M_pad + row]) - 10;
-        int ex[32];
+        int ex[EPC];
 #pragma unroll
-        for (int j = 0; j < 32; ++j) ex[j] = er + clamp_exp(epi.eb[(int64_t)sg * N_pad + col0 + j]);
+        for (int j = 0; j < EPC; ++j)
+          ex[j] = er + clamp_exp(epi.eb[(int64_t)sg * N_pad + col0 + j]);
+        const int bset = seg_count & 1;
         int got = 0;
-        if (lane == 0) got = mbar_wait(tfull, seg_count & 1, abort_flag, wait_ns) ? 1 : 0;
+        if (lane == 0)
+          got = mbar_wait(&tfull[bset], (seg_count >> 1) & 1, abort_flag, wait_ns) ? 1 : 0;
         got = __shfl_sync(0xffffffffu, got, 0);
         if (!got) { ok = false; break; }
         fence_after();
-        const uint32_t tbase =
-            tmem_base + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(half * 32);
+        const uint32_t tbase = tmem_base + ((uint32_t)(quarter * 32) << 16) +
+                               (uint32_t)(bset * ACC_COLS + half * EPC);
+        // the fold of this set overlaps the MMAs of the next segment into the other set
 #pragma unroll 1
         for (int g = 0; g < GROUPS; ++g) {
-          uint32_t r[32];
-          tmem_ld32(tbase + (uint32_t)(g * BN), r);
+          uint32_t r[EPC];
+          tmem_ld16(tbase + (uint32_t)(g * BN), r);
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
+          for (int j = 0; j < EPC; ++j)
             acc[j] = fma((double)__uint_as_float(r[j]), pow2(ex[j] - 6 * g), acc[j]);
         }
         fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(tempty);
+        if (lane == 0) mbar_arrive(&tempty[bset]);
         ++seg_count;
       }
       if (!ok) break;
@@ -404,7 +415,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int64_t rowbase = (int64_t)epi.row_off[I] * epi.n_cols + (row - epi.row_off[I]);
         const int* route_row = epi.t_route + (int64_t)I * epi.nJ;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
+        for (int j = 0; j < EPC; ++j) {
           const int64_t col = col0 + j;
           if (col < epi.n_cols) {
             const int J = epi.col_tile_of[col];
@@ -646,39 +657,49 @@ __global__ void __launch_bounds__(256) oz_digits_b_kernel(MatView M, const int* 
     *reinterpret_cast<unsigned long long*>(panels + t * plane + j * cols_pad + k) = packed[t];
 }
 
-// Low-rank blocks: one CTA per block of M (blocks of another kind return at once), entry (i, j)
-// = sum_t X(i, t) W(j, t) in FP64, computed here for the exponents and again for the digits.
-// a_mode: panel row = M's row, panel k = M's column (threads along j); else panel row = M's
-// column, panel k = M's row (threads along i).
+// Low-rank blocks: their reconstructions X W^T, once, in FP64 into a scratch image of M laid
+// out like its pool (block (R, C) at row_off[R] n_cols + m col_off[C], column-major): one CTA
+// per block of M (blocks of another kind return at once), the register-tiled CTA product.
+// Then the exponents and the digits read the image.  a_mode: panel row = M's row, panel k =
+// M's column (threads along j); else panel row = M's column, panel k = M's row (threads along
+// i).
 struct LrBlock {
-  const double* x;
-  const double* w;
-  int m, n, r;
+  const double* v;   // the reconstruction (m x n, ld m)
+  int m, n;
   int64_t row0, col0;
 };
-__device__ __forceinline__ bool lr_block(const MatView& M, int b, LrBlock* o) {
+__device__ __forceinline__ bool lr_block(const MatView& M, const double* recon, int b,
+                                         LrBlock* o) {
   if (M.kind[b] != CLR_KIND_LR) return false;
   const int R = b / M.nc, Cc = b % M.nc;
   o->m = M.row_off[R + 1] - M.row_off[R];
   o->n = M.col_off[Cc + 1] - M.col_off[Cc];
-  o->r = M.rank[b];
-  o->x = M.pool + (int64_t)M.row_off[R] * M.n_cols + (int64_t)o->m * M.col_off[Cc];
-  o->w = o->x + (int64_t)o->m * o->r;
+  o->v = recon + (int64_t)M.row_off[R] * M.n_cols + (int64_t)o->m * M.col_off[Cc];
   o->row0 = M.row_off[R];
   o->col0 = M.col_off[Cc];
   return true;
 }
-__device__ __forceinline__ double lr_entry(const LrBlock& L, int i, int j) {
-  double v = 0.0;
-  for (int q = 0; q < L.r; ++q) v = fma(L.x[i + (int64_t)q * L.m], L.w[j + (int64_t)q * L.n], v);
-  return v;
+
+__global__ void __launch_bounds__(256) oz_lr_recon_kernel(MatView M, double* recon) {
+  const int b = blockIdx.x;
+  if (M.kind[b] != CLR_KIND_LR) return;
+  const int R = b / M.nc, Cc = b % M.nc;
+  const int m = M.row_off[R + 1] - M.row_off[R];
+  const int n = M.col_off[Cc + 1] - M.col_off[Cc];
+  const int r = M.rank[b];
+  const int64_t slot = (int64_t)M.row_off[R] * M.n_cols + (int64_t)m * M.col_off[Cc];
+  const double* x = M.pool + slot;             // m x r, ld m
+  const double* w = x + (int64_t)m * r;        // n x r, ld n
+  // out(i, j) = sum_q X(i, q) W(j, q)
+  cta_gemm_tiled<256>(m, n, r, x, 1, m, w, n, 1, recon + slot, m, false);
 }
 
-__global__ void __launch_bounds__(256) oz_exp_lr_kernel(MatView M, int* exps, int64_t rows_pad,
+__global__ void __launch_bounds__(256) oz_exp_lr_kernel(MatView M, const double* recon,
+                                                        int* exps, int64_t rows_pad,
                                                         int a_mode) {
   __shared__ int red[CLR_MAX_CLUSTER][2];   // per panel row: the block's (at most) 2 segments
   LrBlock L;
-  if (!lr_block(M, blockIdx.x, &L)) return;
+  if (!lr_block(M, recon, blockIdx.x, &L)) return;
   const int np = a_mode ? L.m : L.n;
   const int64_t k0 = a_mode ? L.col0 : L.row0;    // the block's first panel k
   const int s0 = (int)(k0 / SEG_K);
@@ -687,7 +708,7 @@ __global__ void __launch_bounds__(256) oz_exp_lr_kernel(MatView M, int* exps, in
   for (int e = threadIdx.x; e < L.m * L.n; e += blockDim.x) {
     const int i = a_mode ? e / L.n : e % L.m;
     const int j = a_mode ? e % L.n : e / L.m;
-    const int x = exp_bound(lr_entry(L, i, j));
+    const int x = exp_bound(L.v[i + (int64_t)j * L.m]);
     const int64_t k = k0 + (a_mode ? j : i);
     if (x != INT_MIN) atomicMax(&red[a_mode ? i : j][(int)(k / SEG_K) - s0], x);
   }
@@ -698,12 +719,13 @@ __global__ void __launch_bounds__(256) oz_exp_lr_kernel(MatView M, int* exps, in
       if (red[i][h] != INT_MIN) atomicMax(&exps[(int64_t)(s0 + h) * rows_pad + p0 + i], red[i][h]);
 }
 
-__global__ void __launch_bounds__(256) oz_digits_lr_kernel(MatView M, const int* exps,
+__global__ void __launch_bounds__(256) oz_digits_lr_kernel(MatView M, const double* recon,
+                                                           const int* exps,
                                                            unsigned short* panels,
                                                            int64_t rows_pad, int64_t cols_pad,
                                                            int a_mode) {
   LrBlock L;
-  if (!lr_block(M, blockIdx.x, &L)) return;
+  if (!lr_block(M, recon, blockIdx.x, &L)) return;
   const int64_t plane = rows_pad * cols_pad;
   for (int e = threadIdx.x; e < L.m * L.n; e += blockDim.x) {
     const int i = a_mode ? e / L.n : e % L.m;
@@ -711,7 +733,7 @@ __global__ void __launch_bounds__(256) oz_digits_lr_kernel(MatView M, const int*
     const int64_t prow = a_mode ? L.row0 + i : L.col0 + j;
     const int64_t k = a_mode ? L.col0 + j : L.row0 + i;
     unsigned short d[S];
-    oz_digits(lr_entry(L, i, j), exps[(k / SEG_K) * rows_pad + prow], d);
+    oz_digits(L.v[i + (int64_t)j * L.m], exps[(k / SEG_K) * rows_pad + prow], d);
 #pragma unroll
     for (int t = 0; t < S; ++t) panels[t * plane + prow * cols_pad + k] = d[t];
   }
@@ -756,8 +778,8 @@ bool encode_panel(EncodeFn fn, CUtensorMap* tm, void* base, int64_t k_pad, int64
 }  // namespace oz
 
 void launch_ozaki_stage(const MatView& M, const int* row_idx, const int* col_idx, void* panels,
-                        int* exps, int64_t rows_pad, int64_t cols_pad, int a_mode,
-                        cudaStream_t st) {
+                        int* exps, double* recon, int64_t rows_pad, int64_t cols_pad,
+                        int a_mode, cudaStream_t st) {
   using namespace oz;
   unsigned short* pn = (unsigned short*)panels;
   // sentinel exponent (bytes 0x80: a large negative int) for rows without entries in a segment
@@ -771,7 +793,8 @@ void launch_ozaki_stage(const MatView& M, const int* row_idx, const int* col_idx
     const dim3 ne((unsigned)rows_pad, (unsigned)n_seg);
     oz_exp_b_kernel<<<ne, 256, 0, st>>>(M, row_idx, col_idx, exps, rows_pad, cols_pad);
   }
-  oz_exp_lr_kernel<<<nb, 256, 0, st>>>(M, exps, rows_pad, a_mode);
+  oz_lr_recon_kernel<<<nb, 256, 0, st>>>(M, recon);
+  oz_exp_lr_kernel<<<nb, 256, 0, st>>>(M, recon, exps, rows_pad, a_mode);
   if (a_mode) {
     const unsigned nd = (unsigned)((rows_pad / 32) * (cols_pad / 128));
     oz_digits_a_kernel<<<nd, 256, 0, st>>>(M, row_idx, col_idx, exps, pn, rows_pad, cols_pad);
@@ -780,7 +803,7 @@ void launch_ozaki_stage(const MatView& M, const int* row_idx, const int* col_idx
     oz_digits_b_kernel<<<nd, 256, 0, st>>>(M, row_idx, col_idx, exps, pn, rows_pad, cols_pad);
   }
   // (after the dense pass, which writes zeros at the low-rank blocks' entries)
-  oz_digits_lr_kernel<<<nb, 256, 0, st>>>(M, exps, pn, rows_pad, cols_pad, a_mode);
+  oz_digits_lr_kernel<<<nb, 256, 0, st>>>(M, recon, exps, pn, rows_pad, cols_pad, a_mode);
 }
 
 void launch_ozaki_scale_sums(const int* exps, int64_t rows_pad, const int* off, int n_cl,

@@ -118,7 +118,12 @@ constexpr int kScanQ = 5;
 constexpr int kCostBuckets = 32;
 
 // log2 bucket of a tile's cost (which = 0: QR route recompression, 1: dense SVD, 2: dense x
-// dense products, m n times the tile's number of products)
+// dense products, m n times the tile's number of products).  A dense recompression's cost
+// depends on the path the tile takes (dense certificate ~0.4, pre-reduction ~1.2, full SVD ~5
+// SM cycles per m n min(m, n) on the lattice iterates), known only once it ran: the cycles
+// measured the last time a tile of this matrix was recompressed (Newton-Schulz reuses its
+// matrices for the same products every iteration) replace the size estimate (2 m n min(m, n)
+// cycles) when present.
 __device__ __forceinline__ int cost_bucket(const Plan& p, int t, int which) {
   const int I = t / p.nJ, J = t % p.nJ;
   const long long m = p.row_off[I + 1] - p.row_off[I];
@@ -128,7 +133,8 @@ __device__ __forceinline__ int cost_bucket(const Plan& p, int t, int which) {
     const long long R = p.t_rsum[t];
     c = (m + n) * R * R + R * R * R;
   } else if (which == 1) {
-    c = m * n * (m < n ? m : n);
+    const unsigned kc = p.c_cost ? p.c_cost[t] : 0u;
+    c = kc ? (long long)kc << 10 : 2 * m * n * (m < n ? m : n);
   } else {
     c = m * n * (long long)p.t_count[t];
   }

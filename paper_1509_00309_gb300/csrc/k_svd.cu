@@ -355,7 +355,16 @@ struct SvdShared {
   int qr_perm[CLR_MAX_CLUSTER];
   int qr_pivot;
   double cert;    // tail_lower_bound_sq's result
+  // compress_by_pivoted_qr: each column's trailing norm^2 when it was last summed exactly (the
+  // downdated norms are recomputed once they fall below kDowndateFloor of it), and the FMAs
+  // of those recomputations
+  double qr_nref[CLR_MAX_CLUSTER];
+  unsigned long long qr_recomputed;
 };
+// Downdated column norms^2 are summed again exactly once they fall below this fraction of the
+// last exact value: a downdate nu'^2 = nu^2 - r^2 carries an absolute error of a few u nu_ref^2,
+// so the relative error stays below ~1e-9 between recomputations.
+constexpr double kDowndateFloor = 1e-6;
 
 // Column norms of g, their descending order, and the truncation rank at eps.
 __device__ void sort_and_truncate(const double* g, int p, int q, int64_t ldg, double eps,
@@ -926,8 +935,9 @@ __device__ int rrqr_block(const double* S, int64_t s_r, int64_t s_c, int m, int 
 //
 // A (p x q, the block or its transpose, p >= q) is reduced by Householder QR with column
 // pivoting (at step j the remaining column of largest norm over rows j..p-1, first maximum on
-// ties; the norms are recomputed exactly in the same pass that applies the reflector), stopped
-// at the first step k whose trailing block has ||R_22||_F <= tau = eps/16:
+// ties; the norms are downdated and summed again exactly once they have fallen by 1e6, and the
+// stop is always decided on exact sums), stopped at the first step k whose trailing block has
+// ||R_22||_F <= tau = eps/16:
 //   A P = Q [R_11 R_12; 0 R_22].
 // R_22 is dropped and the k x q factor R = [R_11 R_12] gets the mixed-precision SVD, truncated
 // at the remaining budget sqrt(eps^2 - ||R_22||_F^2).  The two errors are orthogonal (rows
@@ -1032,11 +1042,14 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
     s2 = warp_sum(s2);
     if (l == 0) {
       sh.sigma[c] = s2;
+      sh.qr_nref[c] = s2;
       sh.qr_perm[c] = c;
     }
   }
+  if (threadIdx.x == 0) sh.qr_recomputed = 0;
   __syncthreads();
   unsigned long long fma_count = 0;
+  bool exact = true;   // the trailing norms were all summed exactly at this step
   int k = -1;
   int kc = 0;   // steps completed when the threshold was not met within jmax
   for (int j = 0; j <= jext; ++j) {
@@ -1062,6 +1075,25 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
       }
     }
     __syncthreads();
+    if (sh.kept_sq <= tau2 && !exact) {
+      // the downdated norms meet the threshold: sum the trailing norms exactly and decide (and
+      // pivot) on those
+      for (int c = j + w; c < q; c += kWarps) {
+        const double* y = g + (int64_t)c * p;
+        double s2 = 0.0;
+        for (int i = j + l; i < p; i += 32) s2 = fma(y[i], y[i], s2);
+        s2 = warp_sum(s2);
+        if (l == 0) {
+          sh.sigma[c] = s2;
+          sh.qr_nref[c] = s2;
+        }
+      }
+      fma_count += (unsigned long long)(p - j) * (unsigned long long)(q - j);
+      exact = true;
+      __syncthreads();
+      --j;   // the same step again
+      continue;
+    }
     if (sh.kept_sq <= tau2) {
       if (j <= jmax) k = j;
       else kc = j;   // met only past jmax: R_j is complete up to a negligible trailing block
@@ -1091,6 +1123,9 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
       const double t = sh.sigma[j];
       sh.sigma[j] = sh.sigma[piv];
       sh.sigma[piv] = t;
+      const double tr = sh.qr_nref[j];
+      sh.qr_nref[j] = sh.qr_nref[piv];
+      sh.qr_nref[piv] = tr;
       const int ti = sh.qr_perm[j];
       sh.qr_perm[j] = sh.qr_perm[piv];
       sh.qr_perm[piv] = ti;
@@ -1116,30 +1151,40 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
       sh.qr_tau[j] = t;
     }
     __syncthreads();
-    // apply to the remaining columns, recomputing their norms over rows j+1..p-1
+    // apply to the remaining columns.  The reflector keeps the norm of each column's rows
+    // j..p-1 and moves its row j into R, so the trailing norm^2 over rows j+1..p-1 is the old
+    // one minus the new row-j entry squared (downdate), summed again exactly when it has fallen
+    // below kDowndateFloor of its last exact value (or is not positive).
     for (int c = j + 1 + w; c < q; c += kWarps) {
       double* y = g + (int64_t)c * p;
       double d = 0.0;
       for (int i = j + 1 + l; i < p; i += 32) d = fma(col[i], y[i], d);
       d = warp_sum(d) + y[j];
       const double f = t * d;
-      double s2 = 0.0;
-      for (int i = j + 1 + l; i < p; i += 32) {
-        const double yi = fma(-f, col[i], y[i]);
-        y[i] = yi;
-        s2 = fma(yi, yi, s2);
+      for (int i = j + 1 + l; i < p; i += 32) y[i] = fma(-f, col[i], y[i]);
+      const double yj = y[j] - f;
+      double nu2 = sh.sigma[c] - yj * yj;
+      if (!(nu2 > kDowndateFloor * sh.qr_nref[c])) {
+        double s2 = 0.0;
+        for (int i = j + 1 + l; i < p; i += 32) s2 = fma(y[i], y[i], s2);
+        nu2 = warp_sum(s2);
+        if (l == 0) {
+          sh.qr_nref[c] = nu2;
+          atomicAdd(&sh.qr_recomputed, (unsigned long long)(p - j - 1));
+        }
       }
-      s2 = warp_sum(s2);
+      __syncwarp();
       if (l == 0) {
-        y[j] -= f;
-        sh.sigma[c] = s2;
+        y[j] = yj;
+        sh.sigma[c] = nu2;
       }
     }
-    fma_count += 3ull * (unsigned long long)(p - j) * (unsigned long long)(q - j - 1) + (p - j);
+    fma_count += 2ull * (unsigned long long)(p - j) * (unsigned long long)(q - j - 1) + (p - j);
+    exact = false;
     __syncthreads();
   }
-  if (jstats && threadIdx.x == 0)
-    atomicAdd(&jstats[4], 2ull * fma_count);   // (the QR's flops after the certificate test)
+  if (jstats && threadIdx.x == 0)   // (the QR's flops after the certificate test)
+    atomicAdd(&jstats[4], 2ull * (fma_count + sh.qr_recomputed));
   if (k < 0) {
     // no threshold within jmax steps: dense when sum_{i > q/2} sigma_i^2 > eps^2 is certified
     // by some leading triangle of the kc completed steps, else the full SVD decides
@@ -1250,8 +1295,22 @@ __global__ void __launch_bounds__(kThreads, 1) compress_dense_kernel(
   __shared__ int sh_next;
   double* sc = svd_scratch + (int64_t)blockIdx.x * kSvdScratchPerCta;
   const int n_items = list ? *count : C.nr * C.nc;
+  // each tile's SM kilocycles go to C.cost (the next plan's scheduling cost), written when the
+  // CTA takes its next tile (every path of the loop body ends there) and after the last one
+  int prev_t = -1;
+  long long prev_c = 0;
+  auto record_cost = [&](long long now) {
+    if (C.cost && prev_t >= 0 && threadIdx.x == 0) {
+      const long long kc = (now - prev_c) >> 10;
+      C.cost[prev_t] = (unsigned int)(kc < 1 ? 1 : kc > 0xFFFFFFFFll ? 0xFFFFFFFFll : kc);
+    }
+  };
   for (int it = next_item(sched, &sh_next); it < n_items; it = next_item(sched, &sh_next)) {
     const int t = list ? list[it] : (order ? order[it] : it);
+    const long long now = clock64();
+    record_cost(now);
+    prev_t = t;
+    prev_c = now;
     const int I = t / C.nc, J = t % C.nc;
     const int m = C.row_off[I + 1] - C.row_off[I];
     const int n = C.col_off[J + 1] - C.col_off[J];
@@ -1404,6 +1463,7 @@ __global__ void __launch_bounds__(kThreads, 1) compress_dense_kernel(
       if (r > q / 2) atomicAdd(&jstats[7], 1ull);   // full SVD, stored dense
     }
   }
+  record_cost(clock64());
 }
 
 void launch_compress_dense(const MatView& C, const int* list, const int* count,
