@@ -246,11 +246,13 @@ int clr_multiply_backward(clr_ctx_t ctx, clr_mat_t a, clr_mat_t b, clr_mat_t cba
  * B (k x n) and C (m x n) row-major in page-locked host memory (leading dimensions lda, ldb,
  * ldc >= the column counts), tiled by the cluster sizes rs (rows of A and C), ks (columns of A,
  * rows of B) and cs (columns of B and C).  A moves in two row chunks and B in n_chunks column
- * chunks (whole clusters each), uploaded on a copy stream in the order the products need them
- * (A_0, B_0, A_1, B_1, B_2, ...); the product of row chunk i and column chunk j starts as soon
- * as both are on the device, on one of two streams with their own workspaces (one per row
- * chunk, so that chunk's bf16 panels are staged once), and its tile of C goes back to the
- * host at once: the copy engines' transfers in both directions overlap the products.  Every
+ * chunks (whole clusters each), copied on one stream in the order the products need them
+ * (A_0, B_0, A_1, B_1, B_2, ...) through two alternating device staging buffers and laid out
+ * into matrices on another, so the copies run back to back; the product of row chunk i and
+ * column chunk j starts as soon as both are laid out, on one of two streams with their own
+ * workspaces (one per row chunk, so that chunk's bf16 panels are staged once), and its tile of
+ * C goes back to the host at once from two download streams that do not hold up the products:
+ * the copy engines' transfers in both directions overlap the products.  Every
  * block is kept dense (the eps = 0 build); the products use the context's precision.
  * Synchronises `stream` before returning.  CLR_EINVAL when a buffer is not page-locked or
  * holds non-finite values. */

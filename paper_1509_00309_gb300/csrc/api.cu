@@ -179,6 +179,8 @@ struct clr_ctx_s {
   // NS runs its two independent products of an iteration concurrently on a side stream
   cudaStream_t side = nullptr;
   cudaStream_t up = nullptr;  // host-to-device uploads of the streamed host product
+  cudaStream_t lay = nullptr;      // its layout of uploaded chunks into matrices
+  cudaStream_t dn[2] = {nullptr, nullptr};   // its layouts and copies of C tiles to the host
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   bool reuse_a = false;  // split products may reuse A's staged panels (see WorkSet::staged_a)
   std::vector<cudaEvent_t> event_pool;
@@ -595,6 +597,9 @@ extern "C" int clr_destroy(clr_ctx_t ctx) {
   for (auto& pe : ctx->prof_events) cudaEventDestroy(pe.e);
   if (ctx->side) cudaStreamDestroy(ctx->side);
   if (ctx->up) cudaStreamDestroy(ctx->up);
+  if (ctx->lay) cudaStreamDestroy(ctx->lay);
+  for (cudaStream_t d : ctx->dn)
+    if (d) cudaStreamDestroy(d);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   for (cudaEvent_t e : ctx->event_pool) cudaEventDestroy(e);
@@ -2219,52 +2224,76 @@ extern "C" int clr_multiply_host_stream(clr_ctx_t ctx, const double* a, int64_t 
     }
   if (st) return st;
   if ((st = fork_side(ctx, s))) return st;
-  if (!ctx->up && cudaStreamCreateWithFlags(&ctx->up, cudaStreamNonBlocking) != cudaSuccess)
-    return fail(ctx, CLR_ECUDA, "upload stream");
-  CLR_CUDA(cudaStreamWaitEvent(ctx->up, ctx->ev_fork, 0));
+  // streams: up (host-to-device copies), lay (their layout into the chunk matrices), the two
+  // compute streams (s and side), dn[0..1] (each C tile's layout and device-to-host copy), so
+  // that no copy waits for a kernel it does not depend on
+  for (cudaStream_t* ps : {&ctx->up, &ctx->lay, &ctx->dn[0], &ctx->dn[1]})
+    if (!*ps && cudaStreamCreateWithFlags(ps, cudaStreamNonBlocking) != cudaSuccess)
+      return fail(ctx, CLR_ECUDA, "stream creation");
+  for (cudaStream_t ps : {ctx->up, ctx->lay, ctx->dn[0], ctx->dn[1]})
+    CLR_CUDA(cudaStreamWaitEvent(ps, ctx->ev_fork, 0));
   for (int sl = 0; sl < 2; ++sl) {
     WorkSet* w = ctx->wsets[sl].get();
-    CLR_CUDA(w->host_c.ensure((size_t)c_max * sizeof(double)));
+    CLR_CUDA(w->host_c.ensure((size_t)c_max * sizeof(double)));   // download staging dn[sl]
+    CLR_CUDA(w->host_b.ensure((size_t)up_max * sizeof(double)));   // upload staging, alternating
     w->staged_a = nullptr;
   }
   WorkSet* w0 = ctx->wsets[0].get();
-  CLR_CUDA(w0->host_b.ensure((size_t)up_max * sizeof(double)));  // upload staging (stream up)
   CLR_CUDA(w0->host_err.ensure(sizeof(int)));
-  CLR_CUDA(cudaMemsetAsync(w0->host_err.p, 0, sizeof(int), ctx->up));
-  // one event per uploaded operand chunk (A row chunks, then B column chunks)
-  std::vector<cudaEvent_t> ev(nra + ncb, nullptr);
+  CLR_CUDA(cudaMemsetAsync(w0->host_err.p, 0, sizeof(int), ctx->lay));
+  // per uploaded operand chunk (A row chunks, then B column chunks): copied (on up) and laid
+  // out (on lay: the event the products wait for); per C tile: its product done
+  const int n_up = nra + ncb, n_tiles = nra * ncb;
+  std::vector<cudaEvent_t> ev(n_up, nullptr), ev_cp(n_up, nullptr), ev_pr(n_tiles, nullptr);
   struct EvGuard {
-    std::vector<cudaEvent_t>* v;
+    std::vector<cudaEvent_t>* v[3];
     ~EvGuard() {
-      for (cudaEvent_t e : *v)
-        if (e) cudaEventDestroy(e);
+      for (auto* vv : v)
+        for (cudaEvent_t e : *vv)
+          if (e) cudaEventDestroy(e);
     }
-  } eg{&ev};
-  for (auto& e : ev)
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
-      return fail(ctx, CLR_ECUDA, "events");
-  // uploads on stream up, in the order the products need them: A_0, B_0, A_1, B_1, B_2, ...
+  } eg{{&ev, &ev_cp, &ev_pr}};
+  for (auto* vv : {&ev, &ev_cp, &ev_pr})
+    for (auto& e : *vv)
+      if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+        return fail(ctx, CLR_ECUDA, "events");
+  // uploads in the order the products need them: A_0, B_0, A_1, B_1, B_2, ...; upload u goes
+  // through staging buffer u % 2, whose previous layout (upload u - 2) it waits for
+  int n_issued = 0;
+  std::vector<int> order_of;   // upload index of the n-th issued upload
   auto upload = [&](clr_mat_t M, const double* src, int64_t ld, int64_t rows, int64_t cols,
-                    cudaEvent_t done) -> int {
-    cudaError_t e = cudaMemcpy2DAsync(w0->host_b.p, cols * sizeof(double), src,
-                                      ld * sizeof(double), cols * sizeof(double), rows,
-                                      cudaMemcpyHostToDevice, ctx->up);
+                    int u) -> int {
+    WorkSet* wb = ctx->wsets[n_issued & 1].get();
+    cudaError_t e = cudaSuccess;
+    if (n_issued >= 2) e = cudaStreamWaitEvent(ctx->up, ev[order_of[n_issued - 2]], 0);
+    if (e == cudaSuccess)
+      e = cudaMemcpy2DAsync(wb->host_b.p, cols * sizeof(double), src, ld * sizeof(double),
+                            cols * sizeof(double), rows, cudaMemcpyHostToDevice, ctx->up);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_cp[u], ctx->up);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(ctx->lay, ev_cp[u], 0);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "stream upload");
-    launch_rowmajor_to_pool(M->view(), M->d_row_idx, (const double*)w0->host_b.p, cols, ctx->up);
-    launch_block_norms_dense(M->view(), ctx->up);
-    launch_dense_kinds(M->view(), 0.0, (int*)w0->host_err.p, ctx->up);
-    e = cudaEventRecord(done, ctx->up);
+    launch_rowmajor_to_pool(M->view(), M->d_row_idx, (const double*)wb->host_b.p, cols, ctx->lay);
+    launch_block_norms_dense(M->view(), ctx->lay);
+    launch_dense_kinds(M->view(), 0.0, (int*)w0->host_err.p, ctx->lay);
+    e = cudaEventRecord(ev[u], ctx->lay);
+    ++n_issued;
     return e == cudaSuccess ? CLR_OK : cuda_fail(ctx, e, "stream upload");
   };
   for (int q = 0; q < std::max(nra, ncb) && !st; ++q) {
-    if (q < nra) st = upload(am[q], a + row0[q] * lda, lda, row0[q + 1] - row0[q], k, ev[q]);
-    if (!st && q < ncb)
-      st = upload(bm[q], b + col0[q], ldb, k, col0[q + 1] - col0[q], ev[nra + q]);
+    if (q < nra) {
+      order_of.push_back(q);
+      st = upload(am[q], a + row0[q] * lda, lda, row0[q + 1] - row0[q], k, q);
+    }
+    if (!st && q < ncb) {
+      order_of.push_back(nra + q);
+      st = upload(bm[q], b + col0[q], ldb, k, col0[q + 1] - col0[q], nra + q);
+    }
   }
   WorkSet* saved = ctx->cur;
   ctx->reuse_a = true;  // each stream keeps its row chunk of A: its bf16 panels are staged once
   Tuning t;
   if (!st) t.prec = choose_precision(ctx, am[0], am[0]);
+  int n_done = 0;
   for (int j = 0; j < ncb && !st; ++j)
     for (int i = 0; i < nra && !st; ++i) {
       const int sl = nra > 1 ? (i & 1) : (j & 1);
@@ -2279,18 +2308,32 @@ extern "C" int clr_multiply_host_stream(clr_ctx_t ctx, const double* a, int64_t 
       }
       clr_mat_t Cq = cm[(size_t)i * ncb + j];
       if ((st = multiply_into(ctx, am[i], bm[j], Cq, 1.0, t, nullptr, ss))) break;
-      // C's tile back: layout to row-major, copy engine device -> host
+      // C's tile back on a download stream (alternating, each with its staging buffer): layout
+      // to row-major, copy engine device -> host, while the compute stream goes on
+      const int d = n_done & 1;
+      cudaStream_t sd = ctx->dn[d];
+      e = cudaEventRecord(ev_pr[n_done], ss);
+      if (e == cudaSuccess) e = cudaStreamWaitEvent(sd, ev_pr[n_done], 0);
+      if (e != cudaSuccess) {
+        st = cuda_fail(ctx, e, "stream order");
+        break;
+      }
+      ++n_done;
+      WorkSet* wd = ctx->wsets[d].get();
       const int64_t nk = col0[j + 1] - col0[j];
-      launch_pool_to_rowmajor(Cq->view(), Cq->d_row_idx, Cq->d_col_idx, (double*)w->host_c.p,
-                              nk, ss);
-      e = cudaMemcpy2DAsync(c + row0[i] * ldc + col0[j], ldc * sizeof(double), w->host_c.p,
+      launch_pool_to_rowmajor(Cq->view(), Cq->d_row_idx, Cq->d_col_idx, (double*)wd->host_c.p,
+                              nk, sd);
+      e = cudaMemcpy2DAsync(c + row0[i] * ldc + col0[j], ldc * sizeof(double), wd->host_c.p,
                             nk * sizeof(double), nk * sizeof(double), row0[i + 1] - row0[i],
-                            cudaMemcpyDeviceToHost, ss);
+                            cudaMemcpyDeviceToHost, sd);
       if (e != cudaSuccess) st = cuda_fail(ctx, e, "stream download");
     }
-  // join the upload and side streams back into s
-  cudaError_t ej = cudaEventRecord(ctx->ev_join, ctx->up);
-  if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s, ctx->ev_join, 0);
+  // join the helper streams and the side stream back into s
+  cudaError_t ej = cudaSuccess;
+  for (cudaStream_t ps : {ctx->up, ctx->lay, ctx->dn[0], ctx->dn[1]}) {
+    if (ej == cudaSuccess) ej = cudaEventRecord(ctx->ev_join, ps);
+    if (ej == cudaSuccess) ej = cudaStreamWaitEvent(s, ctx->ev_join, 0);
+  }
   const int sj = join_side(ctx, s);
   ctx->reuse_a = false;
   for (int sl = 0; sl < 2; ++sl) ctx->wsets[sl]->staged_a = nullptr;
