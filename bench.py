@@ -410,7 +410,9 @@ def run_ours(args):
     fp64 = ozaki = None
     if not args.no_fp64 and args.prec != "fp64":
         fp64 = fp64_product(ctx, ga, gb, gc, w, alg_flops, fp64_peak, value, acc, rank)
-        ozaki = ozaki_product(ctx, ga, gb, gc, w, alg_flops, fp64["tflops"], rank)
+    if args.prec != "fp64":
+        ozaki = ozaki_product(ctx, ga, gb, gc, w, alg_flops, fp64["tflops"] if fp64 else None,
+                              rank)
 
     # the 1D-chain product (N = 2048, eps = 1e-8): FP64 against the split forms
     chain = None
@@ -693,6 +695,12 @@ def lattice_ns(clr, w, shape_txt, what, fp64_peak, precision, snapshot=True):
                        (round(c / 1e6, 1) for c in prof["svd_full_cycles"])),
                    blocks_all_stages=prof["svd_full_blocks"],
                    blocks_stored_dense=prof["svd_full_dense"]),
+               "pre_reduced_stages_mcycles": dict(
+                   zip(("pivoted_qr", "fp32_sweeps_on_rt", "fp64_orthonormalise_project",
+                        "fp32_sweeps_on_g", "fp64_orthonormalise_multiply", "fp64_sweeps",
+                        "truncate_recover_store"),
+                       (round(c / 1e6, 1) for c in prof["svd_pre_cycles"])),
+                   blocks=prof["svd_pre_blocks"]),
                "roofline_recompress": recompress_roofline(prof, fp64_peak)}}
     if snapshot:
         out["rank_distribution_iter5"] = {

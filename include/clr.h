@@ -373,6 +373,10 @@ typedef struct clr_profile {
                                   after the first FP32 stage) */
   int64_t svd_full_dense;      /* of those, blocks whose truncation rank exceeded half the
                                   smaller side (stored dense) */
+  double svd_pre_cycles[7];    /* the same for the blocks stored low rank after the pivoted-QR
+                                  pre-reduction: the QR, the five stages of the mixed SVD of
+                                  R^T, truncation, recovery and stores */
+  int64_t svd_pre_blocks;
 } clr_profile;
 int clr_profile_enable(clr_ctx_t ctx, int on);
 int clr_profile_read(clr_ctx_t ctx, clr_profile* out);

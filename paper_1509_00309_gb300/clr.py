@@ -70,7 +70,8 @@ class ClrProfile(C.Structure):
                 ("svd_flops_fp64_qr", C.c_double), ("svd_flops_fp32_qr", C.c_double),
                 ("svd_path_cycles", C.c_double * 3), ("svd_path_blocks", C.c_int64 * 3),
                 ("svd_full_cycles", C.c_double * 7), ("svd_full_blocks", C.c_int64),
-                ("svd_full_dense", C.c_int64)]
+                ("svd_full_dense", C.c_int64), ("svd_pre_cycles", C.c_double * 7),
+                ("svd_pre_blocks", C.c_int64)]
 
 
 _VP = C.c_void_p
@@ -316,7 +317,7 @@ class Context:
         p = ClrProfile()
         self._check(load().clr_profile_read(self.handle, C.byref(p)))
         out = {f: getattr(p, f) for f, _ in ClrProfile._fields_}
-        for f in ("svd_path_cycles", "svd_path_blocks", "svd_full_cycles"):
+        for f in ("svd_path_cycles", "svd_path_blocks", "svd_full_cycles", "svd_pre_cycles"):
             out[f] = list(out[f])
         return out
 

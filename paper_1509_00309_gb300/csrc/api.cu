@@ -467,8 +467,8 @@ const double* host_device_ptr(const void* p) {
 // (compress_qr_kernel), [16, 24) SM cycles and counts of compress_dense_kernel's paths.
 constexpr int kJstatsBlock = 8;
 // counter blocks: 0 compress_dense_kernel, 1 compress_qr_kernel, 2 per-path cycles of
-// compress_dense_kernel, 3 its full-SVD stages
-constexpr int kJstatsBlocks = 4;
+// compress_dense_kernel, 3 its full-SVD stages, 4 its pre-reduced path's stages
+constexpr int kJstatsBlocks = 5;
 unsigned long long* jst(clr_ctx_t ctx, int block = 0) {
   return (ctx->prof_on && !ctx->capturing && ctx->jstats.p)
              ? (unsigned long long*)ctx->jstats.p + block * kJstatsBlock : nullptr;
@@ -1082,7 +1082,9 @@ int run_ozaki_gemm(clr_ctx_t ctx, clr_mat_t a, clr_mat_t c, const Plan& p, cudaS
   const int64_t K_pad = (a->n_cols + 127) / 128 * 128;
   const int n_seg = (int)((K_pad + kOzakiSegK - 1) / kOzakiSegK);
   WorkSet* w = ctx->cur;
-  CLR_CUDA(w->tile_flags.ensure((size_t)(M_pad / 128) * (N_pad / kOzakiTileN)));
+  const size_t n_gemm_tiles = (size_t)(M_pad / 128) * (N_pad / kOzakiTileN);
+  const size_t flag_bytes = (n_gemm_tiles + 15) / 16 * 16;
+  CLR_CUDA(w->tile_flags.ensure(flag_bytes + (n_gemm_tiles + 1) * sizeof(int)));
   MatView cv = c->view();
   int* ea = (int*)w->oz_exps.p;
   OzakiGemmArgs g;
@@ -1098,6 +1100,7 @@ int run_ozaki_gemm(clr_ctx_t ctx, clr_mat_t a, clr_mat_t c, const Plan& p, cudaS
   g.row_tile_of = c->d_row_idx;
   g.col_tile_of = c->d_col_idx;
   g.tile_active = (unsigned char*)w->tile_flags.p;
+  g.active_list = (int*)((char*)w->tile_flags.p + flag_bytes);
   g.n_sm = ctx->n_sm;
   g.err = &p.counters->err;
   g.wait_ns = ctx->opts.wait_timeout_us > 0
@@ -1107,7 +1110,8 @@ int run_ozaki_gemm(clr_ctx_t ctx, clr_mat_t a, clr_mat_t c, const Plan& p, cudaS
   const int st = ozaki_gemm_dd(g, s, &why);
   if (st) return fail(ctx, st, "exact-slice GEMM: " + why);
   CLR_CHECK_LAUNCH("exact-slice GEMM");
-  prof_launches(ctx, 2);   // tile flags + GEMM
+  // tile flags, their compaction, one GEMM launch per K pass
+  prof_launches(ctx, 2 + (int)((K_pad + kOzakiPassK - 1) / kOzakiPassK));
   if (ctx->prof_on) ctx->prof.dense_launches++;
   prof_mark(ctx, s, PH_DENSE);
   return CLR_OK;
@@ -1283,6 +1287,9 @@ extern "C" int clr_profile_read(clr_ctx_t ctx, clr_profile* out) {
     for (int st = 0; st < 7; ++st) ctx->prof.svd_full_cycles[st] = (double)fc[st];
     ctx->prof.svd_full_blocks = (int64_t)fc[7];
     ctx->prof.svd_full_dense = (int64_t)j[7];
+    const unsigned long long* rc = j + 4 * kJstatsBlock;  // pre-reduced path stages
+    for (int st = 0; st < 7; ++st) ctx->prof.svd_pre_cycles[st] = (double)rc[st];
+    ctx->prof.svd_pre_blocks = (int64_t)rc[7];
   }
   *out = ctx->prof;
   return CLR_OK;

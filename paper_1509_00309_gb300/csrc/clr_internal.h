@@ -255,6 +255,7 @@ int split_gemm_dd(const SplitGemmArgs& a, cudaStream_t st, std::string* why);
 constexpr int kOzakiSlices = 8;
 constexpr int kOzakiSegK = 1024;   // K segment: exact FP32 group sums, exponents per segment
 constexpr int kOzakiTileN = 32;    // the GEMM's output tiles are 128 x kOzakiTileN
+constexpr int kOzakiPassK = 2048;  // K per GEMM launch (later launches add into C)
 struct OzakiGemmArgs {
   const MatView* C;
   const Plan* p;
@@ -266,6 +267,7 @@ struct OzakiGemmArgs {
   const int* row_tile_of;
   const int* col_tile_of;
   unsigned char* tile_active;  // (M_pad/128) * (N_pad/kOzakiTileN) flags
+  int* active_list;            // 1 + that many ints: the active tiles' count and ids
   int n_sm;
   int* err;
   unsigned long long wait_ns = 2000000000ull;

@@ -71,6 +71,8 @@ constexpr int NBUF = 2;                 // two sets: a segment's MMAs overlap th
 constexpr int EPC = BN / 2;             // output columns per epilogue thread
 constexpr int SEG_CHUNKS = 32;       // K segment of 1024: exact FP32 group sums
 constexpr int SEG_K = SEG_CHUNKS * BK;
+constexpr int kPassSegments = kOzakiPassK / SEG_K;   // K segments per launch (ozaki_gemm_dd)
+static_assert(kOzakiPassK % SEG_K == 0, "a launch covers whole K segments");
 // the staging kernels' k tiles (256, 128 and 4 x 256 wide) never straddle a segment
 static_assert(SEG_K == 1024 && SEG_K == kOzakiSegK, "staging tiles assume K segments of 1024");
 constexpr int TMEM_COLS = 512;
@@ -217,8 +219,9 @@ __device__ __forceinline__ double pow2(int x) {
 __global__ void __launch_bounds__(THREADS, 1)
     ozaki_gemm_kernel(const __grid_constant__ CUtensorMap tmA,
                       const __grid_constant__ CUtensorMap tmB, Epi epi, int n_m, int n_n,
-                      int num_k, int M_pad, int N_pad, const unsigned char* tile_active,
-                      int* err, unsigned long long wait_ns) {
+                      int k_begin, int k_end, int accumulate, int M_pad, int N_pad,
+                      const int* active, int* err,
+                      unsigned long long wait_ns) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   uint64_t* full = (uint64_t*)(smem + SMEM_DATA);
@@ -230,7 +233,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   volatile int* abort_flag = (volatile int*)(tmem_holder + 1);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
-  const int n_tiles = n_m * n_n;
+  // the active tiles in raster order (oz_compact_kernel): active[0] of them at active[1..]
+  const int n_act = active[0];
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -269,11 +273,11 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool issued[STAGES];
       for (int i = 0; i < STAGES; ++i) issued[i] = false;
       bool ok = true;
-      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
-        if (!tile_active[tile]) continue;
+      for (int it = blockIdx.x; ok && it < n_act; it += gridDim.x) {
+        const int tile = active[1 + it];
         int mb, nb;
         tile_coords(tile, n_m, n_n, &mb, &nb);
-        for (int kc = 0; kc < num_k; ++kc) {
+        for (int kc = k_begin; kc < k_end; ++kc) {
           if (!mbar_wait(&empty[s], phase ^ 1, abort_flag, wait_ns)) { ok = false; break; }
           unsigned char* st = smem + (size_t)s * STAGE;
           mbar_expect_tx(&full[s], STAGE);
@@ -307,10 +311,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       int seg_count = 0;  // segments issued by this CTA
       bool ok = true;
       bool any = false;
-      for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
-        if (!tile_active[tile]) continue;
-        for (int k0 = 0; ok && k0 < num_k; k0 += SEG_CHUNKS) {
-          const int k1 = min(num_k, k0 + SEG_CHUNKS);
+      for (int it = blockIdx.x; ok && it < n_act; it += gridDim.x) {
+        for (int k0 = k_begin; ok && k0 < k_end; k0 += SEG_CHUNKS) {
+          const int k1 = min(k_end, k0 + SEG_CHUNKS);
           // the epilogue has read the group sums of the segment before last from this set
           const int bset = seg_count & 1;
           const uint32_t tp = (seg_count >> 1) & 1;
@@ -367,8 +370,8 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int rl = quarter * 32 + lane;    // row within the tile
     int seg_count = 0;
     bool ok = true;
-    for (int tile = blockIdx.x; ok && tile < n_tiles; tile += gridDim.x) {
-      if (!tile_active[tile]) continue;
+    for (int it = blockIdx.x; ok && it < n_act; it += gridDim.x) {
+      const int tile = active[1 + it];
       int mb, nb;
       tile_coords(tile, n_m, n_n, &mb, &nb);
       double acc[EPC];
@@ -376,7 +379,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (int j = 0; j < EPC; ++j) acc[j] = 0.0;
       const int64_t row = (int64_t)mb * BM + rl;
       const int64_t col0 = (int64_t)nb * BN + half * EPC;
-      for (int k0 = 0; k0 < num_k; k0 += SEG_CHUNKS) {
+      for (int k0 = k_begin; k0 < k_end; k0 += SEG_CHUNKS) {
         // this segment's scale of every entry: 2^(e_i + f_j - 10) with the exponents of its
         // own K range (row i of A, column j of B over the segment's columns / rows)
         const int sg = k0 / SEG_CHUNKS;
@@ -420,7 +423,10 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (col < epi.n_cols) {
             const int J = epi.col_tile_of[col];
             const int route = route_row[J];
-            if (route == ROUTE_DENSE || route == ROUTE_DACC_G) epi.pool[rowbase + col * mI] = acc[j];
+            if (route == ROUTE_DENSE || route == ROUTE_DACC_G) {
+              double* o = epi.pool + rowbase + col * mI;
+              *o = accumulate ? *o + acc[j] : acc[j];
+            }
           }
         }
       }
@@ -460,6 +466,45 @@ __global__ void oz_tile_active_kernel(const int* row_tile_of, const int* col_til
         }
   }
   active[t] = on;
+}
+
+// The active tiles' ids in raster order: out[0] = their number, out[1..] = the ids (one CTA
+// of 1024 threads, a ballot and warp scan per chunk of 1024 flags).  The persistent GEMM CTAs
+// then stride over active tiles only, so each gets the same number of tiles whatever the
+// pattern of inactive ones.
+__global__ void __launch_bounds__(1024) oz_compact_kernel(const unsigned char* flags, int n,
+                                                          int* out) {
+  __shared__ int ws[32];
+  __shared__ int chunk_total;
+  __shared__ int base;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) base = 0;
+  __syncthreads();
+  for (int c0 = 0; c0 < n; c0 += 1024) {
+    const int i = c0 + threadIdx.x;
+    const int f = i < n ? flags[i] : 0;
+    const unsigned m = __ballot_sync(0xffffffffu, f != 0);
+    const int pre = __popc(m & ((1u << lane) - 1u));
+    if (lane == 0) ws[wid] = __popc(m);
+    __syncthreads();
+    if (wid == 0) {
+      const int v = ws[lane];
+      int incl = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      ws[lane] = incl - v;
+      if (lane == 31) chunk_total = incl;
+    }
+    __syncthreads();
+    if (f) out[1 + base + ws[wid] + pre] = i;
+    __syncthreads();
+    if (threadIdx.x == 0) base += chunk_total;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = base;
 }
 
 // ---------------------------------------------------------------------------------------------
@@ -837,6 +882,7 @@ int ozaki_gemm_dd(const OzakiGemmArgs& a, cudaStream_t st, std::string* why) {
   oz_tile_active_kernel<<<(n_m * n_n + 127) / 128, 128, 0, st>>>(
       a.row_tile_of, a.col_tile_of, C.nc, a.p->t_route, n_m, n_n, C.n_rows, C.n_cols,
       a.tile_active);
+  oz_compact_kernel<<<1, 1024, 0, st>>>(a.tile_active, n_m * n_n, a.active_list);
   Epi epi;
   epi.pool = C.pool;
   epi.row_off = C.row_off;
@@ -863,9 +909,17 @@ int ozaki_gemm_dd(const OzakiGemmArgs& a, cudaStream_t st, std::string* why) {
     if (dev >= 0 && dev < 64) attr_done[dev] = true;
   }
   const int grid = std::max(1, std::min(a.n_sm, n_m * n_n));
-  ozaki_gemm_kernel<<<grid, THREADS, SMEM_TOTAL, st>>>(
-      tmA, tmB, epi, n_m, n_n, num_k, (int)a.M_pad, (int)a.N_pad, a.tile_active, a.err,
-      a.wait_ns > 0 ? a.wait_ns : kDrainNs);
+  // K in passes of kPassSegments segments, the later passes adding into C: the CTAs of a wave
+  // share their operand slabs through L2 only while they are at about the same k, and over a
+  // long K they drift apart (at N = 32768 in one pass the kernel streamed every slab from
+  // DRAM); a pass's slabs for one wave, (8 x 128 + 19 x 32) rows x 2048 x 16 B = 53 MB, stay
+  // in L2.  Each later pass reads and writes C once more (16 N^2 bytes).
+  const int pass = kPassSegments * SEG_CHUNKS;
+  for (int k0 = 0; k0 < num_k; k0 += pass) {
+    ozaki_gemm_kernel<<<grid, THREADS, SMEM_TOTAL, st>>>(
+        tmA, tmB, epi, n_m, n_n, k0, std::min(num_k, k0 + pass), k0 > 0 ? 1 : 0,
+        (int)a.M_pad, (int)a.N_pad, a.active_list, a.err, a.wait_ns > 0 ? a.wait_ns : kDrainNs);
+  }
   return CLR_OK;
 }
 

@@ -62,7 +62,8 @@ def ns_rank_distribution(ctx: "clr.Context", s: "clr.Matrix", k: int = 5) -> Dic
                                                   "svd_flops_fp64_qr", "svd_flops_fp32_qr",
                                                   "svd_path_cycles", "svd_path_blocks",
                                                   "svd_full_cycles", "svd_full_blocks",
-                                                  "svd_full_dense")}
+                                                  "svd_full_dense", "svd_pre_cycles",
+                                                  "svd_pre_blocks")}
     ctx.set_opts(ns_snapshot_iter=0)
     return out
 
