@@ -29,8 +29,11 @@ constexpr int kPathCounters = 16;
 // compress_dense_kernel's full-SVD stages while profiling (block 3 of the counters): cycles of
 // the pivoted QR attempt, the five stages of svd_mixed, truncation and stores; then the count
 constexpr int kFullStageCounters = 24;
+// the same for the pre-reduced path (block 4): the QR, the five stages of svd_mixed on R^T,
+// truncation, recovery and the factors' stores; then the count
+constexpr int kPreStageCounters = 32;
 constexpr int kWarps = kThreads / 32;
-constexpr int kFp64SweepCap = 1;  // FP64 sweeps of svd_mixed when the right factor is recovered
+constexpr int kFp64SweepCap = 0;  // FP64 sweeps of svd_mixed when the right factor is recovered
 
 template <typename T>
 __device__ __forceinline__ T warp_sum(T v) {
@@ -689,16 +692,18 @@ __device__ __noinline__ int svd_mixed(const SrcView& a, int p, int q, double* g,
   }
   if (threadIdx.x == 0) sh.v_tracked = track_v ? 1 : 0;
   mark(4);
-  // Without V accumulation the FP64 sweeps stop after kFp64SweepCap: one sweep takes the pairs'
-  // cosines from the FP32 stages' ~1e-5 to ~1e-10 (quadratic step), which fixes the column
-  // norms (the truncation) to ~1e-20 relative; a block whose spectrum has a tight cluster would
-  // converge only linearly (measured up to 17 sweeps on 256 x 256 blocks), and the truncation
-  // does not need it -- with the least-squares right factor (ls_solve) X W^T is the orthogonal
-  // projection of A onto span(G_r) for any G = A V_eff, so the error stays
-  // ||(I - P) G_tail|| <= ||G_tail||_F <= eps, converged or not.
+  // Without V accumulation no FP64 sweep runs (kFp64SweepCap): after stage 3 the columns of G
+  // are orthogonal to the FP32 stages' tolerance (cosines ~1e-5 relative to their own norms),
+  // so the sorted column norms, whose tail decides the rank, are within ~1e-10 of the
+  // singular values; and with the least-squares right factor (ls_solve) X W^T is the
+  // orthogonal projection of A onto span(G_r) for any G = A V_eff with V_eff orthogonal, so the
+  // error is ||(I - P) G_tail|| <= ||G_tail||_F <= eps whether or not the kept columns are
+  // mutually orthogonal.  (One FP64 sweep, the earlier choice, took the cosines to ~1e-10 at
+  // 4 p q^2 FP64 flops; a tight cluster of singular values made it converge only linearly.)
   const int cap64 = track_v || max_sweeps < kFp64SweepCap ? max_sweeps : kFp64SweepCap;
-  const int sw64 = jacobi_svd<double>(g, p, q, p, track_v ? v : nullptr, q, cap64, &sh.flag,
-                                      false, 1.0, floor64 * floor64);
+  const int sw64 = cap64 > 0 ? jacobi_svd<double>(g, p, q, p, track_v ? v : nullptr, q, cap64,
+                                                  &sh.flag, false, 1.0, floor64 * floor64)
+                             : 0;
   if (threadIdx.x == 0) sh.ls_recover = (!track_v && sw64 >= cap64) ? 1 : 0;
   mark(5);
   if (jstats && threadIdx.x == 0) {
@@ -1017,6 +1022,7 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
                                                    double* norm_out, SvdShared& sh,
                                                    unsigned long long* jstats) {
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
+  const long long c_entry = clock64();
   // Once the QR has met the threshold the source is no longer needed: R (k x q) goes to the
   // slot and the SVD factors of R^T (q x k and k x k, at most 0.96 q^2 <= p q doubles for
   // k <= 3q/5) to wv.  Ranks up to q/2 are stored low rank.
@@ -1214,7 +1220,11 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
   const double rfro = sqrt(block_sum(part, sh.red));
   const double budget = sqrt(fmax(eps * eps - trail2, 0.0));
   const SrcView mv{rb, k, 1, false};   // M(i, j) = R(j, i)
-  svd_mixed(mv, q, k, gs, vs, sc, max_sweeps, budget, -1, rfro, sh, jstats);
+  unsigned long long* stage_clk = jstats ? jstats + kPreStageCounters : nullptr;
+  if (stage_clk && threadIdx.x == 0)
+    atomicAdd(&stage_clk[0], (unsigned long long)(clock64() - c_entry));
+  svd_mixed(mv, q, k, gs, vs, sc, max_sweeps, budget, -1, rfro, sh, jstats, stage_clk);
+  const long long c_after = clock64();
   sort_and_truncate(gs, q, k, q, budget, sh);
   const int r = sh.rank;
   if (r == 0) {
@@ -1276,6 +1286,8 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
     if (jstats) {
       atomicAdd(&jstats[4], 4ull * (unsigned long long)p * k * r);
       atomicAdd(&jstats[6], 1ull);
+      atomicAdd(&stage_clk[6], (unsigned long long)(clock64() - c_after));
+      atomicAdd(&stage_clk[7], 1ull);
     }
   }
   __syncthreads();
