@@ -686,8 +686,9 @@ def lattice_ns(clr, w, shape_txt, what, fp64_peak, precision, snapshot=True):
                    name: {"blocks": prof["svd_path_blocks"][i],
                           "mcycles_per_block": prof["svd_path_cycles"][i] / 1e6 /
                           max(1, prof["svd_path_blocks"][i])}
-                   for i, name in enumerate(("pivoted_qr_low_rank", "dense_without_svd",
-                                             "full_svd"))},
+                   for i, name in enumerate(("pivoted_qr_svd_of_r_low_rank",
+                                             "certified_dense_without_svd", "full_svd",
+                                             "pivoted_qr_svd_of_r_dense"))},
                "full_svd_stages_mcycles": dict(
                    zip(("pivoted_qr_attempt", "fp32_sweeps_on_a", "fp64_orthonormalise_project",
                         "fp32_sweeps_on_g", "fp64_orthonormalise_multiply", "fp64_sweeps",

@@ -361,9 +361,12 @@ typedef struct clr_profile {
   double ms_compress_dense;    /* dense truncated SVDs (compress_dense_kernel) */
   double svd_flops_fp64_qr;    /* the part of svd_flops_fp64 done by the QR route */
   double svd_flops_fp32_qr;    /* the part of svd_flops_fp32 done by the QR route */
-  double svd_path_cycles[3];   /* SM cycles in compress_dense_kernel per block, by path: pivoted
-                                  QR with the small SVD, dense without a full SVD, full SVD */
-  int64_t svd_path_blocks[3];  /* blocks by path */
+  double svd_path_cycles[4];   /* SM cycles in compress_dense_kernel summed over blocks, by
+                                  path: pivoted QR and the SVD of its factor R stored low rank;
+                                  certified dense by the QR's triangles (no SVD); the full SVD
+                                  of the block (pre-reduction off); pivoted QR and the SVD of R
+                                  stored dense */
+  int64_t svd_path_blocks[4];  /* blocks by path */
   double svd_full_cycles[7];   /* SM cycles summed over the full-SVD blocks of
                                   compress_dense_kernel, by stage: the pivoted QR attempt, FP32
                                   sweeps on A, FP64 orthonormalisation and A V, FP32 sweeps on G,
@@ -373,9 +376,10 @@ typedef struct clr_profile {
                                   after the first FP32 stage) */
   int64_t svd_full_dense;      /* of those, blocks whose truncation rank exceeded half the
                                   smaller side (stored dense) */
-  double svd_pre_cycles[7];    /* the same for the blocks stored low rank after the pivoted-QR
-                                  pre-reduction: the QR, the five stages of the mixed SVD of
-                                  R^T, truncation, recovery and stores */
+  double svd_pre_cycles[7];    /* the same for the blocks that took the SVD of R after the
+                                  pivoted-QR pre-reduction (stored low rank or dense): the QR,
+                                  the five stages of the mixed SVD of R^T, truncation, recovery
+                                  and stores */
   int64_t svd_pre_blocks;
 } clr_profile;
 int clr_profile_enable(clr_ctx_t ctx, int on);

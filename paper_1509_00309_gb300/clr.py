@@ -68,7 +68,7 @@ class ClrProfile(C.Structure):
                 ("svd_flops_fp32", C.c_double), ("svd_prereduced", C.c_int64),
                 ("ms_compress_qr", C.c_double), ("ms_compress_dense", C.c_double),
                 ("svd_flops_fp64_qr", C.c_double), ("svd_flops_fp32_qr", C.c_double),
-                ("svd_path_cycles", C.c_double * 3), ("svd_path_blocks", C.c_int64 * 3),
+                ("svd_path_cycles", C.c_double * 4), ("svd_path_blocks", C.c_int64 * 4),
                 ("svd_full_cycles", C.c_double * 7), ("svd_full_blocks", C.c_int64),
                 ("svd_full_dense", C.c_int64), ("svd_pre_cycles", C.c_double * 7),
                 ("svd_pre_blocks", C.c_int64)]

@@ -1279,7 +1279,7 @@ extern "C" int clr_profile_read(clr_ctx_t ctx, clr_profile* out) {
     ctx->prof.svd_flops_fp64_qr = (double)q[4];
     ctx->prof.svd_flops_fp32_qr = (double)q[5];
     const unsigned long long* pc = j + 2 * kJstatsBlock;   // per-path SM cycles and counts
-    for (int path = 0; path < 3; ++path) {
+    for (int path = 0; path < 4; ++path) {
       ctx->prof.svd_path_cycles[path] = (double)pc[2 * path];
       ctx->prof.svd_path_blocks[path] = (int64_t)pc[2 * path + 1];
     }

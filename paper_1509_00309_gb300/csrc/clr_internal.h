@@ -196,8 +196,8 @@ void launch_lr_products(const MatView& A, const MatView& B, const MatView& C, co
 // k_svd.cu
 // jstats (may be null): device counters {svd blocks, FP32 sweeps, FP64 sweeps, early dense}
 // svd_scratch: grid x kSvdScratchPerCta doubles (FP32 working copies and an FP64 q x q factor
-// of the mixed-precision SVD).
-constexpr int64_t kSvdScratchPerCta = (int64_t)2 * CLR_MAX_CLUSTER * CLR_MAX_CLUSTER;
+// of the mixed-precision SVD, then the right factor of the pivoted-QR path's SVD of R^T).
+constexpr int64_t kSvdScratchPerCta = (int64_t)3 * CLR_MAX_CLUSTER * CLR_MAX_CLUSTER;
 // sched: a zeroed work counter (dynamic tile distribution).
 void launch_compress_qr(const MatView& C, const int* list, const int* count, const int* rsum,
                         double* ws, double* svd_scratch, double eps, int max_sweeps, int grid,
@@ -209,8 +209,9 @@ void launch_compress_qr(const MatView& C, const int* list, const int* count, con
 // SVD (eps = 0 rule) and store every non-dropped block dense.
 // order (list == nullptr only, may be null): the order in which all blocks are visited.
 // rrqr: truncate by rank-revealing QR instead of the SVD.
-// prereduce: reduce blocks of low numerical rank by a column-pivoted QR (stopped at eps/16)
-// before the SVD of the small factor; blocks whose QR passes floor(q/2) steps take the full SVD.
+// prereduce: reduce every block by a column-pivoted QR (stopped at eps/16) before the SVD of
+// its k x q factor R, unless the QR's triangles certify it dense; without it every block takes
+// the full SVD.
 // jstats (7 counters): SVD blocks, FP32 sweeps, FP64 sweeps, early dense exits, FP64 flops,
 // FP32 flops, pre-reduced blocks.
 void launch_compress_dense(const MatView& C, const int* list, const int* count,

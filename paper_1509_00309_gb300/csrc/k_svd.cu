@@ -955,20 +955,25 @@ __device__ int rrqr_block(const double* S, int64_t s_r, int64_t s_c, int m, int 
 // triangle: R_11 is a submatrix of Q^T A P, so sigma_J(A) >= sigma_min(R_11), and the eps-rank
 // exceeds q/2 as soon as sigma_{q/2+1}(A) > eps.  sigma_min(R_11) is bounded below by
 // 1 / ||R_11^-1||_F (a triangular inverse, J^3/6 FMAs).
-// A block that meets neither goes on; when its QR rank at eps/16 is at most 3q/5 the SVD of its
-// R decides: rank <= q/2 is stored low rank, otherwise the block is stored dense as
-// Q_k [R; 0] P^T (within eps/16 of the block).  Past 3q/5 steps the QR runs on over all q
-// columns and the block is certified dense when a leading triangle R_K' bounds the tail
+// A block that meets neither goes on to its QR rank k at eps/16 (at most q).  Past 3q/5 steps
+// it is first certified dense when a leading triangle R_K' bounds the tail
 // sum_{i > q/2} sigma_i(A)^2 above eps^2: sigma_min alone certifies only blocks whose
 // (q/2 + 1)-th singular value exceeds eps, while the tail of a block with many singular
-// values just below eps also exceeds it (tail_lower_bound_sq).
+// values just below eps also exceeds it (tail_lower_bound_sq).  Otherwise the SVD of its R
+// decides, at any k: rank <= q/2 is stored low rank, else the block is stored dense as
+// Q_k [R; 0] P^T (within eps/16 of the block).  One-sided Jacobi on R^T after a pivoted QR
+// converges in fewer sweeps than on A itself (R is graded by the pivoting: the
+// preconditioning of Drmac and Veselic, "New fast and accurate Jacobi SVD algorithm", SIAM
+// J. Matrix Anal. Appl. 29, 2008), so even k near q costs less than the full SVD of A.
 // Returns 1 when the block is done (low rank or zero, written to slot and the outputs), 2 when
-// it is stored dense (certified with the source untouched, or reconstructed into the slot: the
-// caller stores the kind and copies an external source over it), 0 when the QR passed 3q/5
-// steps without meeting the threshold and without the certificate; the caller then takes the
-// full SVD on the untouched source.
+// it is certified dense with the source untouched, 3 when the SVD of R found it dense and it
+// was reconstructed into the slot (for 2 and 3 the caller stores the kind and copies an
+// external source over the slot), 0 only when a trailing norm is not finite; the caller then
+// takes the full SVD on the untouched source.
 // g: p x q copy (ld p); wv: the tile's second workspace half (p q doubles); slot: the block's
-// m n output slot (also the source of product tiles, read only before R is written there).
+// m n output slot (also the source of product tiles, read only before R is written there);
+// sc: the CTA's SVD scratch (kSvdScratchPerCta doubles: svd_mixed's working copies in the
+// first two CLR_MAX_CLUSTER^2, the k x k right factor of R^T in the third).
 // ---------------------------------------------------------------------------------------------
 // A lower bound on sum_{i > h} sigma_i(A)^2 from the leading K x K upper triangle R_K of the
 // pivoted QR in g (ld p).  For every K' in (h, K], R_K' is the upper part of the first K'
@@ -1024,17 +1029,15 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
   const long long c_entry = clock64();
   // Once the QR has met the threshold the source is no longer needed: R (k x q) goes to the
-  // slot and the SVD factors of R^T (q x k and k x k, at most 0.96 q^2 <= p q doubles for
-  // k <= 3q/5) to wv.  Ranks up to q/2 are stored low rank.
+  // slot, the left SVD factor of R^T (q x k <= p q doubles) to wv and the right one (k x k)
+  // to the third part of sc.  Ranks up to q/2 are stored low rank.
   const int kmax = q / 2;
-  // steps after which a block still above the threshold is tested for the dense certificate,
-  // and the most steps taken (the SVD of R must fit wv)
+  // steps after which a block still above the threshold is tested for the sigma_min
+  // certificate, and the QR rank above which the tail certificate is tried before the SVD
+  // (the steps past jtail cost a few percent of the first ones: their trailing blocks are
+  // small)
   const int jcert = q / 2 + 1 <= q ? q / 2 + 1 : q;
-  const int jmax = (3 * q) / 5 > jcert ? (3 * q) / 5 : jcert;
-  // a block still above the threshold after jmax steps: the QR goes on to all q columns for
-  // the dense certificate over every leading triangle (tail_lower_bound_sq); the steps after
-  // jmax cost a few percent of the first ones (their trailing blocks are small)
-  const int jext = q;
+  const int jtail = (3 * q) / 5 > jcert ? (3 * q) / 5 : jcert;
   const double tau2 = (eps / 16.0) * (eps / 16.0);
   // copy with the column norms
   for (int c = w; c < q; c += kWarps) {
@@ -1057,8 +1060,7 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
   unsigned long long fma_count = 0;
   bool exact = true;   // the trailing norms were all summed exactly at this step
   int k = -1;
-  int kc = 0;   // steps completed when the threshold was not met within jmax
-  for (int j = 0; j <= jext; ++j) {
+  for (int j = 0; j <= q; ++j) {
     // trailing norm and pivot (warp 0)
     if (w == 0) {
       double tot = 0.0, best = -1.0;
@@ -1101,8 +1103,7 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
       continue;
     }
     if (sh.kept_sq <= tau2) {
-      if (j <= jmax) k = j;
-      else kc = j;   // met only past jmax: R_j is complete up to a negligible trailing block
+      k = j;
       break;
     }
     if (j == jcert) {
@@ -1113,7 +1114,8 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
       fma_count = 0;
       if (b2 > eps * eps) return 2;
     }
-    if (j == jext) { kc = j; break; }
+    // (the trailing block after q steps is empty: only a non-finite norm gets here)
+    if (j == q) break;
     const int piv = sh.qr_pivot;
     if (piv != j) {
       double* x = g + (int64_t)j * p;
@@ -1191,13 +1193,14 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
   }
   if (jstats && threadIdx.x == 0)   // (the QR's flops after the certificate test)
     atomicAdd(&jstats[4], 2ull * (fma_count + sh.qr_recomputed));
-  if (k < 0) {
-    // no threshold within jmax steps: dense when sum_{i > q/2} sigma_i^2 > eps^2 is certified
-    // by some leading triangle of the kc completed steps, else the full SVD decides
-    const double b2 = tail_lower_bound_sq(g, p, kmax, kc, wv, sh);
+  if (k < 0) return 0;
+  if (k > jtail) {
+    // dense when sum_{i > q/2} sigma_i^2 > eps^2 is certified by some leading triangle of the
+    // k completed steps, else the SVD of R decides
+    const double b2 = tail_lower_bound_sq(g, p, kmax, k, wv, sh);
     if (jstats && threadIdx.x == 0)
-      atomicAdd(&jstats[4], (unsigned long long)kc * kc * kc / 3);
-    return b2 > eps * eps ? 2 : 0;
+      atomicAdd(&jstats[4], (unsigned long long)k * k * k / 3);
+    if (b2 > eps * eps) return 2;
   }
   const double trail2 = sh.kept_sq;
   __syncthreads();
@@ -1208,8 +1211,8 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
   }
   // R (k x q, ld k, zero below the diagonal) and the SVD of M = R^T (q x k)
   double* rb = slot;
-  double* gs = wv;                    // q x k
-  double* vs = gs + (int64_t)q * k;   // k x k
+  double* gs = wv;                                              // q x k
+  double* vs = sc + 2 * (int64_t)CLR_MAX_CLUSTER * CLR_MAX_CLUSTER;  // k x k
   double part = 0.0;
   for (int e = threadIdx.x; e < k * q; e += kThreads) {
     const int i = e % k, c = e / k;
@@ -1249,10 +1252,13 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
       // A = block (p = m) or block^T (p = n); the slot is the block, column-major, ld m
       slot[tr ? oc + (int64_t)i * m : i + (int64_t)oc * m] = tmp[e];
     }
-    if (jstats && threadIdx.x == 0)
+    if (jstats && threadIdx.x == 0) {
       atomicAdd(&jstats[4], 4ull * (unsigned long long)p * q * k);
+      atomicAdd(&stage_clk[6], (unsigned long long)(clock64() - c_after));
+      atomicAdd(&stage_clk[7], 1ull);
+    }
     __syncthreads();
-    return 2;
+    return 3;
   }
   const bool tracked = sh.v_tracked;
   bool ls = !tracked && sh.ls_recover;
@@ -1401,13 +1407,14 @@ __global__ void __launch_bounds__(kThreads, 1) compress_dense_kernel(
           sort_and_truncate(G, p, q, p, eps, sh);
           r = sh.rank;
         }
-      } else if (pre == 2 && jstats && threadIdx.x == 0) {
+      } else if (pre >= 2 && jstats && threadIdx.x == 0) {
         atomicAdd(&jstats[3], 1ull);   // stored dense without a full SVD
       }
-      // SM cycles per path while profiling (block 2 of the counters): QR and small SVD,
-      // dense without a full SVD, full SVD (after the QR attempt)
+      // SM cycles per path while profiling (block 2 of the counters): QR and the SVD of R
+      // stored low rank, certified dense by the QR's triangles, full SVD (prereduce off, or a
+      // non-finite QR norm), QR and the SVD of R stored dense
       if (jstats && threadIdx.x == 0) {
-        const int path = pre == 1 ? 0 : pre == 2 ? 1 : 2;
+        const int path = pre == 1 ? 0 : pre == 2 ? 1 : pre == 3 ? 3 : 2;
         atomicAdd(&jstats[kPathCounters + 2 * path], (unsigned long long)(clock64() - c0));
         atomicAdd(&jstats[kPathCounters + 2 * path + 1], 1ull);
       }

@@ -40,6 +40,8 @@ def test_struct_layouts_match_header(repo_root, tmp_path):
                    ' offsetof(clr_opts, jacobi_max_sweeps), offsetof(clr_ns_stats, ms_total));'
                    'printf("%zu %zu\\n", offsetof(clr_opts, wait_timeout_us),'
                    ' offsetof(clr_ns_stats, ms_residual));'
+                   'printf("%zu %zu\\n", sizeof(clr_profile),'
+                   ' offsetof(clr_profile, svd_pre_blocks));'
                    'return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(repo_root, "include"), str(src), "-o",
@@ -48,7 +50,8 @@ def test_struct_layouts_match_header(repo_root, tmp_path):
     want = [ctypes.sizeof(clr.ClrOpts), ctypes.sizeof(clr.ClrInfo),
             ctypes.sizeof(clr.ClrProductStats), ctypes.sizeof(clr.ClrNsStats),
             clr.ClrOpts.jacobi_max_sweeps.offset, clr.ClrNsStats.ms_total.offset,
-            clr.ClrOpts.wait_timeout_us.offset, clr.ClrNsStats.ms_residual.offset]
+            clr.ClrOpts.wait_timeout_us.offset, clr.ClrNsStats.ms_residual.offset,
+            ctypes.sizeof(clr.ClrProfile), clr.ClrProfile.svd_pre_blocks.offset]
     assert got == want
 
 
