@@ -249,6 +249,54 @@ def test_build_svd_shared_memory_placements(ctx):
                 assert np.array_equal(g.block_dense(i, j), blk)
 
 
+def _spectrum_block(m, n, lead, tail_top, eps, seed):
+    """U diag(s) V^T with orthonormal U, V: `lead` singular values from 1 down to 1e-2, then a
+    geometric tail of the remaining min(m, n) - lead values from tail_top eps down to
+    2e-3 tail_top eps."""
+    rng = np.random.default_rng(seed)
+    q = min(m, n)
+    u, _ = np.linalg.qr(rng.standard_normal((m, q)))
+    v, _ = np.linalg.qr(rng.standard_normal((n, q)))
+    rho = (2e-3) ** (1.0 / (q - lead - 1))
+    s = np.concatenate([np.logspace(0, -2, lead), tail_top * eps * rho ** np.arange(q - lead)])
+    return (u * s) @ v.T, s
+
+
+@pytest.mark.parametrize("m,n", [(200, 200), (150, 230)])
+def test_build_pivoted_qr_past_three_fifths_takes_svd_of_r(ctx, m, n):
+    # Tiles whose column-pivoted QR needs more than 3q/5 steps to reach eps/16 (the geometric
+    # tail: about 160 of 200 and 120 of 150 steps) and whose rank the QR's triangles cannot
+    # certify (sigma_min(R_11) ~ 0.02-0.16 eps, the tail bound ~ 0.02-0.2 eps^2): the SVD of
+    # the QR's factor R decides.  With 0.45 q leading values and the tail from 0.3 eps the
+    # tail beyond them holds ~0.2 eps^2: low rank at the oracle's rank (within one), within
+    # eps.  With q/2 leading values and the tail from 0.5 eps the tail beyond q/2 holds
+    # ~1.6-2.1 eps^2: dense, stored as the block itself.  The profile counters show the path
+    # (pivoted QR and the SVD of R, stored low rank / stored dense).
+    eps = 1e-8
+    q = min(m, n)
+    for lead, top, want_dense in ((int(0.45 * q), 0.3, False), (q // 2, 0.5, True)):
+        a, s = _spectrum_block(m, n, lead, top, eps, seed=11)
+        r_or = co.compress_block(a, eps).rank
+        assert (r_or > co.dense_rank_limit(m, n)) == want_dense
+        ctx.profile_enable(True)
+        try:
+            mat = ctx.from_dense(a, [m], [n], eps_lr=eps)
+            prof = ctx.profile_read()
+        finally:
+            ctx.profile_enable(False)
+        g = clr_pack.from_library(mat)
+        paths = prof["svd_path_blocks"]
+        if want_dense:
+            assert g.kinds()[0, 0] == co.KIND_DENSE
+            assert np.array_equal(g.block_dense(0, 0), a)
+            assert paths == [0, 0, 0, 1], paths
+        else:
+            assert g.kinds()[0, 0] == co.KIND_LR
+            assert abs(int(g.ranks()[0, 0]) - r_or) <= 1 and r_or == lead
+            assert np.linalg.norm(g.block_dense(0, 0) - a) <= eps * (1 + 1e-6)
+            assert paths == [1, 0, 0, 0], paths
+
+
 def test_rrqr_build_matches_oracle(ctx):
     # the paper's construction (Section 4.1): rank-revealing QR with greedy column pivoting,
     # truncated at ||R_22||_F <= eps; ranks as the oracle's step-by-step pivoted QR (within one
