@@ -119,8 +119,9 @@ constexpr int kCostBuckets = 32;
 
 // log2 bucket of a tile's cost (which = 0: QR route recompression, 1: dense SVD, 2: dense x
 // dense products, m n times the tile's number of products).  A dense recompression's cost
-// depends on the path the tile takes (dense certificate ~0.4, pre-reduction ~1.2, full SVD ~5
-// SM cycles per m n min(m, n) on the lattice iterates), known only once it ran: the cycles
+// depends on the path the tile takes (dense certificate ~0.4, pivoted QR and the SVD of R
+// ~1.1 when stored low rank and ~2 when stored dense, SM cycles per m n min(m, n) on the
+// lattice iterates), known only once it ran: the cycles
 // measured the last time a tile of this matrix was recompressed (Newton-Schulz reuses its
 // matrices for the same products every iteration) replace the size estimate (2 m n min(m, n)
 // cycles) when present.
