@@ -196,8 +196,8 @@ void launch_lr_products(const MatView& A, const MatView& B, const MatView& C, co
 // k_svd.cu
 // jstats (may be null): device counters {svd blocks, FP32 sweeps, FP64 sweeps, early dense}
 // svd_scratch: grid x kSvdScratchPerCta doubles (FP32 working copies and an FP64 q x q factor
-// of the mixed-precision SVD, then the right factor of the pivoted-QR path's SVD of R^T).
-constexpr int64_t kSvdScratchPerCta = (int64_t)3 * CLR_MAX_CLUSTER * CLR_MAX_CLUSTER;
+// of the mixed-precision SVD, then the pivoted-QR path's R and the right factor of its SVD).
+constexpr int64_t kSvdScratchPerCta = (int64_t)4 * CLR_MAX_CLUSTER * CLR_MAX_CLUSTER;
 // sched: a zeroed work counter (dynamic tile distribution).
 void launch_compress_qr(const MatView& C, const int* list, const int* count, const int* rsum,
                         double* ws, double* svd_scratch, double eps, int max_sweeps, int grid,

@@ -960,20 +960,19 @@ __device__ int rrqr_block(const double* S, int64_t s_r, int64_t s_c, int m, int 
 // sum_{i > q/2} sigma_i(A)^2 above eps^2: sigma_min alone certifies only blocks whose
 // (q/2 + 1)-th singular value exceeds eps, while the tail of a block with many singular
 // values just below eps also exceeds it (tail_lower_bound_sq).  Otherwise the SVD of its R
-// decides, at any k: rank <= q/2 is stored low rank, else the block is stored dense as
-// Q_k [R; 0] P^T (within eps/16 of the block).  One-sided Jacobi on R^T after a pivoted QR
+// decides, at any k: rank <= q/2 is stored low rank, else the block is stored dense (the
+// untouched source).  One-sided Jacobi on R^T after a pivoted QR
 // converges in fewer sweeps than on A itself (R is graded by the pivoting: the
 // preconditioning of Drmac and Veselic, "New fast and accurate Jacobi SVD algorithm", SIAM
 // J. Matrix Anal. Appl. 29, 2008), so even k near q costs less than the full SVD of A.
 // Returns 1 when the block is done (low rank or zero, written to slot and the outputs), 2 when
-// it is certified dense with the source untouched, 3 when the SVD of R found it dense and it
-// was reconstructed into the slot (for 2 and 3 the caller stores the kind and copies an
-// external source over the slot), 0 only when a trailing norm is not finite; the caller then
-// takes the full SVD on the untouched source.
+// it is certified dense, 3 when the SVD of R found it dense (for 2 and 3 the source is
+// untouched: the caller stores the kind and copies an external source into the slot), 0 only
+// when a trailing norm is not finite; the caller then takes the full SVD on the source.
 // g: p x q copy (ld p); wv: the tile's second workspace half (p q doubles); slot: the block's
-// m n output slot (also the source of product tiles, read only before R is written there);
+// m n output slot (also the source of product tiles, overwritten only by a low-rank result);
 // sc: the CTA's SVD scratch (kSvdScratchPerCta doubles: svd_mixed's working copies in the
-// first two CLR_MAX_CLUSTER^2, the k x k right factor of R^T in the third).
+// first two CLR_MAX_CLUSTER^2, the k x k right factor of R^T in the third, R in the fourth).
 // ---------------------------------------------------------------------------------------------
 // A lower bound on sum_{i > h} sigma_i(A)^2 from the leading K x K upper triangle R_K of the
 // pivoted QR in g (ld p).  For every K' in (h, K], R_K' is the upper part of the first K'
@@ -1028,9 +1027,10 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
                                                    unsigned long long* jstats) {
   const int w = threadIdx.x / 32, l = threadIdx.x % 32;
   const long long c_entry = clock64();
-  // Once the QR has met the threshold the source is no longer needed: R (k x q) goes to the
-  // slot, the left SVD factor of R^T (q x k <= p q doubles) to wv and the right one (k x k)
-  // to the third part of sc.  Ranks up to q/2 are stored low rank.
+  // Once the QR has met the threshold, R (k x q) goes to the fourth part of sc, the left SVD
+  // factor of R^T (q x k <= p q doubles) to wv and the right one (k x k) to the third part of
+  // sc; the source stays untouched until a low-rank result overwrites it.  Ranks up to q/2
+  // are stored low rank.
   const int kmax = q / 2;
   // steps after which a block still above the threshold is tested for the sigma_min
   // certificate, and the QR rank above which the tail certificate is tried before the SVD
@@ -1210,9 +1210,10 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
     return 1;
   }
   // R (k x q, ld k, zero below the diagonal) and the SVD of M = R^T (q x k)
-  double* rb = slot;
-  double* gs = wv;                                              // q x k
-  double* vs = sc + 2 * (int64_t)CLR_MAX_CLUSTER * CLR_MAX_CLUSTER;  // k x k
+  constexpr int64_t kSq = (int64_t)CLR_MAX_CLUSTER * CLR_MAX_CLUSTER;
+  double* rb = sc + 3 * kSq;   // k x q
+  double* gs = wv;             // q x k
+  double* vs = sc + 2 * kSq;   // k x k
   double part = 0.0;
   for (int e = threadIdx.x; e < k * q; e += kThreads) {
     const int i = e % k, c = e / k;
@@ -1236,24 +1237,9 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
     return 1;
   }
   if (r > kmax) {
-    // stored dense: the slot (overwritten by R) gets Q_k [R; 0] P^T, within ||R_22||_F <=
-    // eps/16 of the block (the caller copies an external source over it)
-    __syncthreads();
-    double* tmp = wv;   // p x q, pivoted column order
-    for (int e = threadIdx.x; e < p * q; e += kThreads) {
-      const int i = e % p, c = e / p;
-      tmp[e] = i < k ? rb[i + (int64_t)c * k] : 0.0;
-    }
-    __syncthreads();
-    apply_q(g, p, k, p, sh.qr_tau, tmp, q, p);
-    for (int e = threadIdx.x; e < p * q; e += kThreads) {
-      const int i = e % p, c = e / p;
-      const int oc = sh.qr_perm[c];
-      // A = block (p = m) or block^T (p = n); the slot is the block, column-major, ld m
-      slot[tr ? oc + (int64_t)i * m : i + (int64_t)oc * m] = tmp[e];
-    }
+    // stored dense: the source is untouched (R lives in the scratch), so the block is kept
+    // exactly (the caller copies an external source into the slot)
     if (jstats && threadIdx.x == 0) {
-      atomicAdd(&jstats[4], 4ull * (unsigned long long)p * q * k);
       atomicAdd(&stage_clk[6], (unsigned long long)(clock64() - c_after));
       atomicAdd(&stage_clk[7], 1ull);
     }
@@ -1265,7 +1251,7 @@ __device__ __noinline__ int compress_by_pivoted_qr(const SrcView& a, int p, int 
   if (!tracked) recover_right(mv, q, k, gs, sh.perm, r, vs, sc);   // Y = R G_r (k x r)
   if (ls) ls = ls_solve(vs, k, r, gs, q, sh.perm, sh.sorted, sc, sh);
   // R = V_M S U_M^T:  X_R = (V_M S)_r (k x r), W_R = (U_M)_r (q x r); A ~ (Q_k X_R) (P W_R)^T
-  // (R in the slot is no longer read: the factors overwrite it)
+  // (the source in the slot is no longer read: the factors overwrite it)
   __syncthreads();
   double* xa = tr ? slot + (int64_t)m * r : slot;   // Q_k X_R: p x r, ld p
   double* wa = tr ? slot : slot + (int64_t)m * r;   // P W_R: q x r, ld q
