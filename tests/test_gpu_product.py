@@ -221,16 +221,22 @@ def test_errors_are_reported(ctx):
         ctx.multiply_into(c, c, c)
 
 
-def test_build_svd_shared_memory_placements(ctx):
+@pytest.mark.parametrize("no_prereduce", [0, 1])
+def test_build_svd_shared_memory_placements(ctx, no_prereduce):
     # clusters of 256 (FP32 copies of the SVD in global scratch), 200 (G32 in shared memory,
     # V32 in scratch) and 37 (both in shared memory), on a smooth kernel whose blocks need
-    # both FP32 stages and the FP64 clean-up to reach eps = 1e-8
+    # both FP32 stages and the FP64 clean-up to reach eps = 1e-8; with the pivoted-QR
+    # pre-reduction (the SVD of R) and without it (the full SVD of every block)
     sizes = [256, 200, 37]
     n = sum(sizes)
     r = np.linspace(0.0, 0.02 * n, n) + np.random.default_rng(3).uniform(-0.004, 0.004, n)
     a = np.exp(-(r[:, None] - r[None, :]) ** 2 / 2.0) + 1e-3 * np.eye(n)
     eps = 1e-8
-    m = ctx.from_dense(a, sizes, eps_lr=eps)
+    ctx.set_opts(svd_no_prereduce=no_prereduce)
+    try:
+        m = ctx.from_dense(a, sizes, eps_lr=eps)
+    finally:
+        ctx.set_opts(svd_no_prereduce=0)
     want = co.build(a, sizes, sizes, eps)
     g = clr_pack.from_library(m)
     gk, wk, gr, wr = g.kinds(), want.kinds(), g.ranks(), want.ranks()
@@ -327,10 +333,12 @@ def test_rrqr_build_matches_oracle(ctx):
             assert np.allclose(x.T @ x, np.eye(x.shape[1]), atol=1e-12)   # X = Q_r
 
 
-def test_build_tight_cluster_least_squares_factor(ctx):
+@pytest.mark.parametrize("no_prereduce", [0, 1])
+def test_build_tight_cluster_least_squares_factor(ctx, no_prereduce):
     # A tight cluster of kept singular values (40 values 1 + 1e-12 k) keeps the FP64 Jacobi from
     # converging within its sweep cap; the right factor is then the least-squares one and X W^T
-    # must still be within eps of the block, with the oracle's rank.  Square and wide blocks.
+    # must still be within eps of the block, with the oracle's rank.  Square and wide blocks,
+    # through the SVD of the pivoted QR's R and through the full SVD of the block.
     rng = np.random.default_rng(17)
     eps = 1e-6
     for m, n in ((200, 200), (120, 230)):
@@ -339,7 +347,11 @@ def test_build_tight_cluster_least_squares_factor(ctx):
         v, _ = np.linalg.qr(rng.standard_normal((n, k)))
         s = np.concatenate([1.0 + 1e-12 * np.arange(40), 1e-9 * rng.uniform(0.5, 1.0, k - 40)])
         a = (u * s) @ v.T
-        mat = ctx.from_dense(a, [m], [n], eps_lr=eps)
+        ctx.set_opts(svd_no_prereduce=no_prereduce)
+        try:
+            mat = ctx.from_dense(a, [m], [n], eps_lr=eps)
+        finally:
+            ctx.set_opts(svd_no_prereduce=0)
         g = clr_pack.from_library(mat)
         assert g.kinds()[0, 0] == co.KIND_LR
         assert g.ranks()[0, 0] == co.compress_block(a, eps).rank == 40
