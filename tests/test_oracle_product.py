@@ -115,6 +115,36 @@ def test_screening_drops_small_tiles():
     assert drop.tile_count[0, 0] == 1 and drop.tile_count[1, 1] == 1
 
 
+def test_screening_uses_the_low_rank_blocks_reconstruction_norm():
+    # A low-rank operand block enters the estimate with ||X W^T||_F (here diag(3, 4, 0, 0): 5),
+    # not with the bound ||X||_F ||W||_F (sqrt(2) 5): the threshold between keeping and
+    # dropping C_01 sits at the estimate 2 * 5e-9 + 5e-9 * 2 = 2e-8 over its 16 entries
+    sizes = [4, 4]
+    x = np.zeros((4, 2))
+    x[0, 0] = x[1, 1] = 1.0
+    w = np.zeros((4, 2))
+    w[0, 0], w[1, 1] = 3e-9, 4e-9
+    a = co.from_blocks(sizes, sizes, [[(1, np.eye(4)), (2, (x, w))],
+                                      [(0, None), (1, np.eye(4))]])
+    assert abs(co.block_norm(a.get(0, 1)) - 5e-9) <= 1e-24
+    est = 2.0 * 5e-9 + 5e-9 * 2.0
+    keep = co.triple_list(a, a, eps_sp=0.99 * est / 16)
+    drop = co.triple_list(a, a, eps_sp=1.01 * est / 16)
+    assert keep.tile_count[0, 1] == 2 and drop.tile_count[0, 1] == 0
+
+
+def test_triple_output_rank_hand_values():
+    # DD has no low-rank form; DL keeps B's rank, LD keeps A's; LL the smaller of the two, and
+    # on a tie the X_A side (Eq. 1 as printed)
+    assert co.triple_out_rank(co.T_DD, 5, 7) == 0
+    assert co.triple_out_rank(co.T_DL, 5, 7) == 7
+    assert co.triple_out_rank(co.T_LD, 5, 7) == 5
+    assert co.triple_out_rank(co.T_LL, 5, 7) == 5
+    assert co.triple_out_rank(co.T_LL, 9, 3) == 3
+    assert co.lr_output_rank(4, 4) == (4, 0)
+    assert co.lr_output_rank(3, 8) == (3, 1) and co.lr_output_rank(8, 3) == (3, 0)
+
+
 def test_recompressed_singular_values_are_those_of_the_sum():
     # Invariant of recompression: the kept singular values of C_IJ are the leading singular
     # values of the exact block sum, and the rank is the count from the sigma tail.
