@@ -44,3 +44,19 @@ def test_split_product_error_bound(mode, rel):
     got = so.split_product(a, b, mode)
     err = np.abs(got - a @ b)
     assert np.all(err <= rel * so.abs_product(a, b))
+
+
+def test_split_product_pair_sets_exactly():
+    # a = 1 + 2^-9 + 2^-18 and b = 1 + 2^-10 + 2^-20 split (no ties) into the bf16 terms
+    # (1, 2^-9, 2^-18) and (1, 2^-10, 2^-20), so every term pair contributes a distinct power of
+    # two and the sum shows exactly which pairs a mode takes: bf16x3 the pairs (0,0), (0,1),
+    # (1,0) of the 2-term split; bf16x6 also (0,2), (1,1), (2,0), leaving out 2^-28, 2^-29 and
+    # 2^-38
+    a = np.array([[1.0 + 2.0 ** -9 + 2.0 ** -18]])
+    b = np.array([[1.0 + 2.0 ** -10 + 2.0 ** -20]])
+    assert [float(t[0, 0]) for t in so.split_terms(a, 3)] == [1.0, 2.0 ** -9, 2.0 ** -18]
+    assert [float(t[0, 0]) for t in so.split_terms(b, 3)] == [1.0, 2.0 ** -10, 2.0 ** -20]
+    assert so.split_product(a, b, "bf16x3")[0, 0] == 1.0 + 2.0 ** -9 + 2.0 ** -10
+    want6 = 1.0 + 2.0 ** -9 + 2.0 ** -10 + 2.0 ** -18 + 2.0 ** -19 + 2.0 ** -20
+    assert so.split_product(a, b, "bf16x6")[0, 0] == want6
+    assert (a @ b)[0, 0] - want6 == 2.0 ** -28 + 2.0 ** -29 + 2.0 ** -38
