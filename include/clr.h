@@ -170,7 +170,14 @@ void clr_opts_default(clr_opts* opts);
  * clr_create: binds a context to CUDA device `device` (made current on the calling thread),
  * checks that it is an sm_103 part, and loads the TMA encoder from the driver.  Fails with
  * CLR_ECUDA when no such device exists.  clr_destroy frees the context's workspaces; it does
- * not free matrices. */
+ * not free matrices.
+ * Workspaces are allocated on first use, grow to the largest product seen and stay until
+ * clr_destroy.  For C = A B they take about 16 bytes per element of C's dense footprint (tile
+ * accumulation and SVD workspace), 2 MiB per CTA of the low-rank and recompression kernels
+ * (2 CTAs per SM unless the autotuner picks another count), and with a tensor-core precision
+ * the operands' panels: 4 (bf16x3), 6 (bf16x6) or 16 (exact slices, plus FP64 images of the
+ * low-rank operand blocks) bytes per element of A and of B.  Newton-Schulz keeps a second set
+ * for its concurrent products; each batch owns one set per graph branch. */
 int clr_create(clr_ctx_t* ctx, int device, const clr_opts* opts);
 int clr_destroy(clr_ctx_t ctx);
 int clr_set_opts(clr_ctx_t ctx, const clr_opts* opts);
