@@ -477,6 +477,9 @@ def run_ours(args):
     batch = None
     if rank == 0 and ws == 1 and not args.no_batch:
         batch = {"autotuned": batch_measure(64, "auto"), "fp64": batch_measure(64, "fp64")}
+        for r in batch.values():
+            if "error" not in r:
+                r["roofline"] = batch_roofline(r, fp64_peak)
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu:
@@ -761,6 +764,24 @@ def recompress_roofline(prof, fp64_peak):
     return {"compress_qr_kernel": qr, "compress_dense_kernel": dn,
             "peak_basis": "FP64: measured FMA rate (clr_probe_fp64_rate); FP32: 152 SMs x 128 "
                           "lanes x 2 x 2.07 GHz (nominal)"}
+
+
+def batch_roofline(r, fp64_peak):
+    """ALU rooflines of a batch run's dominant kernels, from its uncaptured pass: the two
+    recompression kernels, and for FP64 products the dense x dense kernel (its flops counted
+    from the operands' block kinds) against the measured FP64 FMA rate.  {"error": ...} when
+    an input is missing."""
+    try:
+        p = r["roofline_inputs"]
+        out = {"recompression": recompress_roofline(p, fp64_peak)}
+        if r.get("precision_mode") == "fp64" and p.get("dense_dd_flops"):
+            dense = _alu_roofline(p["dense_dd_flops"], 0.0, p["ms_dense"], fp64_peak)
+            if dense is not None:
+                dense["kernel"] = "dd_fp64_kernel"
+            out["dense_fp64"] = dense
+        return out
+    except (KeyError, TypeError, ZeroDivisionError) as e:
+        return {"error": "roofline inputs incomplete: %r" % (e,)}
 
 
 def main():

@@ -109,6 +109,11 @@ def batch_run(n_instances: int = 64, steps: int = 10, warmup: int = 3,
     mats = [ctx.from_dense(torch.from_numpy(w.a).cuda(), w.row_sizes, eps_lr=w.eps_lr,
                            drop_norm=w.drop_norm) for w in ws]
     torch.cuda.synchronize()
+    try:
+        dd_flops = sum(dense_product_flops(m.get_blocks(pool=False)[0], w.row_sizes)
+                       for m, w in zip(mats, ws))
+    except Exception:   # noqa: BLE001 -- the count only feeds a roofline figure
+        dd_flops = None
     batch = ctx.batch(mats, mats, eps=[w.eps_lr for w in ws], tune=True)
     tuned = [batch.tuning(i) for i in range(batch.n)]
     # algorithmic flops of every product (the library's triple statistics) and the device-time
@@ -171,7 +176,21 @@ def batch_run(n_instances: int = 64, steps: int = 10, warmup: int = 3,
                                                        "share": phases[top] / tot if tot else None},
             "svd": {k: prof[k] for k in ("svd_blocks", "svd_sweeps_fp32", "svd_sweeps_fp64",
                                          "svd_flops_fp64", "svd_flops_fp32")},
+            # the uncaptured pass's kernel times and algorithmic flops, for the rooflines
+            "roofline_inputs": dict({k: prof[k] for k in (
+                "ms_dense", "ms_compress_qr", "ms_compress_dense", "svd_flops_fp64",
+                "svd_flops_fp32", "svd_flops_fp64_qr", "svd_flops_fp32_qr")},
+                dense_dd_flops=dd_flops),
             "errors": errs, "all_within_bound": all(e["within_bound"] for e in errs)}
+
+
+def dense_product_flops(kinds, sizes) -> float:
+    """Flops of the dense x dense tile products of M M for a square CLR matrix M with block
+    kinds `kinds` and cluster sizes `sizes`: 2 m_I m_K m_J for every (I, K, J) whose blocks
+    M_IK and M_KJ are both dense, i.e. 2 s^T (D diag(s) D) s with D the dense indicator."""
+    d = (np.asarray(kinds) == clr.KIND_DENSE).astype(np.float64)
+    sz = np.asarray(sizes, dtype=np.float64)
+    return 2.0 * float(sz @ ((d * sz[None, :]) @ d) @ sz)
 
 
 def main() -> None:
