@@ -398,10 +398,14 @@ def run_ours(args):
             marks.append(time.perf_counter())
         torch.cuda.synchronize()
         el = max_over_ranks(time.perf_counter() - t0, ws)
+        each = [1e3 * (b - a) for a, b in zip(marks, marks[1:])]
+        # the host side of the box is shared: the median step beside the mean shows whether
+        # a few steps waited for the host link or host memory
         e2e = {"value": alg_flops * ws * e2e_steps / el / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": 2 * n * n * 8, "d2h_bytes_per_step": n * n * 8,
                "ms_per_step": 1e3 * el / e2e_steps, "steps": e2e_steps,
-               "ms_each": [round(1e3 * (b - a), 2) for a, b in zip(marks, marks[1:])]}
+               "ms_each": [round(x, 2) for x in each],
+               "ms_median": round(statistics.median(each), 2)}
         del a_h, b_h, c_h
 
     fp64_peak = clr.probe_fp64_rate(dev)
